@@ -1,0 +1,394 @@
+/*
+ * ckks_ref.c -- reference CKKS-RNS arithmetic, TEST INFRASTRUCTURE ONLY.
+ *
+ * This is the oracle's exact-integer core: plain, slow and meant to be read
+ * against the definitions.  Nothing in the library links or calls it; only
+ * the tests, the smoke check and the CPU-baseline leg of the benchmark load
+ * it (through ctypes, see ckks_oracle.py).
+ *
+ * Conventions
+ *   - A polynomial over a list of primes is stored limb-major:
+ *     u64[n_limbs][N], every residue canonical in [0, q).
+ *   - All products are exact: (unsigned __int128)a*b % q.
+ *   - Negacyclic means the ring Z_q[X]/(X^N + 1) of the CKKS preliminaries
+ *     (paper, Sec. 2.1: R_Q = Z_Q[X]/(X^N+1), Q = prod q_i).
+ *
+ * Parity status of each function is stated beside it; the pins live in
+ * tests/test_oracle_*.py.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef uint64_t u64;
+typedef int64_t i64;
+typedef unsigned __int128 u128;
+
+/* ------------------------------------------------------------------ */
+/* scalar modular arithmetic                                           */
+/* ------------------------------------------------------------------ */
+
+static u64 mulmod(u64 a, u64 b, u64 q) { return (u64)(((u128)a * b) % q); }
+static u64 addmod(u64 a, u64 b, u64 q) { u64 s = a + b; return s >= q ? s - q : s; }
+static u64 submod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + (q - b); }
+
+static u64 powmod(u64 b, u64 e, u64 q)
+{
+    u64 r = 1 % q;
+    b %= q;
+    while (e) {
+        if (e & 1) r = mulmod(r, b, q);
+        b = mulmod(b, b, q);
+        e >>= 1;
+    }
+    return r;
+}
+
+/* inverse modulo a prime, by Fermat's little theorem */
+static u64 invmod(u64 a, u64 q) { return powmod(a % q, q - 2, q); }
+
+u64 ref_mulmod(u64 a, u64 b, u64 q) { return mulmod(a, b, q); }
+u64 ref_powmod(u64 a, u64 e, u64 q) { return powmod(a, e, q); }
+u64 ref_invmod(u64 a, u64 q) { return invmod(a, q); }
+
+/* ------------------------------------------------------------------ */
+/* primes                                                              */
+/* ------------------------------------------------------------------ */
+
+/* Miller-Rabin with the first twelve primes as witnesses; this set is
+ * deterministic for every n < 3.3e24, hence for every 64-bit n. */
+int ref_is_prime(u64 n)
+{
+    static const u64 wit[12] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    if (n < 2) return 0;
+    for (int i = 0; i < 12; i++) {
+        if (n == wit[i]) return 1;
+        if (n % wit[i] == 0) return 0;
+    }
+    u64 d = n - 1;
+    int s = 0;
+    while ((d & 1) == 0) { d >>= 1; s++; }
+    for (int i = 0; i < 12; i++) {
+        u64 x = powmod(wit[i], d, n);
+        if (x == 1 || x == n - 1) continue;
+        int comp = 1;
+        for (int r = 1; r < s; r++) {
+            x = mulmod(x, x, n);
+            if (x == n - 1) { comp = 0; break; }
+        }
+        if (comp) return 0;
+    }
+    return 1;
+}
+
+/* For each requested bit size b (in order) take the largest prime q < 2^b
+ * with q = 1 (mod 2N) that was not taken before.  q = 1 (mod 2N) is what
+ * makes a primitive 2N-th root of unity exist mod q, so the negacyclic
+ * product can go through an NTT.  Returns 0, or -1 if a size runs dry. */
+int ref_gen_primes(int log_n, int count, const int *bits, u64 *out)
+{
+    u64 two_n = 2ull << log_n;
+    for (int i = 0; i < count; i++) {
+        if (bits[i] < log_n + 2 || bits[i] > 62) return -1;
+        u64 top = 1ull << bits[i];
+        u64 c = top - two_n + 1; /* largest value < 2^b that is 1 mod 2N */
+        int found = 0;
+        while (c > two_n) {
+            int used = 0;
+            for (int j = 0; j < i; j++) if (out[j] == c) used = 1;
+            if (!used && ref_is_prime(c)) { out[i] = c; found = 1; break; }
+            c -= two_n;
+        }
+        if (!found) return -1;
+    }
+    return 0;
+}
+
+/* A primitive 2N-th root of unity mod q: x^((q-1)/2N) for the smallest
+ * x >= 2 whose power psi has psi^N = -1 (then psi has order exactly 2N). */
+u64 ref_find_psi(int n, u64 q)
+{
+    u64 e = (q - 1) / (2 * (u64)n);
+    for (u64 x = 2; x < q; x++) {
+        u64 psi = powmod(x, e, q);
+        if (powmod(psi, (u64)n, q) == q - 1) return psi;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* negacyclic products                                                 */
+/* ------------------------------------------------------------------ */
+
+/* The definition: c = a*b in Z_q[X]/(X^N+1), i.e. X^N = -1.  O(N^2). */
+void ref_negacyclic_mul_schoolbook(const u64 *a, const u64 *b, u64 *c, int n, u64 q)
+{
+    for (int k = 0; k < n; k++) c[k] = 0;
+    for (int i = 0; i < n; i++) {
+        for (int j = 0; j < n; j++) {
+            u64 p = mulmod(a[i], b[j], q);
+            int k = i + j;
+            if (k < n) c[k] = addmod(c[k], p, q);
+            else c[k - n] = submod(c[k - n], p, q);
+        }
+    }
+}
+
+static unsigned bitrev(unsigned x, int bits)
+{
+    unsigned r = 0;
+    for (int i = 0; i < bits; i++) { r = (r << 1) | (x & 1); x >>= 1; }
+    return r;
+}
+
+/* Textbook iterative radix-2 DFT over Z_q: X_k = sum_j x_j w^(jk), with w a
+ * primitive n-th root of unity (bit-reversal permutation, then log n rounds
+ * of butterflies).  In place. */
+static void cyclic_dft(u64 *x, int n, u64 w, u64 q)
+{
+    int logn = 0;
+    while ((1 << logn) < n) logn++;
+    for (int i = 0; i < n; i++) {
+        int j = (int)bitrev((unsigned)i, logn);
+        if (j > i) { u64 t = x[i]; x[i] = x[j]; x[j] = t; }
+    }
+    for (int len = 2; len <= n; len <<= 1) {
+        u64 wl = powmod(w, (u64)(n / len), q); /* primitive len-th root */
+        for (int i = 0; i < n; i += len) {
+            u64 wj = 1;
+            for (int j = 0; j < len / 2; j++) {
+                u64 u = x[i + j];
+                u64 v = mulmod(x[i + j + len / 2], wj, q);
+                x[i + j] = addmod(u, v, q);
+                x[i + j + len / 2] = submod(u, v, q);
+                wj = mulmod(wj, wl, q);
+            }
+        }
+    }
+}
+
+/* Negacyclic product through the convolution theorem: with psi a primitive
+ * 2N-th root, a(X)b(X) mod X^N+1 equals psi^-i * cyclic_conv(psi^i a, psi^i b),
+ * and the cyclic convolution is DFT^-1(DFT(.) . DFT(.)) with w = psi^2. */
+void ref_negacyclic_mul(const u64 *a, const u64 *b, u64 *c, int n, u64 q, u64 psi)
+{
+    u64 *ta = (u64 *)malloc(sizeof(u64) * (size_t)n);
+    u64 *tb = (u64 *)malloc(sizeof(u64) * (size_t)n);
+    u64 w = mulmod(psi, psi, q);
+    u64 pw = 1;
+    for (int i = 0; i < n; i++) {
+        ta[i] = mulmod(a[i], pw, q);
+        tb[i] = mulmod(b[i], pw, q);
+        pw = mulmod(pw, psi, q);
+    }
+    cyclic_dft(ta, n, w, q);
+    cyclic_dft(tb, n, w, q);
+    for (int i = 0; i < n; i++) ta[i] = mulmod(ta[i], tb[i], q);
+    cyclic_dft(ta, n, invmod(w, q), q); /* inverse DFT up to the factor 1/n */
+    u64 ninv = invmod((u64)n, q);
+    u64 psi_inv = invmod(psi, q);
+    pw = ninv;
+    for (int i = 0; i < n; i++) {
+        c[i] = mulmod(ta[i], pw, q);
+        pw = mulmod(pw, psi_inv, q);
+    }
+    free(ta);
+    free(tb);
+}
+
+/* ------------------------------------------------------------------ */
+/* automorphism X -> X^g (rotation, Sec. 2.1)                          */
+/* ------------------------------------------------------------------ */
+
+/* out(X) = a(X^g) mod X^N+1 for odd g: coefficient i moves to i*g mod 2N,
+ * with a sign flip when that exponent lands in [N, 2N). */
+void ref_automorphism(const u64 *a, u64 *out, int n, u64 g, u64 q)
+{
+    u64 two_n = 2 * (u64)n;
+    for (int i = 0; i < n; i++) {
+        u64 e = ((u64)i * g) % two_n;
+        if (e < (u64)n) out[e] = a[i];
+        else out[e - n] = a[i] ? q - a[i] : 0;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* approximate fast base conversion                                    */
+/* ------------------------------------------------------------------ */
+
+/* Conv_{B -> C}(x)_p = sum_i [x_i * (B/b_i)^-1]_{b_i} * (B/b_i)  mod p,
+ * for every target prime p of C, with no correction of the overflow term
+ * (the result equals x + u*B for some 0 <= u < n_in).  Used by ModUp
+ * (B = one key-switching digit) and by ModDown (B = P).
+ * in: u64[n_in][n], out: u64[n_out][n]. */
+void ref_base_convert(const u64 *in, int n_in, const u64 *b_primes,
+                      u64 *out, int n_out, const u64 *c_primes, int n)
+{
+    /* (B/b_i)^-1 mod b_i, and (B/b_i) mod p for each target p */
+    u64 *hat_inv = (u64 *)malloc(sizeof(u64) * (size_t)n_in);
+    u64 *hat_mod = (u64 *)malloc(sizeof(u64) * (size_t)n_in * (size_t)n_out);
+    for (int i = 0; i < n_in; i++) {
+        u64 bi = b_primes[i];
+        u64 h = 1;
+        for (int j = 0; j < n_in; j++) if (j != i) h = mulmod(h, b_primes[j] % bi, bi);
+        hat_inv[i] = invmod(h, bi);
+        for (int k = 0; k < n_out; k++) {
+            u64 p = c_primes[k];
+            u64 hp = 1;
+            for (int j = 0; j < n_in; j++) if (j != i) hp = mulmod(hp, b_primes[j] % p, p);
+            hat_mod[(size_t)i * n_out + k] = hp;
+        }
+    }
+    for (int x = 0; x < n; x++) {
+        for (int k = 0; k < n_out; k++) out[(size_t)k * n + x] = 0;
+        for (int i = 0; i < n_in; i++) {
+            u64 y = mulmod(in[(size_t)i * n + x], hat_inv[i], b_primes[i]);
+            for (int k = 0; k < n_out; k++) {
+                u64 p = c_primes[k];
+                u64 t = mulmod(y % p, hat_mod[(size_t)i * n_out + k], p);
+                out[(size_t)k * n + x] = addmod(out[(size_t)k * n + x], t, p);
+            }
+        }
+    }
+    free(hat_inv);
+    free(hat_mod);
+}
+
+/* ------------------------------------------------------------------ */
+/* rescale and ModDown                                                 */
+/* ------------------------------------------------------------------ */
+
+/* Rescale by the last prime (the level drop that follows a product):
+ * c_i <- (c_i - r) * q_l^-1 mod q_i for i < l, with r = [c]_{q_l} in
+ * [0, q_l) taken as an integer (floor convention).  in: [l+1][n] over
+ * q_0..q_l, out: [l][n]. */
+void ref_rescale(const u64 *in, int n_limbs, const u64 *primes, u64 *out, int n)
+{
+    int l = n_limbs - 1;
+    u64 ql = primes[l];
+    const u64 *r = in + (size_t)l * n;
+    for (int i = 0; i < l; i++) {
+        u64 qi = primes[i];
+        u64 inv = invmod(ql % qi, qi);
+        for (int x = 0; x < n; x++) {
+            u64 d = submod(in[(size_t)i * n + x], r[x] % qi, qi);
+            out[(size_t)i * n + x] = mulmod(d, inv, qi);
+        }
+    }
+}
+
+/* ModDown: (u - Conv_{P->Q}([u]_P)) * P^-1 mod q_i.  in: [nq + np][n] with
+ * the q-limbs first, out: [nq][n]. */
+void ref_moddown(const u64 *in, int nq, const u64 *q_primes, int np,
+                 const u64 *p_primes, u64 *out, int n)
+{
+    u64 *conv = (u64 *)malloc(sizeof(u64) * (size_t)nq * (size_t)n);
+    ref_base_convert(in + (size_t)nq * n, np, p_primes, conv, nq, q_primes, n);
+    for (int i = 0; i < nq; i++) {
+        u64 qi = q_primes[i];
+        u64 P = 1;
+        for (int k = 0; k < np; k++) P = mulmod(P, p_primes[k] % qi, qi);
+        u64 pinv = invmod(P, qi);
+        for (int x = 0; x < n; x++) {
+            u64 d = submod(in[(size_t)i * n + x], conv[(size_t)i * n + x], qi);
+            out[(size_t)i * n + x] = mulmod(d, pinv, qi);
+        }
+    }
+    free(conv);
+}
+
+/* ------------------------------------------------------------------ */
+/* limb-wise helpers                                                   */
+/* ------------------------------------------------------------------ */
+
+void ref_mul_scalar(const u64 *a, u64 s, u64 *out, int n, u64 q)
+{
+    for (int x = 0; x < n; x++) out[x] = mulmod(a[x], s, q);
+}
+
+/* out += a * s  (mod q) */
+void ref_mac_scalar(const u64 *a, u64 s, u64 *out, int n, u64 q)
+{
+    for (int x = 0; x < n; x++) out[x] = addmod(out[x], mulmod(a[x], s, q), q);
+}
+
+/* ------------------------------------------------------------------ */
+/* seeded sampling                                                     */
+/* ------------------------------------------------------------------ */
+
+/* SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014): state += 0x9E3779B97F4A7C15, then the output
+ * mix z ^= z>>30; z *= 0xBF58476D1CE4E5B9; z ^= z>>27; z *= 0x94D049BB133111EB;
+ * z ^= z>>31.  A stream (seed, purpose, index) starts from the state
+ * mix(seed ^ (purpose << 48) ^ index).  Not a cryptographic generator. */
+static u64 sm_mix(u64 z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+typedef struct { u64 s; } sm_stream;
+
+static sm_stream sm_open(u64 seed, u64 purpose, u64 index)
+{
+    sm_stream st;
+    st.s = sm_mix(seed ^ (purpose << 48) ^ index);
+    return st;
+}
+
+static u64 sm_next(sm_stream *st)
+{
+    st->s += 0x9E3779B97F4A7C15ull;
+    return sm_mix(st->s);
+}
+
+u64 ref_splitmix_first(u64 seed, u64 purpose, u64 index, int count, u64 *out)
+{
+    sm_stream st = sm_open(seed, purpose, index);
+    for (int i = 0; i < count; i++) out[i] = sm_next(&st);
+    return count ? out[0] : 0;
+}
+
+/* ternary secret: per coefficient draw r = next >> 62 until r < 3, value r-1 */
+void ref_sample_ternary(u64 seed, u64 purpose, u64 index, int n, i64 *out)
+{
+    sm_stream st = sm_open(seed, purpose, index);
+    for (int x = 0; x < n; x++) {
+        u64 r;
+        do { r = sm_next(&st) >> 62; } while (r == 3);
+        out[x] = (i64)r - 1;
+    }
+}
+
+/* noise: centred binomial with 20 coin pairs (variance 10, sigma ~ 3.16),
+ * one draw per coefficient: popcount(r & 0xFFFFF) - popcount((r>>20) & 0xFFFFF) */
+void ref_sample_cbd(u64 seed, u64 purpose, u64 index, int n, i64 *out)
+{
+    sm_stream st = sm_open(seed, purpose, index);
+    for (int x = 0; x < n; x++) {
+        u64 r = sm_next(&st);
+        int a = __builtin_popcountll(r & 0xFFFFFull);
+        int b = __builtin_popcountll((r >> 20) & 0xFFFFFull);
+        out[x] = (i64)(a - b);
+    }
+}
+
+/* uniform residues: limb by limb in the order given, coefficient by
+ * coefficient, draw r = next & (2^bitlen(q) - 1) until r < q.
+ * out: u64[n_limbs][n]. */
+void ref_sample_uniform(u64 seed, u64 purpose, u64 index, const u64 *primes,
+                        int n_limbs, int n, u64 *out)
+{
+    sm_stream st = sm_open(seed, purpose, index);
+    for (int i = 0; i < n_limbs; i++) {
+        u64 q = primes[i];
+        int bl = 64 - __builtin_clzll(q);
+        u64 mask = bl == 64 ? ~0ull : ((1ull << bl) - 1);
+        for (int x = 0; x < n; x++) {
+            u64 r;
+            do { r = sm_next(&st) & mask; } while (r >= q);
+            out[(size_t)i * n + x] = r;
+        }
+    }
+}

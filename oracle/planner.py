@@ -1,0 +1,315 @@
+"""SpIntra-CA planner of the oracle.  TEST INFRASTRUCTURE ONLY.
+
+Written from the paper's description of the method:
+  * latency-aware packing (Sec. 3.2, App. B.1): J(t; F, n) = 2*ceil(F*n/t) +
+    20*ceil(log t) when M > V*F'; t = 1 when M <= V*F';
+  * column-major packing of t columns per ciphertext (App. B.1), blocks of
+    B = M/t slots, node v of column f of block k at slot k*B + perm[v];
+  * SpIntra-CA (Sec. 3.3): per-node rotation lengths, processed from the low
+    bits upward, nodes whose step bit is 0 stay, moved and kept values are
+    selected by 0/1 masks, a node that reaches its target is removed and
+    added to the result ciphertext, and slot conflicts open extra
+    ciphertexts;
+  * AOO (Sec. 3.3.2): each shift is the shortest cyclic distance;
+  * CPOO (Sec. 3.3.2): consecutive bit steps merged into one rotation (the
+    radix-2^r groups below), and sparse ciphertexts merged (the first-fit
+    lane assignment below).
+
+Readings the paper leaves open (the library implements the same):
+  * a "token" is one edge v <- u (u != v) of A-hat; the self term A[v,v] is
+    multiplied in at group 0;
+  * bits are taken r at a time (radix 2^r): group g handles bits
+    [g*r, g*r + r) of |shift|; one rotation per distinct signed digit
+    amount; one mask product and one rescale per group;
+  * assignment: items (value u at new slot p) are visited in the order
+    (source lane, rotation amount mod M, new slot); an item joins the lowest
+    output lane that already holds u at p, else the lowest lane whose slot
+    p is free, else opens a new lane;
+  * every mask is encoded at scale q_l, l the level of the group, so the
+    rescale that ends the group returns the ciphertext scale to Delta.
+
+The plan is pure structure: which rotations, which masked products, and
+each mask's slot values.  Encoding the masks is ckks.encode's job.
+"""
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+ACC = -1  # destination "accumulator" in a term
+
+
+def packing_objective(t, F, n):
+    """J(t; F, n) = 2*ceil(F*n/t) + 20*ceil(log2 t)  (App. B.1)."""
+    return 2 * (-(-F * n // t)) + 20 * math.ceil(math.log2(t)) if t > 1 else 2 * F * n
+
+
+def choose_t(F, n, V, Fp, M):
+    """Columns per ciphertext: t = 1 if M <= V*F'; otherwise the power of two
+    t <= min(F, M/V) minimising J, ties to the smaller t."""
+    if M <= V * Fp:
+        return 1
+    best_t, best_j = 1, packing_objective(1, F, n)
+    t = 2
+    while t <= F and t * V <= M:
+        j = packing_objective(t, F, n)
+        if j < best_j:
+            best_t, best_j = t, j
+        t *= 2
+    return best_t
+
+
+def shift_amount(src_slot, dst_slot, M, aoo=True):
+    """Rotation amount rho with Rot(ct, rho) carrying slot src to slot dst
+    (Rot(.,k) moves slot j+k to slot j): rho = src - dst mod M; with AOO the
+    representative of least magnitude, in (-M/2, M/2]."""
+    r = (src_slot - dst_slot) % M
+    if aoo and r > M // 2:
+        r -= M
+    return r
+
+
+@dataclass
+class Term:
+    src: int       # input lane
+    k: int         # signed rotation amount, 0 = the lane itself
+    dst: int       # output lane, or ACC
+    mask: int      # index into Plan.masks
+
+
+@dataclass
+class Group:
+    bit_lo: int
+    n_bits: int
+    level: int                 # level of the products; the rescale drops q_level
+    n_in: int
+    n_out: int
+    rotations: list            # [(src lane, k)], k != 0
+    terms: list                # [Term]
+
+
+@dataclass
+class Mask:
+    level: int
+    values: np.ndarray         # M slot values (float64)
+
+
+@dataclass
+class Plan:
+    n: int
+    M: int
+    t: int
+    B: int
+    V: int
+    F: int
+    Fp: int
+    perm: np.ndarray           # node -> slot in [0, B)
+    in_level: int
+    comb_consts: list = None   # t == 1: [F][F'] signed integers round(W*q_l)
+    comb_masks: list = None    # t > 1: [ceil(F/t)][F'] mask indices
+    comb_rots: list = None     # t > 1: rotation amounts B*2^i
+    groups: list = field(default_factory=list)
+    masks: list = field(default_factory=list)
+    out_level: int = 0
+    radix_bits: int = 0
+    aoo: bool = True
+
+    def rotation_amounts(self):
+        ks = set()
+        for k in (self.comb_rots or []):
+            ks.add(k % self.M)
+        for g in self.groups:
+            for (_, k) in g.rotations:
+                ks.add(k % self.M)
+        return sorted(ks)
+
+    def rotation_count(self):
+        return (len(self.comb_rots or []) * self.Fp
+                + sum(len(g.rotations) for g in self.groups) * self.Fp)
+
+
+def build_plan(params, in_level, row_ptr, col, val, V, W, perm, t,
+               radix_bits, aoo=True, min_out_level=0):
+    """Plan of one layer A-hat (X W) for ciphertexts at level in_level."""
+    n, M = params.n, params.slots
+    F, Fp = W.shape
+    B = M // t
+    perm = np.asarray(perm, dtype=np.int64)
+    if perm.shape[0] != V or len(set(perm.tolist())) != V or perm.min() < 0 or perm.max() >= B:
+        raise ValueError("perm must be an injection of the V nodes into [0, B)")
+    plan = Plan(n=n, M=M, t=t, B=B, V=V, F=F, Fp=Fp, perm=perm, in_level=in_level,
+                radix_bits=radix_bits, aoo=aoo)
+
+    # --- combination (App. B.1): Z_j = sum_f W[f,j] X_f, scale kept at Delta
+    ql = params.q[in_level]
+    if t == 1:
+        plan.comb_consts = [[int(_round_half_away(float(W[f, j]) * float(ql)))
+                             for j in range(Fp)] for f in range(F)]
+    else:
+        nb = -(-F // t)
+        plan.comb_masks = []
+        for b in range(nb):
+            row = []
+            for j in range(Fp):
+                vals = np.zeros(M)
+                for kk in range(t):
+                    f = b * t + kk
+                    if f < F:
+                        vals[kk * B:(kk + 1) * B] = W[f, j]
+                plan.masks.append(Mask(level=in_level, values=vals))
+                row.append(len(plan.masks) - 1)
+            plan.comb_masks.append(row)
+        plan.comb_rots = [B << i for i in range(int(math.log2(t)))]
+
+    # --- tokens: one per edge v <- u, u != v
+    self_w = np.zeros(V)
+    toks = []   # [u, lane, pos, rho, dest, w]
+    for v in range(V):
+        for e in range(row_ptr[v], row_ptr[v + 1]):
+            u = int(col[e])
+            w = float(val[e])
+            if u == v:
+                self_w[v] += w
+            else:
+                rho = shift_amount(int(perm[u]), int(perm[v]), M, aoo)
+                toks.append([u, 0, int(perm[u]), rho, int(perm[v]), w])
+    max_abs = max((abs(tk[3]) for tk in toks), default=0)
+    total_bits = max_abs.bit_length()
+    G = max(1, -(-total_bits // radix_bits))
+    level = in_level - 1
+    if level - G < min_out_level:
+        raise ValueError("level budget exhausted: %d groups from level %d" % (G, level))
+
+    n_lanes = 1
+    for g in range(G):
+        lo = g * radix_bits
+        nb = max(0, min(radix_bits, total_bits - lo))
+        gterms = []      # [(src, k, dst, slot values)]
+        if g == 0 and np.any(self_w != 0):
+            vals = np.zeros(M)
+            vals[perm] = self_w
+            gterms.append((0, 0, ACC, vals))
+        # step of every token in this group
+        arrive = {}      # (lane, k) -> {dest slot: weight}
+        items = {}       # (lane, k, newpos) -> [value u, [token indices]]
+        rots = set()
+        for ti, tk in enumerate(toks):
+            u, lane, pos, rho, dest, w = tk
+            digit = (abs(rho) >> lo) & ((1 << nb) - 1) if nb > 0 else 0
+            k = (digit << lo) * (1 if rho > 0 else -1)
+            newpos = (pos - k) % M
+            if k != 0:
+                rots.add((lane, k))
+            if rho - k == 0:
+                d = arrive.setdefault((lane, k), {})
+                assert newpos == dest and dest not in d
+                d[dest] = w
+            else:
+                it = items.setdefault((lane, k, newpos), [u, []])
+                assert it[0] == u
+                it[1].append(ti)
+            tk[3] = rho - k
+            tk[2] = newpos
+        # lane assignment, first fit
+        out_slots = []           # per output lane: {slot: u}
+        placed = {}              # (src lane, k, out lane) -> [slots]
+        new_lane_of = {}
+        for key in sorted(items, key=lambda x: (x[0], x[1] % M, x[2])):
+            lane, k, p = key
+            u, tis = items[key]
+            x = next((i for i, sl in enumerate(out_slots) if sl.get(p) == u), None)
+            if x is None:
+                x = next((i for i, sl in enumerate(out_slots) if p not in sl), None)
+                if x is None:
+                    out_slots.append({})
+                    x = len(out_slots) - 1
+                out_slots[x][p] = u
+                placed.setdefault((lane, k, x), []).append(p)
+            for ti in tis:
+                new_lane_of[ti] = x
+        for (lane, k, x), slots in placed.items():
+            vals = np.zeros(M)
+            vals[slots] = 1.0
+            gterms.append((lane, k, x, vals))
+        for (lane, k), dests in arrive.items():
+            vals = np.zeros(M)
+            for d, w in dests.items():
+                vals[d] = w
+            gterms.append((lane, k, ACC, vals))
+        # canonical order of the terms; masks numbered in that order
+        gterms.sort(key=lambda x: (x[0], x[1] % M, x[2]))
+        terms = []
+        for (src, k, dst, vals) in gterms:
+            plan.masks.append(Mask(level=level, values=vals))
+            terms.append(Term(src, k, dst, len(plan.masks) - 1))
+        plan.groups.append(Group(bit_lo=lo, n_bits=nb, level=level, n_in=n_lanes,
+                                 n_out=len(out_slots),
+                                 rotations=sorted(rots, key=lambda r: (r[0], r[1] % M)),
+                                 terms=terms))
+        # advance: arrived tokens leave, the others take their new lane
+        nxt = []
+        for ti, tk in enumerate(toks):
+            if tk[3] != 0:
+                tk[1] = new_lane_of[ti]
+                nxt.append(tk)
+        toks = nxt
+        n_lanes = len(out_slots)
+        level -= 1
+    assert not toks, "tokens left after the last group"
+    plan.out_level = level
+    return plan
+
+
+def _round_half_away(x):
+    """Nearest integer, ties away from zero (as C round()); exact for every double."""
+    a = abs(x)
+    f = math.floor(a)
+    r = f + (1 if a - f >= 0.5 else 0)
+    return r if x >= 0 else -r
+
+
+# ----------------------------------------------------------------------
+# FP64 simulation of a plan (rotate = np.roll, mask = elementwise)
+# ----------------------------------------------------------------------
+
+def simulate_aggregation(plan, z):
+    """Run the SpIntra-CA part of the plan on a plain slot vector z (length M)."""
+    lanes = [np.asarray(z, dtype=np.float64)]
+    acc = np.zeros(plan.M)
+    for grp in plan.groups:
+        rot = {(a, k): np.roll(lanes[a], -k) for (a, k) in grp.rotations}
+        outs = [np.zeros(plan.M) for _ in range(grp.n_out)]
+        for tm in grp.terms:
+            src = lanes[tm.src] if tm.k == 0 else rot[(tm.src, tm.k)]
+            prod = plan.masks[tm.mask].values * src
+            if tm.dst == ACC:
+                acc = acc + prod
+            else:
+                outs[tm.dst] = outs[tm.dst] + prod
+        lanes = outs
+    return acc
+
+
+def simulate_combination(plan, X, W):
+    """Slot vectors Z_j after the combination, from the packed plain X."""
+    V, F = X.shape
+    M, B, t = plan.M, plan.B, plan.t
+    nb = -(-F // t)
+    packed = []
+    for b in range(nb):
+        v = np.zeros(M)
+        for kk in range(t):
+            f = b * t + kk
+            if f < F:
+                v[kk * B + plan.perm] = X[:, f]
+        packed.append(v)
+    Z = []
+    for j in range(plan.Fp):
+        if t == 1:
+            z = sum(W[f, j] * packed[f] for f in range(F))
+        else:
+            z = sum(plan.masks[plan.comb_masks[b][j]].values * packed[b] for b in range(nb))
+            for k in plan.comb_rots:
+                z = z + np.roll(z, -k)
+        Z.append(z)
+    return Z
