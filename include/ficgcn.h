@@ -1,0 +1,230 @@
+/*
+ * ficgcn.h -- C ABI of a GB300 (sm_103a) library for one encrypted GCN layer
+ * A-hat * X * W under CKKS, following FicGCN (Kan et al., ICML 2025).
+ *
+ * Problem statement (paper Sec. 1 and Sec. 2.4, threat model): the server
+ * holds the plaintext normalised adjacency A-hat and weights W; the client
+ * holds the secret key and sends Enc(X); the server returns Enc(A-hat X W),
+ * which only the client can decrypt.  The server computes the combination
+ * X W first (latency-aware column packing, Sec. 3.2 / App. B.1) and then the
+ * sparse aggregation by SpIntra-CA rotate-and-sum (Sec. 3.3) over a node
+ * order chosen on the server and propagated back to the client packer
+ * (App. B.2).
+ *
+ * Conventions shared by every call
+ *   - Status: every call returns an int, FG_OK (0) or a negative FG_E* code.
+ *     fg_last_error(ctx) gives the text of the last failure on that context.
+ *     No C++ exception crosses this boundary.
+ *   - Ring: N = 2^log_n, M = N/2 slots; primes q_0..q_L (ciphertext modulus)
+ *     and p_0..p_{K-1} (special primes of key switching); level l means the
+ *     ciphertext lives modulo q_0..q_l.
+ *   - Ciphertexts cross the boundary as uint64 [2][l+1][N], limb-major,
+ *     COEFFICIENT domain, every residue canonical in [0, q_i).  A batch of
+ *     ciphertexts is contiguous.  Plaintexts are uint64 [l+1][N], same rules.
+ *   - Buffers: every uint64_t* ciphertext/plaintext argument may point to
+ *     host or device memory (the library asks the CUDA runtime which).  The
+ *     caller owns every buffer it passes; the library owns handles (fg_ctx,
+ *     fg_keys, fg_plan) and the device copies of keys and plans.  Blobs
+ *     returned by the library are freed with fg_free.
+ *   - Streams: the CUDA stream given at context creation carries every
+ *     kernel and copy of that context; calls return once their results are
+ *     in the caller's buffers (device outputs: complete on that stream).
+ *   - Randomness (keys, encryption): SplitMix64 (Steele, Lea & Flood,
+ *     OOPSLA 2014).  Stream (seed, purpose, index) starts from the state
+ *     mix(seed ^ (purpose << 48) ^ index), mix being SplitMix64's output
+ *     function; each draw adds 0x9E3779B97F4A7C15 to the state and returns
+ *     mix(state).  Ternary coefficient: draw >> 62, redrawn while 3, minus 1.
+ *     Noise coefficient: centred binomial popcount(d & 0xFFFFF) -
+ *     popcount((d >> 20) & 0xFFFFF) (variance 10).  Uniform residue mod q:
+ *     d & (2^bitlen(q) - 1), redrawn while >= q; limbs in prime order.
+ *     Purposes: 1 secret (index 0), 2/3 key a/e (index galois << 8 | digit),
+ *     4/5 encryption a/e (index = ciphertext index).  This generator is not
+ *     cryptographic; it makes every run reproducible.
+ */
+#ifndef FICGCN_H
+#define FICGCN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FG_OK 0
+#define FG_EINVAL (-1)    /* bad argument, shape or size */
+#define FG_ELEVEL (-2)    /* level/scale mismatch, level budget exhausted */
+#define FG_EKEY (-3)      /* missing rotation key, bad blob or checksum */
+#define FG_ECUDA (-4)     /* a CUDA runtime call failed */
+#define FG_EOOM (-5)      /* device or host allocation failed */
+#define FG_ETIMEOUT (-6)  /* a bounded device wait ran out */
+#define FG_ENODEV (-7)    /* no usable CUDA device */
+
+typedef struct fg_ctx fg_ctx;
+typedef struct fg_keys fg_keys;
+typedef struct fg_plan fg_plan;
+
+/* RNS-CKKS parameters (paper Sec. 2.1: Q = prod q_i, L levels).
+ * Primes: for each bit size, in the order q_bits then p_bits, the largest
+ * prime below 2^bits that is 1 mod 2N and not taken before.  alpha primes
+ * form one key-switching digit (hybrid key switching).  10 <= log_n <= 16,
+ * 1 <= n_q <= 60, 1 <= n_p <= 8, bit sizes in [log_n + 2, 61]. */
+typedef struct {
+    int log_n;
+    int n_q;
+    const int *q_bits;
+    int n_p;
+    const int *p_bits;
+    int alpha;
+    double log_scale;   /* Delta = 2^log_scale */
+} fg_params;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on the current CUDA device.  cuda_stream: a cudaStream_t
+ * (NULL = the legacy default stream).  Builds the primes, NTT tables and
+ * RNS constants on the device.  FG_ENODEV without a device. */
+int fg_ctx_create(const fg_params *params, void *cuda_stream, fg_ctx **out);
+int fg_ctx_destroy(fg_ctx *ctx);
+const char *fg_last_error(const fg_ctx *ctx);
+/* q_out: n_q primes, p_out: n_p primes (host arrays). */
+int fg_ctx_primes(const fg_ctx *ctx, uint64_t *q_out, uint64_t *p_out);
+/* Device memory the context holds now (tables + workspace), in bytes. */
+int fg_ctx_device_bytes(const fg_ctx *ctx, size_t *bytes);
+void fg_free(void *blob);
+
+/* ---------------------------------------------------------------- client */
+
+/* Secret key and rotation keys (paper Sec. 2.1: Rot needs a key per amount).
+ * Rotation amount k (left rotation by k slots, Rot(v, k) = (v_k, ..,
+ * v_{M-1}, v_0, .., v_{k-1})) uses the Galois element g = 5^(k mod M) mod
+ * 2N.  Each key switches phi_g(s) -> s with hybrid digits: for top-level
+ * digit D_j, b_j = -a_j s + e_j + P [q_i in D_j] phi_g(s) mod q_i and
+ * b_j = -a_j s + e_j mod p_k.  Blobs (host memory, free with fg_free) are
+ * versioned, checksummed and hold keys in the coefficient domain. */
+int fg_keygen(fg_ctx *ctx, uint64_t seed, const int32_t *rot_amounts, int n_rot,
+              void **sk_blob, size_t *sk_len, void **evk_blob, size_t *evk_len);
+
+/* CKKS encoding (canonical embedding, paper Sec. 2.1): real slot values
+ * z_0..z_{n_slots-1} (missing slots are 0) -> coefficients m with
+ * m(zeta^(5^j)) ~ scale * z_j, zeta = exp(i pi/N), rounded half away from
+ * zero, reduced mod q_0..q_level into out [level+1][N].  FP64 on the host. */
+int fg_encode_plain(fg_ctx *ctx, const double *slots, int n_slots, double scale,
+                    int level, uint64_t *out);
+
+/* Secret-key encryption of a plaintext at a level: c = (-a s + m + e, a),
+ * a and e from streams (seed, 4/5, index).  pt: [level+1][N], out: [2][level+1][N]. */
+int fg_encrypt(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t seed,
+               uint64_t index, const uint64_t *pt, int level, uint64_t *out);
+
+/* Client packing (paper Sec. 3.2 and App. B.1, column-major packing of t
+ * columns per ciphertext; App. B.2, node order from the server): X is
+ * double [V][F] row-major; perm[v] in [0, M/t) is node v's slot; ciphertext
+ * b holds column b*t + k in block k: slot k*(M/t) + perm[v].  Encoded at
+ * Delta, encrypted at the top level with stream index b.  out_cts: room for
+ * ceil(F/t) ciphertexts [2][L+1][N]; *n_out receives ceil(F/t). */
+int fg_pack_features(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t seed,
+                     const double *X, int V, int F, const int32_t *perm, int t,
+                     uint64_t *out_cts, int *n_out);
+
+/* Decryption m = c0 + c1 s mod q_i (paper Sec. 2.1).  out_pt: [level+1][N]. */
+int fg_decrypt(fg_ctx *ctx, const void *sk_blob, size_t sk_len, const uint64_t *ct,
+               int level, uint64_t *out_pt);
+
+/* Decryption followed by decoding: out_slots receives the M real slot
+ * values (imaginary parts dropped).  Needs |m| < q_0 q_1 / 2 (q_0 / 2 at
+ * level 0) coefficient-wise, which holds for every ciphertext this library
+ * produces at its scale. */
+int fg_decrypt_decode(fg_ctx *ctx, const void *sk_blob, size_t sk_len, const uint64_t *ct,
+                      int level, double scale, double *out_slots);
+
+/* ---------------------------------------------------------------- server */
+
+/* Copy the rotation keys of an evk blob to the device (NTT domain) after
+ * checking its magic, parameters and checksum (FG_EKEY otherwise). */
+int fg_load_evk(fg_ctx *ctx, const void *evk_blob, size_t len, fg_keys **out);
+int fg_keys_destroy(fg_keys *keys);
+/* Coefficient-domain copy of key `amount`'s digit j: b and a as [L+1+K][N]
+ * (host or device buffers).  FG_EKEY if the amount has no key. */
+int fg_keys_export(const fg_keys *keys, int32_t amount, int digit, uint64_t *b_out,
+                   uint64_t *a_out);
+
+typedef struct {
+    int t;              /* columns per ciphertext; 0 = latency-aware rule J(t) */
+    int radix_bits;     /* SpIntra-CA bits per group; 0 = fewest groups the budget allows */
+    int aoo;            /* 1 = shortest cyclic shift (AOO), 0 = shift in [0, M) */
+    int min_out_level;  /* lowest level the output may reach */
+    int n_sampled;      /* n in J(t;F,n); 0 = mean row length of A-hat, rounded */
+} fg_plan_opts;
+
+/* Plan of one layer (paper Sec. 3.2-3.3): packing t, combination constants,
+ * SpIntra-CA groups (per group: the rotations, the masked products into
+ * lanes and into the accumulator), and every mask encoded at scale q_l on
+ * the device.  A-hat: CSR (row_ptr [V+1], col, val), node v aggregating
+ * column col[e] with weight val[e]; no repeated (row, col) pairs.  W: double
+ * [F][Fp] row-major.  perm: node -> slot in [0, M/t) (injective).
+ * Input ciphertexts are expected at the top level L.  opts may be NULL. */
+int fg_plan_build(fg_ctx *ctx, const int32_t *row_ptr, const int32_t *col,
+                  const double *val, int V, const double *W, int F, int Fp,
+                  const int32_t *perm, const fg_plan_opts *opts, fg_plan **out);
+int fg_plan_destroy(fg_plan *plan);
+
+typedef struct {
+    int t, B, n_in, n_out, in_level, out_level, n_groups, n_masks, n_keys;
+    int64_t rotations;        /* complete Rot ops per layer call (all columns) */
+    int64_t masked_products;  /* plaintext-ciphertext products per layer call */
+} fg_plan_info_t;
+int fg_plan_info(const fg_plan *plan, fg_plan_info_t *info);
+/* The distinct rotation amounts (mod M) the plan needs keys for. */
+int fg_plan_rotation_amounts(const fg_plan *plan, int32_t *out, int cap, int *n);
+/* The plan's structure as int64 records (format in the design doc terms:
+ * header, perm, combination, groups, masks with slot/value-bit pairs).
+ * With out == NULL only *len is set. */
+int fg_plan_describe(const fg_plan *plan, int64_t *out, size_t cap, size_t *len);
+/* Host-only planning (no device, no context): the records fg_plan_describe
+ * would give for the same inputs and parameters.  Lets a server plan
+ * offline, e.g. to tell the client which rotation keys to generate before
+ * any GPU work.  With out == NULL only *len is set. */
+int fg_plan_dry_run(const fg_params *params, const int32_t *row_ptr, const int32_t *col,
+                    const double *val, int V, const double *W, int F, int Fp,
+                    const int32_t *perm, const fg_plan_opts *opts, int64_t *out, size_t cap,
+                    size_t *len);
+/* Replace the encoding of mask `mask` by caller-given coefficients
+ * [level+1][N] (host or device), e.g. an independent encoder's output. */
+int fg_plan_set_plaintext(fg_plan *plan, int mask, const uint64_t *coeffs);
+
+/* The layer (paper Sec. 3.2-3.3): in_cts = n_in packed ciphertexts at the
+ * top level (fg_pack_features layout), out_cts = Fp ciphertexts [2][out_l+1][N]
+ * holding A-hat X W column by column at the plan's node order (block 0 for
+ * t > 1).  *out_level, *out_scale receive the output level and scale. */
+int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *plan,
+                     const uint64_t *in_cts, int n_in, uint64_t *out_cts, int n_out,
+                     int *out_level, double *out_scale);
+
+/* One rotation Rot(ct, k) (paper Sec. 2.1) with hybrid key switching,
+ * ModUp taken before the automorphism (the hoisted order the layer uses).
+ * ct, out: [2][level+1][N] (out may alias ct). */
+int fg_rotate(fg_ctx *ctx, const fg_keys *keys, const uint64_t *ct, int level, int k,
+              uint64_t *out);
+
+/* Rescale by q_level (paper Sec. 2.1 and App. A: after a multiplication the
+ * level drops by one): out_i = (c_i - [c]_{q_l}) q_l^-1 mod q_i, floor
+ * residue in [0, q_l).  ct: [2][level+1][N], out: [2][level][N]. */
+int fg_rescale(fg_ctx *ctx, const uint64_t *ct, int level, uint64_t *out);
+
+/* Negacyclic product c = a * b mod (X^N + 1, q_i) for i <= level through the
+ * device NTT (the ring product of paper Sec. 2.1).  [level+1][N] each. */
+int fg_poly_mul(fg_ctx *ctx, const uint64_t *a, const uint64_t *b, int level, uint64_t *c);
+
+/* Forward (inverse = 0) or inverse NTT in place on DEVICE data
+ * [count][N] whose limb c is taken modulo prime index prime_idx[c %
+ * period] (0..n_q-1 for q_i, n_q.. for p_k).  The forward output order is
+ * private to the library; inverse(forward(x)) = x.  For throughput
+ * measurements. */
+int fg_ntt(fg_ctx *ctx, uint64_t *data, int count, const int *prime_idx, int period,
+           int inverse);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FICGCN_H */

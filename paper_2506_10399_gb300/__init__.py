@@ -1,1 +1,346 @@
-"""GB300-native encrypted GCN layer (placeholder; binding added below)."""
+"""GB300-native encrypted GCN layer A-hat X W under CKKS (FicGCN, ICML 2025).
+
+Thin Python binding of the C ABI in include/ficgcn.h: every function here
+only marshals arguments; all arithmetic runs in libficgcn.so (CUDA kernels
+for sm_103a plus the host planner and encoder).  Buffers are numpy uint64
+arrays (host) or torch int64 tensors holding the same 64-bit words (host or
+CUDA); outputs follow the type of the main input unless `out` is given.
+
+    ctx = Context(**params)
+    sk, evk = keygen(ctx, seed, plan.rotation_amounts())
+    keys = load_evk(ctx, evk)
+    cts = pack_features(ctx, sk, seed, X, perm, t)
+    out, level, scale = gcn_layer_axw(ctx, keys, plan, cts)
+    Y = decrypt_decode(ctx, sk, out[j], level, scale)
+
+Seeded synthetic inputs live in the submodule `workloads` (no arithmetic).
+"""
+import ctypes
+
+import numpy as np
+
+__all__ = ["Context", "Keys", "Plan", "FicgcnError", "ctx_create", "keygen", "load_evk",
+           "encode_plain", "encrypt", "pack_features", "decrypt", "decrypt_decode",
+           "plan_build", "plan_dry_run", "gcn_layer_axw", "rotate", "rescale", "poly_mul", "ntt"]
+
+
+def _lib():
+    from . import _native
+    return _native
+
+
+class FicgcnError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_lib().STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """Raw pointer of a contiguous 64-bit numpy array or torch tensor."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        assert x.is_contiguous() and x.element_size() == 8, "need a contiguous 64-bit tensor"
+        return ctypes.c_void_p(x.data_ptr())
+    assert isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"] and x.itemsize == 8, \
+        "need a contiguous 64-bit numpy array"
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _like(x, shape):
+    if _is_torch(x):
+        torch = _torch()
+        return torch.empty(shape, dtype=torch.int64, device=x.device)
+    return np.empty(shape, dtype=np.uint64)
+
+
+def _check(ctx, rc):
+    if rc != 0:
+        msg = _lib().lib.fg_last_error(ctx._h if ctx is not None else None)
+        raise FicgcnError(rc, (msg or b"").decode())
+
+
+class Context:
+    """fg_ctx: parameters, primes and device tables on the current CUDA device."""
+
+    def __init__(self, log_n, q_bits, p_bits, alpha, log_scale, stream=None, **_):
+        nat = _lib()
+        self.log_n, self.n, self.slots = log_n, 1 << log_n, 1 << (log_n - 1)
+        self.nq, self.np = len(q_bits), len(p_bits)
+        self.alpha, self.log_scale, self.scale = alpha, log_scale, float(2.0 ** log_scale)
+        qb = (ctypes.c_int * len(q_bits))(*q_bits)
+        pb = (ctypes.c_int * len(p_bits))(*p_bits)
+        prm = nat.Params(log_n, len(q_bits), qb, len(p_bits), pb, alpha, float(log_scale))
+        if stream is None:
+            try:
+                torch = _torch()
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except ImportError:
+                stream = None
+        self._stream = stream
+        h = ctypes.c_void_p()
+        self._h = None
+        rc = nat.lib.fg_ctx_create(ctypes.byref(prm), ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        if rc != 0:
+            raise FicgcnError(rc, "context creation failed")
+        self._h = h
+        q = np.zeros(self.nq, np.uint64)
+        p = np.zeros(self.np, np.uint64)
+        nat.lib.fg_ctx_primes(h, _ptr(q), _ptr(p))
+        self.q, self.p = [int(v) for v in q], [int(v) for v in p]
+        self.L = self.nq - 1
+
+    def device_bytes(self):
+        b = ctypes.c_size_t()
+        _check(self, _lib().lib.fg_ctx_device_bytes(self._h, ctypes.byref(b)))
+        return b.value
+
+    def close(self):
+        if self._h is not None:
+            _lib().lib.fg_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ctx_create(**params):
+    return Context(**params)
+
+
+class Keys:
+    """fg_keys: rotation keys on the device."""
+
+    def __init__(self, ctx, h):
+        self.ctx, self._h = ctx, h
+
+    def export(self, amount, digit):
+        """Coefficient-domain (b, a) of one digit of one key, [L+1+K][N] each."""
+        kl = self.ctx.nq + self.ctx.np
+        b = np.zeros((kl, self.ctx.n), np.uint64)
+        a = np.zeros((kl, self.ctx.n), np.uint64)
+        _check(self.ctx, _lib().lib.fg_keys_export(self._h, int(amount), int(digit), _ptr(b), _ptr(a)))
+        return b, a
+
+    def close(self):
+        if self._h is not None:
+            _lib().lib.fg_keys_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def keygen(ctx, seed, rot_amounts):
+    """(secret-key blob, evaluation-key blob) as bytes."""
+    nat = _lib()
+    am = np.ascontiguousarray(np.array(list(rot_amounts), dtype=np.int32))
+    skb, skl, evb, evl = ctypes.c_void_p(), ctypes.c_size_t(), ctypes.c_void_p(), ctypes.c_size_t()
+    _check(ctx, nat.lib.fg_keygen(ctx._h, int(seed), am.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                  len(am), ctypes.byref(skb), ctypes.byref(skl),
+                                  ctypes.byref(evb), ctypes.byref(evl)))
+    sk = ctypes.string_at(skb, skl.value)
+    evk = ctypes.string_at(evb, evl.value)
+    nat.lib.fg_free(skb)
+    nat.lib.fg_free(evb)
+    return sk, evk
+
+
+def load_evk(ctx, evk):
+    h = ctypes.c_void_p()
+    _check(ctx, _lib().lib.fg_load_evk(ctx._h, evk, len(evk), ctypes.byref(h)))
+    return Keys(ctx, h)
+
+
+def encode_plain(ctx, slots, scale, level, out=None):
+    z = np.ascontiguousarray(np.asarray(slots, dtype=np.float64))
+    if out is None:
+        out = np.empty((level + 1, ctx.n), np.uint64)
+    _check(ctx, _lib().lib.fg_encode_plain(ctx._h, _ptr(z), z.size, float(scale), level, _ptr(out)))
+    return out
+
+
+def encrypt(ctx, sk, seed, index, pt, level, out=None):
+    if out is None:
+        out = _like(pt, (2, level + 1, ctx.n))
+    _check(ctx, _lib().lib.fg_encrypt(ctx._h, sk, len(sk), int(seed), int(index), _ptr(pt), level,
+                                      _ptr(out)))
+    return out
+
+
+def pack_features(ctx, sk, seed, X, perm, t, out=None):
+    """ceil(F/t) ciphertexts [2][L+1][N] of the column-packed features."""
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+    perm = np.ascontiguousarray(np.asarray(perm, dtype=np.int32))
+    V, F = X.shape
+    nb = -(-F // t)
+    if out is None:
+        out = np.empty((nb, 2, ctx.nq, ctx.n), np.uint64)
+    n = ctypes.c_int()
+    _check(ctx, _lib().lib.fg_pack_features(ctx._h, sk, len(sk), int(seed), _ptr(X), V, F,
+                                            ctypes.c_void_p(perm.ctypes.data), t, _ptr(out),
+                                            ctypes.byref(n)))
+    return out
+
+
+def decrypt(ctx, sk, ct, level, out=None):
+    if out is None:
+        out = _like(ct, (level + 1, ctx.n))
+    _check(ctx, _lib().lib.fg_decrypt(ctx._h, sk, len(sk), _ptr(ct), level, _ptr(out)))
+    return out
+
+
+def decrypt_decode(ctx, sk, ct, level, scale):
+    out = np.empty(ctx.slots, np.float64)
+    _check(ctx, _lib().lib.fg_decrypt_decode(ctx._h, sk, len(sk), _ptr(ct), level, float(scale),
+                                             _ptr(out)))
+    return out
+
+
+class Plan:
+    """fg_plan: the layer's packing, SpIntra-CA schedule and device masks."""
+
+    def __init__(self, ctx, h):
+        self.ctx, self._h = ctx, h
+
+    def info(self):
+        i = _lib().PlanInfo()
+        _check(self.ctx, _lib().lib.fg_plan_info(self._h, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in i._fields_}
+
+    def rotation_amounts(self):
+        n = ctypes.c_int()
+        _lib().lib.fg_plan_rotation_amounts(self._h, None, 0, ctypes.byref(n))
+        out = np.zeros(max(1, n.value), np.int32)
+        _check(self.ctx, _lib().lib.fg_plan_rotation_amounts(self._h, ctypes.c_void_p(out.ctypes.data),
+                                                             n.value, ctypes.byref(n)))
+        return [int(v) for v in out[:n.value]]
+
+    def describe(self):
+        ln = ctypes.c_size_t()
+        _check(self.ctx, _lib().lib.fg_plan_describe(self._h, None, 0, ctypes.byref(ln)))
+        out = np.zeros(ln.value, np.int64)
+        _check(self.ctx, _lib().lib.fg_plan_describe(self._h, _ptr(out), ln.value, ctypes.byref(ln)))
+        return out
+
+    def set_plaintext(self, mask, coeffs):
+        coeffs = coeffs if _is_torch(coeffs) else np.ascontiguousarray(coeffs, dtype=np.uint64)
+        _check(self.ctx, _lib().lib.fg_plan_set_plaintext(self._h, int(mask), _ptr(coeffs)))
+
+    def close(self):
+        if self._h is not None:
+            _lib().lib.fg_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_build(ctx, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=True, min_out_level=0,
+               n_sampled=0):
+    nat = _lib()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    V = row_ptr.size - 1
+    F, Fp = W.shape
+    o = nat.PlanOpts(int(t), int(radix_bits), 1 if aoo else 0, int(min_out_level), int(n_sampled))
+    h = ctypes.c_void_p()
+    _check(ctx, nat.lib.fg_plan_build(ctx._h, ctypes.c_void_p(row_ptr.ctypes.data),
+                                      ctypes.c_void_p(col.ctypes.data), _ptr(val), V, _ptr(W), F, Fp,
+                                      ctypes.c_void_p(perm.ctypes.data), ctypes.byref(o),
+                                      ctypes.byref(h)))
+    return Plan(ctx, h)
+
+
+def plan_dry_run(params, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=True,
+                 min_out_level=0, n_sampled=0):
+    """Plan records (as Plan.describe()) computed on the host only, no device."""
+    nat = _lib()
+    q_bits, p_bits = params["q_bits"], params["p_bits"]
+    qb = (ctypes.c_int * len(q_bits))(*q_bits)
+    pb = (ctypes.c_int * len(p_bits))(*p_bits)
+    prm = nat.Params(params["log_n"], len(q_bits), qb, len(p_bits), pb, params["alpha"],
+                     float(params["log_scale"]))
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    F, Fp = W.shape
+    o = nat.PlanOpts(int(t), int(radix_bits), 1 if aoo else 0, int(min_out_level), int(n_sampled))
+    args = [ctypes.byref(prm), ctypes.c_void_p(row_ptr.ctypes.data), ctypes.c_void_p(col.ctypes.data),
+            _ptr(val), row_ptr.size - 1, _ptr(W), F, Fp, ctypes.c_void_p(perm.ctypes.data),
+            ctypes.byref(o)]
+    ln = ctypes.c_size_t()
+    rc = nat.lib.fg_plan_dry_run(*args, None, 0, ctypes.byref(ln))
+    if rc != 0:
+        raise FicgcnError(rc, "planning failed")
+    out = np.zeros(ln.value, np.int64)
+    rc = nat.lib.fg_plan_dry_run(*args, _ptr(out), ln.value, ctypes.byref(ln))
+    if rc != 0:
+        raise FicgcnError(rc, "planning failed")
+    return out
+
+
+def gcn_layer_axw(ctx, keys, plan, in_cts, out=None):
+    """(output ciphertexts [F'][2][l+1][N], output level l, scale)."""
+    info = plan.info()
+    if out is None:
+        out = _like(in_cts, (info["n_out"], 2, info["out_level"] + 1, ctx.n))
+    assert int(in_cts.shape[-1]) == ctx.n and int(in_cts.shape[-2]) == ctx.nq, "inputs must be [n][2][L+1][N]"
+    lvl, sc = ctypes.c_int(), ctypes.c_double()
+    _check(ctx, _lib().lib.fg_gcn_layer_axw(ctx._h, keys._h, plan._h, _ptr(in_cts), int(in_cts.shape[0]),
+                                            _ptr(out), info["n_out"], ctypes.byref(lvl),
+                                            ctypes.byref(sc)))
+    return out, lvl.value, sc.value
+
+
+def rotate(ctx, keys, ct, level, k, out=None):
+    if out is None:
+        out = _like(ct, (2, level + 1, ctx.n))
+    _check(ctx, _lib().lib.fg_rotate(ctx._h, keys._h, _ptr(ct), level, int(k), _ptr(out)))
+    return out
+
+
+def rescale(ctx, ct, level, out=None):
+    if out is None:
+        out = _like(ct, (2, level, ctx.n))
+    _check(ctx, _lib().lib.fg_rescale(ctx._h, _ptr(ct), level, _ptr(out)))
+    return out
+
+
+def poly_mul(ctx, a, b, level, out=None):
+    if out is None:
+        out = _like(a, (level + 1, ctx.n))
+    _check(ctx, _lib().lib.fg_poly_mul(ctx._h, _ptr(a), _ptr(b), level, _ptr(out)))
+    return out
+
+
+def ntt(ctx, data, prime_idx, inverse=False):
+    """In-place NTT of a CUDA tensor [count][N]; limb c uses prime prime_idx[c % len]."""
+    pid = (ctypes.c_int * len(prime_idx))(*prime_idx)
+    count = data.numel() // ctx.n
+    _check(ctx, _lib().lib.fg_ntt(ctx._h, _ptr(data), count, pid, len(prime_idx), 1 if inverse else 0))
+    return data

@@ -1,0 +1,80 @@
+"""ctypes loader of libficgcn.so (the C ABI of include/ficgcn.h).
+
+The library must be built in-tree (build.py); importing this module without
+it raises ImportError -- there is no fallback implementation.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libficgcn.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libficgcn.so is missing: build it with paper_2506_10399_gb300/build.py "
+                      "(or __graft_entry__.build()); there is no CPU fallback")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+c_int, c_u64, c_size, c_double = ctypes.c_int, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_double
+c_void_p = ctypes.c_void_p
+P = ctypes.POINTER
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("log_n", c_int), ("n_q", c_int), ("q_bits", P(c_int)), ("n_p", c_int),
+                ("p_bits", P(c_int)), ("alpha", c_int), ("log_scale", c_double)]
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("t", c_int), ("radix_bits", c_int), ("aoo", c_int), ("min_out_level", c_int),
+                ("n_sampled", c_int)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("t", c_int), ("B", c_int), ("n_in", c_int), ("n_out", c_int), ("in_level", c_int),
+                ("out_level", c_int), ("n_groups", c_int), ("n_masks", c_int), ("n_keys", c_int),
+                ("rotations", ctypes.c_int64), ("masked_products", ctypes.c_int64)]
+
+
+SIGS = {
+    "fg_ctx_create": (c_int, [P(Params), c_void_p, P(c_void_p)]),
+    "fg_ctx_destroy": (c_int, [c_void_p]),
+    "fg_last_error": (ctypes.c_char_p, [c_void_p]),
+    "fg_ctx_primes": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "fg_ctx_device_bytes": (c_int, [c_void_p, P(c_size)]),
+    "fg_free": (None, [c_void_p]),
+    "fg_keygen": (c_int, [c_void_p, c_u64, P(ctypes.c_int32), c_int, P(c_void_p), P(c_size),
+                          P(c_void_p), P(c_size)]),
+    "fg_encode_plain": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p]),
+    "fg_encrypt": (c_int, [c_void_p, c_void_p, c_size, c_u64, c_u64, c_void_p, c_int, c_void_p]),
+    "fg_pack_features": (c_int, [c_void_p, c_void_p, c_size, c_u64, c_void_p, c_int, c_int,
+                                 c_void_p, c_int, c_void_p, P(c_int)]),
+    "fg_decrypt": (c_int, [c_void_p, c_void_p, c_size, c_void_p, c_int, c_void_p]),
+    "fg_decrypt_decode": (c_int, [c_void_p, c_void_p, c_size, c_void_p, c_int, c_double, c_void_p]),
+    "fg_load_evk": (c_int, [c_void_p, c_void_p, c_size, P(c_void_p)]),
+    "fg_keys_destroy": (c_int, [c_void_p]),
+    "fg_keys_export": (c_int, [c_void_p, ctypes.c_int32, c_int, c_void_p, c_void_p]),
+    "fg_plan_build": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int,
+                              c_int, c_void_p, P(PlanOpts), P(c_void_p)]),
+    "fg_plan_destroy": (c_int, [c_void_p]),
+    "fg_plan_info": (c_int, [c_void_p, P(PlanInfo)]),
+    "fg_plan_rotation_amounts": (c_int, [c_void_p, c_void_p, c_int, P(c_int)]),
+    "fg_plan_describe": (c_int, [c_void_p, c_void_p, c_size, P(c_size)]),
+    "fg_plan_set_plaintext": (c_int, [c_void_p, c_int, c_void_p]),
+    "fg_plan_dry_run": (c_int, [P(Params), c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_int,
+                                c_void_p, P(PlanOpts), c_void_p, c_size, P(c_size)]),
+    "fg_gcn_layer_axw": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int,
+                                 P(c_int), P(c_double)]),
+    "fg_rotate": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
+    "fg_rescale": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
+    "fg_poly_mul": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+    "fg_ntt": (c_int, [c_void_p, c_void_p, c_int, P(c_int), c_int, c_int]),
+}
+
+for _name, (_res, _args) in SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+STATUS = {0: "FG_OK", -1: "FG_EINVAL", -2: "FG_ELEVEL", -3: "FG_EKEY", -4: "FG_ECUDA",
+          -5: "FG_EOOM", -6: "FG_ETIMEOUT", -7: "FG_ENODEV"}

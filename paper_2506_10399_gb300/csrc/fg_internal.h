@@ -1,0 +1,226 @@
+// fg_internal.h -- host-side structures shared by the library's translation
+// units (context, keys, plan) and the kernel launch wrappers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/ficgcn.h"
+
+typedef uint64_t u64;
+typedef int64_t i64;
+typedef unsigned __int128 u128;
+
+// ------------------------------------------------------------------ errors
+// Internal code throws fg_error; every C entry point catches it and turns it
+// into a status code plus fg_last_error text.
+struct fg_error : std::runtime_error {
+    int code;
+    fg_error(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+#define FG_CHECK(cond, code, msg)                                   \
+    do {                                                            \
+        if (!(cond)) throw fg_error((code), (msg));                 \
+    } while (0)
+
+#define CUDA_TRY(call)                                                              \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess)                                                      \
+            throw fg_error(e_ == cudaErrorMemoryAllocation ? FG_EOOM : FG_ECUDA,    \
+                           std::string(#call) + ": " + cudaGetErrorString(e_));    \
+    } while (0)
+
+// ------------------------------------------------------------------ host math
+namespace hm {
+u64 mulmod(u64 a, u64 b, u64 q);
+u64 powmod(u64 a, u64 e, u64 q);
+u64 invmod(u64 a, u64 q);
+bool is_prime(u64 n);
+std::vector<u64> gen_primes(int log_n, const std::vector<int> &bits);
+u64 find_psi(int n, u64 q);
+u64 shoup(u64 w, u64 q);          // floor(w 2^64 / q)
+u64 mont_qneg(u64 q);             // -q^-1 mod 2^64
+u64 to_mont(u64 x, u64 q);        // x 2^64 mod q
+int bitrev(int x, int bits);
+
+// SplitMix64 streams (see ficgcn.h)
+struct Stream {
+    u64 s;
+    Stream(u64 seed, u64 purpose, u64 index);
+    u64 next();
+};
+void sample_ternary(u64 seed, u64 purpose, u64 index, int n, int8_t *out);
+void sample_cbd(u64 seed, u64 purpose, u64 index, int n, int8_t *out);
+void sample_uniform(u64 seed, u64 purpose, u64 index, const u64 *primes, int n_limbs,
+                    int n, u64 *out);
+
+// CKKS encoding (canonical embedding) in FP64: out [level+1][N]
+void encode(int log_n, const double *slots, int n_slots, double scale, const u64 *primes,
+            int n_limbs, u64 *out);
+// decode from centred integer coefficients (as doubles already divided by scale)
+void decode(int log_n, const double *coef, double *slots_out);
+double round_half_away(double x);
+}  // namespace hm
+
+// ------------------------------------------------------------------ device tables
+struct PrimeC;  // modarith.cuh
+
+struct ConvTab {
+    // approximate base conversion from n_in primes to n_out primes (device)
+    int n_in, n_out;
+    int in_p[8], in_l[8];     // prime index and limb position of each input
+    int out_p[72], out_l[72]; // prime index and limb position of each output
+    u64 hinv[8], hinv_s[8];   // (B/b_k)^-1 mod b_k and its Shoup companion
+    u64 hmod[8][72];          // (B/b_k) mod out prime, Montgomery form
+};
+
+struct fg_ctx {
+    // parameters
+    int log_n = 0, n = 0, slots = 0;
+    int nq = 0, np = 0, alpha = 0;
+    double log_scale = 0, scale = 0;
+    std::vector<u64> primes;     // q_0..q_L then p_0..p_{K-1}
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+
+    // device constants
+    PrimeC *d_primes = nullptr;       // [nq+np]
+    void *d_fwd = nullptr;            // ulonglong2 [nq+np][N] (psi^brv(i), Shoup)
+    void *d_inv = nullptr;            // ulonglong2 [nq+np][N]
+    u64 *d_ninv = nullptr;            // [nq+np][2] N^-1 and Shoup
+    std::vector<u64> h_qneg, h_r2, h_ones;
+
+    // cached RNS constant tables, keyed by (kind, level, digit)
+    std::map<std::tuple<int, int, int>, ConvTab *> conv_tabs;
+    std::map<int, u64 *> rescale_tabs;   // level -> [level][2] q_l^-1 mod q_i + Shoup
+    std::map<int, u64 *> pinv_tabs;      // level -> [level+1][2] P^-1 mod q_i + Shoup
+
+    // workspace (grow-only arena of named device buffers)
+    std::map<std::string, std::pair<void *, size_t>> ws;
+    size_t table_bytes = 0;
+
+    int L() const { return nq - 1; }
+    int ext(int level) const { return level + 1 + np; }
+    int n_digits(int level) const { return (level + 1 + alpha - 1) / alpha; }
+    // prime index of extended limb i at level l
+    int ext_prime(int level, int i) const { return i <= level ? i : nq + (i - level - 1); }
+    void *buf(const std::string &name, size_t bytes);
+    const ConvTab *modup_tabs(int level);   // device array, one per digit
+    const ConvTab *moddown_tab(int level);
+    const u64 *rescale_tab(int level);
+    const u64 *pinv_tab(int level);
+};
+
+struct KeyDev {
+    int32_t amount;   // k mod M
+    uint32_t galois;
+    u64 *d = nullptr; // [beta_L][2][L+1+K][N], NTT domain, Montgomery form
+};
+
+struct fg_keys {
+    fg_ctx *ctx = nullptr;
+    std::map<int32_t, KeyDev> keys;   // amount -> key
+    const KeyDev &get(int32_t amount) const;
+};
+
+// ------------------------------------------------------------------ plan
+struct TermC {
+    int src, k, dst, mask;
+};
+struct GroupC {
+    int bit_lo, n_bits, level, n_in, n_out;
+    std::vector<std::pair<int, int>> rots;   // (src lane, k)
+    std::vector<TermC> terms;
+};
+struct MaskC {
+    int level;
+    std::vector<int32_t> slots;   // sorted
+    std::vector<double> values;
+    u64 *d = nullptr;             // [level+1][N] NTT domain, Montgomery form
+};
+
+struct fg_plan {
+    fg_ctx *ctx = nullptr;
+    int N = 0, M = 0, t = 1, B = 0, V = 0, F = 0, Fp = 0;
+    int in_level = 0, out_level = 0, radix_bits = 0, aoo = 1;
+    std::vector<int32_t> perm;
+    std::vector<i64> comb_consts;          // t == 1: [F][Fp]
+    std::vector<std::vector<int>> comb_masks;   // t > 1: [ceil(F/t)][Fp]
+    std::vector<int> comb_rots;
+    std::vector<GroupC> groups;
+    std::vector<MaskC> masks;
+    u64 *d_comb = nullptr;                 // t == 1: [in_level+1][F][Fp] Montgomery constants
+    int max_lanes = 1;
+};
+
+// ------------------------------------------------------------------ kernels
+namespace kern {
+// rows x per_row limbs: limb (r, c) at base + (r * stride + c) * N, reduced
+// modulo prime pidx[c] (pidx[c] < 0: the limb is left alone)
+struct LimbSet {
+    u64 *base;
+    int stride;
+    int per_row;
+    int rows;
+    std::vector<int> pidx;
+};
+// negacyclic NTT (forward: natural -> private bit-reversed order), src -> dst
+void ntt_fwd(fg_ctx *ctx, const LimbSet &src, const LimbSet &dst);
+void ntt_inv(fg_ctx *ctx, const LimbSet &src, const LimbSet &dst);
+
+// contiguous [count][N] limbs, limb c modulo prime pidx[c % pidx.size()]
+void to_mont(fg_ctx *ctx, u64 *data, int count, const std::vector<int> &pidx);
+void from_mont(fg_ctx *ctx, u64 *data, int count, const std::vector<int> &pidx);
+void pointwise(fg_ctx *ctx, const u64 *a, const u64 *b, u64 *c, int count,
+               const std::vector<int> &pidx);
+void add(fg_ctx *ctx, const u64 *a, const u64 *b, u64 *c, int count, const std::vector<int> &pidx);
+void neg(fg_ctx *ctx, const u64 *a, u64 *c, int count, const std::vector<int> &pidx);
+// c = a * s[c % period] with d_scal = (w, w') pairs per limb column
+void scalar(fg_ctx *ctx, const u64 *a, u64 *c, int count, const std::vector<int> &pidx,
+            const u64 *d_scal);
+// X -> X^g on NTT-domain limbs (same index map for every prime)
+void automorphism(fg_ctx *ctx, const u64 *a, u64 *c, int nlimbs, uint32_t g);
+void small_to_res(fg_ctx *ctx, const int8_t *e, u64 *out, int n_limbs, const int *d_pidx);
+void copy_limbs(fg_ctx *ctx, const u64 *src, int src_ls, u64 *dst, int dst_ls, int npoly, int nl);
+
+// combination: Z[j][p][i] = sum_f c[i][f][j] X[f][p][i], coefficient domain;
+// X: [F][2][level+1][N], consts: [level+1][F][Fp] Montgomery form, Z limb stride z_ls
+void comb_const_mac(fg_ctx *ctx, const u64 *X, int F, int Fp, int level, const u64 *consts,
+                    u64 *Z, int z_ls);
+// rescale by q_level, coefficient domain, npoly polys with limb strides
+void rescale_coef(fg_ctx *ctx, const u64 *in, int in_ls, u64 *out, int out_ls, int npoly,
+                  int level);
+// rescale by q_level in the NTT domain, in place (limbs 0..level-1 remain)
+void rescale_ntt(fg_ctx *ctx, u64 *ct, int ls, int npoly, int level);
+
+// ModUp of the c1 parts of ncol ciphertexts (NTT domain, limb stride ls) at
+// `level`: digits [ncol][beta][E][N], NTT domain, own-digit limbs not written
+void modup(fg_ctx *ctx, const u64 *lane, int ls, int ncol, int level, u64 *digits);
+struct Dest {
+    u64 *out;          // accumulator ciphertexts (limb stride out_ls)
+    const u64 *mask;   // [level+1][N] NTT domain, Montgomery form; null = store R
+};
+// R = Rot(lane, k) from the hoisted digits; every destination gets mask (x) R
+void rotate_mac(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int ncol, int level,
+                const u64 *digits, const std::vector<Dest> &dests, int out_ls);
+// every destination gets mask (x) lane
+void stay_mac(fg_ctx *ctx, const u64 *lane, int ls, int ncol, int level,
+              const std::vector<Dest> &dests, int out_ls);
+}  // namespace kern
+
+// ------------------------------------------------------------------ planner
+namespace planner {
+int choose_t(int F, int n, int V, int Fp, int M);
+void build(fg_plan &pl, const fg_ctx &ctx, const int32_t *row_ptr, const int32_t *col,
+           const double *val, int V, const double *W, int F, int Fp, const int32_t *perm,
+           const fg_plan_opts &opts);
+}  // namespace planner

@@ -1,0 +1,866 @@
+// kernels.cu -- sm_103a kernels of the encrypted GCN layer.
+//
+// Every kernel works on 64-bit RNS words with the reductions of
+// modarith.cuh on CUDA cores.  Layouts are limb-major: a polynomial limb is
+// N consecutive words; a batch of limbs is addressed as rows of `per_row`
+// limbs (row r, column c at base + (r * row_stride + c) * N), and limb
+// column c is reduced modulo prime pidx[c] (pidx < 0: leave that limb).
+#include <cstdio>
+
+#include "fg_internal.h"
+#include "modarith.cuh"
+
+namespace {
+
+constexpr int kPidxMax = 1024;
+
+struct Batch {
+    u64 *src;          // read from
+    u64 *dst;          // written to (may equal src)
+    int src_stride;    // limbs between rows
+    int dst_stride;
+    int per_row;
+    int rows;
+    int8_t pidx[kPidxMax];
+};
+
+Batch make_batch(u64 *src, int src_stride, u64 *dst, int dst_stride, int per_row, int rows,
+                 const std::vector<int> &pidx)
+{
+    FG_CHECK(per_row <= kPidxMax && (int)pidx.size() == per_row, FG_EINVAL,
+             "limb batch wider than the prime-index table");
+    Batch b;
+    b.src = src;
+    b.dst = dst;
+    b.src_stride = src_stride;
+    b.dst_stride = dst_stride;
+    b.per_row = per_row;
+    b.rows = rows;
+    for (int i = 0; i < per_row; i++) b.pidx[i] = (int8_t)pidx[i];
+    return b;
+}
+
+inline void check_launch(const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw fg_error(FG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------------
+// NTT: negacyclic, Cooley-Tukey forward with twiddles psi^brv(m+i) (natural
+// order in, bit-reversed order out: out[j] = a(psi^(2 brv(j) + 1))),
+// Gentleman-Sande inverse, Harvey's lazy butterflies.  N = N1 * N2 with
+// N1 = 2^s1: pass A runs stages 0..s1-1 on the N2 stride-N2 columns, pass B
+// runs the remaining stages inside each of the N1 contiguous rows.
+// ------------------------------------------------------------------------
+constexpr int kNttThreads = 256;
+constexpr int kColsA = 16;       // columns per CTA in pass A
+constexpr int kElemsB = 2048;    // elements per CTA in pass B
+
+__global__ void __launch_bounds__(kNttThreads)
+ntt_fwd_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ tw,
+          int log_n, int s1)
+{
+    const int limb = blockIdx.y;
+    const int col = limb % bt.per_row, row = limb / bt.per_row;
+    const int pi = bt.pidx[col];
+    if (pi < 0) return;
+    const int N = 1 << log_n, N1 = 1 << s1, N2 = N >> s1;
+    extern __shared__ u64 sm[];
+    ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(sm + N1 * kColsA);
+    const u64 q = primes[pi].q;
+    const ulonglong2 *twp = tw + (size_t)pi * N;
+    const u64 *s = bt.src + ((size_t)row * bt.src_stride + col) * N;
+    u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * N;
+    const int c0 = blockIdx.x * kColsA;
+    for (int i = threadIdx.x; i < N1; i += blockDim.x) stw[i] = twp[i];
+    for (int idx = threadIdx.x; idx < N1 * kColsA; idx += blockDim.x) {
+        int r = idx / kColsA, c = idx % kColsA;
+        sm[idx] = s[(size_t)r * N2 + c0 + c];
+    }
+    __syncthreads();
+    const u64 q2 = 2 * q;
+    for (int st = 0; st < s1; st++) {
+        const int half = N1 >> (st + 1);
+        for (int b = threadIdx.x; b < (N1 / 2) * kColsA; b += blockDim.x) {
+            int c = b % kColsA, j = b / kColsA;
+            int i = j / half;
+            int r0 = i * 2 * half + (j % half);
+            ulonglong2 w = stw[(1 << st) + i];
+            u64 X = sm[r0 * kColsA + c], Y = sm[(r0 + half) * kColsA + c];
+            X = X >= q2 ? X - q2 : X;
+            u64 T = shoup_lazy(Y, w.x, w.y, q);
+            sm[r0 * kColsA + c] = X + T;
+            sm[(r0 + half) * kColsA + c] = X - T + q2;
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < N1 * kColsA; idx += blockDim.x) {
+        int r = idx / kColsA, c = idx % kColsA;
+        d[(size_t)r * N2 + c0 + c] = sm[idx];   // lazy, < 4q
+    }
+}
+
+__global__ void __launch_bounds__(kNttThreads)
+ntt_fwd_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ tw,
+          int log_n, int s1, int rows_per_cta)
+{
+    const int limb = blockIdx.y;
+    const int col = limb % bt.per_row, row = limb / bt.per_row;
+    const int pi = bt.pidx[col];
+    if (pi < 0) return;
+    const int N = 1 << log_n, N2 = N >> s1;
+    const int R = rows_per_cta;
+    extern __shared__ u64 sm[];
+    const u64 q = primes[pi].q, q2 = 2 * q;
+    const ulonglong2 *twp = tw + (size_t)pi * N;
+    const int row0 = blockIdx.x * R;
+    u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * N + (size_t)row0 * N2;
+    for (int idx = threadIdx.x; idx < R * N2; idx += blockDim.x) sm[idx] = d[idx];
+    __syncthreads();
+    const int hb = N2 / 2;
+    for (int st = s1; st < log_n; st++) {
+        const int t = N >> (st + 1);
+        for (int b = threadIdx.x; b < R * hb; b += blockDim.x) {
+            int r = b / hb, jj = b % hb;
+            int g = jj / t;
+            int p0 = r * N2 + g * 2 * t + (jj % t);
+            int gi = (row0 + r) * (N2 / (2 * t)) + g;
+            ulonglong2 w = twp[(1 << st) + gi];
+            u64 X = sm[p0], Y = sm[p0 + t];
+            X = X >= q2 ? X - q2 : X;
+            u64 T = shoup_lazy(Y, w.x, w.y, q);
+            sm[p0] = X + T;
+            sm[p0 + t] = X - T + q2;
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < R * N2; idx += blockDim.x) d[idx] = reduce4(sm[idx], q);
+}
+
+__global__ void __launch_bounds__(kNttThreads)
+ntt_inv_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ itw,
+          int log_n, int s1, int rows_per_cta)
+{
+    const int limb = blockIdx.y;
+    const int col = limb % bt.per_row, row = limb / bt.per_row;
+    const int pi = bt.pidx[col];
+    if (pi < 0) return;
+    const int N = 1 << log_n, N2 = N >> s1;
+    const int R = rows_per_cta;
+    extern __shared__ u64 sm[];
+    const u64 q = primes[pi].q, q2 = 2 * q;
+    const ulonglong2 *twp = itw + (size_t)pi * N;
+    const int row0 = blockIdx.x * R;
+    const u64 *s = bt.src + ((size_t)row * bt.src_stride + col) * N + (size_t)row0 * N2;
+    u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * N + (size_t)row0 * N2;
+    for (int idx = threadIdx.x; idx < R * N2; idx += blockDim.x) sm[idx] = s[idx];
+    __syncthreads();
+    const int hb = N2 / 2;
+    for (int st = log_n - 1; st >= s1; st--) {
+        const int t = N >> (st + 1);
+        for (int b = threadIdx.x; b < R * hb; b += blockDim.x) {
+            int r = b / hb, jj = b % hb;
+            int g = jj / t;
+            int p0 = r * N2 + g * 2 * t + (jj % t);
+            int gi = (row0 + r) * (N2 / (2 * t)) + g;
+            ulonglong2 w = twp[(1 << st) + gi];
+            u64 U = sm[p0], V = sm[p0 + t];
+            u64 S = U + V;
+            sm[p0] = S >= q2 ? S - q2 : S;
+            sm[p0 + t] = shoup_lazy(U - V + q2, w.x, w.y, q);
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < R * N2; idx += blockDim.x) d[idx] = sm[idx];   // < 2q
+}
+
+__global__ void __launch_bounds__(kNttThreads)
+ntt_inv_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ itw,
+          const u64 *__restrict__ ninv, int log_n, int s1)
+{
+    const int limb = blockIdx.y;
+    const int col = limb % bt.per_row, row = limb / bt.per_row;
+    const int pi = bt.pidx[col];
+    if (pi < 0) return;
+    const int N = 1 << log_n, N1 = 1 << s1, N2 = N >> s1;
+    extern __shared__ u64 sm[];
+    ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(sm + N1 * kColsA);
+    const u64 q = primes[pi].q, q2 = 2 * q;
+    const ulonglong2 *twp = itw + (size_t)pi * N;
+    u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * N;
+    const int c0 = blockIdx.x * kColsA;
+    for (int i = threadIdx.x; i < N1; i += blockDim.x) stw[i] = twp[i];
+    for (int idx = threadIdx.x; idx < N1 * kColsA; idx += blockDim.x) {
+        int r = idx / kColsA, c = idx % kColsA;
+        sm[idx] = d[(size_t)r * N2 + c0 + c];
+    }
+    __syncthreads();
+    for (int st = s1 - 1; st >= 0; st--) {
+        const int half = N1 >> (st + 1);
+        for (int b = threadIdx.x; b < (N1 / 2) * kColsA; b += blockDim.x) {
+            int c = b % kColsA, j = b / kColsA;
+            int i = j / half;
+            int r0 = i * 2 * half + (j % half);
+            ulonglong2 w = stw[(1 << st) + i];
+            u64 U = sm[r0 * kColsA + c], V = sm[(r0 + half) * kColsA + c];
+            u64 S = U + V;
+            sm[r0 * kColsA + c] = S >= q2 ? S - q2 : S;
+            sm[(r0 + half) * kColsA + c] = shoup_lazy(U - V + q2, w.x, w.y, q);
+        }
+        __syncthreads();
+    }
+    const u64 ni = ninv[2 * pi], nis = ninv[2 * pi + 1];
+    for (int idx = threadIdx.x; idx < N1 * kColsA; idx += blockDim.x) {
+        int r = idx / kColsA, c = idx % kColsA;
+        d[(size_t)r * N2 + c0 + c] = shoup_mul(sm[idx], ni, nis, q);
+    }
+}
+
+// ------------------------------------------------------------------------
+// element-wise kernels over a Batch (grid: x blocks, limbs)
+// ------------------------------------------------------------------------
+__device__ __forceinline__ const u64 *limb_ptr(const u64 *base, int stride, int per_row, int limb,
+                                               int N)
+{
+    return base + ((size_t)(limb / per_row) * stride + (limb % per_row)) * N;
+}
+
+__global__ void k_to_mont(const Batch bt, const PrimeC *__restrict__ primes, int N)
+{
+    const int limb = blockIdx.y;
+    const int pi = bt.pidx[limb % bt.per_row];
+    if (pi < 0) return;
+    const PrimeC P = primes[pi];
+    u64 *d = const_cast<u64 *>(limb_ptr(bt.dst, bt.dst_stride, bt.per_row, limb, N));
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x)
+        d[x] = mont_mul(d[x], P.r2, P);
+}
+
+__global__ void k_from_mont(const Batch bt, const PrimeC *__restrict__ primes, int N)
+{
+    const int limb = blockIdx.y;
+    const int pi = bt.pidx[limb % bt.per_row];
+    if (pi < 0) return;
+    const PrimeC P = primes[pi];
+    u64 *d = const_cast<u64 *>(limb_ptr(bt.dst, bt.dst_stride, bt.per_row, limb, N));
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x)
+        d[x] = redc(0, d[x], P);
+}
+
+// c = a * b (both plain NTT-domain values)
+__global__ void k_pointwise(const u64 *a, const u64 *b, u64 *c, const Batch bt,
+                            const PrimeC *__restrict__ primes, int N)
+{
+    const int limb = blockIdx.y;
+    const int pi = bt.pidx[limb % bt.per_row];
+    if (pi < 0) return;
+    const PrimeC P = primes[pi];
+    const size_t off = (size_t)limb * N;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x)
+        c[off + x] = mont_mul(mont_mul(a[off + x], b[off + x], P), P.r2, P);
+}
+
+__global__ void k_add(const u64 *a, const u64 *b, u64 *c, const Batch bt,
+                      const PrimeC *__restrict__ primes, int N)
+{
+    const int limb = blockIdx.y;
+    const int pi = bt.pidx[limb % bt.per_row];
+    if (pi < 0) return;
+    const u64 q = primes[pi].q;
+    const size_t off = (size_t)limb * N;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x)
+        c[off + x] = add_mod(a[off + x], b[off + x], q);
+}
+
+__global__ void k_neg(const u64 *a, u64 *c, const Batch bt, const PrimeC *__restrict__ primes,
+                      int N)
+{
+    const int limb = blockIdx.y;
+    const int pi = bt.pidx[limb % bt.per_row];
+    if (pi < 0) return;
+    const u64 q = primes[pi].q;
+    const size_t off = (size_t)limb * N;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
+        u64 v = a[off + x];
+        c[off + x] = v ? q - v : 0;
+    }
+}
+
+// c = a * s_limb (scalar per limb column, Shoup), s given as (w, w') pairs
+__global__ void k_scalar(const u64 *a, u64 *c, const Batch bt, const PrimeC *__restrict__ primes,
+                         const u64 *__restrict__ scal, int N)
+{
+    const int limb = blockIdx.y;
+    const int col = limb % bt.per_row;
+    const int pi = bt.pidx[col];
+    if (pi < 0) return;
+    const u64 q = primes[pi].q, w = scal[2 * col], ws = scal[2 * col + 1];
+    const size_t off = (size_t)limb * N;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x)
+        c[off + x] = shoup_mul(a[off + x], w, ws, q);
+}
+
+// automorphism X -> X^g in the bit-reversed NTT order:
+// out[j] = a[brv(((2 brv(j) + 1) g mod 2N - 1) / 2)]
+__device__ __forceinline__ int auto_src(int j, uint32_t g, int log_n)
+{
+    uint32_t r = __brev((uint32_t)j) >> (32 - log_n);
+    uint32_t e = ((2 * r + 1) * g) & ((2u << log_n) - 1);
+    return (int)(__brev((e - 1) >> 1) >> (32 - log_n));
+}
+
+__global__ void k_automorphism(const u64 *a, u64 *c, int nlimbs, uint32_t g, int log_n)
+{
+    const int N = 1 << log_n;
+    const size_t off = (size_t)blockIdx.y * N;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x)
+        c[off + x] = a[off + auto_src(x, g, log_n)];
+}
+
+// small signed coefficients -> residues of each listed prime
+__global__ void k_small_to_res(const int8_t *e, u64 *out, const int *pidx, const PrimeC *primes,
+                               int N)
+{
+    const int limb = blockIdx.y;
+    const u64 q = primes[pidx[limb]].q;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
+        int v = e[x];
+        out[(size_t)limb * N + x] = v < 0 ? q - (u64)(-v) : (u64)v;
+    }
+}
+
+__global__ void k_copy_limbs(const u64 *src, int src_ls, u64 *dst, int dst_ls, int nl, int N)
+{
+    const int poly = blockIdx.z, i = blockIdx.y;
+    const u64 *s = src + ((size_t)poly * src_ls + i) * N;
+    u64 *d = dst + ((size_t)poly * dst_ls + i) * N;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x)
+        d[x] = s[x];
+}
+
+// ------------------------------------------------------------------------
+// combination: Z[j][p][i] = sum_f c[i][f][j] * X[f][p][i]   (coefficient domain)
+// constants in Montgomery form; 128-bit accumulation, high word folded mod q
+// every 128 terms, one Montgomery reduction at the end.
+// ------------------------------------------------------------------------
+constexpr int kCombJ = 16;
+constexpr int kCombChunk = 128;
+
+__global__ void __launch_bounds__(256)
+k_comb(const u64 *__restrict__ X, int F, int Fp, int j0, int level,
+       const u64 *__restrict__ consts, u64 *Z, int z_ls, const PrimeC *__restrict__ primes,
+       int N)
+{
+    __shared__ u64 cs[kCombChunk][kCombJ];
+    const int i = blockIdx.y, p = blockIdx.z;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const PrimeC P = primes[i];
+    const int nl = level + 1;
+    u64 hi[kCombJ], lo[kCombJ];
+#pragma unroll
+    for (int j = 0; j < kCombJ; j++) hi[j] = lo[j] = 0;
+    for (int f0 = 0; f0 < F; f0 += kCombChunk) {
+        const int fc = min(kCombChunk, F - f0);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < kCombChunk * kCombJ; idx += blockDim.x) {
+            int ff = idx / kCombJ, jj = idx % kCombJ;
+            cs[ff][jj] = (ff < fc && j0 + jj < Fp)
+                             ? consts[((size_t)i * F + f0 + ff) * Fp + j0 + jj] : 0;
+        }
+        __syncthreads();
+        if (x < N) {
+            for (int ff = 0; ff < fc; ff++) {
+                const u64 xv = X[(((size_t)(f0 + ff) * 2 + p) * nl + i) * N + x];
+#pragma unroll
+                for (int j = 0; j < kCombJ; j++) mac128(hi[j], lo[j], xv, cs[ff][j]);
+            }
+#pragma unroll
+            for (int j = 0; j < kCombJ; j++) hi[j] = reduce_word(hi[j], P);
+        }
+    }
+    if (x < N) {
+#pragma unroll
+        for (int j = 0; j < kCombJ; j++)
+            if (j0 + j < Fp)
+                Z[(((size_t)(j0 + j) * 2 + p) * z_ls + i) * N + x] = redc(hi[j], lo[j], P);
+    }
+}
+
+// ------------------------------------------------------------------------
+// rescale
+// ------------------------------------------------------------------------
+// coefficient domain: out_i = (in_i - [in_l]_{q_i}) * q_l^-1 mod q_i
+__global__ void k_rescale_coef(const u64 *in, int in_ls, u64 *out, int out_ls, int level,
+                               const PrimeC *__restrict__ primes, const u64 *__restrict__ tab,
+                               int N)
+{
+    const int i = blockIdx.y, poly = blockIdx.z;
+    const PrimeC P = primes[i];
+    const u64 inv = tab[2 * i], invs = tab[2 * i + 1];
+    const u64 *top = in + ((size_t)poly * in_ls + level) * N;
+    const u64 *src = in + ((size_t)poly * in_ls + i) * N;
+    u64 *dst = out + ((size_t)poly * out_ls + i) * N;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
+        u64 r = reduce_word(top[x], P);
+        dst[x] = shoup_mul(sub_mod(src[x], r, P.q), inv, invs, P.q);
+    }
+}
+
+// r (coefficient domain, one limb per poly) -> its residues mod q_0..q_{level-1}
+__global__ void k_bcast_reduce(const u64 *r, int r_ls, int r_limb, u64 *out, int level,
+                               const PrimeC *__restrict__ primes, int N)
+{
+    const int i = blockIdx.y, poly = blockIdx.z;
+    const PrimeC P = primes[i];
+    const u64 *src = r + ((size_t)poly * r_ls + r_limb) * N;
+    u64 *dst = out + ((size_t)poly * level + i) * N;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x)
+        dst[x] = reduce_word(src[x], P);
+}
+
+// NTT domain finish: ct_i = (ct_i - r_i) * q_l^-1
+__global__ void k_rescale_finish(u64 *ct, int ls, const u64 *rr, int level,
+                                 const PrimeC *__restrict__ primes, const u64 *__restrict__ tab,
+                                 int N)
+{
+    const int i = blockIdx.y, poly = blockIdx.z;
+    const u64 q = primes[i].q, inv = tab[2 * i], invs = tab[2 * i + 1];
+    u64 *c = ct + ((size_t)poly * ls + i) * N;
+    const u64 *r = rr + ((size_t)poly * level + i) * N;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x)
+        c[x] = shoup_mul(sub_mod(c[x], r[x], q), inv, invs, q);
+}
+
+
+// ------------------------------------------------------------------------
+// base conversion (approximate, no overflow correction):
+//   out_p = sum_k [x_k * (B/b_k)^-1]_{b_k} * (B/b_k) mod p
+// y_k in [0, b_k), (B/b_k) mod p in Montgomery form, n_in <= 8 products of
+// two words below 2^61 accumulate below p * 2^64, so one Montgomery
+// reduction gives the exact residue.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ u64 conv_point(const ConvTab &T, const u64 *y, int t, const PrimeC &P)
+{
+    u64 hi = 0, lo = 0;
+    for (int k = 0; k < T.n_in; k++) mac128(hi, lo, y[k], T.hmod[k][t]);
+    return redc(hi, lo, P);
+}
+
+// ModUp conversion.  c1c: [ncol][nl][N] coefficient domain (nl = level+1);
+// digits: [ncol][beta][E][N]; writes every limb outside digit dg.
+__global__ void __launch_bounds__(256)
+k_modup_conv(const u64 *__restrict__ c1c, int nl, u64 *digits, int beta, int E,
+             const ConvTab *__restrict__ tabs, const PrimeC *__restrict__ primes, int N)
+{
+    const int f = blockIdx.z / beta, dg = blockIdx.z % beta;
+    const ConvTab &T = tabs[dg];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    u64 y[8];
+    for (int k = 0; k < T.n_in; k++) {
+        const int pi = T.in_p[k];
+        const u64 v = c1c[((size_t)f * nl + T.in_l[k]) * N + x];
+        y[k] = shoup_mul(v, T.hinv[k], T.hinv_s[k], primes[pi].q);
+    }
+    u64 *out = digits + ((size_t)f * beta + dg) * E * N;
+    for (int t = 0; t < T.n_out; t++) {
+        const PrimeC P = primes[T.out_p[t]];
+        out[(size_t)T.out_l[t] * N + x] = conv_point(T, y, t, P);
+    }
+}
+
+// ModDown conversion P -> q_0..q_level.  u: [npoly][E][N] (P limbs in the
+// coefficient domain at positions level+1..), conv: [npoly][level+1][N].
+__global__ void __launch_bounds__(256)
+k_moddown_conv(const u64 *__restrict__ u, int E, u64 *conv, int nl,
+               const ConvTab *__restrict__ tab, const PrimeC *__restrict__ primes, int N)
+{
+    const int poly = blockIdx.y;
+    const ConvTab &T = *tab;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    u64 y[8];
+    for (int k = 0; k < T.n_in; k++) {
+        const u64 v = u[((size_t)poly * E + T.in_l[k]) * N + x];
+        y[k] = shoup_mul(v, T.hinv[k], T.hinv_s[k], primes[T.in_p[k]].q);
+    }
+    for (int t = 0; t < T.n_out; t++) {
+        const PrimeC P = primes[T.out_p[t]];
+        conv[((size_t)poly * nl + T.out_l[t]) * N + x] = conv_point(T, y, t, P);
+    }
+}
+
+// ------------------------------------------------------------------------
+// key switching inner product with the automorphism folded into the gather:
+//   u_p[f][i][x] = sum_d D_d[f][i][sigma_g(x)] * evk_g[d][p][i][x]
+// D_d limb i is the lane's own c1 limb when i belongs to digit d, else the
+// ModUp output.  The key (Montgomery form, [beta_L][2][nq+np][N]) is read
+// once per (x, i) and reused for every column.
+// ------------------------------------------------------------------------
+constexpr int kMaxBeta = 8;
+
+__global__ void __launch_bounds__(256)
+k_ks_ip(const u64 *__restrict__ key, int KL, const u64 *__restrict__ lane, int ls,
+        const u64 *__restrict__ digits, int ncol, int level, int beta, int E, int alpha, int nq,
+        uint32_t g, int log_n, u64 *u, const PrimeC *__restrict__ primes)
+{
+    const int N = 1 << log_n;
+    const int i = blockIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    const int pi = i <= level ? i : nq + (i - level - 1);
+    const PrimeC P = primes[pi];
+    const int src = auto_src(x, g, log_n);
+    const int own = i <= level ? i / alpha : -1;
+    u64 kb[kMaxBeta], ka[kMaxBeta];
+#pragma unroll
+    for (int d = 0; d < kMaxBeta; d++) {
+        if (d < beta) {
+            kb[d] = key[(((size_t)d * 2 + 0) * KL + pi) * N + x];
+            ka[d] = key[(((size_t)d * 2 + 1) * KL + pi) * N + x];
+        }
+    }
+    for (int f = 0; f < ncol; f++) {
+        u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
+#pragma unroll
+        for (int d = 0; d < kMaxBeta; d++) {
+            if (d < beta) {
+                const u64 v = d == own ? lane[(((size_t)f * 2 + 1) * ls + i) * N + src]
+                                       : digits[(((size_t)f * beta + d) * E + i) * N + src];
+                mac128(h0, l0, v, kb[d]);
+                mac128(h1, l1, v, ka[d]);
+            }
+        }
+        u[(((size_t)f * 2 + 0) * E + i) * N + x] = redc(h0, l0, P);
+        u[(((size_t)f * 2 + 1) * E + i) * N + x] = redc(h1, l1, P);
+    }
+}
+
+// ------------------------------------------------------------------------
+// ModDown finish + masked accumulation (the SpIntra-CA products):
+//   R_p = (u_p - conv_p) * P^-1  (+ phi_g(c0) for p = 0)
+//   out_d += mask_d (x) R         (mask in Montgomery form; null mask: out_d = R)
+// ------------------------------------------------------------------------
+constexpr int kMaxDest = 16;
+struct DestList {
+    int n;
+    int out_ls;
+    u64 *out[kMaxDest];
+    const u64 *mask[kMaxDest];
+};
+
+__global__ void __launch_bounds__(256)
+k_moddown_finish_mac(const u64 *__restrict__ u, int E, const u64 *__restrict__ conv,
+                     const u64 *__restrict__ lane, int ls, int ncol, int level, uint32_t g,
+                     int log_n, const u64 *__restrict__ pinv, const DestList dl,
+                     const PrimeC *__restrict__ primes)
+{
+    const int N = 1 << log_n;
+    const int i = blockIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    const PrimeC P = primes[i];
+    const u64 q = P.q, pv = pinv[2 * i], pvs = pinv[2 * i + 1];
+    const int src = auto_src(x, g, log_n);
+    const int nl = level + 1;
+    u64 m[kMaxDest];
+#pragma unroll
+    for (int d = 0; d < kMaxDest; d++)
+        if (d < dl.n) m[d] = dl.mask[d] ? dl.mask[d][(size_t)i * N + x] : 0;
+    for (int f = 0; f < ncol; f++) {
+#pragma unroll
+        for (int p = 0; p < 2; p++) {
+            const int poly = f * 2 + p;
+            u64 r = shoup_mul(sub_mod(u[((size_t)poly * E + i) * N + x],
+                                      conv[((size_t)poly * nl + i) * N + x], q), pv, pvs, q);
+            if (p == 0) r = add_mod(r, lane[((size_t)(f * 2) * ls + i) * N + src], q);
+#pragma unroll
+            for (int d = 0; d < kMaxDest; d++) {
+                if (d < dl.n) {
+                    u64 *o = dl.out[d] + ((size_t)poly * dl.out_ls + i) * N + x;
+                    *o = dl.mask[d] ? add_mod(*o, mont_mul(r, m[d], P), q) : r;
+                }
+            }
+        }
+    }
+}
+
+// out_d += mask_d (x) lane (the kept values of a lane, rotation 0)
+__global__ void __launch_bounds__(256)
+k_stay_mac(const u64 *__restrict__ lane, int ls, int ncol, int level, const DestList dl,
+           const PrimeC *__restrict__ primes, int N)
+{
+    const int i = blockIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    const PrimeC P = primes[i];
+    u64 m[kMaxDest];
+#pragma unroll
+    for (int d = 0; d < kMaxDest; d++)
+        if (d < dl.n) m[d] = dl.mask[d][(size_t)i * N + x];
+    for (int f = 0; f < ncol; f++) {
+#pragma unroll
+        for (int p = 0; p < 2; p++) {
+            const int poly = f * 2 + p;
+            const u64 v = lane[((size_t)poly * ls + i) * N + x];
+#pragma unroll
+            for (int d = 0; d < kMaxDest; d++) {
+                if (d < dl.n) {
+                    u64 *o = dl.out[d] + ((size_t)poly * dl.out_ls + i) * N + x;
+                    *o = add_mod(*o, mont_mul(v, m[d], P), P.q);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+// ========================================================================
+// host wrappers
+// ========================================================================
+namespace kern {
+
+static inline int s1_of(int log_n) { return log_n / 2; }
+
+static void launch_ntt(fg_ctx *ctx, const LimbSet &src, const LimbSet &dst, bool inverse)
+{
+    FG_CHECK(src.per_row == dst.per_row && src.rows == dst.rows, FG_EINVAL, "ntt: shape mismatch");
+    if (src.rows == 0 || src.per_row == 0) return;
+    const int log_n = ctx->log_n, N = ctx->n, s1 = s1_of(log_n);
+    const int N1 = 1 << s1, N2 = N >> s1;
+    Batch bt = make_batch(src.base, src.stride, dst.base, dst.stride, src.per_row, src.rows,
+                          src.pidx);
+    const int count = src.rows * src.per_row;
+    const int R = std::min(kElemsB / N2, N1);
+    const size_t smA = (size_t)N1 * kColsA * 8 + (size_t)N1 * 16;
+    const size_t smB = (size_t)R * N2 * 8;
+    const auto *fwd = (const ulonglong2 *)ctx->d_fwd;
+    const auto *inv = (const ulonglong2 *)ctx->d_inv;
+    FG_CHECK(count <= 65535, FG_EINVAL, "ntt: more than 65535 limbs in one batch");
+    dim3 gA(N2 / kColsA, count), gB(N1 / R, count);
+    if (!inverse) {
+        ntt_fwd_a<<<gA, kNttThreads, smA, ctx->stream>>>(bt, ctx->d_primes, fwd, log_n, s1);
+        Batch b2 = bt;
+        b2.src = b2.dst;
+        b2.src_stride = b2.dst_stride;
+        ntt_fwd_b<<<gB, kNttThreads, smB, ctx->stream>>>(b2, ctx->d_primes, fwd, log_n, s1, R);
+    } else {
+        ntt_inv_b<<<gB, kNttThreads, smB, ctx->stream>>>(bt, ctx->d_primes, inv, log_n, s1, R);
+        Batch b2 = bt;
+        b2.src = b2.dst;
+        b2.src_stride = b2.dst_stride;
+        ntt_inv_a<<<gA, kNttThreads, smA, ctx->stream>>>(b2, ctx->d_primes, inv, ctx->d_ninv,
+                                                         log_n, s1);
+    }
+    check_launch("ntt");
+}
+
+void ntt_fwd(fg_ctx *ctx, const LimbSet &src, const LimbSet &dst) { launch_ntt(ctx, src, dst, false); }
+void ntt_inv(fg_ctx *ctx, const LimbSet &src, const LimbSet &dst) { launch_ntt(ctx, src, dst, true); }
+
+static inline dim3 ew_grid(int N, int count) { return dim3((N + 255) / 256, count); }
+
+static Batch contiguous(u64 *p, int count, const std::vector<int> &pidx)
+{
+    const int per = (int)pidx.size();
+    return make_batch(p, per, p, per, per, count / per, pidx);
+}
+
+void to_mont(fg_ctx *ctx, u64 *data, int count, const std::vector<int> &pidx)
+{
+    if (!count) return;
+    k_to_mont<<<ew_grid(ctx->n, count), 256, 0, ctx->stream>>>(contiguous(data, count, pidx),
+                                                               ctx->d_primes, ctx->n);
+    check_launch("to_mont");
+}
+
+void from_mont(fg_ctx *ctx, u64 *data, int count, const std::vector<int> &pidx)
+{
+    if (!count) return;
+    k_from_mont<<<ew_grid(ctx->n, count), 256, 0, ctx->stream>>>(contiguous(data, count, pidx),
+                                                                 ctx->d_primes, ctx->n);
+    check_launch("from_mont");
+}
+
+void pointwise(fg_ctx *ctx, const u64 *a, const u64 *b, u64 *c, int count,
+               const std::vector<int> &pidx)
+{
+    if (!count) return;
+    k_pointwise<<<ew_grid(ctx->n, count), 256, 0, ctx->stream>>>(
+        a, b, c, contiguous(c, count, pidx), ctx->d_primes, ctx->n);
+    check_launch("pointwise");
+}
+
+void add(fg_ctx *ctx, const u64 *a, const u64 *b, u64 *c, int count, const std::vector<int> &pidx)
+{
+    if (!count) return;
+    k_add<<<ew_grid(ctx->n, count), 256, 0, ctx->stream>>>(a, b, c, contiguous(c, count, pidx),
+                                                           ctx->d_primes, ctx->n);
+    check_launch("add");
+}
+
+void neg(fg_ctx *ctx, const u64 *a, u64 *c, int count, const std::vector<int> &pidx)
+{
+    if (!count) return;
+    k_neg<<<ew_grid(ctx->n, count), 256, 0, ctx->stream>>>(a, c, contiguous(c, count, pidx),
+                                                           ctx->d_primes, ctx->n);
+    check_launch("neg");
+}
+
+void scalar(fg_ctx *ctx, const u64 *a, u64 *c, int count, const std::vector<int> &pidx,
+            const u64 *d_scal)
+{
+    if (!count) return;
+    k_scalar<<<ew_grid(ctx->n, count), 256, 0, ctx->stream>>>(
+        a, c, contiguous(c, count, pidx), ctx->d_primes, d_scal, ctx->n);
+    check_launch("scalar");
+}
+
+void automorphism(fg_ctx *ctx, const u64 *a, u64 *c, int nlimbs, uint32_t g)
+{
+    if (!nlimbs) return;
+    k_automorphism<<<ew_grid(ctx->n, nlimbs), 256, 0, ctx->stream>>>(a, c, nlimbs, g, ctx->log_n);
+    check_launch("automorphism");
+}
+
+void small_to_res(fg_ctx *ctx, const int8_t *e, u64 *out, int n_limbs, const int *d_pidx)
+{
+    k_small_to_res<<<ew_grid(ctx->n, n_limbs), 256, 0, ctx->stream>>>(e, out, d_pidx,
+                                                                      ctx->d_primes, ctx->n);
+    check_launch("small_to_res");
+}
+
+void copy_limbs(fg_ctx *ctx, const u64 *src, int src_ls, u64 *dst, int dst_ls, int npoly, int nl)
+{
+    if (!npoly || !nl) return;
+    dim3 g((ctx->n + 255) / 256, nl, npoly);
+    k_copy_limbs<<<g, 256, 0, ctx->stream>>>(src, src_ls, dst, dst_ls, nl, ctx->n);
+    check_launch("copy_limbs");
+}
+
+void comb_const_mac(fg_ctx *ctx, const u64 *X, int F, int Fp, int level, const u64 *consts, u64 *Z,
+                    int z_ls)
+{
+    for (int j0 = 0; j0 < Fp; j0 += kCombJ) {
+        dim3 g((ctx->n + 255) / 256, level + 1, 2);
+        k_comb<<<g, 256, 0, ctx->stream>>>(X, F, Fp, j0, level, consts, Z, z_ls, ctx->d_primes,
+                                           ctx->n);
+        check_launch("comb");
+    }
+}
+
+void rescale_coef(fg_ctx *ctx, const u64 *in, int in_ls, u64 *out, int out_ls, int npoly, int level)
+{
+    FG_CHECK(level >= 1, FG_ELEVEL, "rescale needs level >= 1");
+    dim3 g((ctx->n + 255) / 256, level, npoly);
+    k_rescale_coef<<<g, 256, 0, ctx->stream>>>(in, in_ls, out, out_ls, level, ctx->d_primes,
+                                               ctx->rescale_tab(level), ctx->n);
+    check_launch("rescale_coef");
+}
+
+void rescale_ntt(fg_ctx *ctx, u64 *ct, int ls, int npoly, int level)
+{
+    FG_CHECK(level >= 1, FG_ELEVEL, "rescale needs level >= 1");
+    const int N = ctx->n;
+    // top limb back to the coefficient domain (in place; it is dropped anyway)
+    std::vector<int> top(ls, -1);
+    top[level] = level;
+    LimbSet s{ct, ls, ls, npoly, top};
+    ntt_inv(ctx, s, s);
+    u64 *rr = (u64 *)ctx->buf("rescale_r", (size_t)npoly * level * N * 8);
+    dim3 g((N + 255) / 256, level, npoly);
+    k_bcast_reduce<<<g, 256, 0, ctx->stream>>>(ct, ls, level, rr, level, ctx->d_primes, N);
+    check_launch("bcast_reduce");
+    std::vector<int> pid(level);
+    for (int i = 0; i < level; i++) pid[i] = i;
+    LimbSet r{rr, level, level, npoly, pid};
+    ntt_fwd(ctx, r, r);
+    k_rescale_finish<<<g, 256, 0, ctx->stream>>>(ct, ls, rr, level, ctx->d_primes,
+                                                 ctx->rescale_tab(level), N);
+    check_launch("rescale_finish");
+}
+
+void modup(fg_ctx *ctx, const u64 *lane, int ls, int ncol, int level, u64 *digits)
+{
+    const int N = ctx->n, nl = level + 1, E = ctx->ext(level), beta = ctx->n_digits(level);
+    u64 *c1c = (u64 *)ctx->buf("modup_c1", (size_t)ncol * nl * N * 8);
+    std::vector<int> pid(nl);
+    for (int i = 0; i < nl; i++) pid[i] = i;
+    LimbSet src{const_cast<u64 *>(lane) + (size_t)ls * N, 2 * ls, nl, ncol, pid};
+    LimbSet dst{c1c, nl, nl, ncol, pid};
+    ntt_inv(ctx, src, dst);
+    dim3 g((N + 255) / 256, 1, ncol * beta);
+    k_modup_conv<<<g, 256, 0, ctx->stream>>>(c1c, nl, digits, beta, E, ctx->modup_tabs(level),
+                                             ctx->d_primes, N);
+    check_launch("modup_conv");
+    std::vector<int> dp(beta * E);
+    for (int d = 0; d < beta; d++)
+        for (int i = 0; i < E; i++)
+            dp[d * E + i] = (i <= level && i / ctx->alpha == d) ? -1 : ctx->ext_prime(level, i);
+    LimbSet ds{digits, beta * E, beta * E, ncol, dp};
+    ntt_fwd(ctx, ds, ds);
+}
+
+void rotate_mac(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int ncol, int level,
+                const u64 *digits, const std::vector<Dest> &dests, int out_ls)
+{
+    const int N = ctx->n, nl = level + 1, E = ctx->ext(level), beta = ctx->n_digits(level);
+    FG_CHECK(beta <= kMaxBeta, FG_EINVAL, "too many key-switching digits");
+    const int KL = ctx->nq + ctx->np;
+    u64 *u = (u64 *)ctx->buf("ks_u", (size_t)ncol * 2 * E * N * 8);
+    dim3 g1((N + 255) / 256, E);
+    k_ks_ip<<<g1, 256, 0, ctx->stream>>>(key.d, KL, lane, ls, digits, ncol, level, beta, E,
+                                         ctx->alpha, ctx->nq, key.galois, ctx->log_n, u,
+                                         ctx->d_primes);
+    check_launch("ks_ip");
+    std::vector<int> pp(E);
+    for (int i = 0; i < E; i++) pp[i] = i <= level ? -1 : ctx->ext_prime(level, i);
+    LimbSet us{u, E, E, 2 * ncol, pp};
+    ntt_inv(ctx, us, us);
+    u64 *conv = (u64 *)ctx->buf("ks_conv", (size_t)ncol * 2 * nl * N * 8);
+    dim3 g2((N + 255) / 256, 2 * ncol);
+    k_moddown_conv<<<g2, 256, 0, ctx->stream>>>(u, E, conv, nl, ctx->moddown_tab(level),
+                                                ctx->d_primes, N);
+    check_launch("moddown_conv");
+    std::vector<int> pq(nl);
+    for (int i = 0; i < nl; i++) pq[i] = i;
+    LimbSet cs{conv, nl, nl, 2 * ncol, pq};
+    ntt_fwd(ctx, cs, cs);
+    for (size_t d0 = 0; d0 < dests.size() || d0 == 0; d0 += kMaxDest) {
+        DestList dl;
+        dl.n = (int)std::min<size_t>(kMaxDest, dests.size() - d0);
+        dl.out_ls = out_ls;
+        for (int d = 0; d < dl.n; d++) {
+            dl.out[d] = dests[d0 + d].out;
+            dl.mask[d] = dests[d0 + d].mask;
+        }
+        dim3 g3((N + 255) / 256, nl);
+        k_moddown_finish_mac<<<g3, 256, 0, ctx->stream>>>(u, E, conv, lane, ls, ncol, level,
+                                                          key.galois, ctx->log_n,
+                                                          ctx->pinv_tab(level), dl, ctx->d_primes);
+        check_launch("moddown_finish_mac");
+        if (dests.empty()) break;
+    }
+}
+
+void stay_mac(fg_ctx *ctx, const u64 *lane, int ls, int ncol, int level,
+              const std::vector<Dest> &dests, int out_ls)
+{
+    const int N = ctx->n;
+    for (size_t d0 = 0; d0 < dests.size(); d0 += kMaxDest) {
+        DestList dl;
+        dl.n = (int)std::min<size_t>(kMaxDest, dests.size() - d0);
+        dl.out_ls = out_ls;
+        for (int d = 0; d < dl.n; d++) {
+            dl.out[d] = dests[d0 + d].out;
+            dl.mask[d] = dests[d0 + d].mask;
+        }
+        dim3 g((N + 255) / 256, level + 1);
+        k_stay_mac<<<g, 256, 0, ctx->stream>>>(lane, ls, ncol, level, dl, ctx->d_primes, N);
+        check_launch("stay_mac");
+    }
+}
+
+}  // namespace kern

@@ -1,0 +1,432 @@
+// layer.cu -- plans on the device and the encrypted layer A-hat X W.
+//
+// Execution of a plan (paper Sec. 3.2-3.3; the plan itself is planner.cpp):
+//   1. combination: t = 1: integer constants times each packed input,
+//      summed in the coefficient domain (one pass over X for all output
+//      columns), one rescale, then the column ciphertexts go to the NTT
+//      domain; t > 1: NTT of the inputs, block-replicated W masks,
+//      rescale, log t rotate-and-sum steps;
+//   2. SpIntra-CA groups: per input lane one ModUp of c1 (hoisted, shared by
+//      all its rotation amounts), per rotation one key-switching inner
+//      product and ModDown whose epilogue multiplies the rotated ciphertext
+//      by every mask that uses it and adds it into the output lanes and the
+//      accumulator; kept values (rotation 0) are masked the same way; then
+//      every output and the group's accumulator are rescaled and the running
+//      accumulator, dropped one limb, receives the group's arrivals;
+//   3. the accumulator returns to the coefficient domain.
+// All F' output columns share the plan, so every kernel runs over all
+// columns at once and each rotation key is read once per rotation.
+#include <omp.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "fg_internal.h"
+#include "modarith.cuh"
+
+namespace {
+
+bool is_dev(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+std::vector<int> iota(int n, int start = 0)
+{
+    std::vector<int> v(n);
+    for (int i = 0; i < n; i++) v[i] = start + i;
+    return v;
+}
+
+// encode one mask of the plan at scale q_level and put it on the device
+// (NTT domain, Montgomery form)
+void upload_mask(fg_ctx *ctx, MaskC &m, const u64 *coeffs_host_or_dev)
+{
+    const int N = ctx->n, nl = m.level + 1;
+    if (!m.d) CUDA_TRY(cudaMalloc(&m.d, (size_t)nl * N * 8));
+    CUDA_TRY(cudaMemcpyAsync(m.d, coeffs_host_or_dev, (size_t)nl * N * 8, cudaMemcpyDefault,
+                             ctx->stream));
+    const std::vector<int> pid = iota(nl);
+    kern::LimbSet s{m.d, nl, nl, 1, pid};
+    kern::ntt_fwd(ctx, s, s);
+    kern::to_mont(ctx, m.d, nl, pid);
+}
+
+void encode_mask(const fg_ctx *ctx, const MaskC &m, u64 *out)
+{
+    std::vector<double> z(ctx->slots, 0.0);
+    for (size_t i = 0; i < m.slots.size(); i++) z[m.slots[i]] = m.values[i];
+    hm::encode(ctx->log_n, z.data(), ctx->slots, (double)ctx->primes[m.level], ctx->primes.data(),
+               m.level + 1, out);
+}
+
+}  // namespace
+
+extern "C" {
+
+int fg_plan_build(fg_ctx *ctx, const int32_t *row_ptr, const int32_t *col, const double *val,
+                  int V, const double *W, int F, int Fp, const int32_t *perm,
+                  const fg_plan_opts *opts, fg_plan **out)
+{
+    if (!ctx) return FG_EINVAL;
+    fg_plan *pl = nullptr;
+    try {
+        FG_CHECK(row_ptr && (col || V == 0) && W && perm && out, FG_EINVAL, "null argument");
+        *out = nullptr;
+        fg_plan_opts o{0, 0, 1, 0, 0};
+        if (opts) o = *opts;
+        pl = new fg_plan;
+        pl->ctx = ctx;
+        planner::build(*pl, *ctx, row_ptr, col, val, V, W, F, Fp, perm, o);
+        // masks: encode on the host (all cores), upload, NTT, Montgomery form
+        const int N = ctx->n;
+        const int nm = (int)pl->masks.size();
+        const int chunk = 32;
+        std::vector<std::vector<u64>> enc(chunk);
+        for (int m0 = 0; m0 < nm; m0 += chunk) {
+            const int cn = std::min(chunk, nm - m0);
+            int bad = 0;
+#pragma omp parallel for schedule(dynamic) reduction(| : bad)
+            for (int c = 0; c < cn; c++) {
+                const MaskC &m = pl->masks[m0 + c];
+                enc[c].resize((size_t)(m.level + 1) * N);
+                try {
+                    encode_mask(ctx, m, enc[c].data());
+                } catch (...) {
+                    bad = 1;
+                }
+            }
+            FG_CHECK(!bad, FG_EINVAL, "mask cannot be encoded");
+            for (int c = 0; c < cn; c++) upload_mask(ctx, pl->masks[m0 + c], enc[c].data());
+            CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        }
+        if (pl->t == 1) {
+            const int l0 = pl->in_level, nl = l0 + 1;
+            std::vector<u64> h((size_t)nl * F * Fp);
+            for (int i = 0; i < nl; i++) {
+                const u64 q = ctx->primes[i];
+                for (size_t e = 0; e < (size_t)F * Fp; e++) {
+                    const i64 c = pl->comb_consts[e];
+                    const u64 r = c >= 0 ? (u64)c % q : (q - ((u64)(-(c + 1)) % q + 1) % q) % q;
+                    h[(size_t)i * F * Fp + e] = hm::to_mont(r, q);
+                }
+            }
+            CUDA_TRY(cudaMalloc(&pl->d_comb, h.size() * 8));
+            CUDA_TRY(cudaMemcpy(pl->d_comb, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
+        }
+        *out = pl;
+        return FG_OK;
+    } catch (const fg_error &e) {
+        ctx->err = e.what();
+        fg_plan_destroy(pl);
+        return e.code;
+    } catch (const std::exception &e) {
+        ctx->err = e.what();
+        fg_plan_destroy(pl);
+        return FG_EOOM;
+    }
+}
+
+int fg_plan_destroy(fg_plan *plan)
+{
+    if (!plan) return FG_OK;
+    if (plan->ctx) cudaStreamSynchronize(plan->ctx->stream);
+    for (auto &m : plan->masks) cudaFree(m.d);
+    cudaFree(plan->d_comb);
+    delete plan;
+    return FG_OK;
+}
+
+int fg_plan_info(const fg_plan *pl, fg_plan_info_t *info)
+{
+    if (!pl || !info) return FG_EINVAL;
+    memset(info, 0, sizeof(*info));
+    info->t = pl->t;
+    info->B = pl->B;
+    info->n_in = pl->t == 1 ? pl->F : (pl->F + pl->t - 1) / pl->t;
+    info->n_out = pl->Fp;
+    info->in_level = pl->in_level;
+    info->out_level = pl->out_level;
+    info->n_groups = (int)pl->groups.size();
+    info->n_masks = (int)pl->masks.size();
+    int32_t tmp[1];
+    int nk = 0;
+    fg_plan_rotation_amounts(pl, tmp, 0, &nk);
+    info->n_keys = nk;
+    int64_t rots = (int64_t)pl->comb_rots.size(), prods = 0;
+    for (auto &g : pl->groups) {
+        rots += (int64_t)g.rots.size();
+        prods += (int64_t)g.terms.size();
+    }
+    if (pl->t > 1) prods += (int64_t)pl->comb_masks.size() * pl->Fp;
+    info->rotations = rots * pl->Fp;
+    info->masked_products = prods * pl->Fp;
+    return FG_OK;
+}
+
+int fg_plan_rotation_amounts(const fg_plan *pl, int32_t *out, int cap, int *n)
+{
+    if (!pl || !n) return FG_EINVAL;
+    std::vector<int32_t> ks;
+    for (int k : pl->comb_rots) ks.push_back(((k % pl->M) + pl->M) % pl->M);
+    for (auto &g : pl->groups)
+        for (auto &r : g.rots) ks.push_back(((r.second % pl->M) + pl->M) % pl->M);
+    std::sort(ks.begin(), ks.end());
+    ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
+    *n = (int)ks.size();
+    if (out)
+        for (int i = 0; i < std::min(cap, (int)ks.size()); i++) out[i] = ks[i];
+    return (out && cap < (int)ks.size()) ? FG_EINVAL : FG_OK;
+}
+
+static std::vector<int64_t> describe_records(const fg_plan *pl)
+{
+    std::vector<int64_t> r = {pl->N, pl->M, pl->t, pl->B, pl->V, pl->F, pl->Fp, pl->in_level,
+                              pl->out_level, pl->radix_bits, pl->aoo, (int64_t)pl->groups.size(),
+                              (int64_t)pl->masks.size()};
+    for (int v : pl->perm) r.push_back(v);
+    if (pl->t == 1) {
+        for (i64 c : pl->comb_consts) r.push_back(c);
+    } else {
+        for (auto &row : pl->comb_masks)
+            for (int m : row) r.push_back(m);
+        r.push_back((int64_t)pl->comb_rots.size());
+        for (int k : pl->comb_rots) r.push_back(k);
+    }
+    for (auto &g : pl->groups) {
+        r.insert(r.end(), {g.bit_lo, g.n_bits, g.level, g.n_in, g.n_out, (int64_t)g.rots.size()});
+        for (auto &rk : g.rots) r.insert(r.end(), {rk.first, rk.second});
+        r.push_back((int64_t)g.terms.size());
+        for (auto &t : g.terms) r.insert(r.end(), {t.src, t.k, t.dst, t.mask});
+    }
+    for (auto &m : pl->masks) {
+        r.push_back(m.level);
+        r.push_back((int64_t)m.slots.size());
+        for (size_t i = 0; i < m.slots.size(); i++) {
+            int64_t bits;
+            memcpy(&bits, &m.values[i], 8);
+            r.push_back(m.slots[i]);
+            r.push_back(bits);
+        }
+    }
+    return r;
+}
+
+static int copy_records(const std::vector<int64_t> &r, int64_t *out, size_t cap, size_t *len)
+{
+    *len = r.size();
+    if (!out) return FG_OK;
+    if (cap < r.size()) return FG_EINVAL;
+    memcpy(out, r.data(), r.size() * 8);
+    return FG_OK;
+}
+
+// Records: [N, M, t, B, V, F, Fp, in_level, out_level, radix_bits, aoo,
+//  n_groups, n_masks], perm[V], combination (t == 1: F*Fp constants; t > 1:
+//  nb*Fp mask ids, n_rots, rots), per group [bit_lo, n_bits, level, n_in,
+//  n_out, n_rots, (src, k)*, n_terms, (src, k, dst, mask)*], per mask
+//  [level, nnz, (slot, value bits)*].
+int fg_plan_describe(const fg_plan *pl, int64_t *out, size_t cap, size_t *len)
+{
+    if (!pl || !len) return FG_EINVAL;
+    return copy_records(describe_records(pl), out, cap, len);
+}
+
+int fg_plan_dry_run(const fg_params *prm, const int32_t *row_ptr, const int32_t *col,
+                    const double *val, int V, const double *W, int F, int Fp, const int32_t *perm,
+                    const fg_plan_opts *opts, int64_t *out, size_t cap, size_t *len)
+{
+    if (!prm || !row_ptr || !W || !perm || !len) return FG_EINVAL;
+    try {
+        FG_CHECK(prm->log_n >= 10 && prm->log_n <= 16 && prm->n_q >= 2 && prm->n_q <= 60 &&
+                     prm->n_p >= 1 && prm->n_p <= 8 && prm->q_bits && prm->p_bits,
+                 FG_EINVAL, "bad parameters");
+        fg_ctx c;   // host-only: primes and sizes, no device tables
+        c.log_n = prm->log_n;
+        c.n = 1 << prm->log_n;
+        c.slots = c.n / 2;
+        c.nq = prm->n_q;
+        c.np = prm->n_p;
+        c.alpha = prm->alpha;
+        std::vector<int> bits(prm->q_bits, prm->q_bits + prm->n_q);
+        bits.insert(bits.end(), prm->p_bits, prm->p_bits + prm->n_p);
+        c.primes = hm::gen_primes(c.log_n, bits);
+        fg_plan_opts o{0, 0, 1, 0, 0};
+        if (opts) o = *opts;
+        fg_plan pl;
+        planner::build(pl, c, row_ptr, col, val, V, W, F, Fp, perm, o);
+        return copy_records(describe_records(&pl), out, cap, len);
+    } catch (const fg_error &e) {
+        return e.code;
+    } catch (const std::exception &) {
+        return FG_EOOM;
+    }
+}
+
+int fg_plan_set_plaintext(fg_plan *pl, int mask, const uint64_t *coeffs)
+{
+    if (!pl || !pl->ctx) return FG_EINVAL;
+    fg_ctx *ctx = pl->ctx;
+    try {
+        FG_CHECK(mask >= 0 && mask < (int)pl->masks.size() && coeffs, FG_EINVAL, "bad mask index");
+        upload_mask(ctx, pl->masks[mask], coeffs);
+        CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    } catch (const fg_error &e) {
+        ctx->err = e.what();
+        return e.code;
+    }
+    return FG_OK;
+}
+
+// ------------------------------------------------------------------ the layer
+int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, const uint64_t *in_cts,
+                     int n_in, uint64_t *out_cts, int n_out, int *out_level, double *out_scale)
+{
+    if (!ctx) return FG_EINVAL;
+    try {
+        FG_CHECK(keys && pl && in_cts && out_cts, FG_EINVAL, "null argument");
+        FG_CHECK(pl->ctx == ctx && keys->ctx == ctx, FG_EINVAL, "plan or keys of another context");
+        const int N = ctx->n, M = ctx->slots, Fp = pl->Fp, F = pl->F, t = pl->t;
+        const int l0 = pl->in_level, nl0 = l0 + 1;
+        const int nb = t == 1 ? F : (F + t - 1) / t;
+        FG_CHECK(n_in == nb, FG_EINVAL, "number of input ciphertexts does not match the plan");
+        FG_CHECK(n_out == Fp, FG_EINVAL, "number of output ciphertexts does not match the plan");
+        // every rotation key the plan needs must be present before any work
+        for (int k : pl->comb_rots) keys->get(((k % M) + M) % M);
+        for (auto &g : pl->groups)
+            for (auto &r : g.rots) keys->get(((r.second % M) + M) % M);
+
+        const size_t in_w = (size_t)nb * 2 * nl0 * N;
+        const u64 *X = in_cts;
+        if (!is_dev(in_cts)) {
+            u64 *d = (u64 *)ctx->buf("layer_in", in_w * 8);
+            CUDA_TRY(cudaMemcpyAsync(d, in_cts, in_w * 8, cudaMemcpyHostToDevice, ctx->stream));
+            X = d;
+        }
+        const int l1 = l0 - 1, LS = l1 + 1;           // lanes keep a fixed limb stride
+        const size_t lane_w = (size_t)Fp * 2 * LS * N;
+        const int max_lanes = std::max(1, pl->max_lanes);
+        std::vector<u64 *> bufA(max_lanes), bufB(max_lanes);
+        for (int i = 0; i < max_lanes; i++) {
+            bufA[i] = (u64 *)ctx->buf("lane_a" + std::to_string(i), lane_w * 8);
+            bufB[i] = (u64 *)ctx->buf("lane_b" + std::to_string(i), lane_w * 8);
+        }
+        u64 *acc = (u64 *)ctx->buf("acc", lane_w * 8);
+        u64 *acc_new = (u64 *)ctx->buf("acc_new", lane_w * 8);
+
+        // ---- 1. combination
+        const std::vector<int> pid_l1 = iota(LS);
+        if (t == 1) {
+            u64 *Zc = (u64 *)ctx->buf("comb_z", (size_t)Fp * 2 * nl0 * N * 8);
+            kern::comb_const_mac(ctx, X, F, Fp, l0, pl->d_comb, Zc, nl0);
+            kern::rescale_coef(ctx, Zc, nl0, bufA[0], LS, Fp * 2, l0);
+            kern::LimbSet z{bufA[0], LS, LS, Fp * 2, pid_l1};
+            kern::ntt_fwd(ctx, z, z);
+        } else {
+            const std::vector<int> pid0 = iota(nl0);
+            u64 *Xn = (u64 *)ctx->buf("comb_xn", in_w * 8);
+            kern::LimbSet xs{const_cast<u64 *>(X), nl0, nl0, nb * 2, pid0}, xd{Xn, nl0, nl0, nb * 2, pid0};
+            kern::ntt_fwd(ctx, xs, xd);
+            u64 *Za = (u64 *)ctx->buf("comb_acc", (size_t)Fp * 2 * nl0 * N * 8);
+            CUDA_TRY(cudaMemsetAsync(Za, 0, (size_t)Fp * 2 * nl0 * N * 8, ctx->stream));
+            for (int b = 0; b < nb; b++) {
+                std::vector<kern::Dest> ds;
+                for (int j = 0; j < Fp; j++)
+                    ds.push_back({Za + (size_t)j * 2 * nl0 * N, pl->masks[pl->comb_masks[b][j]].d});
+                kern::stay_mac(ctx, Xn + (size_t)b * 2 * nl0 * N, nl0, 1, l0, ds, nl0);
+            }
+            kern::rescale_ntt(ctx, Za, nl0, Fp * 2, l0);
+            kern::copy_limbs(ctx, Za, nl0, bufA[0], LS, Fp * 2, LS);
+            u64 *digits = (u64 *)ctx->buf("digits", (size_t)Fp * ctx->n_digits(l1) * ctx->ext(l1) * N * 8);
+            u64 *tmp = acc_new;
+            for (int k : pl->comb_rots) {
+                kern::modup(ctx, bufA[0], LS, Fp, l1, digits);
+                kern::rotate_mac(ctx, keys->get(((k % M) + M) % M), bufA[0], LS, Fp, l1, digits,
+                                 {{tmp, nullptr}}, LS);
+                kern::add(ctx, bufA[0], tmp, bufA[0], Fp * 2 * LS, pid_l1);
+            }
+        }
+
+        // ---- 2. SpIntra-CA groups
+        std::vector<u64 *> *in = &bufA, *outb = &bufB;
+        bool have_acc = false;
+        int level = l1;
+        for (const GroupC &g : pl->groups) {
+            FG_CHECK(g.level == level, FG_ELEVEL, "plan level mismatch");
+            for (int x = 0; x < g.n_out; x++)
+                CUDA_TRY(cudaMemsetAsync((*outb)[x], 0, lane_w * 8, ctx->stream));
+            CUDA_TRY(cudaMemsetAsync(acc_new, 0, lane_w * 8, ctx->stream));
+            bool any_acc = false;
+            // destinations per (src, k)
+            std::map<std::pair<int, int>, std::vector<kern::Dest>> dests;
+            for (const TermC &tm : g.terms) {
+                u64 *o = tm.dst < 0 ? acc_new : (*outb)[tm.dst];
+                any_acc |= tm.dst < 0;
+                dests[{tm.src, tm.k}].push_back({o, pl->masks[tm.mask].d});
+            }
+            u64 *digits = (u64 *)ctx->buf("digits",
+                                          (size_t)Fp * ctx->n_digits(level) * ctx->ext(level) * N * 8);
+            int cur = -1;
+            for (auto &rk : g.rots) {
+                const int a = rk.first, k = rk.second;
+                if (a != cur) {
+                    kern::modup(ctx, (*in)[a], LS, Fp, level, digits);
+                    cur = a;
+                }
+                auto it = dests.find({a, k});
+                if (it == dests.end()) continue;
+                kern::rotate_mac(ctx, keys->get(((k % M) + M) % M), (*in)[a], LS, Fp, level, digits,
+                                 it->second, LS);
+            }
+            for (auto &kv : dests)
+                if (kv.first.second == 0)
+                    kern::stay_mac(ctx, (*in)[kv.first.first], LS, Fp, level, kv.second, LS);
+            for (int x = 0; x < g.n_out; x++) kern::rescale_ntt(ctx, (*outb)[x], LS, Fp * 2, level);
+            if (any_acc) {
+                kern::rescale_ntt(ctx, acc_new, LS, Fp * 2, level);
+                if (have_acc) {
+                    std::vector<int> pidx(LS, -1);
+                    for (int i = 0; i < level; i++) pidx[i] = i;
+                    kern::add(ctx, acc, acc_new, acc, Fp * 2 * LS, pidx);
+                } else {
+                    std::swap(acc, acc_new);
+                    have_acc = true;
+                }
+            }
+            std::swap(in, outb);
+            level--;
+        }
+        FG_CHECK(have_acc, FG_EINVAL, "the plan produced no output term");
+        FG_CHECK(level == pl->out_level, FG_ELEVEL, "plan output level mismatch");
+
+        // ---- 3. back to the coefficient domain, compact [Fp][2][level+1][N]
+        const int nlo = level + 1;
+        std::vector<int> pidx(LS, -1);
+        for (int i = 0; i < nlo; i++) pidx[i] = i;
+        kern::LimbSet as{acc, LS, LS, Fp * 2, pidx};
+        kern::ntt_inv(ctx, as, as);
+        const size_t out_w = (size_t)Fp * 2 * nlo * N;
+        u64 *o = is_dev(out_cts) ? out_cts : (u64 *)ctx->buf("layer_out", out_w * 8);
+        kern::copy_limbs(ctx, acc, LS, o, nlo, Fp * 2, nlo);
+        if (o != out_cts)
+            CUDA_TRY(cudaMemcpyAsync(out_cts, o, out_w * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        if (out_level) *out_level = level;
+        if (out_scale) *out_scale = ctx->scale;
+    } catch (const fg_error &e) {
+        ctx->err = e.what();
+        return e.code;
+    } catch (const std::exception &e) {
+        ctx->err = e.what();
+        return FG_EOOM;
+    }
+    return FG_OK;
+}
+
+}  // extern "C"

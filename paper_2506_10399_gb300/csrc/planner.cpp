@@ -1,0 +1,305 @@
+// planner.cpp -- host planner of one encrypted GCN layer (FicGCN).
+//
+//  * latency-aware packing (paper Sec. 3.2, App. B.1): t = 1 when M <= V F';
+//    otherwise the power of two t <= min(F, M/V) minimising
+//    J(t; F, n) = 2 ceil(F n / t) + 20 ceil(log2 t), ties to the smaller t;
+//  * combination constants round(W[f][j] q_l) (t = 1) or block-replicated W
+//    masks plus the log t rotate-and-sum amounts B 2^i (t > 1);
+//  * SpIntra-CA (Sec. 3.3): one token per edge v <- u (u != v) carrying
+//    node u's value from slot perm[u] to slot perm[v]; the shift is taken
+//    shortest-way round the ring (AOO, Sec. 3.3.2) and consumed r bits per
+//    group from the low end (radix 2^r groups merge consecutive bit steps
+//    into one rotation, the rotation merging of CPOO); in each group every
+//    (lane, signed digit amount) is one rotation, tokens whose shift runs
+//    out are removed into the accumulator with their weight A[v][u], the
+//    others are placed first-fit into output lanes (a slot holds one value
+//    per lane; a clash opens a new lane -- the paper's conflict; filling the
+//    lowest lane first merges sparse lanes, CPOO's ciphertext merging);
+//  * the self weights A[v][v] multiply the column ciphertext in group 0.
+// Every mask is applied at the group's level with scale q_level, so the
+// rescale that closes the group keeps the ciphertext scale at Delta.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <unordered_map>
+
+#include "fg_internal.h"
+
+namespace planner {
+
+static i64 packing_objective(i64 t, i64 F, i64 n)
+{
+    i64 pm = (F * n + t - 1) / t;
+    i64 lg = 0;
+    while ((1ll << lg) < t) lg++;
+    return 2 * pm + 20 * lg;
+}
+
+int choose_t(int F, int n, int V, int Fp, int M)
+{
+    if ((i64)M <= (i64)V * Fp) return 1;
+    int best = 1;
+    i64 bj = packing_objective(1, F, n);
+    for (int t = 2; t <= F && (i64)t * V <= M; t *= 2) {
+        i64 j = packing_objective(t, F, n);
+        if (j < bj) {
+            bj = j;
+            best = t;
+        }
+    }
+    return best;
+}
+
+static int shift_amount(int src, int dst, int M, bool aoo)
+{
+    int r = ((src - dst) % M + M) % M;
+    if (aoo && r > M / 2) r -= M;
+    return r;
+}
+
+static int bitlen(i64 x)
+{
+    int b = 0;
+    while (x) {
+        b++;
+        x >>= 1;
+    }
+    return b;
+}
+
+struct Token {
+    int u, lane, pos, rho, dest;
+    double w;
+};
+
+static void push_mask(fg_plan &pl, int level, std::vector<std::pair<int, double>> vals)
+{
+    std::sort(vals.begin(), vals.end());
+    MaskC m;
+    m.level = level;
+    for (auto &sv : vals)
+        if (sv.second != 0.0) {
+            m.slots.push_back(sv.first);
+            m.values.push_back(sv.second);
+        }
+    pl.masks.push_back(std::move(m));
+}
+
+void build(fg_plan &pl, const fg_ctx &ctx, const int32_t *row_ptr, const int32_t *col,
+           const double *val, int V, const double *W, int F, int Fp, const int32_t *perm,
+           const fg_plan_opts &o)
+{
+    const int M = ctx.slots;
+    FG_CHECK(V >= 1 && F >= 1 && Fp >= 1, FG_EINVAL, "empty layer");
+    FG_CHECK(row_ptr[0] == 0, FG_EINVAL, "row_ptr[0] must be 0");
+    for (int v = 0; v < V; v++)
+        FG_CHECK(row_ptr[v + 1] >= row_ptr[v], FG_EINVAL, "row_ptr must not decrease");
+    const i64 nnz = row_ptr[V];
+    for (i64 e = 0; e < nnz; e++)
+        FG_CHECK(col[e] >= 0 && col[e] < V && std::isfinite(val[e]), FG_EINVAL, "bad A entry");
+    for (i64 e = 0; e < (i64)F * Fp; e++) FG_CHECK(std::isfinite(W[e]), FG_EINVAL, "W not finite");
+
+    int n = o.n_sampled;
+    if (n <= 0) n = (int)std::llround((double)nnz / V);
+    int t = o.t > 0 ? o.t : choose_t(F, n, V, Fp, M);
+    FG_CHECK(t >= 1 && (t & (t - 1)) == 0 && t <= M, FG_EINVAL, "t must be a power of two");
+    const int B = M / t;
+    FG_CHECK((i64)V <= B, FG_EINVAL, "V nodes do not fit one block of M/t slots");
+    std::vector<char> seen(B, 0);
+    for (int v = 0; v < V; v++) {
+        FG_CHECK(perm[v] >= 0 && perm[v] < B && !seen[perm[v]], FG_EINVAL,
+                 "perm must be an injection of the nodes into [0, M/t)");
+        seen[perm[v]] = 1;
+    }
+    pl.N = ctx.n;
+    pl.M = M;
+    pl.t = t;
+    pl.B = B;
+    pl.V = V;
+    pl.F = F;
+    pl.Fp = Fp;
+    pl.in_level = ctx.nq - 1;
+    pl.aoo = o.aoo ? 1 : 0;
+    pl.perm.assign(perm, perm + V);
+
+    // ---- combination
+    const int l0 = pl.in_level;
+    FG_CHECK(l0 >= 1, FG_ELEVEL, "the combination needs one level");
+    if (t == 1) {
+        const double ql = (double)ctx.primes[l0];
+        pl.comb_consts.resize((size_t)F * Fp);
+        for (i64 e = 0; e < (i64)F * Fp; e++) {
+            double c = std::round(W[e] * ql);
+            FG_CHECK(std::fabs(c) < 9.2e18, FG_EINVAL, "weight too large for the scale");
+            pl.comb_consts[e] = (i64)c;
+        }
+    } else {
+        const int nb = (F + t - 1) / t;
+        pl.comb_masks.assign(nb, std::vector<int>(Fp));
+        for (int b = 0; b < nb; b++)
+            for (int j = 0; j < Fp; j++) {
+                std::vector<std::pair<int, double>> vals;
+                for (int k = 0; k < t; k++) {
+                    int f = b * t + k;
+                    if (f < F)
+                        for (int s = 0; s < B; s++) vals.push_back({k * B + s, W[(size_t)f * Fp + j]});
+                }
+                push_mask(pl, l0, std::move(vals));
+                pl.comb_masks[b][j] = (int)pl.masks.size() - 1;
+            }
+        for (int s = 1; s < t; s *= 2) pl.comb_rots.push_back(B * s);
+    }
+
+    // ---- tokens
+    std::vector<double> self_w(V, 0.0);
+    std::vector<Token> toks;
+    for (int v = 0; v < V; v++)
+        for (i64 e = row_ptr[v]; e < row_ptr[v + 1]; e++) {
+            int u = col[e];
+            if (u == v) {
+                self_w[v] += val[e];
+            } else {
+                int rho = shift_amount(perm[u], perm[v], M, pl.aoo);
+                toks.push_back({u, 0, perm[u], rho, perm[v], val[e]});
+            }
+        }
+    i64 max_abs = 0;
+    for (auto &tk : toks) max_abs = std::max<i64>(max_abs, std::llabs(tk.rho));
+    const int total_bits = bitlen(max_abs);
+    int level = l0 - 1;
+    const int budget = level - o.min_out_level;
+    int r = o.radix_bits;
+    if (r <= 0) {
+        r = 1;
+        while (std::max(1, (total_bits + r - 1) / r) > budget && r < 30) r++;
+    }
+    const int G = std::max(1, (total_bits + r - 1) / r);
+    FG_CHECK(level - G >= o.min_out_level && level - G >= 0, FG_ELEVEL,
+             "level budget exhausted: " + std::to_string(G) + " groups from level " +
+                 std::to_string(level));
+    pl.radix_bits = r;
+
+    int n_lanes = 1;
+    pl.max_lanes = 1;
+    for (int g = 0; g < G; g++) {
+        const int lo = g * r;
+        const int nb = std::max(0, std::min(r, total_bits - lo));
+        struct GT {
+            int src, k, dst;
+            std::vector<std::pair<int, double>> vals;
+        };
+        std::vector<GT> gterms;
+        if (g == 0) {
+            bool any = false;
+            for (double w : self_w) any |= (w != 0.0);
+            if (any) {
+                GT s{0, 0, -1, {}};
+                for (int v = 0; v < V; v++) s.vals.push_back({perm[v], self_w[v]});
+                gterms.push_back(std::move(s));
+            }
+        }
+        std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> arrive;
+        std::map<std::pair<int, int>, int> rot_set;   // (lane, k) -> 1
+        struct Item {
+            int lane, kmod, k, pos, u, tok;
+        };
+        std::vector<Item> items;
+        for (size_t ti = 0; ti < toks.size(); ti++) {
+            Token &tk = toks[ti];
+            int digit = nb > 0 ? (int)((std::abs(tk.rho) >> lo) & ((1 << nb) - 1)) : 0;
+            int k = (digit << lo) * (tk.rho > 0 ? 1 : -1);
+            int newpos = ((tk.pos - k) % M + M) % M;
+            if (k != 0) rot_set[{tk.lane, k}] = 1;
+            if (tk.rho - k == 0) {
+                FG_CHECK(newpos == tk.dest, FG_EINVAL, "planner: token missed its target");
+                arrive[{tk.lane, k}].push_back({tk.dest, tk.w});
+            } else {
+                items.push_back({tk.lane, ((k % M) + M) % M, k, newpos, tk.u, (int)ti});
+            }
+            tk.rho -= k;
+            tk.pos = newpos;
+        }
+        std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) {
+            if (a.lane != b.lane) return a.lane < b.lane;
+            if (a.kmod != b.kmod) return a.kmod < b.kmod;
+            return a.pos < b.pos;
+        });
+        std::vector<std::unordered_map<int, int>> out_slots;   // slot -> value id
+        std::map<std::tuple<int, int, int>, std::vector<int>> placed;  // (lane,k,x) -> slots
+        std::vector<int> new_lane(toks.size(), -1);
+        for (size_t a = 0; a < items.size();) {
+            size_t b = a;
+            while (b < items.size() && items[b].lane == items[a].lane && items[b].k == items[a].k &&
+                   items[b].pos == items[a].pos)
+                b++;
+            const Item &it = items[a];
+            int x = -1;
+            for (size_t l = 0; l < out_slots.size() && x < 0; l++) {
+                auto f = out_slots[l].find(it.pos);
+                if (f != out_slots[l].end() && f->second == it.u) x = (int)l;
+            }
+            if (x < 0) {
+                for (size_t l = 0; l < out_slots.size() && x < 0; l++)
+                    if (!out_slots[l].count(it.pos)) x = (int)l;
+                if (x < 0) {
+                    out_slots.emplace_back();
+                    x = (int)out_slots.size() - 1;
+                }
+                out_slots[x][it.pos] = it.u;
+                placed[{it.lane, it.k, x}].push_back(it.pos);
+            }
+            for (size_t c = a; c < b; c++) {
+                FG_CHECK(items[c].u == it.u, FG_EINVAL, "planner: two values share a lane slot");
+                new_lane[items[c].tok] = x;
+            }
+            a = b;
+        }
+        for (auto &pkv : placed) {
+            GT tm{std::get<0>(pkv.first), std::get<1>(pkv.first), std::get<2>(pkv.first), {}};
+            for (int s : pkv.second) tm.vals.push_back({s, 1.0});
+            gterms.push_back(std::move(tm));
+        }
+        for (auto &akv : arrive) {
+            GT tm{akv.first.first, akv.first.second, -1, akv.second};
+            gterms.push_back(std::move(tm));
+        }
+        std::sort(gterms.begin(), gterms.end(), [M](const GT &a, const GT &b) {
+            int ka = ((a.k % M) + M) % M, kb = ((b.k % M) + M) % M;
+            if (a.src != b.src) return a.src < b.src;
+            if (ka != kb) return ka < kb;
+            return a.dst < b.dst;
+        });
+        GroupC grp;
+        grp.bit_lo = lo;
+        grp.n_bits = nb;
+        grp.level = level;
+        grp.n_in = n_lanes;
+        grp.n_out = (int)out_slots.size();
+        for (auto &rk : rot_set) grp.rots.push_back(rk.first);
+        std::sort(grp.rots.begin(), grp.rots.end(),
+                  [M](const std::pair<int, int> &a, const std::pair<int, int> &b) {
+                      int ka = ((a.second % M) + M) % M, kb = ((b.second % M) + M) % M;
+                      return a.first != b.first ? a.first < b.first : ka < kb;
+                  });
+        for (auto &gt : gterms) {
+            push_mask(pl, level, std::move(gt.vals));
+            grp.terms.push_back({gt.src, gt.k, gt.dst, (int)pl.masks.size() - 1});
+        }
+        pl.groups.push_back(std::move(grp));
+        // advance: arrived tokens leave, the others take their new lane
+        std::vector<Token> nxt;
+        for (size_t ti = 0; ti < toks.size(); ti++)
+            if (toks[ti].rho != 0) {
+                toks[ti].lane = new_lane[ti];
+                nxt.push_back(toks[ti]);
+            }
+        toks.swap(nxt);
+        n_lanes = (int)out_slots.size();
+        pl.max_lanes = std::max(pl.max_lanes, n_lanes);
+        level--;
+    }
+    FG_CHECK(toks.empty(), FG_EINVAL, "planner: tokens left after the last group");
+    pl.out_level = level;
+}
+
+}  // namespace planner
