@@ -68,7 +68,8 @@ typedef struct fg_plan fg_plan;
  * Primes: for each bit size, in the order q_bits then p_bits, the largest
  * prime below 2^bits that is 1 mod 2N and not taken before.  alpha primes
  * form one key-switching digit (hybrid key switching).  10 <= log_n <= 16,
- * 1 <= n_q <= 60, 1 <= n_p <= 8, bit sizes in [log_n + 2, 61]. */
+ * 2 <= n_q <= 60, 1 <= n_p <= 8, bit sizes in [log_n + 2, 60], at most 16
+ * digits (ceil(n_q / alpha)). */
 typedef struct {
     int log_n;
     int n_q;
@@ -86,6 +87,7 @@ typedef struct {
  * RNS constants on the device.  FG_ENODEV without a device. */
 int fg_ctx_create(const fg_params *params, void *cuda_stream, fg_ctx **out);
 int fg_ctx_destroy(fg_ctx *ctx);
+/* ctx == NULL: the text of the last failed fg_ctx_create. */
 const char *fg_last_error(const fg_ctx *ctx);
 /* q_out: n_q primes, p_out: n_p primes (host arrays). */
 int fg_ctx_primes(const fg_ctx *ctx, uint64_t *q_out, uint64_t *p_out);

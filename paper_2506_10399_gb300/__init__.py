@@ -92,7 +92,7 @@ class Context:
         self._h = None
         rc = nat.lib.fg_ctx_create(ctypes.byref(prm), ctypes.c_void_p(stream or 0), ctypes.byref(h))
         if rc != 0:
-            raise FicgcnError(rc, "context creation failed")
+            raise FicgcnError(rc, "context creation failed: " + nat.lib.fg_last_error(None).decode())
         self._h = h
         q = np.zeros(self.nq, np.uint64)
         p = np.zeros(self.np, np.uint64)

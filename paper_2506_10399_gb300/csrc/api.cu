@@ -15,6 +15,7 @@
 namespace {
 
 constexpr int kMaxQ = 60, kMaxP = 8;
+std::string g_create_err = "no context";
 
 bool is_device_ptr(const void *p)
 {
@@ -370,7 +371,7 @@ int fg_ctx_create(const fg_params *prm, void *cuda_stream, fg_ctx **out)
         ctx->alpha = prm->alpha;
         ctx->log_scale = prm->log_scale;
         ctx->scale = std::ldexp(1.0, 0) * std::pow(2.0, prm->log_scale);
-        FG_CHECK(ctx->n_digits(ctx->L()) <= 8, FG_EINVAL, "more than 8 key-switching digits");
+        FG_CHECK(ctx->n_digits(ctx->L()) <= 16, FG_EINVAL, "more than 16 key-switching digits");
         std::vector<int> bits(prm->q_bits, prm->q_bits + prm->n_q);
         bits.insert(bits.end(), prm->p_bits, prm->p_bits + prm->n_p);
         ctx->primes = hm::gen_primes(ctx->log_n, bits);
@@ -430,9 +431,11 @@ int fg_ctx_create(const fg_params *prm, void *cuda_stream, fg_ctx **out)
         g_pidx_all[ctx] = dpi;
     } catch (const fg_error &e) {
         int code = e.code;
+        g_create_err = e.what();
         fg_ctx_destroy(ctx);
         return code;
-    } catch (const std::exception &) {
+    } catch (const std::exception &e) {
+        g_create_err = e.what();
         fg_ctx_destroy(ctx);
         return FG_EOOM;
     }
@@ -471,7 +474,7 @@ int fg_ctx_destroy(fg_ctx *ctx)
     return FG_OK;
 }
 
-const char *fg_last_error(const fg_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+const char *fg_last_error(const fg_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
 
 int fg_ctx_primes(const fg_ctx *ctx, uint64_t *q_out, uint64_t *p_out)
 {

@@ -53,7 +53,7 @@ std::vector<u64> gen_primes(int log_n, const std::vector<int> &bits)
     const u64 step = 2ull << log_n;   // primes must be 1 mod 2N
     std::vector<u64> out;
     for (int b : bits) {
-        FG_CHECK(b >= log_n + 2 && b <= 61, FG_EINVAL, "prime bit size out of range");
+        FG_CHECK(b >= log_n + 2 && b <= 60, FG_EINVAL, "prime bit size out of range");
         u64 c = (1ull << b) - step + 1;
         bool found = false;
         for (; c > step; c -= step) {

@@ -498,7 +498,7 @@ k_moddown_conv(const u64 *__restrict__ u, int E, u64 *conv, int nl,
 // ModUp output.  The key (Montgomery form, [beta_L][2][nq+np][N]) is read
 // once per (x, i) and reused for every column.
 // ------------------------------------------------------------------------
-constexpr int kMaxBeta = 8;
+constexpr int kMaxBeta = 16;   // beta * p^2 < p * 2^64 needs beta * p < 2^64: p < 2^60
 
 __global__ void __launch_bounds__(256)
 k_ks_ip(const u64 *__restrict__ key, int KL, const u64 *__restrict__ lane, int ls,
