@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of one encrypted GCN layer A-hat X W (FicGCN hot path) at N = 2^16.
+
+Workload (synthetic, seeded): power-law graph with 19,717 nodes and mean
+degree 4.5, X 19,717 x 500 TF-IDF-like (10% dense, row-normalised), W
+500 x 16 Glorot; CKKS N = 2^16, scale 2^45, 20 primes (60 + 19 x 45 bits),
+4 special primes, 5 key-switching digits; one layer = combination + rescale
++ radix-4 SpIntra-CA groups (output at level >= 10, leaving the levels a
+second layer needs), nodes at seeded random slots (no reordering).  One
+step = one call of fg_gcn_layer_axw on HBM-resident packed inputs (10.5 GB,
+larger than L2).
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload instead.  --profile runs one warm step
+and one step inside the NVTX range "fg_layer" (for ncu --nvtx-include
+fg_layer/) and prints nothing else; --features F shrinks the input width
+for small captures.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "pubmed_like"
+RADIX_BITS = 2
+MIN_OUT_LEVEL = 10
+SEED = 2025
+METRIC = "encrypted A.X.W layer latency (ms) at N=2^16"
+UNIT = "ms/layer"
+CLASSES = ["ntt", "ks_ip", "moddown_mac", "moddown_conv", "modup_conv", "comb", "rescale", "stay_mac"]
+
+
+def config_desc():
+    from paper_2506_10399_gb300 import workloads as wl
+    c = wl.CONFIGS[WORKLOAD]
+    return {"workload": "one encrypted GCN layer A.X.W, synthetic citation-graph-like (power law 2.5, "
+                        "V=19717, mean degree 4.5, F=500, F'=16), CKKS N=2^16, 20 primes 60+19x45 bit, "
+                        "K=4 special, dnum=5, radix-4 SpIntra-CA, seeded random node order (no NOO)",
+            "log_n": c["log_n"], "V": c["V"], "F": c["F"], "Fp": c["Fp"], "n_primes": len(c["q_bits"]),
+            "radix_bits": RADIX_BITS, "min_out_level": MIN_OUT_LEVEL,
+            "l2": "inputs larger than L2 (10.5 GB of packed ciphertexts), no flush needed"}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_for(cls):
+    """dram bytes per call of a kernel class from the committed ncu summary,
+    or None when absent or taken on a different version of the kernels."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            t = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2506_10399_gb300", "csrc", "kernels.cu"), "rb").read()
+        if t.get("kernels_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return t["per_call_bytes"].get(cls)
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.lines = index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(plan_counts, budget_s=25.0):
+    """Time the oracle on bounded pieces of the workload (one hoisted rotation
+    at level 14, one limb product, one const-MAC limb pass, all at N = 2^16)
+    and extrapolate to the whole layer with the plan's operation counts."""
+    import oracle
+    oracle.build()
+    from oracle import _ref, ckks
+    from paper_2506_10399_gb300 import workloads as wl
+    c = wl.CONFIGS[WORKLOAD]
+    P = ckks.Params(c["log_n"], c["q_bits"], c["p_bits"], c["alpha"], c["log_scale"])
+    rng = np.random.default_rng(0)
+    lvl = 14
+    ct = np.stack([np.stack([rng.integers(0, q, P.n, dtype=np.uint64) for q in P.q[:lvl + 1]])
+                   for _ in range(2)])
+    allp = P.q + P.p
+    beta_l = len(P.digits(P.L))
+    key = [(np.stack([rng.integers(0, q, P.n, dtype=np.uint64) for q in allp]),
+            np.stack([rng.integers(0, q, P.n, dtype=np.uint64) for q in allp])) for _ in range(beta_l)]
+    for q in allp:
+        P.psi(q)
+    t0 = time.perf_counter()
+    ckks.rotate(P, ct, 1, key)
+    t_rot = time.perf_counter() - t0
+    a = ct[0, 0]
+    t0 = time.perf_counter()
+    _ref.negacyclic_mul(a, ct[1, 0], P.q[0], P.psi(P.q[0]))
+    t_prod = time.perf_counter() - t0
+    acc = np.zeros(P.n, np.uint64)
+    t0 = time.perf_counter()
+    for _ in range(8):
+        _ref.mac_scalar(a, 12345, acc, P.q[0])
+    t_mac = (time.perf_counter() - t0) / 8
+    work_s = lambda lv: len(P.digits(lv)) * (lv + 1 + P.K)
+    est = 0.0
+    for (lv, nrot) in plan_counts["rotations_by_level"]:
+        est += nrot * t_rot * work_s(lv) / work_s(lvl)
+    for (lv, nprod) in plan_counts["products_by_level"]:
+        est += nprod * 2 * (lv + 1) * t_prod
+    est += plan_counts["comb_limb_macs"] * t_mac
+    return {"value": est * 1e3, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "oracle at N=2^16 on the host: one hoisted rotation at level 14 (%.2f s), one "
+                      "limb negacyclic product (%.3f s), one const-MAC limb pass (%.4f s); layer time "
+                      "extrapolated with the plan's rotation, product and MAC counts per level "
+                      "(rescales and additions not counted)" % (t_rot, t_prod, t_mac),
+            "seconds_sampled": t_rot + t_prod + 8 * t_mac}
+
+
+def oracle_plan_counts():
+    from oracle import ckks, planner
+    from paper_2506_10399_gb300 import workloads as wl
+    c = wl.CONFIGS[WORKLOAD]
+    P = ckks.Params(c["log_n"], c["q_bits"], c["p_bits"], c["alpha"], c["log_scale"])
+    w = wl.config_workload(WORKLOAD)
+    perm = wl.random_order(w.V, P.slots, SEED)
+    plan = planner.build_plan(P, P.L, w.row_ptr, w.col, w.val, w.V, w.W, perm, 1, RADIX_BITS, True,
+                              MIN_OUT_LEVEL)
+    rot = {}
+    prod = {}
+    for g in plan.groups:
+        rot[g.level] = rot.get(g.level, 0) + len(g.rotations) * plan.Fp
+        prod[g.level] = prod.get(g.level, 0) + len(g.terms) * plan.Fp
+    return {"rotations_by_level": sorted(rot.items()), "products_by_level": sorted(prod.items()),
+            "comb_limb_macs": plan.F * plan.Fp * 2 * (plan.in_level + 1),
+            "rotations": plan.rotation_count()}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    counts = oracle_plan_counts()
+    base = oracle_sample(counts)
+    line = {"impl": "reference", "metric": METRIC, "value": round(base["value"], 3), "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(base["value"], 3), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": config_desc(),
+            "cpu_baseline": {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": round(base["value"], 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    import __graft_entry__
+    fg = __graft_entry__.build()
+    from paper_2506_10399_gb300 import workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    c = wl.CONFIGS[WORKLOAD]
+    w = wl.config_workload(WORKLOAD, **({"F": args.features} if args.features else {}))
+    perm = wl.random_order(w.V, 1 << (c["log_n"] - 1), SEED)
+    t_setup = time.perf_counter()
+    ctx = fg.Context(**c)
+    plan = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=1, radix_bits=RADIX_BITS,
+                         min_out_level=MIN_OUT_LEVEL)
+    info = plan.info()
+    sk, evk = fg.keygen(ctx, SEED + rank, plan.rotation_amounts())
+    keys = fg.load_evk(ctx, evk)
+    del evk
+    F, Fp, N = info["n_in"], info["n_out"], ctx.n
+    in_dev = torch.empty((F, 2, ctx.nq, N), dtype=torch.int64, device="cuda")
+    fg.pack_features(ctx, sk, SEED + rank, w.X, perm, 1, out=in_dev)
+    out_dev = torch.empty((Fp, 2, info["out_level"] + 1, N), dtype=torch.int64, device="cuda")
+    setup_s = time.perf_counter() - t_setup
+
+    def step(src, dst):
+        return fg.gcn_layer_axw(ctx, keys, plan, src, out=dst)
+
+    if args.profile:
+        step(in_dev, out_dev)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("fg_layer")
+        step(in_dev, out_dev)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": True, "launches_per_layer": None, "rotations": info["rotations"],
+                          "n_groups": info["n_groups"], "n_masks": info["n_masks"]}))
+        return 0
+
+    # correctness of this very configuration: decrypted output vs FP64
+    _, lvl, scale = step(in_dev, out_dev)
+    torch.cuda.synchronize()
+    ref = w.reference_output()
+    err = 0.0
+    for j in (0, Fp - 1):
+        d = fg.decrypt_decode(ctx, sk, out_dev[j].contiguous(), lvl, scale)
+        err = max(err, float(np.max(np.abs(d[perm] - ref[:, j]))))
+
+    # warm-up
+    for _ in range(args.warmup):
+        step(in_dev, out_dev)
+    torch.cuda.synchronize()
+
+    # breakdown (untimed pass per kernel class) to pick the dominant kernel
+    breakdown = {}
+    for cls in CLASSES:
+        ctx.time_kernels(cls)
+        step(in_dev, out_dev)
+        ms, calls, by = ctx.kernel_times()
+        breakdown[cls] = {"ms": round(ms, 3), "calls": calls,
+                          "GB_per_s": round(by / ms / 1e6, 1) if ms > 0 else None}
+    ctx.time_kernels(None)
+    dominant = max(breakdown, key=lambda k: breakdown[k]["ms"])
+
+    # ---- timed region: K steps, HBM-resident inputs
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ctx.time_kernels(dominant)
+    n0 = ctx.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step(in_dev, out_dev)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    launches = ctx.launch_count() - n0
+    k_ms, k_calls, k_bytes = ctx.kernel_times()
+    ctx.time_kernels(None)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- end to end through the C ABI with host buffers (copies inside)
+    in_host = in_dev.cpu().pin_memory()
+    out_host = torch.empty(out_dev.shape, dtype=torch.int64).pin_memory()
+    step(in_host, out_host)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(in_host, out_host)
+        _ = int(out_host[0, 0, 0, 0])   # the result is on the host
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    h2d = in_host.numel() * 8
+    d2h = out_host.numel() * 8
+
+    peak, peak_kind = peaks()
+    achieved = k_bytes / (k_ms / 1e3) / 1e9 if k_ms > 0 else 0.0
+    traffic = traffic_for(dominant)
+    rotations = info["rotations"]
+    line = {
+        "metric": METRIC, "value": round(ms, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": config_desc(),
+        "rotations_per_layer": rotations,
+        "rotations_per_s": round(rotations * world / (ms / 1e3), 1),
+        "decrypt_max_abs_err_vs_fp64": err,
+        "out_level": lvl,
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1),
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "calls_timed": k_calls,
+                     "alg_bytes_per_call": round(k_bytes / max(1, k_calls))},
+        "breakdown_ms": breakdown,
+        "e2e": {"value": round(e2e_ms, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "setup_s": round(setup_s, 1),
+        "plan": {k: info[k] for k in ("n_groups", "n_masks", "n_keys", "masked_products", "out_level")},
+        "device_bytes": ctx.device_bytes(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        counts = oracle_plan_counts()
+        base = oracle_sample(counts)
+        line["cpu_baseline"] = {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true")
+    ap.add_argument("--features", type=int, default=0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -95,6 +95,20 @@ int fg_ctx_primes(const fg_ctx *ctx, uint64_t *q_out, uint64_t *p_out);
 int fg_ctx_device_bytes(const fg_ctx *ctx, size_t *bytes);
 void fg_free(void *blob);
 
+/* Instrumentation (no counterpart in the paper, which times on one CPU
+ * thread).  fg_ctx_time_kernels: from now on record a CUDA event pair on the
+ * context's stream around every call of one kernel class -- "ntt" (one call
+ * = the two kernels of a batched transform), "ks_ip", "moddown_conv",
+ * "moddown_mac", "modup_conv", "comb", "rescale", "stay_mac" -- with the
+ * call's algorithmic bytes (each operand read once, each result written
+ * once); NULL or "" stops.  Earlier records are dropped.
+ * fg_ctx_kernel_times: waits for the stream, returns the summed device time
+ * in ms, the number of calls and their algorithmic bytes, and clears the
+ * records.  fg_ctx_launch_count: kernels this context has launched so far. */
+int fg_ctx_time_kernels(fg_ctx *ctx, const char *kernel_class);
+int fg_ctx_kernel_times(fg_ctx *ctx, double *ms, int64_t *calls, double *alg_bytes);
+int fg_ctx_launch_count(const fg_ctx *ctx, int64_t *launches);
+
 /* ---------------------------------------------------------------- client */
 
 /* Secret key and rotation keys (paper Sec. 2.1: Rot needs a key per amount).

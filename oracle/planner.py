@@ -21,10 +21,17 @@ Readings the paper leaves open (the library implements the same):
   * bits are taken r at a time (radix 2^r): group g handles bits
     [g*r, g*r + r) of |shift|; one rotation per distinct signed digit
     amount; one mask product and one rescale per group;
-  * assignment: items (value u at new slot p) are visited in the order
-    (source lane, rotation amount mod M, new slot); an item joins the lowest
-    output lane that already holds u at p, else the lowest lane whose slot
-    p is free, else opens a new lane;
+  * in-flight reduction: moving tokens that reach the same slot on the way
+    to the same destination are summed from then on -- each multiplied by
+    its edge weight in that step's mask -- and travel as one carrier with
+    weight 1 (an extension of the paper's removal-on-arrival: the sum is
+    formed earlier, so converging neighbours of a hub need no extra lanes);
+  * assignment: unchanged tokens are grouped into items (one source slot and
+    rotation, one new slot) visited in the order (source lane, rotation
+    amount mod M, new slot), then the new carriers in the order (new slot,
+    destination); an item joins the lowest output lane that already holds
+    its content at that slot, else the lowest lane whose slot is free, else
+    opens a new lane (the conflict);
   * every mask is encoded at scale q_l, l the level of the group, so the
     rescale that ends the group returns the ciphertext scale to Delta.
 
@@ -163,7 +170,7 @@ def build_plan(params, in_level, row_ptr, col, val, V, W, perm, t,
 
     # --- tokens: one per edge v <- u, u != v
     self_w = np.zeros(V)
-    toks = []   # [u, lane, pos, rho, dest, w]
+    toks = []   # [content, lane, pos, rho, dest, w]; content u >= 0 is node u's value
     for v in range(V):
         for e in range(row_ptr[v], row_ptr[v + 1]):
             u = int(col[e])
@@ -181,77 +188,90 @@ def build_plan(params, in_level, row_ptr, col, val, V, W, perm, t,
         raise ValueError("level budget exhausted: %d groups from level %d" % (G, level))
 
     n_lanes = 1
+    n_carriers = 0
     for g in range(G):
         lo = g * radix_bits
         nb = max(0, min(radix_bits, total_bits - lo))
-        gterms = []      # [(src, k, dst, slot values)]
+        gterms = {}      # (src lane, k, dst) -> {slot: mask value}
         if g == 0 and np.any(self_w != 0):
-            vals = np.zeros(M)
-            vals[perm] = self_w
-            gterms.append((0, 0, ACC, vals))
+            gterms[(0, 0, ACC)] = {int(perm[v]): float(self_w[v]) for v in range(V) if self_w[v] != 0}
         # step of every token in this group
-        arrive = {}      # (lane, k) -> {dest slot: weight}
-        items = {}       # (lane, k, newpos) -> [value u, [token indices]]
         rots = set()
-        for ti, tk in enumerate(toks):
-            u, lane, pos, rho, dest, w = tk
+        moving = []      # (token, k, new slot)
+        for tk in toks:
+            content, lane, pos, rho, dest, w = tk
             digit = (abs(rho) >> lo) & ((1 << nb) - 1) if nb > 0 else 0
             k = (digit << lo) * (1 if rho > 0 else -1)
             newpos = (pos - k) % M
             if k != 0:
                 rots.add((lane, k))
-            if rho - k == 0:
-                d = arrive.setdefault((lane, k), {})
+            if rho - k == 0:                       # arrival: removed into the accumulator
+                d = gterms.setdefault((lane, k, ACC), {})
                 assert newpos == dest and dest not in d
                 d[dest] = w
             else:
-                it = items.setdefault((lane, k, newpos), [u, []])
-                assert it[0] == u
-                it[1].append(ti)
-            tk[3] = rho - k
-            tk[2] = newpos
-        # lane assignment, first fit
-        out_slots = []           # per output lane: {slot: u}
-        placed = {}              # (src lane, k, out lane) -> [slots]
-        new_lane_of = {}
-        for key in sorted(items, key=lambda x: (x[0], x[1] % M, x[2])):
-            lane, k, p = key
-            u, tis = items[key]
-            x = next((i for i, sl in enumerate(out_slots) if sl.get(p) == u), None)
+                moving.append((tk, k, newpos))
+        # tokens meeting at one slot on the way to one destination are summed
+        # from here on (each weighted by its own edge weight in this step's mask)
+        by_pd = {}
+        for m in moving:
+            by_pd.setdefault((m[2], m[0][4]), []).append(m)
+        items = {}       # (lane, k, new slot) -> tokens carried unchanged
+        merged = []
+        for (p, d), ms in by_pd.items():
+            if len(ms) >= 2:
+                merged.append((p, d, ms))
+            else:
+                tk, k, _ = ms[0]
+                items.setdefault((tk[1], k, p), []).append(tk)
+        out_slots = []   # per output lane: {slot: content}
+        nxt = []
+
+        def place(p, content):
+            x = next((i for i, sl in enumerate(out_slots) if sl.get(p) == content), None)
+            if x is not None:
+                return x, True
+            x = next((i for i, sl in enumerate(out_slots) if p not in sl), None)
             if x is None:
-                x = next((i for i, sl in enumerate(out_slots) if p not in sl), None)
-                if x is None:
-                    out_slots.append({})
-                    x = len(out_slots) - 1
-                out_slots[x][p] = u
-                placed.setdefault((lane, k, x), []).append(p)
-            for ti in tis:
-                new_lane_of[ti] = x
-        for (lane, k, x), slots in placed.items():
-            vals = np.zeros(M)
-            vals[slots] = 1.0
-            gterms.append((lane, k, x, vals))
-        for (lane, k), dests in arrive.items():
-            vals = np.zeros(M)
-            for d, w in dests.items():
-                vals[d] = w
-            gterms.append((lane, k, ACC, vals))
+                out_slots.append({})
+                x = len(out_slots) - 1
+            out_slots[x][p] = content
+            return x, False
+
+        for key in sorted(items, key=lambda z: (z[0], z[1] % M, z[2])):
+            lane, k, p = key
+            tks = items[key]
+            content = tks[0][0]
+            assert all(t[0] == content for t in tks)
+            x, joined = place(p, content)
+            if not joined:
+                gterms.setdefault((lane, k, x), {})[p] = 1.0
+            for t in tks:
+                nxt.append([content, x, p, t[3] - k, t[4], t[5]])
+        for (p, d, ms) in sorted(merged, key=lambda z: (z[0], z[1])):
+            n_carriers += 1
+            content = -n_carriers
+            x, joined = place(p, content)
+            assert not joined
+            for (tk, k, _) in ms:
+                entry = gterms.setdefault((tk[1], k, x), {})
+                assert p not in entry
+                entry[p] = tk[5]
+            rho2 = ms[0][0][3] - ms[0][1]
+            assert all(t[3] - kk == rho2 for (t, kk, _) in ms)
+            nxt.append([content, x, p, rho2, d, 1.0])
         # canonical order of the terms; masks numbered in that order
-        gterms.sort(key=lambda x: (x[0], x[1] % M, x[2]))
         terms = []
-        for (src, k, dst, vals) in gterms:
+        for (src, k, dst) in sorted(gterms, key=lambda z: (z[0], z[1] % M, z[2])):
+            vals = np.zeros(M)
+            for sl, v in gterms[(src, k, dst)].items():
+                vals[sl] = v
             plan.masks.append(Mask(level=level, values=vals))
             terms.append(Term(src, k, dst, len(plan.masks) - 1))
         plan.groups.append(Group(bit_lo=lo, n_bits=nb, level=level, n_in=n_lanes,
                                  n_out=len(out_slots),
                                  rotations=sorted(rots, key=lambda r: (r[0], r[1] % M)),
                                  terms=terms))
-        # advance: arrived tokens leave, the others take their new lane
-        nxt = []
-        for ti, tk in enumerate(toks):
-            if tk[3] != 0:
-                tk[1] = new_lane_of[ti]
-                nxt.append(tk)
         toks = nxt
         n_lanes = len(out_slots)
         level -= 1

@@ -105,6 +105,23 @@ class Context:
         _check(self, _lib().lib.fg_ctx_device_bytes(self._h, ctypes.byref(b)))
         return b.value
 
+    def time_kernels(self, kernel_class):
+        """Start CUDA-event timing of one kernel class (None stops)."""
+        _check(self, _lib().lib.fg_ctx_time_kernels(
+            self._h, kernel_class.encode() if kernel_class else None))
+
+    def kernel_times(self):
+        """(device ms, calls, algorithmic bytes) of the timed class since the last read."""
+        ms, n, by = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        _check(self, _lib().lib.fg_ctx_kernel_times(self._h, ctypes.byref(ms), ctypes.byref(n),
+                                                    ctypes.byref(by)))
+        return ms.value, n.value, by.value
+
+    def launch_count(self):
+        n = ctypes.c_int64()
+        _check(self, _lib().lib.fg_ctx_launch_count(self._h, ctypes.byref(n)))
+        return n.value
+
     def close(self):
         if self._h is not None:
             _lib().lib.fg_ctx_destroy(self._h)

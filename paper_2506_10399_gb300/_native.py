@@ -43,6 +43,9 @@ SIGS = {
     "fg_ctx_primes": (c_int, [c_void_p, c_void_p, c_void_p]),
     "fg_ctx_device_bytes": (c_int, [c_void_p, P(c_size)]),
     "fg_free": (None, [c_void_p]),
+    "fg_ctx_time_kernels": (c_int, [c_void_p, ctypes.c_char_p]),
+    "fg_ctx_kernel_times": (c_int, [c_void_p, P(c_double), P(ctypes.c_int64), P(c_double)]),
+    "fg_ctx_launch_count": (c_int, [c_void_p, P(ctypes.c_int64)]),
     "fg_keygen": (c_int, [c_void_p, c_u64, P(ctypes.c_int32), c_int, P(c_void_p), P(c_size),
                           P(c_void_p), P(c_size)]),
     "fg_encode_plain": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p]),

@@ -122,6 +122,16 @@ void *fg_ctx::buf(const std::string &name, size_t bytes)
     return p;
 }
 
+cudaEvent_t fg_ctx::event()
+{
+    if (ev_next == ev_pool.size()) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreate(&e));
+        ev_pool.push_back(e);
+    }
+    return ev_pool[ev_next++];
+}
+
 static ConvTab make_conv(const fg_ctx &c, const std::vector<int> &in_p, const std::vector<int> &in_l,
                          const std::vector<int> &out_p, const std::vector<int> &out_l)
 {
@@ -455,6 +465,7 @@ int fg_ctx_destroy(fg_ctx *ctx)
     for (auto &kv : ctx->rescale_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->pinv_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->ws) cudaFree(kv.second.first);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     auto s = g_sk.find(ctx);
     if (s != g_sk.end()) {
         cudaFree(s->second.d);
@@ -494,6 +505,44 @@ int fg_ctx_device_bytes(const fg_ctx *ctx, size_t *bytes)
 }
 
 void fg_free(void *blob) { free(blob); }
+
+int fg_ctx_time_kernels(fg_ctx *ctx, const char *kernel_class)
+{
+    if (!ctx) return FG_EINVAL;
+    API_TRY
+    sync(ctx);
+    ctx->time_class = kernel_class ? kernel_class : "";
+    ctx->timed.clear();
+    ctx->ev_next = 0;
+    API_CATCH(ctx)
+}
+
+int fg_ctx_kernel_times(fg_ctx *ctx, double *ms, int64_t *calls, double *alg_bytes)
+{
+    if (!ctx || !ms || !calls || !alg_bytes) return FG_EINVAL;
+    API_TRY
+    sync(ctx);
+    double t = 0, b = 0;
+    for (auto &r : ctx->timed) {
+        float e = 0;
+        CUDA_TRY(cudaEventElapsedTime(&e, r.a, r.b));
+        t += e;
+        b += r.bytes;
+    }
+    *ms = t;
+    *calls = (int64_t)ctx->timed.size();
+    *alg_bytes = b;
+    ctx->timed.clear();
+    ctx->ev_next = 0;
+    API_CATCH(ctx)
+}
+
+int fg_ctx_launch_count(const fg_ctx *ctx, int64_t *launches)
+{
+    if (!ctx || !launches) return FG_EINVAL;
+    *launches = ctx->launches;
+    return FG_OK;
+}
 
 // ---------------------------------------------------------------- client side
 int fg_keygen(fg_ctx *ctx, uint64_t seed, const int32_t *rot_amounts, int n_rot, void **sk_blob,

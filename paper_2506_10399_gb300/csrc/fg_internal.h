@@ -104,6 +104,19 @@ struct fg_ctx {
     std::map<int, u64 *> rescale_tabs;   // level -> [level][2] q_l^-1 mod q_i + Shoup
     std::map<int, u64 *> pinv_tabs;      // level -> [level+1][2] P^-1 mod q_i + Shoup
 
+    // instrumentation: kernel launch count, and CUDA-event timing of every
+    // launch of one kernel class with its algorithmic bytes
+    int64_t launches = 0;
+    std::string time_class;
+    struct Timed {
+        cudaEvent_t a, b;
+        double bytes;
+    };
+    std::vector<Timed> timed;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_next = 0;
+    cudaEvent_t event();
+
     // workspace (grow-only arena of named device buffers)
     std::map<std::string, std::pair<void *, size_t>> ws;
     size_t table_bytes = 0;
@@ -164,6 +177,15 @@ struct fg_plan {
 
 // ------------------------------------------------------------------ kernels
 namespace kern {
+// CUDA events around the launches of one kernel class when the context times it
+struct KTimer {
+    fg_ctx *ctx;
+    bool on;
+    cudaEvent_t a = nullptr;
+    double bytes;
+    KTimer(fg_ctx *c, const char *cls, double alg_bytes);
+    ~KTimer();
+};
 // rows x per_row limbs: limb (r, c) at base + (r * stride + c) * N, reduced
 // modulo prime pidx[c] (pidx[c] < 0: the limb is left alone)
 struct LimbSet {

@@ -40,10 +40,13 @@ Batch make_batch(u64 *src, int src_stride, u64 *dst, int dst_stride, int per_row
     return b;
 }
 
-inline void check_launch(const char *what)
+fg_ctx *g_launch_ctx = nullptr;   // context of the wrapper being run (for launch counting)
+
+inline void check_launch(const char *what, int kernels = 1)
 {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw fg_error(FG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    if (g_launch_ctx) g_launch_ctx->launches += kernels;
 }
 
 // ------------------------------------------------------------------------
@@ -622,6 +625,25 @@ k_stay_mac(const u64 *__restrict__ lane, int ls, int ncol, int level, const Dest
 // ========================================================================
 namespace kern {
 
+KTimer::KTimer(fg_ctx *c, const char *cls, double alg_bytes) : ctx(c), bytes(alg_bytes)
+{
+    g_launch_ctx = c;
+    on = !c->time_class.empty() && c->time_class == cls;
+    if (on) {
+        a = c->event();
+        cudaEventRecord(a, c->stream);
+    }
+}
+
+KTimer::~KTimer()
+{
+    if (on) {
+        cudaEvent_t b = ctx->event();
+        cudaEventRecord(b, ctx->stream);
+        ctx->timed.push_back({a, b, bytes});
+    }
+}
+
 static inline int s1_of(int log_n) { return log_n / 2; }
 
 static void launch_ntt(fg_ctx *ctx, const LimbSet &src, const LimbSet &dst, bool inverse)
@@ -640,6 +662,9 @@ static void launch_ntt(fg_ctx *ctx, const LimbSet &src, const LimbSet &dst, bool
     const auto *inv = (const ulonglong2 *)ctx->d_inv;
     FG_CHECK(count <= 65535, FG_EINVAL, "ntt: more than 65535 limbs in one batch");
     dim3 gA(N2 / kColsA, count), gB(N1 / R, count);
+    int active = 0;
+    for (int v : src.pidx) active += v >= 0;
+    KTimer kt(ctx, "ntt", (double)active * src.rows * N * 8 * 2);
     if (!inverse) {
         ntt_fwd_a<<<gA, kNttThreads, smA, ctx->stream>>>(bt, ctx->d_primes, fwd, log_n, s1);
         Batch b2 = bt;
@@ -654,7 +679,7 @@ static void launch_ntt(fg_ctx *ctx, const LimbSet &src, const LimbSet &dst, bool
         ntt_inv_a<<<gA, kNttThreads, smA, ctx->stream>>>(b2, ctx->d_primes, inv, ctx->d_ninv,
                                                          log_n, s1);
     }
-    check_launch("ntt");
+    check_launch("ntt", 2);
 }
 
 void ntt_fwd(fg_ctx *ctx, const LimbSet &src, const LimbSet &dst) { launch_ntt(ctx, src, dst, false); }
@@ -671,6 +696,7 @@ static Batch contiguous(u64 *p, int count, const std::vector<int> &pidx)
 void to_mont(fg_ctx *ctx, u64 *data, int count, const std::vector<int> &pidx)
 {
     if (!count) return;
+    KTimer kt(ctx, "to_mont", 0);
     k_to_mont<<<ew_grid(ctx->n, count), 256, 0, ctx->stream>>>(contiguous(data, count, pidx),
                                                                ctx->d_primes, ctx->n);
     check_launch("to_mont");
@@ -679,6 +705,7 @@ void to_mont(fg_ctx *ctx, u64 *data, int count, const std::vector<int> &pidx)
 void from_mont(fg_ctx *ctx, u64 *data, int count, const std::vector<int> &pidx)
 {
     if (!count) return;
+    KTimer kt(ctx, "from_mont", 0);
     k_from_mont<<<ew_grid(ctx->n, count), 256, 0, ctx->stream>>>(contiguous(data, count, pidx),
                                                                  ctx->d_primes, ctx->n);
     check_launch("from_mont");
@@ -688,6 +715,7 @@ void pointwise(fg_ctx *ctx, const u64 *a, const u64 *b, u64 *c, int count,
                const std::vector<int> &pidx)
 {
     if (!count) return;
+    KTimer kt(ctx, "pointwise", 0);
     k_pointwise<<<ew_grid(ctx->n, count), 256, 0, ctx->stream>>>(
         a, b, c, contiguous(c, count, pidx), ctx->d_primes, ctx->n);
     check_launch("pointwise");
@@ -696,6 +724,7 @@ void pointwise(fg_ctx *ctx, const u64 *a, const u64 *b, u64 *c, int count,
 void add(fg_ctx *ctx, const u64 *a, const u64 *b, u64 *c, int count, const std::vector<int> &pidx)
 {
     if (!count) return;
+    KTimer kt(ctx, "add", 0);
     k_add<<<ew_grid(ctx->n, count), 256, 0, ctx->stream>>>(a, b, c, contiguous(c, count, pidx),
                                                            ctx->d_primes, ctx->n);
     check_launch("add");
@@ -704,6 +733,7 @@ void add(fg_ctx *ctx, const u64 *a, const u64 *b, u64 *c, int count, const std::
 void neg(fg_ctx *ctx, const u64 *a, u64 *c, int count, const std::vector<int> &pidx)
 {
     if (!count) return;
+    KTimer kt(ctx, "neg", 0);
     k_neg<<<ew_grid(ctx->n, count), 256, 0, ctx->stream>>>(a, c, contiguous(c, count, pidx),
                                                            ctx->d_primes, ctx->n);
     check_launch("neg");
@@ -713,6 +743,7 @@ void scalar(fg_ctx *ctx, const u64 *a, u64 *c, int count, const std::vector<int>
             const u64 *d_scal)
 {
     if (!count) return;
+    KTimer kt(ctx, "scalar", 0);
     k_scalar<<<ew_grid(ctx->n, count), 256, 0, ctx->stream>>>(
         a, c, contiguous(c, count, pidx), ctx->d_primes, d_scal, ctx->n);
     check_launch("scalar");
@@ -721,12 +752,14 @@ void scalar(fg_ctx *ctx, const u64 *a, u64 *c, int count, const std::vector<int>
 void automorphism(fg_ctx *ctx, const u64 *a, u64 *c, int nlimbs, uint32_t g)
 {
     if (!nlimbs) return;
+    KTimer kt(ctx, "automorphism", 0);
     k_automorphism<<<ew_grid(ctx->n, nlimbs), 256, 0, ctx->stream>>>(a, c, nlimbs, g, ctx->log_n);
     check_launch("automorphism");
 }
 
 void small_to_res(fg_ctx *ctx, const int8_t *e, u64 *out, int n_limbs, const int *d_pidx)
 {
+    KTimer kt(ctx, "small_to_res", 0);
     k_small_to_res<<<ew_grid(ctx->n, n_limbs), 256, 0, ctx->stream>>>(e, out, d_pidx,
                                                                       ctx->d_primes, ctx->n);
     check_launch("small_to_res");
@@ -735,6 +768,7 @@ void small_to_res(fg_ctx *ctx, const int8_t *e, u64 *out, int n_limbs, const int
 void copy_limbs(fg_ctx *ctx, const u64 *src, int src_ls, u64 *dst, int dst_ls, int npoly, int nl)
 {
     if (!npoly || !nl) return;
+    KTimer kt(ctx, "copy", (double)npoly * nl * ctx->n * 16);
     dim3 g((ctx->n + 255) / 256, nl, npoly);
     k_copy_limbs<<<g, 256, 0, ctx->stream>>>(src, src_ls, dst, dst_ls, nl, ctx->n);
     check_launch("copy_limbs");
@@ -744,6 +778,8 @@ void comb_const_mac(fg_ctx *ctx, const u64 *X, int F, int Fp, int level, const u
                     int z_ls)
 {
     for (int j0 = 0; j0 < Fp; j0 += kCombJ) {
+        const int jn = std::min(kCombJ, Fp - j0);
+        KTimer kt(ctx, "comb", ((double)F + jn) * 2 * (level + 1) * ctx->n * 8);
         dim3 g((ctx->n + 255) / 256, level + 1, 2);
         k_comb<<<g, 256, 0, ctx->stream>>>(X, F, Fp, j0, level, consts, Z, z_ls, ctx->d_primes,
                                            ctx->n);
@@ -754,6 +790,7 @@ void comb_const_mac(fg_ctx *ctx, const u64 *X, int F, int Fp, int level, const u
 void rescale_coef(fg_ctx *ctx, const u64 *in, int in_ls, u64 *out, int out_ls, int npoly, int level)
 {
     FG_CHECK(level >= 1, FG_ELEVEL, "rescale needs level >= 1");
+    KTimer kt(ctx, "rescale", (double)npoly * (2 * level + 1) * ctx->n * 8);
     dim3 g((ctx->n + 255) / 256, level, npoly);
     k_rescale_coef<<<g, 256, 0, ctx->stream>>>(in, in_ls, out, out_ls, level, ctx->d_primes,
                                                ctx->rescale_tab(level), ctx->n);
@@ -771,12 +808,16 @@ void rescale_ntt(fg_ctx *ctx, u64 *ct, int ls, int npoly, int level)
     ntt_inv(ctx, s, s);
     u64 *rr = (u64 *)ctx->buf("rescale_r", (size_t)npoly * level * N * 8);
     dim3 g((N + 255) / 256, level, npoly);
-    k_bcast_reduce<<<g, 256, 0, ctx->stream>>>(ct, ls, level, rr, level, ctx->d_primes, N);
-    check_launch("bcast_reduce");
+    {
+        KTimer kt(ctx, "rescale", (double)npoly * (level + 1) * N * 8);
+        k_bcast_reduce<<<g, 256, 0, ctx->stream>>>(ct, ls, level, rr, level, ctx->d_primes, N);
+        check_launch("bcast_reduce");
+    }
     std::vector<int> pid(level);
     for (int i = 0; i < level; i++) pid[i] = i;
     LimbSet r{rr, level, level, npoly, pid};
     ntt_fwd(ctx, r, r);
+    KTimer kt(ctx, "rescale", (double)npoly * level * N * 8 * 3);
     k_rescale_finish<<<g, 256, 0, ctx->stream>>>(ct, ls, rr, level, ctx->d_primes,
                                                  ctx->rescale_tab(level), N);
     check_launch("rescale_finish");
@@ -792,9 +833,12 @@ void modup(fg_ctx *ctx, const u64 *lane, int ls, int ncol, int level, u64 *digit
     LimbSet dst{c1c, nl, nl, ncol, pid};
     ntt_inv(ctx, src, dst);
     dim3 g((N + 255) / 256, 1, ncol * beta);
+    {
+    KTimer kt(ctx, "modup_conv", (double)ncol * (nl + (double)beta * E - nl) * N * 8);
     k_modup_conv<<<g, 256, 0, ctx->stream>>>(c1c, nl, digits, beta, E, ctx->modup_tabs(level),
                                              ctx->d_primes, N);
     check_launch("modup_conv");
+    }
     std::vector<int> dp(beta * E);
     for (int d = 0; d < beta; d++)
         for (int i = 0; i < E; i++)
@@ -811,19 +855,25 @@ void rotate_mac(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int nco
     const int KL = ctx->nq + ctx->np;
     u64 *u = (u64 *)ctx->buf("ks_u", (size_t)ncol * 2 * E * N * 8);
     dim3 g1((N + 255) / 256, E);
+    {
+    KTimer kt(ctx, "ks_ip", ((double)ncol * beta * E + 2.0 * beta * E + 2.0 * ncol * E) * N * 8);
     k_ks_ip<<<g1, 256, 0, ctx->stream>>>(key.d, KL, lane, ls, digits, ncol, level, beta, E,
                                          ctx->alpha, ctx->nq, key.galois, ctx->log_n, u,
                                          ctx->d_primes);
     check_launch("ks_ip");
+    }
     std::vector<int> pp(E);
     for (int i = 0; i < E; i++) pp[i] = i <= level ? -1 : ctx->ext_prime(level, i);
     LimbSet us{u, E, E, 2 * ncol, pp};
     ntt_inv(ctx, us, us);
     u64 *conv = (u64 *)ctx->buf("ks_conv", (size_t)ncol * 2 * nl * N * 8);
     dim3 g2((N + 255) / 256, 2 * ncol);
+    {
+    KTimer kt(ctx, "moddown_conv", (double)2 * ncol * (ctx->np + nl) * N * 8);
     k_moddown_conv<<<g2, 256, 0, ctx->stream>>>(u, E, conv, nl, ctx->moddown_tab(level),
                                                 ctx->d_primes, N);
     check_launch("moddown_conv");
+    }
     std::vector<int> pq(nl);
     for (int i = 0; i < nl; i++) pq[i] = i;
     LimbSet cs{conv, nl, nl, 2 * ncol, pq};
@@ -837,6 +887,11 @@ void rotate_mac(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int nco
             dl.mask[d] = dests[d0 + d].mask;
         }
         dim3 g3((N + 255) / 256, nl);
+        int masked = 0;
+        for (int d = 0; d < dl.n; d++) masked += dl.mask[d] != nullptr;
+        KTimer kt(ctx, "moddown_mac",
+                  ((double)5 * ncol * nl + (double)masked * nl +
+                   (double)masked * ncol * 2 * nl * 2 + (double)(dl.n - masked) * ncol * 2 * nl) * N * 8);
         k_moddown_finish_mac<<<g3, 256, 0, ctx->stream>>>(u, E, conv, lane, ls, ncol, level,
                                                           key.galois, ctx->log_n,
                                                           ctx->pinv_tab(level), dl, ctx->d_primes);
@@ -858,6 +913,9 @@ void stay_mac(fg_ctx *ctx, const u64 *lane, int ls, int ncol, int level,
             dl.mask[d] = dests[d0 + d].mask;
         }
         dim3 g((N + 255) / 256, level + 1);
+        const int nl = level + 1;
+        KTimer kt(ctx, "stay_mac", ((double)2 * ncol * nl + (double)dl.n * nl +
+                                     (double)dl.n * ncol * 2 * nl * 2) * N * 8);
         k_stay_mac<<<g, 256, 0, ctx->stream>>>(lane, ls, ncol, level, dl, ctx->d_primes, N);
         check_launch("stay_mac");
     }

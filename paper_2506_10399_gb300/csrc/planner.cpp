@@ -11,10 +11,13 @@
 //    group from the low end (radix 2^r groups merge consecutive bit steps
 //    into one rotation, the rotation merging of CPOO); in each group every
 //    (lane, signed digit amount) is one rotation, tokens whose shift runs
-//    out are removed into the accumulator with their weight A[v][u], the
-//    others are placed first-fit into output lanes (a slot holds one value
-//    per lane; a clash opens a new lane -- the paper's conflict; filling the
-//    lowest lane first merges sparse lanes, CPOO's ciphertext merging);
+//    out are removed into the accumulator with their weight A[v][u], moving
+//    tokens that meet at one slot on the way to one destination are summed
+//    from then on (each weighted in that step's mask; an extension of the
+//    removal rule that keeps hubs' converging neighbours in one lane), and
+//    the rest are placed first-fit into output lanes (a slot holds one
+//    value per lane; a clash opens a new lane -- the paper's conflict;
+//    filling the lowest lane first merges sparse lanes, CPOO's merging);
 //  * the self weights A[v][v] multiply the column ciphertext in group 0.
 // Every mask is applied at the group's level with scale q_level, so the
 // rescale that closes the group keeps the ciphertext scale at Delta.
@@ -181,94 +184,107 @@ void build(fg_plan &pl, const fg_ctx &ctx, const int32_t *row_ptr, const int32_t
 
     int n_lanes = 1;
     pl.max_lanes = 1;
+    int n_carriers = 0;
     for (int g = 0; g < G; g++) {
         const int lo = g * r;
         const int nb = std::max(0, std::min(r, total_bits - lo));
-        struct GT {
-            int src, k, dst;
-            std::vector<std::pair<int, double>> vals;
-        };
-        std::vector<GT> gterms;
+        // (src lane, k, dst) -> slot -> mask value; dst -1 = accumulator
+        std::map<std::tuple<int, int, int>, std::map<int, double>> gterms;
         if (g == 0) {
-            bool any = false;
-            for (double w : self_w) any |= (w != 0.0);
-            if (any) {
-                GT s{0, 0, -1, {}};
-                for (int v = 0; v < V; v++) s.vals.push_back({perm[v], self_w[v]});
-                gterms.push_back(std::move(s));
-            }
+            std::map<int, double> sv;
+            for (int v = 0; v < V; v++)
+                if (self_w[v] != 0.0) sv[perm[v]] = self_w[v];
+            if (!sv.empty()) gterms[std::make_tuple(0, 0, -1)] = sv;
         }
-        std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> arrive;
-        std::map<std::pair<int, int>, int> rot_set;   // (lane, k) -> 1
-        struct Item {
-            int lane, kmod, k, pos, u, tok;
+        std::map<std::pair<int, int>, int> rot_set;   // (lane, k)
+        struct Move {
+            int tok, k, pos;
         };
-        std::vector<Item> items;
+        std::vector<Move> moving;
         for (size_t ti = 0; ti < toks.size(); ti++) {
-            Token &tk = toks[ti];
-            int digit = nb > 0 ? (int)((std::abs(tk.rho) >> lo) & ((1 << nb) - 1)) : 0;
-            int k = (digit << lo) * (tk.rho > 0 ? 1 : -1);
-            int newpos = ((tk.pos - k) % M + M) % M;
+            const Token &tk = toks[ti];
+            const int digit = nb > 0 ? (int)((std::abs(tk.rho) >> lo) & ((1 << nb) - 1)) : 0;
+            const int k = (digit << lo) * (tk.rho > 0 ? 1 : -1);
+            const int newpos = ((tk.pos - k) % M + M) % M;
             if (k != 0) rot_set[{tk.lane, k}] = 1;
-            if (tk.rho - k == 0) {
+            if (tk.rho - k == 0) {   // arrival: removed into the accumulator
                 FG_CHECK(newpos == tk.dest, FG_EINVAL, "planner: token missed its target");
-                arrive[{tk.lane, k}].push_back({tk.dest, tk.w});
+                auto &m = gterms[std::make_tuple(tk.lane, k, -1)];
+                FG_CHECK(!m.count(tk.dest), FG_EINVAL, "planner: repeated edge");
+                m[tk.dest] = tk.w;
             } else {
-                items.push_back({tk.lane, ((k % M) + M) % M, k, newpos, tk.u, (int)ti});
+                moving.push_back({(int)ti, k, newpos});
             }
-            tk.rho -= k;
-            tk.pos = newpos;
         }
-        std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) {
-            if (a.lane != b.lane) return a.lane < b.lane;
-            if (a.kmod != b.kmod) return a.kmod < b.kmod;
-            return a.pos < b.pos;
-        });
-        std::vector<std::unordered_map<int, int>> out_slots;   // slot -> value id
-        std::map<std::tuple<int, int, int>, std::vector<int>> placed;  // (lane,k,x) -> slots
-        std::vector<int> new_lane(toks.size(), -1);
-        for (size_t a = 0; a < items.size();) {
-            size_t b = a;
-            while (b < items.size() && items[b].lane == items[a].lane && items[b].k == items[a].k &&
-                   items[b].pos == items[a].pos)
-                b++;
-            const Item &it = items[a];
-            int x = -1;
-            for (size_t l = 0; l < out_slots.size() && x < 0; l++) {
-                auto f = out_slots[l].find(it.pos);
-                if (f != out_slots[l].end() && f->second == it.u) x = (int)l;
+        // tokens meeting at one slot on the way to one destination are summed
+        std::map<std::pair<int, int>, std::vector<int>> by_pd;   // (new slot, dest) -> moves
+        for (size_t i = 0; i < moving.size(); i++)
+            by_pd[{moving[i].pos, toks[moving[i].tok].dest}].push_back((int)i);
+        std::map<std::tuple<int, int, int>, std::vector<int>> items;   // (lane, kmod, slot) -> moves
+        std::vector<std::pair<std::pair<int, int>, std::vector<int>>> merged;
+        for (auto &kv : by_pd) {
+            if (kv.second.size() >= 2) {
+                merged.push_back(kv);
+            } else {
+                const Move &mv = moving[kv.second[0]];
+                items[std::make_tuple(toks[mv.tok].lane, ((mv.k % M) + M) % M, mv.pos)].push_back(
+                    kv.second[0]);
             }
-            if (x < 0) {
-                for (size_t l = 0; l < out_slots.size() && x < 0; l++)
-                    if (!out_slots[l].count(it.pos)) x = (int)l;
-                if (x < 0) {
-                    out_slots.emplace_back();
-                    x = (int)out_slots.size() - 1;
+        }
+        std::vector<std::unordered_map<int, int>> out_slots;   // slot -> content
+        auto place = [&](int p, int content, bool &joined) {
+            for (size_t l = 0; l < out_slots.size(); l++) {
+                auto f = out_slots[l].find(p);
+                if (f != out_slots[l].end() && f->second == content) {
+                    joined = true;
+                    return (int)l;
                 }
-                out_slots[x][it.pos] = it.u;
-                placed[{it.lane, it.k, x}].push_back(it.pos);
             }
-            for (size_t c = a; c < b; c++) {
-                FG_CHECK(items[c].u == it.u, FG_EINVAL, "planner: two values share a lane slot");
-                new_lane[items[c].tok] = x;
+            joined = false;
+            for (size_t l = 0; l < out_slots.size(); l++)
+                if (!out_slots[l].count(p)) {
+                    out_slots[l][p] = content;
+                    return (int)l;
+                }
+            out_slots.emplace_back();
+            out_slots.back()[p] = content;
+            return (int)out_slots.size() - 1;
+        };
+        std::vector<Token> nxt;
+        for (auto &it : items) {   // ordered by (lane, k mod M, slot)
+            const int p = std::get<2>(it.first);
+            const Move &m0 = moving[it.second[0]];
+            const int lane = toks[m0.tok].lane, k = m0.k, content = toks[m0.tok].u;
+            bool joined;
+            const int x = place(p, content, joined);
+            if (!joined) gterms[std::make_tuple(lane, k, x)][p] = 1.0;
+            for (int mi : it.second) {
+                const Move &mv = moving[mi];
+                Token t = toks[mv.tok];
+                FG_CHECK(t.u == content, FG_EINVAL, "planner: two values share a lane slot");
+                t.lane = x;
+                t.pos = p;
+                t.rho -= mv.k;
+                nxt.push_back(t);
             }
-            a = b;
         }
-        for (auto &pkv : placed) {
-            GT tm{std::get<0>(pkv.first), std::get<1>(pkv.first), std::get<2>(pkv.first), {}};
-            for (int s : pkv.second) tm.vals.push_back({s, 1.0});
-            gterms.push_back(std::move(tm));
+        for (auto &mg : merged) {   // ordered by (slot, dest)
+            const int p = mg.first.first, d = mg.first.second;
+            const int content = -(++n_carriers);
+            bool joined;
+            const int x = place(p, content, joined);
+            const Move &m0 = moving[mg.second[0]];
+            const int rho2 = toks[m0.tok].rho - m0.k;
+            for (int mi : mg.second) {
+                const Move &mv = moving[mi];
+                const Token &t = toks[mv.tok];
+                FG_CHECK(t.rho - mv.k == rho2, FG_EINVAL, "planner: carrier shift mismatch");
+                auto &m = gterms[std::make_tuple(t.lane, mv.k, x)];
+                FG_CHECK(!m.count(p), FG_EINVAL, "planner: carrier slot used twice");
+                m[p] = t.w;
+            }
+            nxt.push_back({content, x, p, rho2, d, 1.0});
         }
-        for (auto &akv : arrive) {
-            GT tm{akv.first.first, akv.first.second, -1, akv.second};
-            gterms.push_back(std::move(tm));
-        }
-        std::sort(gterms.begin(), gterms.end(), [M](const GT &a, const GT &b) {
-            int ka = ((a.k % M) + M) % M, kb = ((b.k % M) + M) % M;
-            if (a.src != b.src) return a.src < b.src;
-            if (ka != kb) return ka < kb;
-            return a.dst < b.dst;
-        });
         GroupC grp;
         grp.bit_lo = lo;
         grp.n_bits = nb;
@@ -276,23 +292,27 @@ void build(fg_plan &pl, const fg_ctx &ctx, const int32_t *row_ptr, const int32_t
         grp.n_in = n_lanes;
         grp.n_out = (int)out_slots.size();
         for (auto &rk : rot_set) grp.rots.push_back(rk.first);
+        auto kmod = [M](int k) { return ((k % M) + M) % M; };
         std::sort(grp.rots.begin(), grp.rots.end(),
-                  [M](const std::pair<int, int> &a, const std::pair<int, int> &b) {
-                      int ka = ((a.second % M) + M) % M, kb = ((b.second % M) + M) % M;
-                      return a.first != b.first ? a.first < b.first : ka < kb;
+                  [&](const std::pair<int, int> &a, const std::pair<int, int> &b) {
+                      return a.first != b.first ? a.first < b.first : kmod(a.second) < kmod(b.second);
                   });
-        for (auto &gt : gterms) {
-            push_mask(pl, level, std::move(gt.vals));
-            grp.terms.push_back({gt.src, gt.k, gt.dst, (int)pl.masks.size() - 1});
+        std::vector<std::tuple<int, int, int>> tkeys;
+        for (auto &kv : gterms) tkeys.push_back(kv.first);
+        std::sort(tkeys.begin(), tkeys.end(), [&](const std::tuple<int, int, int> &a,
+                                                  const std::tuple<int, int, int> &b) {
+            if (std::get<0>(a) != std::get<0>(b)) return std::get<0>(a) < std::get<0>(b);
+            if (kmod(std::get<1>(a)) != kmod(std::get<1>(b)))
+                return kmod(std::get<1>(a)) < kmod(std::get<1>(b));
+            return std::get<2>(a) < std::get<2>(b);
+        });
+        for (auto &tkey : tkeys) {
+            std::vector<std::pair<int, double>> vals(gterms[tkey].begin(), gterms[tkey].end());
+            push_mask(pl, level, std::move(vals));
+            grp.terms.push_back({std::get<0>(tkey), std::get<1>(tkey), std::get<2>(tkey),
+                                 (int)pl.masks.size() - 1});
         }
         pl.groups.push_back(std::move(grp));
-        // advance: arrived tokens leave, the others take their new lane
-        std::vector<Token> nxt;
-        for (size_t ti = 0; ti < toks.size(); ti++)
-            if (toks[ti].rho != 0) {
-                toks[ti].lane = new_lane[ti];
-                nxt.push_back(toks[ti]);
-            }
         toks.swap(nxt);
         n_lanes = (int)out_slots.size();
         pl.max_lanes = std::max(pl.max_lanes, n_lanes);

@@ -71,3 +71,21 @@ def test_auto_radix_fits_budget_and_errors():
     with pytest.raises(fg.FicgcnError) as e:
         fg.plan_dry_run(prm, w.row_ptr, w.col, w.val, w.W, bad, t=1)
     assert e.value.code == -1   # FG_EINVAL
+
+
+def test_benchmark_plan_matches_oracle_and_merges():
+    """The benchmark's own layer plan (power-law graph with hubs, 19,717 nodes,
+    N = 2^16, radix 4): identical in both planners, and in-flight sums occur
+    (masks other than the accumulator's carrying edge weights)."""
+    c = wl.CONFIGS["pubmed_like"]
+    P = ckks.Params(c["log_n"], c["q_bits"], c["p_bits"], c["alpha"], c["log_scale"])
+    w = wl.config_workload("pubmed_like")
+    perm = wl.random_order(w.V, P.slots, 2025)
+    op = planner.build_plan(P, P.L, w.row_ptr, w.col, w.val, w.V, w.W, perm, 1, 2, True, 10)
+    got = fg.plan_dry_run(c, w.row_ptr, w.col, w.val, w.W, perm, t=1, radix_bits=2, min_out_level=10)
+    np.testing.assert_array_equal(got, oracle_records(op))
+    weighted = sum(1 for g in op.groups for tm in g.terms
+                   if tm.dst >= 0 and np.any((op.masks[tm.mask].values != 0) &
+                                             (op.masks[tm.mask].values != 1)))
+    assert weighted > 0
+    assert max(g.n_out for g in op.groups) <= 32
