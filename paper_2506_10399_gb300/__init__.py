@@ -165,23 +165,39 @@ class Keys:
 
 
 def keygen(ctx, seed, rot_amounts):
-    """(secret-key blob, evaluation-key blob) as bytes."""
+    """(secret-key blob as bytes, evaluation-key blob as a numpy uint8 array)."""
     nat = _lib()
     am = np.ascontiguousarray(np.array(list(rot_amounts), dtype=np.int32))
     skb, skl, evb, evl = ctypes.c_void_p(), ctypes.c_size_t(), ctypes.c_void_p(), ctypes.c_size_t()
     _check(ctx, nat.lib.fg_keygen(ctx._h, int(seed), am.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                   len(am), ctypes.byref(skb), ctypes.byref(skl),
                                   ctypes.byref(evb), ctypes.byref(evl)))
-    sk = ctypes.string_at(skb, skl.value)
-    evk = ctypes.string_at(evb, evl.value)
+    sk = _copy_blob(skb, skl.value).tobytes()
+    evk = _copy_blob(evb, evl.value)
     nat.lib.fg_free(skb)
     nat.lib.fg_free(evb)
     return sk, evk
 
 
+def _copy_blob(ptr, n):
+    """Copy a library-owned blob (any size; ctypes.string_at takes a C int)."""
+    if n == 0:
+        return np.zeros(0, np.uint8)
+    return np.frombuffer((ctypes.c_uint8 * n).from_address(ptr.value), dtype=np.uint8).copy()
+
+
+def _blob_arg(b):
+    if isinstance(b, np.ndarray):
+        assert b.dtype == np.uint8 and b.flags["C_CONTIGUOUS"]
+        return ctypes.c_void_p(b.ctypes.data), b.size
+    return b, len(b)
+
+
 def load_evk(ctx, evk):
+    """Keys from an evk blob (bytes or a numpy uint8 array, as keygen returns)."""
     h = ctypes.c_void_p()
-    _check(ctx, _lib().lib.fg_load_evk(ctx._h, evk, len(evk), ctypes.byref(h)))
+    ptr, n = _blob_arg(evk)
+    _check(ctx, _lib().lib.fg_load_evk(ctx._h, ptr, n, ctypes.byref(h)))
     return Keys(ctx, h)
 
 

@@ -104,6 +104,7 @@ def test_ntt_roundtrip_ragged_batches(fg, name):
 
 def parse_evk(blob, P):
     import struct
+    blob = bytes(blob) if not isinstance(blob, bytes) else blob
     assert blob[:8] == b"FGEVK001"
     ver, log_n, nq, np_, alpha, nk = struct.unpack_from("<6I", blob, 8)
     off = 8 + 24 + 8 * (nq + np_)
