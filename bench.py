@@ -208,6 +208,51 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ NTT throughput
+def run_ntt(args, fg=None):
+    """Batched forward + inverse NTT on the shape the layer uses most (the
+    ModDown batch at level 14: 16 columns x 2 parts x 15 limbs = 480 limbs of
+    N = 2^16, 246 MB, larger than L2).  Returns limb-NTTs/s and GB/s."""
+    import torch
+    if fg is None:
+        import __graft_entry__
+        fg = __graft_entry__.build()
+    from paper_2506_10399_gb300 import workloads as wl
+    c = wl.CONFIGS[WORKLOAD]
+    ctx = fg.Context(**c)
+    nl, count = 15, 480
+    pidx = list(range(nl))
+    g = torch.Generator(device="cuda").manual_seed(1)
+    data = torch.randint(0, 1 << 40, (count, ctx.n), dtype=torch.int64, device="cuda", generator=g)
+    if args.profile:
+        fg.ntt(ctx, data, pidx)
+        fg.ntt(ctx, data, pidx, inverse=True)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("fg_ntt")
+        fg.ntt(ctx, data, pidx)
+        fg.ntt(ctx, data, pidx, inverse=True)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        return None
+    for _ in range(3):
+        fg.ntt(ctx, data, pidx)
+        fg.ntt(ctx, data, pidx, inverse=True)
+    torch.cuda.synchronize()
+    reps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fg.ntt(ctx, data, pidx)
+        fg.ntt(ctx, data, pidx, inverse=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / (2 * reps)   # per batched transform
+    ctx.close()
+    return {"limb_ntts_per_s": round(count / (ms / 1e3)), "ms_per_batch": round(ms, 4),
+            "batch_limbs": count, "log_n": c["log_n"],
+            "alg_GB_per_s": round(count * ctx.n * 16 / (ms / 1e3) / 1e9, 1)}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import torch
@@ -228,8 +273,18 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
+    if args.ntt:
+        r = run_ntt(args, fg)
+        if r is not None and rank == 0:
+            print(json.dumps({"ntt": r}))
+        return 0
     c = wl.CONFIGS[WORKLOAD]
-    w = wl.config_workload(WORKLOAD, **({"F": args.features} if args.features else {}))
+    over = {}
+    if args.features:
+        over["F"] = args.features
+    if args.nodes:
+        over["V"] = args.nodes
+    w = wl.config_workload(WORKLOAD, **over)
     perm = wl.random_order(w.V, 1 << (c["log_n"] - 1), SEED)
     t_setup = time.perf_counter()
     ctx = fg.Context(**c)
@@ -347,6 +402,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
+        "ntt": run_ntt(args, fg),
         "setup_s": round(setup_s, 1),
         "plan": {k: info[k] for k in ("n_groups", "n_masks", "n_keys", "masked_products", "out_level")},
         "device_bytes": ctx.device_bytes(),
@@ -371,6 +427,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true")
     ap.add_argument("--features", type=int, default=0)
+    ap.add_argument("--nodes", type=int, default=0)
+    ap.add_argument("--ntt", action="store_true", help="NTT throughput only")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

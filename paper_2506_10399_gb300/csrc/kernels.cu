@@ -60,164 +60,274 @@ constexpr int kNttThreads = 256;
 constexpr int kColsA = 16;       // columns per CTA in pass A
 constexpr int kElemsB = 2048;    // elements per CTA in pass B
 
-__global__ void __launch_bounds__(kNttThreads)
-ntt_fwd_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ tw,
-          int log_n, int s1)
+__device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, const ulonglong2 w, u64 q, u64 q2)
 {
+    X = X >= q2 ? X - q2 : X;               // X < 2q, Y < 4q in; both < 4q out
+    const u64 T = shoup_lazy(Y, w.x, w.y, q);
+    Y = X - T + q2;
+    X = X + T;
+}
+
+__device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, const ulonglong2 w, u64 q, u64 q2)
+{
+    const u64 U = X, V = Y;                 // both < 2q in and out
+    const u64 S = U + V;
+    X = S >= q2 ? S - q2 : S;
+    Y = shoup_lazy(U - V + q2, w.x, w.y, q);
+}
+
+// Stages are taken two at a time (radix-4 rounds: four elements, four
+// butterflies, one shared-memory round trip and one barrier per two
+// stages).  Within a sub-transform of 2^LS elements, a round on stages
+// (s, s+1) (s counted inside the sub-transform) works on element groups
+// {r, r + h/2, r + h, r + 3h/2} with h = 2^(LS-s-1), r = (i << (LS-s)) + j,
+// i = unit >> (LS-s-2), j = unit & (h/2 - 1); stage s uses twiddle index
+// 2^s + i, stage s+1 uses 2^(s+1) + 2i and 2^(s+1) + 2i + 1 (offset by the
+// sub-transform's position in the global stage numbering, see callers).
+
+template <int LOGN>
+__global__ void __launch_bounds__(kNttThreads)
+ntt_fwd_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ tw)
+{
+    constexpr int S1 = LOGN / 2, N = 1 << LOGN, N1 = 1 << S1, N2 = N >> S1;
+    constexpr int LC = 4;   // log2 kColsA
     const int limb = blockIdx.y;
     const int col = limb % bt.per_row, row = limb / bt.per_row;
     const int pi = bt.pidx[col];
     if (pi < 0) return;
-    const int N = 1 << log_n, N1 = 1 << s1, N2 = N >> s1;
     extern __shared__ u64 sm[];
     ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(sm + N1 * kColsA);
-    const u64 q = primes[pi].q;
+    const u64 q = primes[pi].q, q2 = 2 * q;
     const ulonglong2 *twp = tw + (size_t)pi * N;
-    const u64 *s = bt.src + ((size_t)row * bt.src_stride + col) * N;
-    u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * N;
+    const u64 *src = bt.src + ((size_t)row * bt.src_stride + col) * N;
+    u64 *dst = bt.dst + ((size_t)row * bt.dst_stride + col) * N;
     const int c0 = blockIdx.x * kColsA;
-    for (int i = threadIdx.x; i < N1; i += blockDim.x) stw[i] = twp[i];
-    for (int idx = threadIdx.x; idx < N1 * kColsA; idx += blockDim.x) {
-        int r = idx / kColsA, c = idx % kColsA;
-        sm[idx] = s[(size_t)r * N2 + c0 + c];
-    }
+    for (int i = threadIdx.x; i < N1; i += kNttThreads) stw[i] = twp[i];
+    for (int idx = threadIdx.x; idx < N1 * kColsA; idx += kNttThreads)
+        sm[idx] = src[(size_t)(idx >> LC) * N2 + c0 + (idx & (kColsA - 1))];
     __syncthreads();
-    const u64 q2 = 2 * q;
-    for (int st = 0; st < s1; st++) {
-        const int half = N1 >> (st + 1);
-        for (int b = threadIdx.x; b < (N1 / 2) * kColsA; b += blockDim.x) {
-            int c = b % kColsA, j = b / kColsA;
-            int i = j / half;
-            int r0 = i * 2 * half + (j % half);
-            ulonglong2 w = stw[(1 << st) + i];
-            u64 X = sm[r0 * kColsA + c], Y = sm[(r0 + half) * kColsA + c];
-            X = X >= q2 ? X - q2 : X;
-            u64 T = shoup_lazy(Y, w.x, w.y, q);
-            sm[r0 * kColsA + c] = X + T;
-            sm[(r0 + half) * kColsA + c] = X - T + q2;
+    int s = 0;
+#pragma unroll
+    for (; s + 1 < S1; s += 2) {
+        const int lq = S1 - s - 2;   // log of h/2
+#pragma unroll 2
+        for (int b = threadIdx.x; b < (N1 / 4) * kColsA; b += kNttThreads) {
+            const int c = b & (kColsA - 1), u = b >> LC;
+            const int i = u >> lq, j = u & ((1 << lq) - 1);
+            const int r = (i << (lq + 2)) + j;
+            const ulonglong2 w1 = stw[(1 << s) + i];
+            const ulonglong2 w2 = stw[(2 << s) + 2 * i], w3 = stw[(2 << s) + 2 * i + 1];
+            u64 *p0 = sm + r * kColsA + c;
+            const int dq = (1 << lq) * kColsA;
+            u64 a0 = p0[0], a1 = p0[dq], a2 = p0[2 * dq], a3 = p0[3 * dq];
+            ct_bfly(a0, a2, w1, q, q2);
+            ct_bfly(a1, a3, w1, q, q2);
+            ct_bfly(a0, a1, w2, q, q2);
+            ct_bfly(a2, a3, w3, q, q2);
+            p0[0] = a0;
+            p0[dq] = a1;
+            p0[2 * dq] = a2;
+            p0[3 * dq] = a3;
         }
         __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < N1 * kColsA; idx += blockDim.x) {
-        int r = idx / kColsA, c = idx % kColsA;
-        d[(size_t)r * N2 + c0 + c] = sm[idx];   // lazy, < 4q
+    if (s < S1) {   // odd stage count: last radix-2 stage (h = 1)
+        for (int b = threadIdx.x; b < (N1 / 2) * kColsA; b += kNttThreads) {
+            const int c = b & (kColsA - 1), i = b >> LC;
+            u64 *p0 = sm + (2 * i) * kColsA + c;
+            u64 a0 = p0[0], a1 = p0[kColsA];
+            ct_bfly(a0, a1, stw[(1 << s) + i], q, q2);
+            p0[0] = a0;
+            p0[kColsA] = a1;
+        }
+        __syncthreads();
     }
+    for (int idx = threadIdx.x; idx < N1 * kColsA; idx += kNttThreads)
+        dst[(size_t)(idx >> LC) * N2 + c0 + (idx & (kColsA - 1))] = sm[idx];   // lazy, < 4q
 }
 
+template <int LOGN>
 __global__ void __launch_bounds__(kNttThreads)
-ntt_fwd_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ tw,
-          int log_n, int s1, int rows_per_cta)
+ntt_fwd_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ tw)
 {
+    constexpr int S1 = LOGN / 2, N = 1 << LOGN, N1 = 1 << S1, LN2 = LOGN - S1, N2 = 1 << LN2;
+    constexpr int R = (kElemsB / N2) < N1 ? (kElemsB / N2) : N1;
     const int limb = blockIdx.y;
     const int col = limb % bt.per_row, row = limb / bt.per_row;
     const int pi = bt.pidx[col];
     if (pi < 0) return;
-    const int N = 1 << log_n, N2 = N >> s1;
-    const int R = rows_per_cta;
     extern __shared__ u64 sm[];
     const u64 q = primes[pi].q, q2 = 2 * q;
     const ulonglong2 *twp = tw + (size_t)pi * N;
     const int row0 = blockIdx.x * R;
     u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * N + (size_t)row0 * N2;
-    for (int idx = threadIdx.x; idx < R * N2; idx += blockDim.x) sm[idx] = d[idx];
+    for (int idx = threadIdx.x; idx < R * N2; idx += kNttThreads) sm[idx] = d[idx];
     __syncthreads();
-    const int hb = N2 / 2;
-    for (int st = s1; st < log_n; st++) {
-        const int t = N >> (st + 1);
-        for (int b = threadIdx.x; b < R * hb; b += blockDim.x) {
-            int r = b / hb, jj = b % hb;
-            int g = jj / t;
-            int p0 = r * N2 + g * 2 * t + (jj % t);
-            int gi = (row0 + r) * (N2 / (2 * t)) + g;
-            ulonglong2 w = twp[(1 << st) + gi];
-            u64 X = sm[p0], Y = sm[p0 + t];
-            X = X >= q2 ? X - q2 : X;
-            u64 T = shoup_lazy(Y, w.x, w.y, q);
-            sm[p0] = X + T;
-            sm[p0 + t] = X - T + q2;
+    int ls = 0;   // stage inside the row; global stage S1 + ls
+#pragma unroll
+    for (; ls + 1 < LN2; ls += 2) {
+        const int s = S1 + ls;
+        const int lq = LN2 - ls - 2;
+#pragma unroll 2
+        for (int b = threadIdx.x; b < R * (N2 / 4); b += kNttThreads) {
+            const int r = b >> (LN2 - 2), u = b & (N2 / 4 - 1);
+            const int i = u >> lq, j = u & ((1 << lq) - 1);
+            const int pos = (i << (lq + 2)) + j;
+            const int gi = ((row0 + r) << ls) + i;
+            const ulonglong2 w1 = twp[(1 << s) + gi];
+            const ulonglong2 w2 = twp[(2 << s) + 2 * gi], w3 = twp[(2 << s) + 2 * gi + 1];
+            u64 *p0 = sm + r * N2 + pos;
+            const int dq = 1 << lq;
+            u64 a0 = p0[0], a1 = p0[dq], a2 = p0[2 * dq], a3 = p0[3 * dq];
+            ct_bfly(a0, a2, w1, q, q2);
+            ct_bfly(a1, a3, w1, q, q2);
+            ct_bfly(a0, a1, w2, q, q2);
+            ct_bfly(a2, a3, w3, q, q2);
+            p0[0] = a0;
+            p0[dq] = a1;
+            p0[2 * dq] = a2;
+            p0[3 * dq] = a3;
         }
         __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < R * N2; idx += blockDim.x) d[idx] = reduce4(sm[idx], q);
+    if (ls < LN2) {   // last radix-2 stage, half distance 1
+        const int s = S1 + ls;
+        for (int b = threadIdx.x; b < R * (N2 / 2); b += kNttThreads) {
+            const int r = b >> (LN2 - 1), i = b & (N2 / 2 - 1);
+            u64 *p0 = sm + r * N2 + 2 * i;
+            u64 a0 = p0[0], a1 = p0[1];
+            ct_bfly(a0, a1, twp[(1 << s) + ((row0 + r) << ls) + i], q, q2);
+            p0[0] = a0;
+            p0[1] = a1;
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < R * N2; idx += kNttThreads) d[idx] = reduce4(sm[idx], q);
 }
 
+template <int LOGN>
 __global__ void __launch_bounds__(kNttThreads)
-ntt_inv_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ itw,
-          int log_n, int s1, int rows_per_cta)
+ntt_inv_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ itw)
 {
+    constexpr int S1 = LOGN / 2, N = 1 << LOGN, N1 = 1 << S1, LN2 = LOGN - S1, N2 = 1 << LN2;
+    constexpr int R = (kElemsB / N2) < N1 ? (kElemsB / N2) : N1;
     const int limb = blockIdx.y;
     const int col = limb % bt.per_row, row = limb / bt.per_row;
     const int pi = bt.pidx[col];
     if (pi < 0) return;
-    const int N = 1 << log_n, N2 = N >> s1;
-    const int R = rows_per_cta;
     extern __shared__ u64 sm[];
     const u64 q = primes[pi].q, q2 = 2 * q;
     const ulonglong2 *twp = itw + (size_t)pi * N;
     const int row0 = blockIdx.x * R;
-    const u64 *s = bt.src + ((size_t)row * bt.src_stride + col) * N + (size_t)row0 * N2;
+    const u64 *sr = bt.src + ((size_t)row * bt.src_stride + col) * N + (size_t)row0 * N2;
     u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * N + (size_t)row0 * N2;
-    for (int idx = threadIdx.x; idx < R * N2; idx += blockDim.x) sm[idx] = s[idx];
+    for (int idx = threadIdx.x; idx < R * N2; idx += kNttThreads) sm[idx] = sr[idx];
     __syncthreads();
-    const int hb = N2 / 2;
-    for (int st = log_n - 1; st >= s1; st--) {
-        const int t = N >> (st + 1);
-        for (int b = threadIdx.x; b < R * hb; b += blockDim.x) {
-            int r = b / hb, jj = b % hb;
-            int g = jj / t;
-            int p0 = r * N2 + g * 2 * t + (jj % t);
-            int gi = (row0 + r) * (N2 / (2 * t)) + g;
-            ulonglong2 w = twp[(1 << st) + gi];
-            u64 U = sm[p0], V = sm[p0 + t];
-            u64 S = U + V;
-            sm[p0] = S >= q2 ? S - q2 : S;
-            sm[p0 + t] = shoup_lazy(U - V + q2, w.x, w.y, q);
+    int ls = LN2 - 1;
+    if (LN2 & 1) {   // odd: the last stage (half distance 1) alone first
+        const int s = S1 + ls;
+        for (int b = threadIdx.x; b < R * (N2 / 2); b += kNttThreads) {
+            const int r = b >> (LN2 - 1), i = b & (N2 / 2 - 1);
+            u64 *p0 = sm + r * N2 + 2 * i;
+            u64 a0 = p0[0], a1 = p0[1];
+            gs_bfly(a0, a1, twp[(1 << s) + ((row0 + r) << ls) + i], q, q2);
+            p0[0] = a0;
+            p0[1] = a1;
+        }
+        __syncthreads();
+        ls--;
+    }
+#pragma unroll
+    for (; ls >= 1; ls -= 2) {   // stages (ls-1, ls), higher one first
+        const int lo = ls - 1, s = S1 + lo;
+        const int lq = LN2 - lo - 2;
+#pragma unroll 2
+        for (int b = threadIdx.x; b < R * (N2 / 4); b += kNttThreads) {
+            const int r = b >> (LN2 - 2), u = b & (N2 / 4 - 1);
+            const int i = u >> lq, j = u & ((1 << lq) - 1);
+            const int pos = (i << (lq + 2)) + j;
+            const int gi = ((row0 + r) << lo) + i;
+            const ulonglong2 w1 = twp[(1 << s) + gi];
+            const ulonglong2 w2 = twp[(2 << s) + 2 * gi], w3 = twp[(2 << s) + 2 * gi + 1];
+            u64 *p0 = sm + r * N2 + pos;
+            const int dq = 1 << lq;
+            u64 a0 = p0[0], a1 = p0[dq], a2 = p0[2 * dq], a3 = p0[3 * dq];
+            gs_bfly(a0, a1, w2, q, q2);
+            gs_bfly(a2, a3, w3, q, q2);
+            gs_bfly(a0, a2, w1, q, q2);
+            gs_bfly(a1, a3, w1, q, q2);
+            p0[0] = a0;
+            p0[dq] = a1;
+            p0[2 * dq] = a2;
+            p0[3 * dq] = a3;
         }
         __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < R * N2; idx += blockDim.x) d[idx] = sm[idx];   // < 2q
+    for (int idx = threadIdx.x; idx < R * N2; idx += kNttThreads) d[idx] = sm[idx];   // < 2q
 }
 
+template <int LOGN>
 __global__ void __launch_bounds__(kNttThreads)
 ntt_inv_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ itw,
-          const u64 *__restrict__ ninv, int log_n, int s1)
+          const u64 *__restrict__ ninv)
 {
+    constexpr int S1 = LOGN / 2, N = 1 << LOGN, N1 = 1 << S1, N2 = N >> S1;
+    constexpr int LC = 4;
     const int limb = blockIdx.y;
     const int col = limb % bt.per_row, row = limb / bt.per_row;
     const int pi = bt.pidx[col];
     if (pi < 0) return;
-    const int N = 1 << log_n, N1 = 1 << s1, N2 = N >> s1;
     extern __shared__ u64 sm[];
     ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(sm + N1 * kColsA);
     const u64 q = primes[pi].q, q2 = 2 * q;
     const ulonglong2 *twp = itw + (size_t)pi * N;
     u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * N;
     const int c0 = blockIdx.x * kColsA;
-    for (int i = threadIdx.x; i < N1; i += blockDim.x) stw[i] = twp[i];
-    for (int idx = threadIdx.x; idx < N1 * kColsA; idx += blockDim.x) {
-        int r = idx / kColsA, c = idx % kColsA;
-        sm[idx] = d[(size_t)r * N2 + c0 + c];
-    }
+    for (int i = threadIdx.x; i < N1; i += kNttThreads) stw[i] = twp[i];
+    for (int idx = threadIdx.x; idx < N1 * kColsA; idx += kNttThreads)
+        sm[idx] = d[(size_t)(idx >> LC) * N2 + c0 + (idx & (kColsA - 1))];
     __syncthreads();
-    for (int st = s1 - 1; st >= 0; st--) {
-        const int half = N1 >> (st + 1);
-        for (int b = threadIdx.x; b < (N1 / 2) * kColsA; b += blockDim.x) {
-            int c = b % kColsA, j = b / kColsA;
-            int i = j / half;
-            int r0 = i * 2 * half + (j % half);
-            ulonglong2 w = stw[(1 << st) + i];
-            u64 U = sm[r0 * kColsA + c], V = sm[(r0 + half) * kColsA + c];
-            u64 S = U + V;
-            sm[r0 * kColsA + c] = S >= q2 ? S - q2 : S;
-            sm[(r0 + half) * kColsA + c] = shoup_lazy(U - V + q2, w.x, w.y, q);
+    int s = S1 - 1;
+    if (S1 & 1) {   // odd: last stage (h = 1) alone first
+        for (int b = threadIdx.x; b < (N1 / 2) * kColsA; b += kNttThreads) {
+            const int c = b & (kColsA - 1), i = b >> LC;
+            u64 *p0 = sm + (2 * i) * kColsA + c;
+            u64 a0 = p0[0], a1 = p0[kColsA];
+            gs_bfly(a0, a1, stw[(1 << s) + i], q, q2);
+            p0[0] = a0;
+            p0[kColsA] = a1;
+        }
+        __syncthreads();
+        s--;
+    }
+#pragma unroll
+    for (; s >= 1; s -= 2) {   // stages (s-1, s), higher one first
+        const int lo = s - 1;
+        const int lq = S1 - lo - 2;
+#pragma unroll 2
+        for (int b = threadIdx.x; b < (N1 / 4) * kColsA; b += kNttThreads) {
+            const int c = b & (kColsA - 1), u = b >> LC;
+            const int i = u >> lq, j = u & ((1 << lq) - 1);
+            const int r = (i << (lq + 2)) + j;
+            const ulonglong2 w1 = stw[(1 << lo) + i];
+            const ulonglong2 w2 = stw[(2 << lo) + 2 * i], w3 = stw[(2 << lo) + 2 * i + 1];
+            u64 *p0 = sm + r * kColsA + c;
+            const int dq = (1 << lq) * kColsA;
+            u64 a0 = p0[0], a1 = p0[dq], a2 = p0[2 * dq], a3 = p0[3 * dq];
+            gs_bfly(a0, a1, w2, q, q2);
+            gs_bfly(a2, a3, w3, q, q2);
+            gs_bfly(a0, a2, w1, q, q2);
+            gs_bfly(a1, a3, w1, q, q2);
+            p0[0] = a0;
+            p0[dq] = a1;
+            p0[2 * dq] = a2;
+            p0[3 * dq] = a3;
         }
         __syncthreads();
     }
     const u64 ni = ninv[2 * pi], nis = ninv[2 * pi + 1];
-    for (int idx = threadIdx.x; idx < N1 * kColsA; idx += blockDim.x) {
-        int r = idx / kColsA, c = idx % kColsA;
-        d[(size_t)r * N2 + c0 + c] = shoup_mul(sm[idx], ni, nis, q);
-    }
+    for (int idx = threadIdx.x; idx < N1 * kColsA; idx += kNttThreads)
+        d[(size_t)(idx >> LC) * N2 + c0 + (idx & (kColsA - 1))] = shoup_mul(sm[idx], ni, nis, q);
 }
 
 // ------------------------------------------------------------------------
@@ -503,40 +613,53 @@ k_moddown_conv(const u64 *__restrict__ u, int E, u64 *conv, int nl,
 // ------------------------------------------------------------------------
 constexpr int kMaxBeta = 16;   // beta * p^2 < p * 2^64 needs beta * p < 2^64: p < 2^60
 
-__global__ void __launch_bounds__(256)
+// Each thread owns two adjacent slots x, x+1 (16-byte accesses).  In the
+// bit-reversed NTT order the automorphism maps every aligned pair {x, x+1}
+// onto an aligned pair {2m, 2m+1}, so the gather is one 16-byte load plus a
+// swap when sigma(x) is odd.
+__device__ __forceinline__ ulonglong2 gather_pair(const u64 *limb, int m2, bool swap)
+{
+    const ulonglong2 v = reinterpret_cast<const ulonglong2 *>(limb)[m2 >> 1];
+    return swap ? make_ulonglong2(v.y, v.x) : v;
+}
+
+template <int BETA>
+__global__ void __launch_bounds__(256, 3)
 k_ks_ip(const u64 *__restrict__ key, int KL, const u64 *__restrict__ lane, int ls,
-        const u64 *__restrict__ digits, int ncol, int level, int beta, int E, int alpha, int nq,
+        const u64 *__restrict__ digits, int ncol, int level, int E, int alpha, int nq,
         uint32_t g, int log_n, u64 *u, const PrimeC *__restrict__ primes)
 {
     const int N = 1 << log_n;
     const int i = blockIdx.y;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (x >= N) return;
     const int pi = i <= level ? i : nq + (i - level - 1);
     const PrimeC P = primes[pi];
-    const int src = auto_src(x, g, log_n);
+    const int sx = auto_src(x, g, log_n);
+    const bool swap = sx & 1;
     const int own = i <= level ? i / alpha : -1;
-    u64 kb[kMaxBeta], ka[kMaxBeta];
+    ulonglong2 kb[BETA], ka[BETA];
 #pragma unroll
-    for (int d = 0; d < kMaxBeta; d++) {
-        if (d < beta) {
-            kb[d] = key[(((size_t)d * 2 + 0) * KL + pi) * N + x];
-            ka[d] = key[(((size_t)d * 2 + 1) * KL + pi) * N + x];
-        }
+    for (int d = 0; d < BETA; d++) {
+        kb[d] = *reinterpret_cast<const ulonglong2 *>(key + (((size_t)d * 2 + 0) * KL + pi) * N + x);
+        ka[d] = *reinterpret_cast<const ulonglong2 *>(key + (((size_t)d * 2 + 1) * KL + pi) * N + x);
     }
     for (int f = 0; f < ncol; f++) {
-        u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
+        u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0, h2 = 0, l2 = 0, h3 = 0, l3 = 0;
 #pragma unroll
-        for (int d = 0; d < kMaxBeta; d++) {
-            if (d < beta) {
-                const u64 v = d == own ? lane[(((size_t)f * 2 + 1) * ls + i) * N + src]
-                                       : digits[(((size_t)f * beta + d) * E + i) * N + src];
-                mac128(h0, l0, v, kb[d]);
-                mac128(h1, l1, v, ka[d]);
-            }
+        for (int d = 0; d < BETA; d++) {
+            const u64 *limb = d == own ? lane + (((size_t)f * 2 + 1) * ls + i) * N
+                                       : digits + (((size_t)f * BETA + d) * E + i) * N;
+            const ulonglong2 v = gather_pair(limb, sx, swap);
+            mac128(h0, l0, v.x, kb[d].x);
+            mac128(h1, l1, v.y, kb[d].y);
+            mac128(h2, l2, v.x, ka[d].x);
+            mac128(h3, l3, v.y, ka[d].y);
         }
-        u[(((size_t)f * 2 + 0) * E + i) * N + x] = redc(h0, l0, P);
-        u[(((size_t)f * 2 + 1) * E + i) * N + x] = redc(h1, l1, P);
+        *reinterpret_cast<ulonglong2 *>(u + (((size_t)f * 2 + 0) * E + i) * N + x) =
+            make_ulonglong2(redc(h0, l0, P), redc(h1, l1, P));
+        *reinterpret_cast<ulonglong2 *>(u + (((size_t)f * 2 + 1) * E + i) * N + x) =
+            make_ulonglong2(redc(h2, l2, P), redc(h3, l3, P));
     }
 }
 
@@ -545,7 +668,7 @@ k_ks_ip(const u64 *__restrict__ key, int KL, const u64 *__restrict__ lane, int l
 //   R_p = (u_p - conv_p) * P^-1  (+ phi_g(c0) for p = 0)
 //   out_d += mask_d (x) R         (mask in Montgomery form; null mask: out_d = R)
 // ------------------------------------------------------------------------
-constexpr int kMaxDest = 16;
+constexpr int kMaxDest = 8;
 struct DestList {
     int n;
     int out_ls;
@@ -561,28 +684,43 @@ k_moddown_finish_mac(const u64 *__restrict__ u, int E, const u64 *__restrict__ c
 {
     const int N = 1 << log_n;
     const int i = blockIdx.y;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (x >= N) return;
     const PrimeC P = primes[i];
     const u64 q = P.q, pv = pinv[2 * i], pvs = pinv[2 * i + 1];
-    const int src = auto_src(x, g, log_n);
+    const int sx = auto_src(x, g, log_n);
+    const bool swap = sx & 1;
     const int nl = level + 1;
-    u64 m[kMaxDest];
+    ulonglong2 m[kMaxDest];
 #pragma unroll
     for (int d = 0; d < kMaxDest; d++)
-        if (d < dl.n) m[d] = dl.mask[d] ? dl.mask[d][(size_t)i * N + x] : 0;
+        if (d < dl.n && dl.mask[d])
+            m[d] = *reinterpret_cast<const ulonglong2 *>(dl.mask[d] + (size_t)i * N + x);
     for (int f = 0; f < ncol; f++) {
 #pragma unroll
         for (int p = 0; p < 2; p++) {
             const int poly = f * 2 + p;
-            u64 r = shoup_mul(sub_mod(u[((size_t)poly * E + i) * N + x],
-                                      conv[((size_t)poly * nl + i) * N + x], q), pv, pvs, q);
-            if (p == 0) r = add_mod(r, lane[((size_t)(f * 2) * ls + i) * N + src], q);
+            const ulonglong2 uu = *reinterpret_cast<const ulonglong2 *>(u + ((size_t)poly * E + i) * N + x);
+            const ulonglong2 cc = *reinterpret_cast<const ulonglong2 *>(conv + ((size_t)poly * nl + i) * N + x);
+            u64 r0 = shoup_mul(sub_mod(uu.x, cc.x, q), pv, pvs, q);
+            u64 r1 = shoup_mul(sub_mod(uu.y, cc.y, q), pv, pvs, q);
+            if (p == 0) {
+                const ulonglong2 c0 = gather_pair(lane + ((size_t)(f * 2) * ls + i) * N, sx, swap);
+                r0 = add_mod(r0, c0.x, q);
+                r1 = add_mod(r1, c0.y, q);
+            }
 #pragma unroll
             for (int d = 0; d < kMaxDest; d++) {
                 if (d < dl.n) {
-                    u64 *o = dl.out[d] + ((size_t)poly * dl.out_ls + i) * N + x;
-                    *o = dl.mask[d] ? add_mod(*o, mont_mul(r, m[d], P), q) : r;
+                    ulonglong2 *o = reinterpret_cast<ulonglong2 *>(dl.out[d] + ((size_t)poly * dl.out_ls + i) * N + x);
+                    if (dl.mask[d]) {
+                        ulonglong2 ov = *o;
+                        ov.x = add_mod(ov.x, mont_mul(r0, m[d].x, P), q);
+                        ov.y = add_mod(ov.y, mont_mul(r1, m[d].y, P), q);
+                        *o = ov;
+                    } else {
+                        *o = make_ulonglong2(r0, r1);
+                    }
                 }
             }
         }
@@ -595,23 +733,26 @@ k_stay_mac(const u64 *__restrict__ lane, int ls, int ncol, int level, const Dest
            const PrimeC *__restrict__ primes, int N)
 {
     const int i = blockIdx.y;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (x >= N) return;
     const PrimeC P = primes[i];
-    u64 m[kMaxDest];
+    ulonglong2 m[kMaxDest];
 #pragma unroll
     for (int d = 0; d < kMaxDest; d++)
-        if (d < dl.n) m[d] = dl.mask[d][(size_t)i * N + x];
+        if (d < dl.n) m[d] = *reinterpret_cast<const ulonglong2 *>(dl.mask[d] + (size_t)i * N + x);
     for (int f = 0; f < ncol; f++) {
 #pragma unroll
         for (int p = 0; p < 2; p++) {
             const int poly = f * 2 + p;
-            const u64 v = lane[((size_t)poly * ls + i) * N + x];
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(lane + ((size_t)poly * ls + i) * N + x);
 #pragma unroll
             for (int d = 0; d < kMaxDest; d++) {
                 if (d < dl.n) {
-                    u64 *o = dl.out[d] + ((size_t)poly * dl.out_ls + i) * N + x;
-                    *o = add_mod(*o, mont_mul(v, m[d], P), P.q);
+                    ulonglong2 *o = reinterpret_cast<ulonglong2 *>(dl.out[d] + ((size_t)poly * dl.out_ls + i) * N + x);
+                    ulonglong2 ov = *o;
+                    ov.x = add_mod(ov.x, mont_mul(v.x, m[d].x, P), P.q);
+                    ov.y = add_mod(ov.y, mont_mul(v.y, m[d].y, P), P.q);
+                    *o = ov;
                 }
             }
         }
@@ -644,40 +785,49 @@ KTimer::~KTimer()
     }
 }
 
-static inline int s1_of(int log_n) { return log_n / 2; }
+
+template <int LOGN>
+static void ntt_launch_t(fg_ctx *ctx, const Batch &bt, int count, bool inverse)
+{
+    constexpr int S1 = LOGN / 2, N = 1 << LOGN, N1 = 1 << S1, N2 = N >> S1;
+    constexpr int R = (kElemsB / N2) < N1 ? (kElemsB / N2) : N1;
+    const size_t smA = (size_t)N1 * kColsA * 8 + (size_t)N1 * 16;
+    const size_t smB = (size_t)R * N2 * 8;
+    const auto *fwd = (const ulonglong2 *)ctx->d_fwd;
+    const auto *inv = (const ulonglong2 *)ctx->d_inv;
+    dim3 gA(N2 / kColsA, count), gB(N1 / R, count);
+    Batch b2 = bt;
+    b2.src = b2.dst;
+    b2.src_stride = b2.dst_stride;
+    if (!inverse) {
+        ntt_fwd_a<LOGN><<<gA, kNttThreads, smA, ctx->stream>>>(bt, ctx->d_primes, fwd);
+        ntt_fwd_b<LOGN><<<gB, kNttThreads, smB, ctx->stream>>>(b2, ctx->d_primes, fwd);
+    } else {
+        ntt_inv_b<LOGN><<<gB, kNttThreads, smB, ctx->stream>>>(bt, ctx->d_primes, inv);
+        ntt_inv_a<LOGN><<<gA, kNttThreads, smA, ctx->stream>>>(b2, ctx->d_primes, inv, ctx->d_ninv);
+    }
+}
 
 static void launch_ntt(fg_ctx *ctx, const LimbSet &src, const LimbSet &dst, bool inverse)
 {
     FG_CHECK(src.per_row == dst.per_row && src.rows == dst.rows, FG_EINVAL, "ntt: shape mismatch");
     if (src.rows == 0 || src.per_row == 0) return;
-    const int log_n = ctx->log_n, N = ctx->n, s1 = s1_of(log_n);
-    const int N1 = 1 << s1, N2 = N >> s1;
     Batch bt = make_batch(src.base, src.stride, dst.base, dst.stride, src.per_row, src.rows,
                           src.pidx);
     const int count = src.rows * src.per_row;
-    const int R = std::min(kElemsB / N2, N1);
-    const size_t smA = (size_t)N1 * kColsA * 8 + (size_t)N1 * 16;
-    const size_t smB = (size_t)R * N2 * 8;
-    const auto *fwd = (const ulonglong2 *)ctx->d_fwd;
-    const auto *inv = (const ulonglong2 *)ctx->d_inv;
     FG_CHECK(count <= 65535, FG_EINVAL, "ntt: more than 65535 limbs in one batch");
-    dim3 gA(N2 / kColsA, count), gB(N1 / R, count);
     int active = 0;
     for (int v : src.pidx) active += v >= 0;
-    KTimer kt(ctx, "ntt", (double)active * src.rows * N * 8 * 2);
-    if (!inverse) {
-        ntt_fwd_a<<<gA, kNttThreads, smA, ctx->stream>>>(bt, ctx->d_primes, fwd, log_n, s1);
-        Batch b2 = bt;
-        b2.src = b2.dst;
-        b2.src_stride = b2.dst_stride;
-        ntt_fwd_b<<<gB, kNttThreads, smB, ctx->stream>>>(b2, ctx->d_primes, fwd, log_n, s1, R);
-    } else {
-        ntt_inv_b<<<gB, kNttThreads, smB, ctx->stream>>>(bt, ctx->d_primes, inv, log_n, s1, R);
-        Batch b2 = bt;
-        b2.src = b2.dst;
-        b2.src_stride = b2.dst_stride;
-        ntt_inv_a<<<gA, kNttThreads, smA, ctx->stream>>>(b2, ctx->d_primes, inv, ctx->d_ninv,
-                                                         log_n, s1);
+    KTimer kt(ctx, "ntt", (double)active * src.rows * ctx->n * 8 * 2);
+    switch (ctx->log_n) {
+    case 10: ntt_launch_t<10>(ctx, bt, count, inverse); break;
+    case 11: ntt_launch_t<11>(ctx, bt, count, inverse); break;
+    case 12: ntt_launch_t<12>(ctx, bt, count, inverse); break;
+    case 13: ntt_launch_t<13>(ctx, bt, count, inverse); break;
+    case 14: ntt_launch_t<14>(ctx, bt, count, inverse); break;
+    case 15: ntt_launch_t<15>(ctx, bt, count, inverse); break;
+    case 16: ntt_launch_t<16>(ctx, bt, count, inverse); break;
+    default: throw fg_error(FG_EINVAL, "ntt: unsupported ring degree");
     }
     check_launch("ntt", 2);
 }
@@ -854,12 +1004,22 @@ void rotate_mac(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int nco
     FG_CHECK(beta <= kMaxBeta, FG_EINVAL, "too many key-switching digits");
     const int KL = ctx->nq + ctx->np;
     u64 *u = (u64 *)ctx->buf("ks_u", (size_t)ncol * 2 * E * N * 8);
-    dim3 g1((N + 255) / 256, E);
+    dim3 g1((N / 2 + 255) / 256, E);
     {
     KTimer kt(ctx, "ks_ip", ((double)ncol * beta * E + 2.0 * beta * E + 2.0 * ncol * E) * N * 8);
-    k_ks_ip<<<g1, 256, 0, ctx->stream>>>(key.d, KL, lane, ls, digits, ncol, level, beta, E,
-                                         ctx->alpha, ctx->nq, key.galois, ctx->log_n, u,
-                                         ctx->d_primes);
+#define FG_KS_CASE(B)                                                                       \
+    case B:                                                                                 \
+        k_ks_ip<B><<<g1, 256, 0, ctx->stream>>>(key.d, KL, lane, ls, digits, ncol, level, E, \
+                                                ctx->alpha, ctx->nq, key.galois, ctx->log_n, \
+                                                u, ctx->d_primes);                          \
+        break;
+    switch (beta) {
+        FG_KS_CASE(1) FG_KS_CASE(2) FG_KS_CASE(3) FG_KS_CASE(4) FG_KS_CASE(5) FG_KS_CASE(6)
+        FG_KS_CASE(7) FG_KS_CASE(8) FG_KS_CASE(9) FG_KS_CASE(10) FG_KS_CASE(11) FG_KS_CASE(12)
+        FG_KS_CASE(13) FG_KS_CASE(14) FG_KS_CASE(15) FG_KS_CASE(16)
+    default: throw fg_error(FG_EINVAL, "too many key-switching digits");
+    }
+#undef FG_KS_CASE
     check_launch("ks_ip");
     }
     std::vector<int> pp(E);
@@ -886,7 +1046,7 @@ void rotate_mac(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int nco
             dl.out[d] = dests[d0 + d].out;
             dl.mask[d] = dests[d0 + d].mask;
         }
-        dim3 g3((N + 255) / 256, nl);
+        dim3 g3((N / 2 + 255) / 256, nl);
         int masked = 0;
         for (int d = 0; d < dl.n; d++) masked += dl.mask[d] != nullptr;
         KTimer kt(ctx, "moddown_mac",
@@ -912,7 +1072,7 @@ void stay_mac(fg_ctx *ctx, const u64 *lane, int ls, int ncol, int level,
             dl.out[d] = dests[d0 + d].out;
             dl.mask[d] = dests[d0 + d].mask;
         }
-        dim3 g((N + 255) / 256, level + 1);
+        dim3 g((N / 2 + 255) / 256, level + 1);
         const int nl = level + 1;
         KTimer kt(ctx, "stay_mac", ((double)2 * ncol * nl + (double)dl.n * nl +
                                      (double)dl.n * ncol * 2 * nl * 2) * N * 8);
