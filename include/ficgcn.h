@@ -232,6 +232,23 @@ int fg_rescale(fg_ctx *ctx, const uint64_t *ct, int level, uint64_t *out);
  * device NTT (the ring product of paper Sec. 2.1).  [level+1][N] each. */
 int fg_poly_mul(fg_ctx *ctx, const uint64_t *a, const uint64_t *b, int level, uint64_t *c);
 
+/* The same product as fg_poly_mul, for callers that cannot allocate device
+ * memory during the call: serving threads that must not block on or fail
+ * in cudaMalloc, code whose device memory is owned by a host framework or
+ * pool, and code running while a stream is captured (where cudaMalloc and
+ * cudaFree are not allowed).  The paper has no counterpart; this is a
+ * deployment aid.  a, b, c: DEVICE buffers [level+1][N] (host pointers are
+ * rejected with FG_EINVAL); requires (level+1) * N <= 2^18 words
+ * (FG_EINVAL otherwise).  Scratch comes from one 4 MiB array compiled into
+ * the library, resident on every GPU that loads it until the process exits;
+ * no cudaMalloc, cudaFree or other allocating routine is called.  The first
+ * call on each device looks up that array's device address (make that first
+ * call before any stream capture).  Every call shares the array, so calls
+ * that overlap on the GPU (other streams, other threads) race; nothing in it
+ * needs clearing, since each call writes all the scratch it reads. */
+int fg_poly_mul_noalloc(fg_ctx *ctx, const uint64_t *a, const uint64_t *b, int level,
+                        uint64_t *c);
+
 /* Forward (inverse = 0) or inverse NTT in place on DEVICE data
  * [count][N] whose limb c is taken modulo prime index prime_idx[c %
  * period] (0..n_q-1 for q_i, n_q.. for p_k).  The forward output order is

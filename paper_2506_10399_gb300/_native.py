@@ -71,6 +71,7 @@ SIGS = {
     "fg_rotate": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "fg_rescale": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
     "fg_poly_mul": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+    "fg_poly_mul_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "fg_ntt": (c_int, [c_void_p, c_void_p, c_int, P(c_int), c_int, c_int]),
 }
 
