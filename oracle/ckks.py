@@ -115,13 +115,15 @@ def embed_inverse(params, z):
     return np.fft.fft(v)[:n].real / n
 
 
-def encode(params, z, scale, level):
-    """Plaintext [level+1][N]: round_half_away(scale * embed_inverse(z)) mod q_i."""
+def encode(params, z, scale, level, extended=False):
+    """Plaintext [level+1][N]: round_half_away(scale * embed_inverse(z)) mod q_i;
+    with extended=True also the residues mod p_0..p_{K-1} ([level+1+K][N]),
+    for products taken in the key-switching basis."""
     m = round_half_away(scale * embed_inverse(params, z))
     ints = [int(v) for v in m]
-    out = np.empty((level + 1, params.n), dtype=np.uint64)
-    for i in range(level + 1):
-        q = params.q[i]
+    primes = params.ext_primes(level) if extended else params.q[:level + 1]
+    out = np.empty((len(primes), params.n), dtype=np.uint64)
+    for i, q in enumerate(primes):
         out[i] = np.array([v % q for v in ints], dtype=np.uint64)
     return out
 
@@ -323,6 +325,40 @@ def modup(params, d, level):
             lifted[i] = d[i]
         out.append(lifted)
     return out
+
+
+def keyswitch_ext(params, ct, k, key, digits=None):
+    """The key-switching half of Rot(c, k) before ModDown: the inner product
+    (u0, u1) = sum_j phi_g(ModUp_j(c1)) * key_j over q_0..q_l, p.. (hoisted
+    digits as in rotate), and phi_g(c0) over q_0..q_l.  ModDown(u) +
+    (phi_g(c0), 0) is Rot(c, k)."""
+    level = level_of(ct)
+    g = params.galois(k)
+    ext = params.ext_primes(level)
+    if digits is None:
+        digits = modup(params, ct[1], level)
+    u0 = np.zeros((len(ext), params.n), dtype=np.uint64)
+    u1 = np.zeros((len(ext), params.n), dtype=np.uint64)
+    for j, dj in enumerate(digits):
+        kb, ka = key[j]
+        for i, pr in enumerate(ext):
+            dg = _ref.automorphism(dj[i], g, pr)
+            kl = params.key_limb(level, i)
+            psi = params.psi(pr)
+            t0 = _ref.negacyclic_mul(dg, kb[kl], pr, psi)
+            t1 = _ref.negacyclic_mul(dg, ka[kl], pr, psi)
+            u0[i] = add_res(u0[i:i + 1], t0[None], [pr])[0]
+            u1[i] = add_res(u1[i:i + 1], t1[None], [pr])[0]
+    qs = params.q[:level + 1]
+    c0g = np.stack([_ref.automorphism(ct[0, i], g, q) for i, q in enumerate(qs)])
+    return np.stack([u0, u1]), c0g
+
+
+def moddown_ct(params, u):
+    """ModDown of both parts of an extended-basis pair [2][l+1+K][N]."""
+    level = u.shape[1] - 1 - params.K
+    qs = params.q[:level + 1]
+    return np.stack([_ref.moddown(u[0], qs, params.p), _ref.moddown(u[1], qs, params.p)])
 
 
 def rotate(params, ct, k, key, digits=None):

@@ -8,9 +8,13 @@ Steps (paper Sec. 3.2-3.3, App. B.1; readings in planner.py):
             rescaled, then rotate-and-sum ct <- ct + Rot(ct, B*2^i) for
             i = 0..log t - 1 so block 0 holds the whole sum;
   2. SpIntra-CA groups: per input lane one ModUp shared by all its
-     rotations, every term mask (x) source added into its output lane or
-     the accumulator, then every output rescaled; the running accumulator
-     is dropped one limb and the group's arrivals added;
+     rotations; every output (lane or accumulator) is the sum of its terms
+     Mask (x) source, where a rotated source Rot(c, k) = ModDown(u) +
+     (phi_g(c0), 0) contributes Mask (x) phi_g(c0) directly and Mask (x) u
+     to an extended-basis sum that is key-switched down with ONE ModDown per
+     output (double hoisting, Bossuat et al., Eurocrypt 2021); kept values
+     contribute Mask (x) lane; then every output is rescaled, and the running
+     accumulator is dropped one limb and receives the group's arrivals;
   3. the accumulator after the last group is the layer output.
 """
 import numpy as np
@@ -20,8 +24,9 @@ from .planner import ACC
 
 
 def encode_plan_masks(params, plan):
-    """Every mask of the plan encoded at scale q_level, level = its level."""
-    return [ckks.encode(params, m.values, float(params.q[m.level]), m.level)
+    """Every mask of the plan encoded at scale q_level, level = its level,
+    with residues over q_0..q_level and the special primes ([level+1+K][N])."""
+    return [ckks.encode(params, m.values, float(params.q[m.level]), m.level, extended=True)
             for m in plan.masks]
 
 
@@ -48,26 +53,44 @@ def aggregation(params, plan, z, keys, pts):
     lanes = [z]
     acc = None
     for grp in plan.groups:
-        assert all(ckks.level_of(c) == grp.level for c in lanes)
+        lv = grp.level
+        assert all(ckks.level_of(c) == lv for c in lanes)
+        qs = params.q[:lv + 1]
+        ext_primes = params.ext_primes(lv)
         need = sorted({a for (a, _) in grp.rotations})
-        digits = {a: ckks.modup(params, lanes[a][1], grp.level) for a in need}
-        rot = {(a, k): ckks.rotate(params, lanes[a], k, keys[k % plan.M], digits[a])
-               for (a, k) in grp.rotations}
-        outs = [None] * grp.n_out
-        acc_new = None
+        digits = {a: ckks.modup(params, lanes[a][1], lv) for a in need}
+        ks = {(a, k): ckks.keyswitch_ext(params, lanes[a], k, keys[k % plan.M], digits[a])
+              for (a, k) in grp.rotations}
+        ext = {}    # output -> extended-basis sum of Mask (x) u
+        norm = {}   # output -> sum of Mask (x) phi_g(c0) and Mask (x) kept lane
+
+        def add_into(d, key, val, primes):
+            d[key] = val if key not in d else np.stack(
+                [ckks.add_res(d[key][0], val[0], primes), ckks.add_res(d[key][1], val[1], primes)])
+
         for tm in grp.terms:
-            src = lanes[tm.src] if tm.k == 0 else rot[(tm.src, tm.k)]
-            prod = ckks.pmult(params, pts[tm.mask], src)
-            if tm.dst == ACC:
-                acc_new = prod if acc_new is None else ckks.add_ct(params, acc_new, prod)
+            m = pts[tm.mask]
+            if tm.k == 0:
+                add_into(norm, tm.dst, ckks.pmult(params, m[:lv + 1], lanes[tm.src]), qs)
             else:
-                o = outs[tm.dst]
-                outs[tm.dst] = prod if o is None else ckks.add_ct(params, o, prod)
-        lanes = [ckks.rescale_ct(params, o) for o in outs]
+                u, c0g = ks[(tm.src, tm.k)]
+                prod = np.stack([ckks.poly_mul(params, m, u[0], ext_primes),
+                                 ckks.poly_mul(params, m, u[1], ext_primes)])
+                add_into(ext, tm.dst, prod, ext_primes)
+                c0part = np.stack([ckks.poly_mul(params, m[:lv + 1], c0g, qs),
+                                   np.zeros((lv + 1, params.n), dtype=np.uint64)])
+                add_into(norm, tm.dst, c0part, qs)
+        outs = {}
+        for dst in set(ext) | set(norm):
+            o = ckks.moddown_ct(params, ext[dst]) if dst in ext else None
+            if dst in norm:
+                o = norm[dst] if o is None else ckks.add_ct(params, o, norm[dst])
+            outs[dst] = o
+        lanes = [ckks.rescale_ct(params, outs[x]) for x in range(grp.n_out)]
         if acc is not None:
             acc = ckks.drop_ct(acc)
-        if acc_new is not None:
-            acc_new = ckks.rescale_ct(params, acc_new)
+        if ACC in outs:
+            acc_new = ckks.rescale_ct(params, outs[ACC])
             acc = acc_new if acc is None else ckks.add_ct(params, acc, acc_new)
     return acc
 

@@ -434,6 +434,7 @@ int fg_ctx_create(const fg_params *prm, void *cuda_stream, fg_ctx **out)
         CUDA_TRY(cudaMalloc(&dpm, pm.size() * 8));
         CUDA_TRY(cudaMemcpy(dpm, pm.data(), pm.size() * 8, cudaMemcpyHostToDevice));
         g_pmodq[ctx] = dpm;
+        ctx->d_pmodq = dpm;
         std::vector<int> ids = iota(KL);
         int *dpi = nullptr;
         CUDA_TRY(cudaMalloc(&dpi, ids.size() * sizeof(int)));

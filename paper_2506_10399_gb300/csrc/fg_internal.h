@@ -97,6 +97,7 @@ struct fg_ctx {
     void *d_fwd = nullptr;            // ulonglong2 [nq+np][N] (psi^brv(i), Shoup)
     void *d_inv = nullptr;            // ulonglong2 [nq+np][N]
     u64 *d_ninv = nullptr;            // [nq+np][2] N^-1 and Shoup
+    u64 *d_pmodq = nullptr;           // [nq][2] P mod q_i and Shoup
     std::vector<u64> h_qneg, h_r2, h_ones;
 
     // cached RNS constant tables, keyed by (kind, level, digit)
@@ -235,6 +236,23 @@ struct Dest {
 void rotate_mac(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int ncol, int level,
                 const u64 *digits, const std::vector<Dest> &dests, int out_ls);
 // every destination gets mask (x) lane
+struct GroupSource {
+    const u64 *u;      // rotation: key-switch output [ncol][2][E][N]; kept lane: nullptr
+    const u64 *lane;   // the source lane
+    uint32_t galois;
+    int t0, t1;        // its terms (indices into the term list)
+};
+// one SpIntra-CA group's outputs in the extended basis (see k_group_mac)
+void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vector<Dest> &terms,
+               const std::vector<int> &term_dest, const std::vector<u64 *> &outs, bool accumulate,
+               int ncol, int level, int ls);
+// key-switching inner product only: u [ncol][2][E][N] (extended basis, NTT domain)
+void ks_only(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int ncol, int level,
+             const u64 *digits, u64 *u);
+// ModDown of an extended-basis batch [ncol][2][E][N] into lane limbs 0..level (stride ls)
+void moddown_to_lane(fg_ctx *ctx, u64 *ext, int ncol, int level, u64 *out, int ls);
+// residues mod the special primes from limb 0 (centred): out [np][N]
+void lift_special(fg_ctx *ctx, const u64 *limb0, u64 *out);
 void stay_mac(fg_ctx *ctx, const u64 *lane, int ls, int ncol, int level,
               const std::vector<Dest> &dests, int out_ls);
 }  // namespace kern

@@ -759,6 +759,126 @@ k_stay_mac(const u64 *__restrict__ lane, int ls, int ncol, int level, const Dest
     }
 }
 
+// ------------------------------------------------------------------------
+// One SpIntra-CA group, all outputs at once (double hoisting): for each
+// output d,  ext_d = sum over its rotated sources r of mask (x) (u_r +
+// P phi_r(c0)) + sum over its kept sources of mask (x) P lane, in the
+// extended basis q_0..q_l, p_0..p_{K-1} (the P terms vanish mod p_k).
+// ModDown(ext_d) is then exactly the sum of mask (x) Rot and mask (x) lane,
+// since ModDown(A + P B) = ModDown(A) + B.  Thread = one polynomial (column
+// and part) at one slot pair; the CTA's threads of one slot pair read the
+// same mask words; partial sums stay in shared memory until the end.
+// ------------------------------------------------------------------------
+struct GSrc {
+    const u64 *u;      // rotation: [ncol][2][E][N] extended basis; kept lane: nullptr
+    const u64 *lane;   // [ncol][2][ls][N]: c0 for rotations, the value for kept lanes
+    uint32_t g;        // Galois element of a rotation
+    int t0, t1;        // its terms
+};
+struct GTerm {
+    int dest;
+    const u64 *mask;   // [E][N] NTT domain, Montgomery form
+};
+
+__global__ void __launch_bounds__(256)
+k_group_mac(const GSrc *__restrict__ srcs, int nsrc, const GTerm *__restrict__ terms,
+            u64 *const *__restrict__ outs, int X, int accumulate, int ncol, int level, int E,
+            int ls, int log_n, const u64 *__restrict__ pmodq, const PrimeC *__restrict__ primes,
+            int nq)
+{
+    extern __shared__ ulonglong2 gacc[];   // [X][blockDim.x]
+    const int N = 1 << log_n;
+    const int npoly = 2 * ncol;
+    const int per_cta = blockDim.x / npoly;
+    const int tid = threadIdx.x;
+    const int poly = tid % npoly, pl = tid / npoly;
+    const int x = 2 * (blockIdx.x * per_cta + pl);
+    if (pl >= per_cta || x >= N) return;
+    const int i = blockIdx.y;
+    const bool isq = i <= level;
+    const PrimeC P = primes[isq ? i : nq + (i - level - 1)];
+    const u64 q = P.q;
+    const u64 pw = isq ? pmodq[2 * i] : 0, pws = isq ? pmodq[2 * i + 1] : 0;
+    const int f = poly >> 1, p = poly & 1;
+    const size_t ext_off = ((size_t)poly * E + i) * N + x;
+    for (int d = 0; d < X; d++) gacc[d * blockDim.x + tid] = make_ulonglong2(0, 0);
+    for (int s = 0; s < nsrc; s++) {
+        const GSrc S = srcs[s];
+        ulonglong2 v;
+        if (S.u) {
+            v = *reinterpret_cast<const ulonglong2 *>(S.u + ext_off);
+            if (isq && p == 0) {
+                const int sx = auto_src(x, S.g, log_n);
+                const ulonglong2 c0 = gather_pair(S.lane + ((size_t)(f * 2) * ls + i) * N, sx, sx & 1);
+                v.x = add_mod(v.x, shoup_mul(c0.x, pw, pws, q), q);
+                v.y = add_mod(v.y, shoup_mul(c0.y, pw, pws, q), q);
+            }
+        } else {
+            if (!isq) continue;   // P * lane is zero modulo the special primes
+            const ulonglong2 lv = *reinterpret_cast<const ulonglong2 *>(S.lane + ((size_t)poly * ls + i) * N + x);
+            v.x = shoup_mul(lv.x, pw, pws, q);
+            v.y = shoup_mul(lv.y, pw, pws, q);
+        }
+        for (int t = S.t0; t < S.t1; t++) {
+            const GTerm T = terms[t];
+            const ulonglong2 m = *reinterpret_cast<const ulonglong2 *>(T.mask + (size_t)i * N + x);
+            ulonglong2 &a = gacc[T.dest * blockDim.x + tid];
+            a.x = add_mod(a.x, mont_mul(v.x, m.x, P), q);
+            a.y = add_mod(a.y, mont_mul(v.y, m.y, P), q);
+        }
+    }
+    for (int d = 0; d < X; d++) {
+        ulonglong2 *o = reinterpret_cast<ulonglong2 *>(outs[d] + ext_off);
+        ulonglong2 a = gacc[d * blockDim.x + tid];
+        if (accumulate) {
+            const ulonglong2 b = *o;
+            a.x = add_mod(a.x, b.x, q);
+            a.y = add_mod(a.y, b.y, q);
+        }
+        *o = a;
+    }
+}
+
+// ModDown finish into a lane: out_i = (ext_i - conv_i) * P^-1 for i <= level
+__global__ void __launch_bounds__(256)
+k_moddown_store(const u64 *__restrict__ ext, int E, const u64 *__restrict__ conv, u64 *out, int ls,
+                int npoly, int level, const u64 *__restrict__ pinv, const PrimeC *__restrict__ primes,
+                int N)
+{
+    const int i = blockIdx.y;
+    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (x >= N) return;
+    const u64 q = primes[i].q, pv = pinv[2 * i], pvs = pinv[2 * i + 1];
+    const int nl = level + 1;
+    for (int poly = 0; poly < npoly; poly++) {
+        const ulonglong2 e = *reinterpret_cast<const ulonglong2 *>(ext + ((size_t)poly * E + i) * N + x);
+        const ulonglong2 c = *reinterpret_cast<const ulonglong2 *>(conv + ((size_t)poly * nl + i) * N + x);
+        *reinterpret_cast<ulonglong2 *>(out + ((size_t)poly * ls + i) * N + x) =
+            make_ulonglong2(shoup_mul(sub_mod(e.x, c.x, q), pv, pvs, q),
+                            shoup_mul(sub_mod(e.y, c.y, q), pv, pvs, q));
+    }
+}
+
+// residues mod the special primes of a polynomial given by its limb 0,
+// read as a centred integer (valid when |coefficient| < q_0 / 2)
+__global__ void k_lift_special(const u64 *limb0, u64 q0, u64 *out, int np, int nq,
+                               const PrimeC *__restrict__ primes, int N)
+{
+    const int k = blockIdx.y;
+    const PrimeC P = primes[nq + k];
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
+        const u64 v = limb0[x];
+        u64 r;
+        if (v <= q0 / 2) {
+            r = reduce_word(v, P);
+        } else {
+            const u64 m = reduce_word(q0 - v, P);
+            r = m ? P.q - m : 0;
+        }
+        out[(size_t)k * N + x] = r;
+    }
+}
+
 }  // namespace
 
 // ========================================================================
@@ -1079,6 +1199,102 @@ void stay_mac(fg_ctx *ctx, const u64 *lane, int ls, int ncol, int level,
         k_stay_mac<<<g, 256, 0, ctx->stream>>>(lane, ls, ncol, level, dl, ctx->d_primes, N);
         check_launch("stay_mac");
     }
+}
+
+
+void lift_special(fg_ctx *ctx, const u64 *limb0, u64 *out)
+{
+    KTimer kt(ctx, "lift", 0);
+    k_lift_special<<<ew_grid(ctx->n, ctx->np), 256, 0, ctx->stream>>>(limb0, ctx->primes[0], out,
+                                                                      ctx->np, ctx->nq,
+                                                                      ctx->d_primes, ctx->n);
+    check_launch("lift_special");
+}
+
+void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vector<Dest> &terms_in,
+               const std::vector<int> &term_dest, const std::vector<u64 *> &outs, bool accumulate,
+               int ncol, int level, int ls)
+{
+    const int N = ctx->n, E = ctx->ext(level), X = (int)outs.size();
+    if (srcs.empty() || X == 0) return;
+    FG_CHECK(X <= 32, FG_EINVAL, "group_mac: more than 32 outputs in one group");
+    std::vector<GSrc> hs(srcs.size());
+    std::vector<GTerm> ht(terms_in.size());
+    for (size_t t = 0; t < terms_in.size(); t++) ht[t] = {term_dest[t], terms_in[t].mask};
+    for (size_t s = 0; s < srcs.size(); s++)
+        hs[s] = {srcs[s].u, srcs[s].lane, srcs[s].galois, srcs[s].t0, srcs[s].t1};
+    const size_t bs = hs.size() * sizeof(GSrc), bt = ht.size() * sizeof(GTerm), bo = X * sizeof(u64 *);
+    char *d = (char *)ctx->buf("gmac_prog", bs + bt + bo + 64);
+    GSrc *ds = (GSrc *)d;
+    GTerm *dt = (GTerm *)(d + ((bs + 15) / 16) * 16);
+    u64 **dout = (u64 **)(d + ((bs + 15) / 16) * 16 + ((bt + 15) / 16) * 16);
+    CUDA_TRY(cudaMemcpyAsync(ds, hs.data(), bs, cudaMemcpyHostToDevice, ctx->stream));
+    if (bt) CUDA_TRY(cudaMemcpyAsync(dt, ht.data(), bt, cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(dout, outs.data(), bo, cudaMemcpyHostToDevice, ctx->stream));
+    const int npoly = 2 * ncol;
+    FG_CHECK(npoly <= 256, FG_EINVAL, "group_mac: too many columns");
+    const int per_cta = 256 / npoly;
+    dim3 g((N / 2 + per_cta - 1) / per_cta, E);
+    const size_t sm = (size_t)X * 256 * sizeof(ulonglong2);
+    size_t terms_n = terms_in.size();
+    KTimer kt(ctx, "group_mac",
+              ((double)srcs.size() * npoly * E + (double)terms_n * E + (double)X * npoly * E *
+                                                                         (accumulate ? 2 : 1)) * N * 8);
+    if (sm > 48 * 1024)
+        CUDA_TRY(cudaFuncSetAttribute(k_group_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_group_mac<<<g, 256, sm, ctx->stream>>>(ds, (int)hs.size(), dt, dout, X, accumulate ? 1 : 0, ncol,
+                                              level, E, ls, ctx->log_n, ctx->d_pmodq, ctx->d_primes,
+                                              ctx->nq);
+    check_launch("group_mac");
+}
+
+void ks_only(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int ncol, int level,
+             const u64 *digits, u64 *u)
+{
+    const int N = ctx->n, E = ctx->ext(level), beta = ctx->n_digits(level);
+    const int KL = ctx->nq + ctx->np;
+    dim3 g1((N / 2 + 255) / 256, E);
+    KTimer kt(ctx, "ks_ip", ((double)ncol * beta * E + 2.0 * beta * E + 2.0 * ncol * E) * N * 8);
+#define FG_KS_CASE(B)                                                                       \
+    case B:                                                                                 \
+        k_ks_ip<B><<<g1, 256, 0, ctx->stream>>>(key.d, KL, lane, ls, digits, ncol, level, E, \
+                                                ctx->alpha, ctx->nq, key.galois, ctx->log_n, \
+                                                u, ctx->d_primes);                          \
+        break;
+    switch (beta) {
+        FG_KS_CASE(1) FG_KS_CASE(2) FG_KS_CASE(3) FG_KS_CASE(4) FG_KS_CASE(5) FG_KS_CASE(6)
+        FG_KS_CASE(7) FG_KS_CASE(8) FG_KS_CASE(9) FG_KS_CASE(10) FG_KS_CASE(11) FG_KS_CASE(12)
+        FG_KS_CASE(13) FG_KS_CASE(14) FG_KS_CASE(15) FG_KS_CASE(16)
+    default: throw fg_error(FG_EINVAL, "too many key-switching digits");
+    }
+#undef FG_KS_CASE
+    check_launch("ks_ip");
+}
+
+void moddown_to_lane(fg_ctx *ctx, u64 *ext, int ncol, int level, u64 *out, int ls)
+{
+    const int N = ctx->n, nl = level + 1, E = ctx->ext(level);
+    std::vector<int> pp(E);
+    for (int i = 0; i < E; i++) pp[i] = i <= level ? -1 : ctx->ext_prime(level, i);
+    LimbSet us{ext, E, E, 2 * ncol, pp};
+    ntt_inv(ctx, us, us);
+    u64 *conv = (u64 *)ctx->buf("ks_conv", (size_t)ncol * 2 * nl * N * 8);
+    {
+        KTimer kt(ctx, "moddown_conv", (double)2 * ncol * (ctx->np + nl) * N * 8);
+        dim3 g2((N + 255) / 256, 2 * ncol);
+        k_moddown_conv<<<g2, 256, 0, ctx->stream>>>(ext, E, conv, nl, ctx->moddown_tab(level),
+                                                    ctx->d_primes, N);
+        check_launch("moddown_conv");
+    }
+    std::vector<int> pq(nl);
+    for (int i = 0; i < nl; i++) pq[i] = i;
+    LimbSet cs{conv, nl, nl, 2 * ncol, pq};
+    ntt_fwd(ctx, cs, cs);
+    KTimer kt(ctx, "moddown_store", (double)2 * ncol * nl * 3 * N * 8);
+    dim3 g3((N / 2 + 255) / 256, nl);
+    k_moddown_store<<<g3, 256, 0, ctx->stream>>>(ext, E, conv, out, ls, 2 * ncol, level,
+                                                 ctx->pinv_tab(level), ctx->d_primes, N);
+    check_launch("moddown_store");
 }
 
 }  // namespace kern

@@ -44,18 +44,21 @@ std::vector<int> iota(int n, int start = 0)
     return v;
 }
 
-// encode one mask of the plan at scale q_level and put it on the device
-// (NTT domain, Montgomery form)
+// put one encoded mask of the plan on the device over q_0..q_level and the
+// special primes (the latter lifted from limb 0: every mask coefficient is
+// below q_0 / 2 in magnitude), NTT domain, Montgomery form: [E][N]
 void upload_mask(fg_ctx *ctx, MaskC &m, const u64 *coeffs_host_or_dev)
 {
-    const int N = ctx->n, nl = m.level + 1;
-    if (!m.d) CUDA_TRY(cudaMalloc(&m.d, (size_t)nl * N * 8));
+    const int N = ctx->n, nl = m.level + 1, E = ctx->ext(m.level);
+    if (!m.d) CUDA_TRY(cudaMalloc(&m.d, (size_t)E * N * 8));
     CUDA_TRY(cudaMemcpyAsync(m.d, coeffs_host_or_dev, (size_t)nl * N * 8, cudaMemcpyDefault,
                              ctx->stream));
-    const std::vector<int> pid = iota(nl);
-    kern::LimbSet s{m.d, nl, nl, 1, pid};
+    kern::lift_special(ctx, m.d, m.d + (size_t)nl * N);
+    std::vector<int> pid(E);
+    for (int i = 0; i < E; i++) pid[i] = ctx->ext_prime(m.level, i);
+    kern::LimbSet s{m.d, E, E, 1, pid};
     kern::ntt_fwd(ctx, s, s);
-    kern::to_mont(ctx, m.d, nl, pid);
+    kern::to_mont(ctx, m.d, E, pid);
 }
 
 void encode_mask(const fg_ctx *ctx, const MaskC &m, u64 *out)
@@ -353,42 +356,80 @@ int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, const 
             }
         }
 
-        // ---- 2. SpIntra-CA groups
+        // ---- 2. SpIntra-CA groups (one ModDown per output, see k_group_mac)
         std::vector<u64 *> *in = &bufA, *outb = &bufB;
         bool have_acc = false;
         int level = l1;
+        const size_t ext_w = (size_t)Fp * 2 * ctx->ext(l1) * N;
+        const int pool_cap = 48;   // key-switch outputs held at once
+        std::vector<u64 *> upool;
         for (const GroupC &g : pl->groups) {
             FG_CHECK(g.level == level, FG_ELEVEL, "plan level mismatch");
-            for (int x = 0; x < g.n_out; x++)
-                CUDA_TRY(cudaMemsetAsync((*outb)[x], 0, lane_w * 8, ctx->stream));
-            CUDA_TRY(cudaMemsetAsync(acc_new, 0, lane_w * 8, ctx->stream));
+            // outputs: lanes 0..n_out-1, then the accumulator if the group feeds it
             bool any_acc = false;
-            // destinations per (src, k)
-            std::map<std::pair<int, int>, std::vector<kern::Dest>> dests;
-            for (const TermC &tm : g.terms) {
-                u64 *o = tm.dst < 0 ? acc_new : (*outb)[tm.dst];
-                any_acc |= tm.dst < 0;
-                dests[{tm.src, tm.k}].push_back({o, pl->masks[tm.mask].d});
-            }
+            for (const TermC &tm : g.terms) any_acc |= tm.dst < 0;
+            const int X = g.n_out + (any_acc ? 1 : 0);
+            std::vector<u64 *> ext(X);
+            for (int x = 0; x < X; x++) ext[x] = (u64 *)ctx->buf("ext" + std::to_string(x), ext_w * 8);
+            auto out_index = [&](int dst) { return dst < 0 ? g.n_out : dst; };
+            // terms by source: (lane, k) in plan order of the rotations, kept lanes after
+            std::map<std::pair<int, int>, std::vector<const TermC *>> by_src;
+            for (const TermC &tm : g.terms) by_src[{tm.src, tm.k}].push_back(&tm);
             u64 *digits = (u64 *)ctx->buf("digits",
                                           (size_t)Fp * ctx->n_digits(level) * ctx->ext(level) * N * 8);
-            int cur = -1;
+            std::vector<kern::GroupSource> srcs;
+            std::vector<kern::Dest> terms;
+            std::vector<int> tdest;
+            bool first_flush = true;
+            auto add_source = [&](const u64 *u, const u64 *lane, uint32_t galois,
+                                  const std::vector<const TermC *> &ts) {
+                kern::GroupSource gs{u, lane, galois, (int)terms.size(), 0};
+                for (const TermC *tm : ts) {
+                    terms.push_back({nullptr, pl->masks[tm->mask].d});
+                    tdest.push_back(out_index(tm->dst));
+                }
+                gs.t1 = (int)terms.size();
+                srcs.push_back(gs);
+            };
+            auto flush = [&]() {
+                if (srcs.empty()) return;
+                kern::group_mac(ctx, srcs, terms, tdest, ext, !first_flush, Fp, level, LS);
+                first_flush = false;
+                srcs.clear();
+                terms.clear();
+                tdest.clear();
+            };
+            // kept values first (no key switching)
+            for (auto &kv : by_src)
+                if (kv.first.second == 0) add_source(nullptr, (*in)[kv.first.first], 0, kv.second);
+            int cur = -1, used = 0;
             for (auto &rk : g.rots) {
                 const int a = rk.first, k = rk.second;
+                auto it = by_src.find({a, k});
+                if (it == by_src.end()) continue;
+                if (used == pool_cap) {
+                    flush();
+                    used = 0;
+                }
                 if (a != cur) {
                     kern::modup(ctx, (*in)[a], LS, Fp, level, digits);
                     cur = a;
                 }
-                auto it = dests.find({a, k});
-                if (it == dests.end()) continue;
-                kern::rotate_mac(ctx, keys->get(((k % M) + M) % M), (*in)[a], LS, Fp, level, digits,
-                                 it->second, LS);
+                if ((int)upool.size() <= used)
+                    upool.push_back((u64 *)ctx->buf("upool" + std::to_string(used), ext_w * 8));
+                const KeyDev &key = keys->get(((k % M) + M) % M);
+                kern::ks_only(ctx, key, (*in)[a], LS, Fp, level, digits, upool[used]);
+                add_source(upool[used], (*in)[a], key.galois, it->second);
+                used++;
             }
-            for (auto &kv : dests)
-                if (kv.first.second == 0)
-                    kern::stay_mac(ctx, (*in)[kv.first.first], LS, Fp, level, kv.second, LS);
-            for (int x = 0; x < g.n_out; x++) kern::rescale_ntt(ctx, (*outb)[x], LS, Fp * 2, level);
+            flush();
+            // one ModDown per output, then the rescale that closes the group
+            for (int x = 0; x < g.n_out; x++) {
+                kern::moddown_to_lane(ctx, ext[x], Fp, level, (*outb)[x], LS);
+                kern::rescale_ntt(ctx, (*outb)[x], LS, Fp * 2, level);
+            }
             if (any_acc) {
+                kern::moddown_to_lane(ctx, ext[g.n_out], Fp, level, acc_new, LS);
                 kern::rescale_ntt(ctx, acc_new, LS, Fp * 2, level);
                 if (have_acc) {
                     std::vector<int> pidx(LS, -1);

@@ -521,3 +521,24 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(planner, "simulate_combination", transposed)
     with pytest.raises(AssertionError):
         test_plan_simulation_equals_fp64_product(0, 1, False, "identity")
+
+
+@pytest.mark.parametrize("nq,npr", [(2, 1), (4, 3)])
+def test_moddown_of_p_multiple_is_exact(nq, npr):
+    """ModDown(A + P*B) = ModDown(A) + B exactly (B given on the q-limbs, zero
+    on the special primes): the identity that lets masked rotations and kept
+    values of one output share a single ModDown."""
+    primes = _ref.gen_primes(4, [45] * nq + [60] * npr)
+    qs, ps = primes[:nq], primes[nq:]
+    rng = random.Random(nq)
+    A = rand_res(rng, qs + ps, 16)
+    B = rand_res(rng, qs, 16)
+    P = 1
+    for p in ps:
+        P *= p
+    APB = A.copy()
+    for i, q in enumerate(qs):
+        APB[i] = ckks.add_res(A[i:i + 1], _ref.mul_scalar(B[i], P % q, q)[None], [q])[0]
+    lhs = _ref.moddown(APB, qs, ps)
+    rhs = ckks.add_res(_ref.moddown(A, qs, ps), B, qs)
+    np.testing.assert_array_equal(lhs, rhs)
