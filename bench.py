@@ -37,7 +37,8 @@ MIN_OUT_LEVEL = 10
 SEED = 2025
 METRIC = "encrypted A.X.W layer latency (ms) at N=2^16"
 UNIT = "ms/layer"
-CLASSES = ["ntt", "ks_ip", "moddown_mac", "moddown_conv", "modup_conv", "comb", "rescale", "stay_mac"]
+CLASSES = ["ntt", "ks_ip", "group_mac", "moddown_conv", "moddown_store", "modup_conv", "comb",
+           "rescale", "lift"]
 
 
 def config_desc():
@@ -278,8 +279,13 @@ def run_ours(args):
         if r is not None and rank == 0:
             print(json.dumps({"ntt": r}))
         return 0
-    c = wl.CONFIGS[WORKLOAD]
+    c = dict(wl.CONFIGS[WORKLOAD])
     over = {}
+    radix, min_out = RADIX_BITS, MIN_OUT_LEVEL
+    if args.small:   # same ring and columns, fewer primes and nodes: small ncu captures
+        c.update(q_bits=[60] + [45] * 7, p_bits=[60] * 2, alpha=4)
+        over.update(V=4000, F=32)
+        radix, min_out = 3, 0
     if args.features:
         over["F"] = args.features
     if args.nodes:
@@ -288,8 +294,8 @@ def run_ours(args):
     perm = wl.random_order(w.V, 1 << (c["log_n"] - 1), SEED)
     t_setup = time.perf_counter()
     ctx = fg.Context(**c)
-    plan = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=1, radix_bits=RADIX_BITS,
-                         min_out_level=MIN_OUT_LEVEL)
+    plan = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=1, radix_bits=radix,
+                         min_out_level=min_out)
     info = plan.info()
     sk, evk = fg.keygen(ctx, SEED + rank, plan.rotation_amounts())
     keys = fg.load_evk(ctx, evk)
@@ -428,6 +434,7 @@ def main():
     ap.add_argument("--profile", action="store_true")
     ap.add_argument("--features", type=int, default=0)
     ap.add_argument("--nodes", type=int, default=0)
+    ap.add_argument("--small", action="store_true", help="small parameter set for ncu captures")
     ap.add_argument("--ntt", action="store_true", help="NTT throughput only")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -776,66 +776,118 @@ struct GSrc {
     int t0, t1;        // its terms
 };
 struct GTerm {
-    int dest;
+    int src;           // source index (terms are sorted by output)
     const u64 *mask;   // [E][N] NTT domain, Montgomery form
 };
 
-__global__ void __launch_bounds__(256)
-k_group_mac(const GSrc *__restrict__ srcs, int nsrc, const GTerm *__restrict__ terms,
-            u64 *const *__restrict__ outs, int X, int accumulate, int ncol, int level, int E,
-            int ls, int log_n, const u64 *__restrict__ pmodq, const PrimeC *__restrict__ primes,
-            int nq)
+// Partial sums are the raw 128-bit products v * m~ (m~ = mask R mod q, its
+// Montgomery form), added without reduction; one Montgomery reduction of the
+// total gives sum v * m mod q.  That needs total < q 2^64: every product is
+// below q^2 < 2^120, so up to 255 terms per output and launch are safe after
+// folding the high word mod q (a launch takes at most kGmacSrc sources, and
+// each source feeds an output at most once).
+//
+// Thread = one polynomial (column, part) at one slot pair; a CTA covers the
+// npoly polynomials of 128 / npoly slot pairs of one limb.  Phase 1 stages,
+// with independent loads, every source value of the thread (u + P phi(c0)
+// for rotations, P lane for kept values) and the CTA's mask words in shared
+// memory; phase 2 walks the outputs, each a register sum over its terms.
+constexpr int kGmacThreads = 128;
+constexpr int kGmacSrc = 24;
+constexpr int kGmacBatch = 4;   // source loads in flight per thread
+
+__global__ void __launch_bounds__(kGmacThreads)
+k_group_mac(const GSrc *__restrict__ srcs, int nsrc, const GTerm *__restrict__ terms, int nterm,
+            const int *__restrict__ dest_first, u64 *const *__restrict__ outs, int X,
+            int accumulate, int ncol, int level, int E, int ls, int log_n,
+            const u64 *__restrict__ pmodq, const PrimeC *__restrict__ primes, int nq)
 {
-    extern __shared__ ulonglong2 gacc[];   // [X][blockDim.x]
-    const int N = 1 << log_n;
+    extern __shared__ __align__(16) unsigned char gsm[];
     const int npoly = 2 * ncol;
-    const int per_cta = blockDim.x / npoly;
+    const int pp_n = kGmacThreads / npoly;          // slot pairs per CTA
+    ulonglong2 *vsm = reinterpret_cast<ulonglong2 *>(gsm);                  // [nsrc][threads]
+    ulonglong2 *msm = vsm + (size_t)nsrc * kGmacThreads;                    // [nterm][pp_n]
+    GSrc *ssrc = reinterpret_cast<GSrc *>(msm + (size_t)nterm * pp_n);      // [nsrc]
+    int *tsrc = reinterpret_cast<int *>(ssrc + nsrc);                       // [nterm]
+    int *dfirst = tsrc + nterm;                                             // [X + 1]
+    const int N = 1 << log_n;
     const int tid = threadIdx.x;
-    const int poly = tid % npoly, pl = tid / npoly;
-    const int x = 2 * (blockIdx.x * per_cta + pl);
-    if (pl >= per_cta || x >= N) return;
+    for (int k = tid; k < nsrc; k += kGmacThreads) ssrc[k] = srcs[k];
+    for (int k = tid; k < nterm; k += kGmacThreads) tsrc[k] = terms[k].src;
+    for (int k = tid; k <= X; k += kGmacThreads) dfirst[k] = dest_first[k];
+    const int poly = tid % npoly, pp = tid / npoly;
+    const int x = 2 * (blockIdx.x * pp_n + pp);
+    const bool act = pp < pp_n && x < N;
     const int i = blockIdx.y;
     const bool isq = i <= level;
     const PrimeC P = primes[isq ? i : nq + (i - level - 1)];
     const u64 q = P.q;
     const u64 pw = isq ? pmodq[2 * i] : 0, pws = isq ? pmodq[2 * i + 1] : 0;
-    const int f = poly >> 1, p = poly & 1;
     const size_t ext_off = ((size_t)poly * E + i) * N + x;
-    for (int d = 0; d < X; d++) gacc[d * blockDim.x + tid] = make_ulonglong2(0, 0);
-    for (int s = 0; s < nsrc; s++) {
-        const GSrc S = srcs[s];
-        ulonglong2 v;
-        if (S.u) {
-            v = *reinterpret_cast<const ulonglong2 *>(S.u + ext_off);
-            if (isq && p == 0) {
-                const int sx = auto_src(x, S.g, log_n);
-                const ulonglong2 c0 = gather_pair(S.lane + ((size_t)(f * 2) * ls + i) * N, sx, sx & 1);
-                v.x = add_mod(v.x, shoup_mul(c0.x, pw, pws, q), q);
-                v.y = add_mod(v.y, shoup_mul(c0.y, pw, pws, q), q);
+    // masks: term t, pair k of this CTA
+    for (int e = tid; e < nterm * pp_n; e += kGmacThreads) {
+        const int t = e / pp_n, k = e % pp_n;
+        const int xx = 2 * (blockIdx.x * pp_n + k);
+        msm[e] = xx < N ? *reinterpret_cast<const ulonglong2 *>(terms[t].mask + (size_t)i * N + xx)
+                        : make_ulonglong2(0, 0);
+    }
+    __syncthreads();
+    if (act) {
+        const int f = poly >> 1, p = poly & 1;
+        const bool add_c0 = isq && p == 0;
+        for (int s0 = 0; s0 < nsrc; s0 += kGmacBatch) {
+            ulonglong2 vv[kGmacBatch], cc[kGmacBatch];
+#pragma unroll
+            for (int k = 0; k < kGmacBatch; k++) {   // issue every load of the batch first
+                vv[k] = make_ulonglong2(0, 0);
+                cc[k] = make_ulonglong2(0, 0);
+                if (s0 + k < nsrc) {
+                    const GSrc &S = ssrc[s0 + k];
+                    if (S.u) {
+                        vv[k] = *reinterpret_cast<const ulonglong2 *>(S.u + ext_off);
+                        if (add_c0) {
+                            const int sx = auto_src(x, S.g, log_n);
+                            cc[k] = gather_pair(S.lane + ((size_t)(f * 2) * ls + i) * N, sx, sx & 1);
+                        }
+                    } else if (isq) {
+                        cc[k] = *reinterpret_cast<const ulonglong2 *>(S.lane + ((size_t)poly * ls + i) * N + x);
+                    }
+                }
             }
-        } else {
-            if (!isq) continue;   // P * lane is zero modulo the special primes
-            const ulonglong2 lv = *reinterpret_cast<const ulonglong2 *>(S.lane + ((size_t)poly * ls + i) * N + x);
-            v.x = shoup_mul(lv.x, pw, pws, q);
-            v.y = shoup_mul(lv.y, pw, pws, q);
-        }
-        for (int t = S.t0; t < S.t1; t++) {
-            const GTerm T = terms[t];
-            const ulonglong2 m = *reinterpret_cast<const ulonglong2 *>(T.mask + (size_t)i * N + x);
-            ulonglong2 &a = gacc[T.dest * blockDim.x + tid];
-            a.x = add_mod(a.x, mont_mul(v.x, m.x, P), q);
-            a.y = add_mod(a.y, mont_mul(v.y, m.y, P), q);
+#pragma unroll
+            for (int k = 0; k < kGmacBatch; k++) {
+                if (s0 + k < nsrc) {
+                    ulonglong2 v = vv[k];
+                    if (isq && (add_c0 || !ssrc[s0 + k].u)) {
+                        // rotation: u + P phi(c0); kept lane: P lane (0 mod the special primes)
+                        v.x = add_mod(v.x, shoup_mul(cc[k].x, pw, pws, q), q);
+                        v.y = add_mod(v.y, shoup_mul(cc[k].y, pw, pws, q), q);
+                    }
+                    vsm[(size_t)(s0 + k) * kGmacThreads + tid] = v;
+                }
+            }
         }
     }
+    __syncthreads();
+    if (!act) return;
     for (int d = 0; d < X; d++) {
+        u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
+        const int t1 = dfirst[d + 1];
+#pragma unroll 4
+        for (int t = dfirst[d]; t < t1; t++) {
+            const ulonglong2 v = vsm[(size_t)tsrc[t] * kGmacThreads + tid];
+            const ulonglong2 m = msm[t * pp_n + pp];
+            mac128(hi0, lo0, v.x, m.x);
+            mac128(hi1, lo1, v.y, m.y);
+        }
+        ulonglong2 r = make_ulonglong2(redc(reduce_word(hi0, P), lo0, P), redc(reduce_word(hi1, P), lo1, P));
         ulonglong2 *o = reinterpret_cast<ulonglong2 *>(outs[d] + ext_off);
-        ulonglong2 a = gacc[d * blockDim.x + tid];
         if (accumulate) {
             const ulonglong2 b = *o;
-            a.x = add_mod(a.x, b.x, q);
-            a.y = add_mod(a.y, b.y, q);
+            r.x = add_mod(r.x, b.x, q);
+            r.y = add_mod(r.y, b.y, q);
         }
-        *o = a;
+        *o = r;
     }
 }
 
@@ -1217,34 +1269,47 @@ void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vec
 {
     const int N = ctx->n, E = ctx->ext(level), X = (int)outs.size();
     if (srcs.empty() || X == 0) return;
-    FG_CHECK(X <= 32, FG_EINVAL, "group_mac: more than 32 outputs in one group");
-    std::vector<GSrc> hs(srcs.size());
-    std::vector<GTerm> ht(terms_in.size());
-    for (size_t t = 0; t < terms_in.size(); t++) ht[t] = {term_dest[t], terms_in[t].mask};
+    FG_CHECK((int)srcs.size() <= kGmacSrc, FG_EINVAL, "group_mac: too many sources in one launch");
+    // terms sorted by output, each naming its source
+    std::vector<int> src_of(terms_in.size());
     for (size_t s = 0; s < srcs.size(); s++)
-        hs[s] = {srcs[s].u, srcs[s].lane, srcs[s].galois, srcs[s].t0, srcs[s].t1};
-    const size_t bs = hs.size() * sizeof(GSrc), bt = ht.size() * sizeof(GTerm), bo = X * sizeof(u64 *);
-    char *d = (char *)ctx->buf("gmac_prog", bs + bt + bo + 64);
+        for (int t = srcs[s].t0; t < srcs[s].t1; t++) src_of[t] = (int)s;
+    std::vector<GTerm> ht;
+    std::vector<int> first(X + 1, 0);
+    for (int d = 0; d < X; d++) {
+        first[d] = (int)ht.size();
+        for (size_t t = 0; t < terms_in.size(); t++)
+            if (term_dest[t] == d) ht.push_back({src_of[t], terms_in[t].mask});
+    }
+    first[X] = (int)ht.size();
+    std::vector<GSrc> hs(srcs.size());
+    for (size_t s = 0; s < srcs.size(); s++) hs[s] = {srcs[s].u, srcs[s].lane, srcs[s].galois, 0, 0};
+    const size_t bs = hs.size() * sizeof(GSrc), bt = ht.size() * sizeof(GTerm);
+    const size_t bf = first.size() * sizeof(int), bo = X * sizeof(u64 *);
+    auto up = [](size_t b) { return ((b + 15) / 16) * 16; };
+    char *d = (char *)ctx->buf("gmac_prog", up(bs) + up(bt) + up(bf) + up(bo) + 64);
     GSrc *ds = (GSrc *)d;
-    GTerm *dt = (GTerm *)(d + ((bs + 15) / 16) * 16);
-    u64 **dout = (u64 **)(d + ((bs + 15) / 16) * 16 + ((bt + 15) / 16) * 16);
+    GTerm *dt = (GTerm *)(d + up(bs));
+    int *df = (int *)(d + up(bs) + up(bt));
+    u64 **dout = (u64 **)(d + up(bs) + up(bt) + up(bf));
     CUDA_TRY(cudaMemcpyAsync(ds, hs.data(), bs, cudaMemcpyHostToDevice, ctx->stream));
     if (bt) CUDA_TRY(cudaMemcpyAsync(dt, ht.data(), bt, cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(df, first.data(), bf, cudaMemcpyHostToDevice, ctx->stream));
     CUDA_TRY(cudaMemcpyAsync(dout, outs.data(), bo, cudaMemcpyHostToDevice, ctx->stream));
     const int npoly = 2 * ncol;
-    FG_CHECK(npoly <= 256, FG_EINVAL, "group_mac: too many columns");
-    const int per_cta = 256 / npoly;
-    dim3 g((N / 2 + per_cta - 1) / per_cta, E);
-    const size_t sm = (size_t)X * 256 * sizeof(ulonglong2);
-    size_t terms_n = terms_in.size();
+    FG_CHECK(npoly <= kGmacThreads, FG_EINVAL, "group_mac: too many columns");
+    const int pp_n = kGmacThreads / npoly;
+    dim3 g((N / 2 + pp_n - 1) / pp_n, E);
+    const size_t sm = (size_t)hs.size() * kGmacThreads * 16 + (size_t)ht.size() * pp_n * 16 +
+                      hs.size() * sizeof(GSrc) + ht.size() * sizeof(int) + (X + 1) * sizeof(int) + 16;
+    FG_CHECK(sm <= 220 * 1024, FG_EINVAL, "group_mac: group program too large for shared memory");
     KTimer kt(ctx, "group_mac",
-              ((double)srcs.size() * npoly * E + (double)terms_n * E + (double)X * npoly * E *
-                                                                         (accumulate ? 2 : 1)) * N * 8);
-    if (sm > 48 * 1024)
-        CUDA_TRY(cudaFuncSetAttribute(k_group_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_group_mac<<<g, 256, sm, ctx->stream>>>(ds, (int)hs.size(), dt, dout, X, accumulate ? 1 : 0, ncol,
-                                              level, E, ls, ctx->log_n, ctx->d_pmodq, ctx->d_primes,
-                                              ctx->nq);
+              ((double)srcs.size() * npoly * E + (double)ht.size() * E +
+               (double)X * npoly * E * (accumulate ? 2 : 1)) * N * 8);
+    CUDA_TRY(cudaFuncSetAttribute(k_group_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_group_mac<<<g, kGmacThreads, sm, ctx->stream>>>(ds, (int)hs.size(), dt, (int)ht.size(), df, dout, X,
+                                                      accumulate ? 1 : 0, ncol, level, E, ls,
+                                                      ctx->log_n, ctx->d_pmodq, ctx->d_primes, ctx->nq);
     check_launch("group_mac");
 }
 

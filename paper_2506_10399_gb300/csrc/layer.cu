@@ -361,7 +361,7 @@ int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, const 
         bool have_acc = false;
         int level = l1;
         const size_t ext_w = (size_t)Fp * 2 * ctx->ext(l1) * N;
-        const int pool_cap = 48;   // key-switch outputs held at once
+        const int pool_cap = 24;   // key-switch outputs held at once (sources per group_mac)
         std::vector<u64 *> upool;
         for (const GroupC &g : pl->groups) {
             FG_CHECK(g.level == level, FG_ELEVEL, "plan level mismatch");
@@ -381,8 +381,10 @@ int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, const 
             std::vector<kern::Dest> terms;
             std::vector<int> tdest;
             bool first_flush = true;
+            std::vector<int> dest_terms(X, 0);   // terms per output since the last flush
             auto add_source = [&](const u64 *u, const u64 *lane, uint32_t galois,
                                   const std::vector<const TermC *> &ts) {
+                for (const TermC *tm : ts) dest_terms[out_index(tm->dst)]++;
                 kern::GroupSource gs{u, lane, galois, (int)terms.size(), 0};
                 for (const TermC *tm : ts) {
                     terms.push_back({nullptr, pl->masks[tm->mask].d});
@@ -393,11 +395,35 @@ int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, const 
             };
             auto flush = [&]() {
                 if (srcs.empty()) return;
-                kern::group_mac(ctx, srcs, terms, tdest, ext, !first_flush, Fp, level, LS);
+                // outputs in slices of at most 20 (shared-memory partial sums)
+                for (int x0 = 0; x0 < X; x0 += 64) {
+                    const int xn = std::min(64, X - x0);
+                    std::vector<kern::GroupSource> ss;
+                    std::vector<kern::Dest> tt;
+                    std::vector<int> td;
+                    for (const auto &gs : srcs) {
+                        kern::GroupSource g2 = gs;
+                        g2.t0 = (int)tt.size();
+                        for (int t = gs.t0; t < gs.t1; t++)
+                            if (tdest[t] >= x0 && tdest[t] < x0 + xn) {
+                                tt.push_back(terms[t]);
+                                td.push_back(tdest[t] - x0);
+                            }
+                        g2.t1 = (int)tt.size();
+                        if (g2.t1 > g2.t0) ss.push_back(g2);
+                    }
+                    std::vector<u64 *> oo(ext.begin() + x0, ext.begin() + x0 + xn);
+                    if (ss.empty() && first_flush) {
+                        for (u64 *o : oo) CUDA_TRY(cudaMemsetAsync(o, 0, ext_w * 8, ctx->stream));
+                        continue;
+                    }
+                    if (!ss.empty()) kern::group_mac(ctx, ss, tt, td, oo, !first_flush, Fp, level, LS);
+                }
                 first_flush = false;
                 srcs.clear();
                 terms.clear();
                 tdest.clear();
+                std::fill(dest_terms.begin(), dest_terms.end(), 0);
             };
             // kept values first (no key switching)
             for (auto &kv : by_src)
@@ -407,7 +433,9 @@ int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, const 
                 const int a = rk.first, k = rk.second;
                 auto it = by_src.find({a, k});
                 if (it == by_src.end()) continue;
-                if (used == pool_cap) {
+                bool full = used == pool_cap || (int)srcs.size() >= 24;
+                for (const TermC *tm : it->second) full |= dest_terms[out_index(tm->dst)] >= 255;
+                if (full) {
                     flush();
                     used = 0;
                 }
