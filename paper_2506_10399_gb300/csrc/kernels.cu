@@ -76,6 +76,264 @@ __device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, const ulonglong2 w, u64 
     Y = shoup_lazy(U - V + q2, w.x, w.y, q);
 }
 
+// ------------------------------------------------------------------------
+// log N = 16: radix-16 rounds.  Every thread holds 16 elements in registers
+// for four stages, so each pass makes two shared-memory round trips
+// (N = 256 x 256; pass A on columns, pass B on rows).  For primes below
+// 2^47 the butterflies skip every conditional reduction: forward values
+// grow by at most 2q per stage (< 33q after 16 stages), inverse values
+// double per stage (< 2^16 q), both far below 2^64; one reduction at the
+// end restores [0, q).  Larger primes keep Harvey's bounds (< 4q, < 2q).
+// ------------------------------------------------------------------------
+template <bool LAZY>
+__device__ __forceinline__ void ct16(u64 (&v)[16], const ulonglong2 (&w)[15], u64 q, u64 q2)
+{
+#pragma unroll
+    for (int st = 0; st < 4; st++) {
+        const int h = 8 >> st;
+#pragma unroll
+        for (int m = 0; m < 16; m++) {
+            if ((m & h) == 0) {
+                const ulonglong2 tw = w[(1 << st) - 1 + (m >> (4 - st))];
+                u64 X = v[m], Y = v[m + h];
+                if (!LAZY) X = X >= q2 ? X - q2 : X;
+                const u64 T = shoup_lazy(Y, tw.x, tw.y, q);
+                v[m + h] = X - T + q2;
+                v[m] = X + T;
+            }
+        }
+    }
+}
+
+// k0: number of inverse stages already applied to these values (lazy bound 2^k0 q)
+template <bool LAZY>
+__device__ __forceinline__ void gs16(u64 (&v)[16], const ulonglong2 (&w)[15], u64 q, u64 q2, int k0)
+{
+#pragma unroll
+    for (int st = 3; st >= 0; st--) {
+        const int h = 8 >> st;
+        const u64 qb = LAZY ? (q << (k0 + 3 - st)) : q2;
+#pragma unroll
+        for (int m = 0; m < 16; m++) {
+            if ((m & h) == 0) {
+                const ulonglong2 tw = w[(1 << st) - 1 + (m >> (4 - st))];
+                const u64 U = v[m], V = v[m + h];
+                const u64 S = U + V;
+                v[m] = LAZY ? S : (S >= q2 ? S - q2 : S);
+                v[m + h] = shoup_lazy(U - V + qb, tw.x, tw.y, q);
+            }
+        }
+    }
+}
+
+constexpr int kR16Row = 272;   // 256 elements + 16 pad words per row (pass B shared memory)
+__device__ __forceinline__ int pad16(int pos) { return pos + (pos >> 4); }
+
+template <bool LAZY>
+__device__ __forceinline__ void fwd_a16_body(const u64 *s, u64 *d, const ulonglong2 *stw, u64 q, u64 *sm)
+{
+    const int t = threadIdx.x, c = t & 15, r = t >> 4;   // r: r0 in round 1, r1 in round 2
+    constexpr int N2 = 256;
+    const u64 q2 = 2 * q;
+    u64 v[16];
+    ulonglong2 w[15];
+#pragma unroll
+    for (int m = 0; m < 16; m++) v[m] = s[(size_t)(r + 16 * m) * N2 + c];
+#pragma unroll
+    for (int k = 0; k < 15; k++) w[k] = stw[k + 1];   // stage st, group g at (1 << st) + g
+    ct16<LAZY>(v, w, q, q2);
+#pragma unroll
+    for (int m = 0; m < 16; m++) sm[(r + 16 * m) * 16 + c] = v[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; m++) v[m] = sm[(16 * r + m) * 16 + c];
+#pragma unroll
+    for (int st = 0; st < 4; st++)
+#pragma unroll
+        for (int g = 0; g < (1 << st); g++) w[(1 << st) - 1 + g] = stw[(1 << (st + 4)) + (r << st) + g];
+    ct16<LAZY>(v, w, q, q2);
+#pragma unroll
+    for (int m = 0; m < 16; m++) d[(size_t)(16 * r + m) * N2 + c] = v[m];   // lazy
+}
+
+__global__ void __launch_bounds__(256)
+ntt16_fwd_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ tw)
+{
+    const int limb = blockIdx.y;
+    const int col = limb % bt.per_row, row = limb / bt.per_row;
+    const int pi = bt.pidx[col];
+    if (pi < 0) return;
+    __shared__ u64 sm[256 * 16];
+    __shared__ ulonglong2 stw[256];
+    const u64 q = primes[pi].q;
+    const ulonglong2 *twp = tw + (size_t)pi * 65536;
+    stw[threadIdx.x] = twp[threadIdx.x];
+    __syncthreads();
+    const int c0 = blockIdx.x * 16;
+    const u64 *src = bt.src + ((size_t)row * bt.src_stride + col) * 65536 + c0;
+    u64 *dst = bt.dst + ((size_t)row * bt.dst_stride + col) * 65536 + c0;
+    if (q < (1ull << 47)) fwd_a16_body<true>(src, dst, stw, q, sm);
+    else fwd_a16_body<false>(src, dst, stw, q, sm);
+}
+
+template <bool LAZY>
+__device__ __forceinline__ void fwd_b16_body(u64 *d, const ulonglong2 *twp, int row0, const PrimeC &P,
+                                             u64 *sm)
+{
+    const int t = threadIdx.x, j = t & 15, r = t >> 4;
+    constexpr int S1 = 8;
+    const u64 q = P.q, q2 = 2 * q;
+    u64 v[16];
+    ulonglong2 w[15];
+    const int grow = row0 + r;
+    u64 *drow = d + (size_t)r * 256;
+#pragma unroll
+    for (int m = 0; m < 16; m++) v[m] = drow[j + 16 * m];
+#pragma unroll
+    for (int st = 0; st < 4; st++)
+#pragma unroll
+        for (int g = 0; g < (1 << st); g++) w[(1 << st) - 1 + g] = twp[(1 << (S1 + st)) + (grow << st) + g];
+    ct16<LAZY>(v, w, q, q2);
+    u64 *srow = sm + r * kR16Row;
+#pragma unroll
+    for (int m = 0; m < 16; m++) srow[pad16(j + 16 * m)] = v[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; m++) v[m] = srow[pad16(16 * j + m)];
+#pragma unroll
+    for (int st = 0; st < 4; st++)
+#pragma unroll
+        for (int g = 0; g < (1 << st); g++)
+            w[(1 << st) - 1 + g] = twp[(1 << (S1 + 4 + st)) + (grow << (4 + st)) + (j << st) + g];
+    ct16<LAZY>(v, w, q, q2);
+    ulonglong2 *o = reinterpret_cast<ulonglong2 *>(drow + 16 * j);
+#pragma unroll
+    for (int m = 0; m < 16; m += 2)
+        o[m / 2] = LAZY ? make_ulonglong2(reduce_word(v[m], P), reduce_word(v[m + 1], P))
+                        : make_ulonglong2(reduce4(v[m], q), reduce4(v[m + 1], q));
+}
+
+__global__ void __launch_bounds__(256)
+ntt16_fwd_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ tw)
+{
+    const int limb = blockIdx.y;
+    const int col = limb % bt.per_row, row = limb / bt.per_row;
+    const int pi = bt.pidx[col];
+    if (pi < 0) return;
+    __shared__ u64 sm[16 * kR16Row];
+    const PrimeC P = primes[pi];
+    const ulonglong2 *twp = tw + (size_t)pi * 65536;
+    const int row0 = blockIdx.x * 16;
+    u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * 65536 + (size_t)row0 * 256;
+    if (P.q < (1ull << 47)) fwd_b16_body<true>(d, twp, row0, P, sm);
+    else fwd_b16_body<false>(d, twp, row0, P, sm);
+}
+
+template <bool LAZY>
+__device__ __forceinline__ void inv_b16_body(const u64 *s, u64 *d, const ulonglong2 *twp, int row0,
+                                             u64 q, u64 *sm)
+{
+    const int t = threadIdx.x, j = t & 15, r = t >> 4;
+    constexpr int S1 = 8;
+    const u64 q2 = 2 * q;
+    u64 v[16];
+    ulonglong2 w[15];
+    const int grow = row0 + r;
+    const ulonglong2 *in = reinterpret_cast<const ulonglong2 *>(s + (size_t)r * 256 + 16 * j);
+#pragma unroll
+    for (int m = 0; m < 16; m += 2) {
+        const ulonglong2 a = in[m / 2];
+        v[m] = a.x;
+        v[m + 1] = a.y;
+    }
+#pragma unroll
+    for (int st = 0; st < 4; st++)
+#pragma unroll
+        for (int g = 0; g < (1 << st); g++)
+            w[(1 << st) - 1 + g] = twp[(1 << (S1 + 4 + st)) + (grow << (4 + st)) + (j << st) + g];
+    gs16<LAZY>(v, w, q, q2, 0);
+    u64 *srow = sm + r * kR16Row;
+#pragma unroll
+    for (int m = 0; m < 16; m++) srow[pad16(16 * j + m)] = v[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; m++) v[m] = srow[pad16(j + 16 * m)];
+#pragma unroll
+    for (int st = 0; st < 4; st++)
+#pragma unroll
+        for (int g = 0; g < (1 << st); g++) w[(1 << st) - 1 + g] = twp[(1 << (S1 + st)) + (grow << st) + g];
+    gs16<LAZY>(v, w, q, q2, 4);
+    u64 *drow = d + (size_t)r * 256;
+#pragma unroll
+    for (int m = 0; m < 16; m++) drow[j + 16 * m] = v[m];   // lazy (< 2^8 q or < 2q)
+}
+
+__global__ void __launch_bounds__(256)
+ntt16_inv_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ itw)
+{
+    const int limb = blockIdx.y;
+    const int col = limb % bt.per_row, row = limb / bt.per_row;
+    const int pi = bt.pidx[col];
+    if (pi < 0) return;
+    __shared__ u64 sm[16 * kR16Row];
+    const u64 q = primes[pi].q;
+    const ulonglong2 *twp = itw + (size_t)pi * 65536;
+    const int row0 = blockIdx.x * 16;
+    const u64 *s = bt.src + ((size_t)row * bt.src_stride + col) * 65536 + (size_t)row0 * 256;
+    u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * 65536 + (size_t)row0 * 256;
+    if (q < (1ull << 47)) inv_b16_body<true>(s, d, twp, row0, q, sm);
+    else inv_b16_body<false>(s, d, twp, row0, q, sm);
+}
+
+template <bool LAZY>
+__device__ __forceinline__ void inv_a16_body(u64 *d, const ulonglong2 *stw, u64 q, u64 ni, u64 nis,
+                                             u64 *sm)
+{
+    const int t = threadIdx.x, c = t & 15, r = t >> 4;
+    constexpr int N2 = 256;
+    const u64 q2 = 2 * q;
+    u64 v[16];
+    ulonglong2 w[15];
+#pragma unroll
+    for (int m = 0; m < 16; m++) v[m] = d[(size_t)(16 * r + m) * N2 + c];
+#pragma unroll
+    for (int st = 0; st < 4; st++)
+#pragma unroll
+        for (int g = 0; g < (1 << st); g++) w[(1 << st) - 1 + g] = stw[(1 << (st + 4)) + (r << st) + g];
+    gs16<LAZY>(v, w, q, q2, 8);
+#pragma unroll
+    for (int m = 0; m < 16; m++) sm[(16 * r + m) * 16 + c] = v[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; m++) v[m] = sm[(r + 16 * m) * 16 + c];
+#pragma unroll
+    for (int k = 0; k < 15; k++) w[k] = stw[k + 1];
+    gs16<LAZY>(v, w, q, q2, 12);
+#pragma unroll
+    for (int m = 0; m < 16; m++) d[(size_t)(r + 16 * m) * N2 + c] = shoup_mul(v[m], ni, nis, q);
+}
+
+__global__ void __launch_bounds__(256)
+ntt16_inv_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ itw,
+            const u64 *__restrict__ ninv)
+{
+    const int limb = blockIdx.y;
+    const int col = limb % bt.per_row, row = limb / bt.per_row;
+    const int pi = bt.pidx[col];
+    if (pi < 0) return;
+    __shared__ u64 sm[256 * 16];
+    __shared__ ulonglong2 stw[256];
+    const u64 q = primes[pi].q;
+    const ulonglong2 *twp = itw + (size_t)pi * 65536;
+    stw[threadIdx.x] = twp[threadIdx.x];
+    __syncthreads();
+    const int c0 = blockIdx.x * 16;
+    u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * 65536 + c0;
+    const u64 ni = ninv[2 * pi], nis = ninv[2 * pi + 1];
+    if (q < (1ull << 47)) inv_a16_body<true>(d, stw, q, ni, nis, sm);
+    else inv_a16_body<false>(d, stw, q, ni, nis, sm);
+}
+
 // Stages are taken two at a time (radix-4 rounds: four elements, four
 // butterflies, one shared-memory round trip and one barrier per two
 // stages).  Within a sub-transform of 2^LS elements, a round on stages
@@ -769,16 +1027,6 @@ k_stay_mac(const u64 *__restrict__ lane, int ls, int ncol, int level, const Dest
 // and part) at one slot pair; the CTA's threads of one slot pair read the
 // same mask words; partial sums stay in shared memory until the end.
 // ------------------------------------------------------------------------
-struct GSrc {
-    const u64 *u;      // rotation: [ncol][2][E][N] extended basis; kept lane: nullptr
-    const u64 *lane;   // [ncol][2][ls][N]: c0 for rotations, the value for kept lanes
-    uint32_t g;        // Galois element of a rotation
-    int t0, t1;        // its terms
-};
-struct GTerm {
-    int src;           // source index (terms are sorted by output)
-    const u64 *mask;   // [E][N] NTT domain, Montgomery form
-};
 
 // Partial sums are the raw 128-bit products v * m~ (m~ = mask R mod q, its
 // Montgomery form), added without reduction; one Montgomery reduction of the
@@ -793,28 +1041,36 @@ struct GTerm {
 // for rotations, P lane for kept values) and the CTA's mask words in shared
 // memory; phase 2 walks the outputs, each a register sum over its terms.
 constexpr int kGmacThreads = 128;
-constexpr int kGmacSrc = 24;
-constexpr int kGmacBatch = 4;   // source loads in flight per thread
+constexpr int kGmacSrc = 24;      // sources per launch
+constexpr int kGmacTerms = 192;   // terms per launch
+constexpr int kGmacOut = 64;      // outputs per launch
+constexpr int kGmacBatch = 4;     // source loads in flight per thread
+
+// the launch's program, passed by value (kernel parameters sit in the
+// constant bank: uniform reads need no global loads)
+struct GProg {
+    int nsrc, nterm, X, accumulate;
+    const u64 *su[kGmacSrc];      // rotation: key-switch output; kept lane: nullptr
+    const u64 *slane[kGmacSrc];
+    uint32_t sg[kGmacSrc];
+    int tsrc[kGmacTerms];         // terms sorted by output
+    const u64 *tmask[kGmacTerms];
+    int dfirst[kGmacOut + 1];
+    u64 *outs[kGmacOut];
+};
 
 __global__ void __launch_bounds__(kGmacThreads)
-k_group_mac(const GSrc *__restrict__ srcs, int nsrc, const GTerm *__restrict__ terms, int nterm,
-            const int *__restrict__ dest_first, u64 *const *__restrict__ outs, int X,
-            int accumulate, int ncol, int level, int E, int ls, int log_n,
+k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
             const u64 *__restrict__ pmodq, const PrimeC *__restrict__ primes, int nq)
 {
     extern __shared__ __align__(16) unsigned char gsm[];
     const int npoly = 2 * ncol;
     const int pp_n = kGmacThreads / npoly;          // slot pairs per CTA
+    const int nsrc = pg.nsrc, nterm = pg.nterm;
     ulonglong2 *vsm = reinterpret_cast<ulonglong2 *>(gsm);                  // [nsrc][threads]
     ulonglong2 *msm = vsm + (size_t)nsrc * kGmacThreads;                    // [nterm][pp_n]
-    GSrc *ssrc = reinterpret_cast<GSrc *>(msm + (size_t)nterm * pp_n);      // [nsrc]
-    int *tsrc = reinterpret_cast<int *>(ssrc + nsrc);                       // [nterm]
-    int *dfirst = tsrc + nterm;                                             // [X + 1]
     const int N = 1 << log_n;
     const int tid = threadIdx.x;
-    for (int k = tid; k < nsrc; k += kGmacThreads) ssrc[k] = srcs[k];
-    for (int k = tid; k < nterm; k += kGmacThreads) tsrc[k] = terms[k].src;
-    for (int k = tid; k <= X; k += kGmacThreads) dfirst[k] = dest_first[k];
     const int poly = tid % npoly, pp = tid / npoly;
     const int x = 2 * (blockIdx.x * pp_n + pp);
     const bool act = pp < pp_n && x < N;
@@ -824,14 +1080,14 @@ k_group_mac(const GSrc *__restrict__ srcs, int nsrc, const GTerm *__restrict__ t
     const u64 q = P.q;
     const u64 pw = isq ? pmodq[2 * i] : 0, pws = isq ? pmodq[2 * i + 1] : 0;
     const size_t ext_off = ((size_t)poly * E + i) * N + x;
-    // masks: term t, pair k of this CTA
+    // masks: term t, pair k of this CTA (independent loads)
+#pragma unroll 4
     for (int e = tid; e < nterm * pp_n; e += kGmacThreads) {
-        const int t = e / pp_n, k = e % pp_n;
+        const int t = e / pp_n, k = e - t * pp_n;
         const int xx = 2 * (blockIdx.x * pp_n + k);
-        msm[e] = xx < N ? *reinterpret_cast<const ulonglong2 *>(terms[t].mask + (size_t)i * N + xx)
+        msm[e] = xx < N ? *reinterpret_cast<const ulonglong2 *>(pg.tmask[t] + (size_t)i * N + xx)
                         : make_ulonglong2(0, 0);
     }
-    __syncthreads();
     if (act) {
         const int f = poly >> 1, p = poly & 1;
         const bool add_c0 = isq && p == 0;
@@ -841,48 +1097,50 @@ k_group_mac(const GSrc *__restrict__ srcs, int nsrc, const GTerm *__restrict__ t
             for (int k = 0; k < kGmacBatch; k++) {   // issue every load of the batch first
                 vv[k] = make_ulonglong2(0, 0);
                 cc[k] = make_ulonglong2(0, 0);
-                if (s0 + k < nsrc) {
-                    const GSrc &S = ssrc[s0 + k];
-                    if (S.u) {
-                        vv[k] = *reinterpret_cast<const ulonglong2 *>(S.u + ext_off);
+                const int sidx = s0 + k;
+                if (sidx < nsrc) {
+                    const u64 *su = pg.su[sidx];
+                    if (su) {
+                        vv[k] = *reinterpret_cast<const ulonglong2 *>(su + ext_off);
                         if (add_c0) {
-                            const int sx = auto_src(x, S.g, log_n);
-                            cc[k] = gather_pair(S.lane + ((size_t)(f * 2) * ls + i) * N, sx, sx & 1);
+                            const int sx = auto_src(x, pg.sg[sidx], log_n);
+                            cc[k] = gather_pair(pg.slane[sidx] + ((size_t)(f * 2) * ls + i) * N, sx, sx & 1);
                         }
                     } else if (isq) {
-                        cc[k] = *reinterpret_cast<const ulonglong2 *>(S.lane + ((size_t)poly * ls + i) * N + x);
+                        cc[k] = *reinterpret_cast<const ulonglong2 *>(pg.slane[sidx] + ((size_t)poly * ls + i) * N + x);
                     }
                 }
             }
 #pragma unroll
             for (int k = 0; k < kGmacBatch; k++) {
-                if (s0 + k < nsrc) {
+                const int sidx = s0 + k;
+                if (sidx < nsrc) {
                     ulonglong2 v = vv[k];
-                    if (isq && (add_c0 || !ssrc[s0 + k].u)) {
+                    if (isq && (add_c0 || !pg.su[sidx])) {
                         // rotation: u + P phi(c0); kept lane: P lane (0 mod the special primes)
                         v.x = add_mod(v.x, shoup_mul(cc[k].x, pw, pws, q), q);
                         v.y = add_mod(v.y, shoup_mul(cc[k].y, pw, pws, q), q);
                     }
-                    vsm[(size_t)(s0 + k) * kGmacThreads + tid] = v;
+                    vsm[(size_t)sidx * kGmacThreads + tid] = v;
                 }
             }
         }
     }
     __syncthreads();
     if (!act) return;
-    for (int d = 0; d < X; d++) {
+    for (int d = 0; d < pg.X; d++) {
         u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
-        const int t1 = dfirst[d + 1];
+        const int t1 = pg.dfirst[d + 1];
 #pragma unroll 4
-        for (int t = dfirst[d]; t < t1; t++) {
-            const ulonglong2 v = vsm[(size_t)tsrc[t] * kGmacThreads + tid];
+        for (int t = pg.dfirst[d]; t < t1; t++) {
+            const ulonglong2 v = vsm[(size_t)pg.tsrc[t] * kGmacThreads + tid];
             const ulonglong2 m = msm[t * pp_n + pp];
             mac128(hi0, lo0, v.x, m.x);
             mac128(hi1, lo1, v.y, m.y);
         }
         ulonglong2 r = make_ulonglong2(redc(reduce_word(hi0, P), lo0, P), redc(reduce_word(hi1, P), lo1, P));
-        ulonglong2 *o = reinterpret_cast<ulonglong2 *>(outs[d] + ext_off);
-        if (accumulate) {
+        ulonglong2 *o = reinterpret_cast<ulonglong2 *>(pg.outs[d] + ext_off);
+        if (pg.accumulate) {
             const ulonglong2 b = *o;
             r.x = add_mod(r.x, b.x, q);
             r.y = add_mod(r.y, b.y, q);
@@ -958,6 +1216,23 @@ KTimer::~KTimer()
 }
 
 
+static void ntt16_launch(fg_ctx *ctx, const Batch &bt, int count, bool inverse)
+{
+    const auto *fwd = (const ulonglong2 *)ctx->d_fwd;
+    const auto *inv = (const ulonglong2 *)ctx->d_inv;
+    dim3 gA(16, count), gB(16, count);
+    Batch b2 = bt;
+    b2.src = b2.dst;
+    b2.src_stride = b2.dst_stride;
+    if (!inverse) {
+        ntt16_fwd_a<<<gA, 256, 0, ctx->stream>>>(bt, ctx->d_primes, fwd);
+        ntt16_fwd_b<<<gB, 256, 0, ctx->stream>>>(b2, ctx->d_primes, fwd);
+    } else {
+        ntt16_inv_b<<<gB, 256, 0, ctx->stream>>>(bt, ctx->d_primes, inv);
+        ntt16_inv_a<<<gA, 256, 0, ctx->stream>>>(b2, ctx->d_primes, inv, ctx->d_ninv);
+    }
+}
+
 template <int LOGN>
 static void ntt_launch_t(fg_ctx *ctx, const Batch &bt, int count, bool inverse)
 {
@@ -998,7 +1273,7 @@ static void launch_ntt(fg_ctx *ctx, const LimbSet &src, const LimbSet &dst, bool
     case 13: ntt_launch_t<13>(ctx, bt, count, inverse); break;
     case 14: ntt_launch_t<14>(ctx, bt, count, inverse); break;
     case 15: ntt_launch_t<15>(ctx, bt, count, inverse); break;
-    case 16: ntt_launch_t<16>(ctx, bt, count, inverse); break;
+    case 16: ntt16_launch(ctx, bt, count, inverse); break;
     default: throw fg_error(FG_EINVAL, "ntt: unsupported ring degree");
     }
     check_launch("ntt", 2);
@@ -1269,47 +1544,45 @@ void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vec
 {
     const int N = ctx->n, E = ctx->ext(level), X = (int)outs.size();
     if (srcs.empty() || X == 0) return;
-    FG_CHECK((int)srcs.size() <= kGmacSrc, FG_EINVAL, "group_mac: too many sources in one launch");
-    // terms sorted by output, each naming its source
+    FG_CHECK((int)srcs.size() <= kGmacSrc && (int)terms_in.size() <= kGmacTerms && X <= kGmacOut,
+             FG_EINVAL, "group_mac: launch larger than its program limits");
+    GProg pg;
+    memset(&pg, 0, sizeof(pg));
+    pg.nsrc = (int)srcs.size();
+    pg.nterm = (int)terms_in.size();
+    pg.X = X;
+    pg.accumulate = accumulate ? 1 : 0;
     std::vector<int> src_of(terms_in.size());
-    for (size_t s = 0; s < srcs.size(); s++)
+    for (size_t s = 0; s < srcs.size(); s++) {
+        pg.su[s] = srcs[s].u;
+        pg.slane[s] = srcs[s].lane;
+        pg.sg[s] = srcs[s].galois;
         for (int t = srcs[s].t0; t < srcs[s].t1; t++) src_of[t] = (int)s;
-    std::vector<GTerm> ht;
-    std::vector<int> first(X + 1, 0);
-    for (int d = 0; d < X; d++) {
-        first[d] = (int)ht.size();
-        for (size_t t = 0; t < terms_in.size(); t++)
-            if (term_dest[t] == d) ht.push_back({src_of[t], terms_in[t].mask});
     }
-    first[X] = (int)ht.size();
-    std::vector<GSrc> hs(srcs.size());
-    for (size_t s = 0; s < srcs.size(); s++) hs[s] = {srcs[s].u, srcs[s].lane, srcs[s].galois, 0, 0};
-    const size_t bs = hs.size() * sizeof(GSrc), bt = ht.size() * sizeof(GTerm);
-    const size_t bf = first.size() * sizeof(int), bo = X * sizeof(u64 *);
-    auto up = [](size_t b) { return ((b + 15) / 16) * 16; };
-    char *d = (char *)ctx->buf("gmac_prog", up(bs) + up(bt) + up(bf) + up(bo) + 64);
-    GSrc *ds = (GSrc *)d;
-    GTerm *dt = (GTerm *)(d + up(bs));
-    int *df = (int *)(d + up(bs) + up(bt));
-    u64 **dout = (u64 **)(d + up(bs) + up(bt) + up(bf));
-    CUDA_TRY(cudaMemcpyAsync(ds, hs.data(), bs, cudaMemcpyHostToDevice, ctx->stream));
-    if (bt) CUDA_TRY(cudaMemcpyAsync(dt, ht.data(), bt, cudaMemcpyHostToDevice, ctx->stream));
-    CUDA_TRY(cudaMemcpyAsync(df, first.data(), bf, cudaMemcpyHostToDevice, ctx->stream));
-    CUDA_TRY(cudaMemcpyAsync(dout, outs.data(), bo, cudaMemcpyHostToDevice, ctx->stream));
+    int n = 0;
+    for (int d = 0; d < X; d++) {   // terms sorted by output
+        pg.dfirst[d] = n;
+        pg.outs[d] = outs[d];
+        for (size_t t = 0; t < terms_in.size(); t++)
+            if (term_dest[t] == d) {
+                pg.tsrc[n] = src_of[t];
+                pg.tmask[n] = terms_in[t].mask;
+                n++;
+            }
+    }
+    pg.dfirst[X] = n;
     const int npoly = 2 * ncol;
     FG_CHECK(npoly <= kGmacThreads, FG_EINVAL, "group_mac: too many columns");
     const int pp_n = kGmacThreads / npoly;
     dim3 g((N / 2 + pp_n - 1) / pp_n, E);
-    const size_t sm = (size_t)hs.size() * kGmacThreads * 16 + (size_t)ht.size() * pp_n * 16 +
-                      hs.size() * sizeof(GSrc) + ht.size() * sizeof(int) + (X + 1) * sizeof(int) + 16;
-    FG_CHECK(sm <= 220 * 1024, FG_EINVAL, "group_mac: group program too large for shared memory");
+    const size_t sm = (size_t)pg.nsrc * kGmacThreads * 16 + (size_t)pg.nterm * pp_n * 16;
     KTimer kt(ctx, "group_mac",
-              ((double)srcs.size() * npoly * E + (double)ht.size() * E +
+              ((double)srcs.size() * npoly * E + (double)pg.nterm * E +
                (double)X * npoly * E * (accumulate ? 2 : 1)) * N * 8);
-    CUDA_TRY(cudaFuncSetAttribute(k_group_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_group_mac<<<g, kGmacThreads, sm, ctx->stream>>>(ds, (int)hs.size(), dt, (int)ht.size(), df, dout, X,
-                                                      accumulate ? 1 : 0, ncol, level, E, ls,
-                                                      ctx->log_n, ctx->d_pmodq, ctx->d_primes, ctx->nq);
+    if (sm > 48 * 1024)
+        CUDA_TRY(cudaFuncSetAttribute(k_group_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_group_mac<<<g, kGmacThreads, sm, ctx->stream>>>(pg, ncol, level, E, ls, ctx->log_n,
+                                                      ctx->d_pmodq, ctx->d_primes, ctx->nq);
     check_launch("group_mac");
 }
 

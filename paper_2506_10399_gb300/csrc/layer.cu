@@ -425,17 +425,23 @@ int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, const 
                 tdest.clear();
                 std::fill(dest_terms.begin(), dest_terms.end(), 0);
             };
+            auto needs_flush = [&](const std::vector<const TermC *> &ts) {
+                bool full = (int)srcs.size() >= 24 || terms.size() + ts.size() > 192;
+                for (const TermC *tm : ts) full |= dest_terms[out_index(tm->dst)] >= 255;
+                return full;
+            };
             // kept values first (no key switching)
             for (auto &kv : by_src)
-                if (kv.first.second == 0) add_source(nullptr, (*in)[kv.first.first], 0, kv.second);
+                if (kv.first.second == 0) {
+                    if (needs_flush(kv.second)) flush();
+                    add_source(nullptr, (*in)[kv.first.first], 0, kv.second);
+                }
             int cur = -1, used = 0;
             for (auto &rk : g.rots) {
                 const int a = rk.first, k = rk.second;
                 auto it = by_src.find({a, k});
                 if (it == by_src.end()) continue;
-                bool full = used == pool_cap || (int)srcs.size() >= 24;
-                for (const TermC *tm : it->second) full |= dest_terms[out_index(tm->dst)] >= 255;
-                if (full) {
+                if (used == pool_cap || needs_flush(it->second)) {
                     flush();
                     used = 0;
                 }
