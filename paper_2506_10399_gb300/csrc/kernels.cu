@@ -881,11 +881,15 @@ __device__ __forceinline__ ulonglong2 gather_pair(const u64 *limb, int m2, bool 
     return swap ? make_ulonglong2(v.y, v.x) : v;
 }
 
+// With pmodq given, part 0 also receives P phi_g(c0) on the limbs of Q
+// (P mod q_i and its Shoup companion at pmodq[2i], pmodq[2i+1]), so that
+// ModDown of u is Rot(c) itself: ModDown(A + P B) = ModDown(A) + B exactly.
 template <int BETA>
 __global__ void __launch_bounds__(256, 3)
 k_ks_ip(const u64 *__restrict__ key, int KL, const u64 *__restrict__ lane, int ls,
         const u64 *__restrict__ digits, int ncol, int level, int E, int alpha, int nq,
-        uint32_t g, int log_n, u64 *u, const PrimeC *__restrict__ primes)
+        uint32_t g, int log_n, u64 *u, const PrimeC *__restrict__ primes,
+        const u64 *__restrict__ pmodq)
 {
     const int N = 1 << log_n;
     const int i = blockIdx.y;
@@ -914,8 +918,14 @@ k_ks_ip(const u64 *__restrict__ key, int KL, const u64 *__restrict__ lane, int l
             mac128(h2, l2, v.x, ka[d].x);
             mac128(h3, l3, v.y, ka[d].y);
         }
-        *reinterpret_cast<ulonglong2 *>(u + (((size_t)f * 2 + 0) * E + i) * N + x) =
-            make_ulonglong2(redc(h0, l0, P), redc(h1, l1, P));
+        ulonglong2 r0 = make_ulonglong2(redc(h0, l0, P), redc(h1, l1, P));
+        if (pmodq && i <= level) {
+            const ulonglong2 c0 = gather_pair(lane + (((size_t)f * 2) * ls + i) * N, sx, swap);
+            const u64 pw = pmodq[2 * i], pws = pmodq[2 * i + 1];
+            r0.x = add_mod(r0.x, shoup_mul(c0.x, pw, pws, P.q), P.q);
+            r0.y = add_mod(r0.y, shoup_mul(c0.y, pw, pws, P.q), P.q);
+        }
+        *reinterpret_cast<ulonglong2 *>(u + (((size_t)f * 2 + 0) * E + i) * N + x) = r0;
         *reinterpret_cast<ulonglong2 *>(u + (((size_t)f * 2 + 1) * E + i) * N + x) =
             make_ulonglong2(redc(h2, l2, P), redc(h3, l3, P));
     }
@@ -1028,36 +1038,81 @@ k_stay_mac(const u64 *__restrict__ lane, int ls, int ncol, int level, const Dest
 // same mask words; partial sums stay in shared memory until the end.
 // ------------------------------------------------------------------------
 
-// Partial sums are the raw 128-bit products v * m~ (m~ = mask R mod q, its
-// Montgomery form), added without reduction; one Montgomery reduction of the
-// total gives sum v * m mod q.  That needs total < q 2^64: every product is
-// below q^2 < 2^120, so up to 255 terms per output and launch are safe after
+// Partial sums are products v * m~ (m~ = mask R mod q, its Montgomery form)
+// added without reduction; one Montgomery reduction of the total gives
+// sum v * m mod q.  That needs total < q 2^64: every product is below
+// q^2 < 2^120, so up to 255 terms per output and launch are safe after
 // folding the high word mod q (a launch takes at most kGmacSrc sources, and
 // each source feeds an output at most once).
 //
+// For primes below 2^46 both factors are split into 23-bit halves,
+// v = v0 + v1 2^23, and the three partial sums  A0 = sum v0 m0,
+// A1 = sum (v0 m1 + v1 m0), A2 = sum v1 m1  are kept in 64-bit words
+// (below 2^55 for 255 terms): four 32 x 32 -> 64-bit multiply-adds per
+// product instead of a 64 x 64 -> 128-bit one.  The halves are stored as
+// v0 | v1 << 32, so each factor is a register pair read without shifts.
+// Other primes (q_0 and the special primes, up to 60 bits) use the
+// 128-bit sum.
+//
 // Thread = one polynomial (column, part) at one slot pair; a CTA covers the
-// npoly polynomials of 128 / npoly slot pairs of one limb.  Phase 1 stages,
-// with independent loads, every source value of the thread (u + P phi(c0)
-// for rotations, P lane for kept values) and the CTA's mask words in shared
-// memory; phase 2 walks the outputs, each a register sum over its terms.
+// npoly polynomials of 128 / npoly slot pairs of one limb, neighbouring
+// threads on neighbouring pairs of one polynomial.  Phase 1 copies every
+// source value of the thread (the key-switch output, which already holds
+// u + P phi(c0), or the kept lane) and the CTA's mask words into shared
+// memory with asynchronous copies, all in flight at once; phase 2 turns
+// kept lanes into P lane and splits words in place; phase 3 walks the
+// outputs, each a register sum over its terms.
 constexpr int kGmacThreads = 128;
 constexpr int kGmacSrc = 24;      // sources per launch
 constexpr int kGmacTerms = 192;   // terms per launch
 constexpr int kGmacOut = 64;      // outputs per launch
-constexpr int kGmacBatch = 4;     // source loads in flight per thread
 
 // the launch's program, passed by value (kernel parameters sit in the
 // constant bank: uniform reads need no global loads)
 struct GProg {
     int nsrc, nterm, X, accumulate;
     const u64 *su[kGmacSrc];      // rotation: key-switch output; kept lane: nullptr
-    const u64 *slane[kGmacSrc];
-    uint32_t sg[kGmacSrc];
+    const u64 *slane[kGmacSrc];   // kept lane
     int tsrc[kGmacTerms];         // terms sorted by output
     const u64 *tmask[kGmacTerms];
     int dfirst[kGmacOut + 1];
     u64 *outs[kGmacOut];
 };
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ u64 split23(u64 v) { return (v & 0x7FFFFF) | ((v >> 23) << 32); }
+
+__device__ __forceinline__ void mac_split(u64 &a0, u64 &a1, u64 &a2, u64 v, u64 m)
+{
+    const u32 v0 = (u32)v, v1 = (u32)(v >> 32), m0 = (u32)m, m1 = (u32)(m >> 32);
+    a0 += (u64)v0 * m0;
+    a1 += (u64)v0 * m1;
+    a1 += (u64)v1 * m0;
+    a2 += (u64)v1 * m1;
+}
+
+// (A0 + A1 2^23 + A2 2^46) R^-1 mod q
+__device__ __forceinline__ u64 fold_split(u64 a0, u64 a1, u64 a2, const PrimeC &P)
+{
+    u64 lo = a0, hi = (a1 >> 41) + (a2 >> 18);
+    u64 t = a1 << 23;
+    lo += t;
+    hi += lo < t;
+    t = a2 << 46;
+    lo += t;
+    hi += lo < t;
+    return redc(reduce_word(hi, P), lo, P);
+}
 
 __global__ void __launch_bounds__(kGmacThreads)
 k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
@@ -1071,77 +1126,85 @@ k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
     ulonglong2 *msm = vsm + (size_t)nsrc * kGmacThreads;                    // [nterm][pp_n]
     const int N = 1 << log_n;
     const int tid = threadIdx.x;
-    const int poly = tid % npoly, pp = tid / npoly;
+    const int poly = tid / pp_n, pp = tid - poly * pp_n;
     const int x = 2 * (blockIdx.x * pp_n + pp);
-    const bool act = pp < pp_n && x < N;
+    const bool act = poly < npoly && x < N;
     const int i = blockIdx.y;
     const bool isq = i <= level;
     const PrimeC P = primes[isq ? i : nq + (i - level - 1)];
     const u64 q = P.q;
-    const u64 pw = isq ? pmodq[2 * i] : 0, pws = isq ? pmodq[2 * i + 1] : 0;
+    const bool split = q < (1ull << 46);
     const size_t ext_off = ((size_t)poly * E + i) * N + x;
-    // masks: term t, pair k of this CTA (independent loads)
-#pragma unroll 4
+    // 1. asynchronous copies
     for (int e = tid; e < nterm * pp_n; e += kGmacThreads) {
         const int t = e / pp_n, k = e - t * pp_n;
         const int xx = 2 * (blockIdx.x * pp_n + k);
-        msm[e] = xx < N ? *reinterpret_cast<const ulonglong2 *>(pg.tmask[t] + (size_t)i * N + xx)
-                        : make_ulonglong2(0, 0);
+        if (xx < N) cp_async16(msm + e, pg.tmask[t] + (size_t)i * N + xx);
+        else msm[e] = make_ulonglong2(0, 0);
     }
     if (act) {
-        const int f = poly >> 1, p = poly & 1;
-        const bool add_c0 = isq && p == 0;
-        for (int s0 = 0; s0 < nsrc; s0 += kGmacBatch) {
-            ulonglong2 vv[kGmacBatch], cc[kGmacBatch];
-#pragma unroll
-            for (int k = 0; k < kGmacBatch; k++) {   // issue every load of the batch first
-                vv[k] = make_ulonglong2(0, 0);
-                cc[k] = make_ulonglong2(0, 0);
-                const int sidx = s0 + k;
-                if (sidx < nsrc) {
-                    const u64 *su = pg.su[sidx];
-                    if (su) {
-                        vv[k] = *reinterpret_cast<const ulonglong2 *>(su + ext_off);
-                        if (add_c0) {
-                            const int sx = auto_src(x, pg.sg[sidx], log_n);
-                            cc[k] = gather_pair(pg.slane[sidx] + ((size_t)(f * 2) * ls + i) * N, sx, sx & 1);
-                        }
-                    } else if (isq) {
-                        cc[k] = *reinterpret_cast<const ulonglong2 *>(pg.slane[sidx] + ((size_t)poly * ls + i) * N + x);
-                    }
-                }
+        for (int s = 0; s < nsrc; s++) {
+            ulonglong2 *dst = vsm + (size_t)s * kGmacThreads + tid;
+            if (pg.su[s]) cp_async16(dst, pg.su[s] + ext_off);
+            else if (isq) cp_async16(dst, pg.slane[s] + ((size_t)poly * ls + i) * N + x);
+            else *dst = make_ulonglong2(0, 0);   // P lane vanishes mod the special primes
+        }
+    }
+    cp_async_wait_all();
+    // 2. in place, each thread on the words it copied
+    if (split)
+        for (int e = tid; e < nterm * pp_n; e += kGmacThreads) {
+            const ulonglong2 m = msm[e];
+            msm[e] = make_ulonglong2(split23(m.x), split23(m.y));
+        }
+    if (act && (split || isq)) {
+        const u64 pw = isq ? pmodq[2 * i] : 0, pws = isq ? pmodq[2 * i + 1] : 0;
+        for (int s = 0; s < nsrc; s++) {
+            const bool kept = isq && !pg.su[s];
+            if (!split && !kept) continue;
+            ulonglong2 *dst = vsm + (size_t)s * kGmacThreads + tid;
+            ulonglong2 v = *dst;
+            if (kept) {
+                v.x = shoup_mul(v.x, pw, pws, q);
+                v.y = shoup_mul(v.y, pw, pws, q);
             }
-#pragma unroll
-            for (int k = 0; k < kGmacBatch; k++) {
-                const int sidx = s0 + k;
-                if (sidx < nsrc) {
-                    ulonglong2 v = vv[k];
-                    if (isq && (add_c0 || !pg.su[sidx])) {
-                        // rotation: u + P phi(c0); kept lane: P lane (0 mod the special primes)
-                        v.x = add_mod(v.x, shoup_mul(cc[k].x, pw, pws, q), q);
-                        v.y = add_mod(v.y, shoup_mul(cc[k].y, pw, pws, q), q);
-                    }
-                    vsm[(size_t)sidx * kGmacThreads + tid] = v;
-                }
+            if (split) {
+                v.x = split23(v.x);
+                v.y = split23(v.y);
             }
+            *dst = v;
         }
     }
     __syncthreads();
     if (!act) return;
+    // 3. outputs
     for (int d = 0; d < pg.X; d++) {
-        u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
-        const int t1 = pg.dfirst[d + 1];
-#pragma unroll 4
-        for (int t = pg.dfirst[d]; t < t1; t++) {
-            const ulonglong2 v = vsm[(size_t)pg.tsrc[t] * kGmacThreads + tid];
-            const ulonglong2 m = msm[t * pp_n + pp];
-            mac128(hi0, lo0, v.x, m.x);
-            mac128(hi1, lo1, v.y, m.y);
-        }
-        ulonglong2 r = make_ulonglong2(redc(reduce_word(hi0, P), lo0, P), redc(reduce_word(hi1, P), lo1, P));
         ulonglong2 *o = reinterpret_cast<ulonglong2 *>(pg.outs[d] + ext_off);
+        const ulonglong2 b = pg.accumulate ? *o : make_ulonglong2(0, 0);
+        const int t0 = pg.dfirst[d], t1 = pg.dfirst[d + 1];
+        ulonglong2 r;
+        if (split) {
+            u64 a0 = 0, a1 = 0, a2 = 0, c0 = 0, c1 = 0, c2 = 0;
+#pragma unroll 4
+            for (int t = t0; t < t1; t++) {
+                const ulonglong2 v = vsm[(size_t)pg.tsrc[t] * kGmacThreads + tid];
+                const ulonglong2 m = msm[t * pp_n + pp];
+                mac_split(a0, a1, a2, v.x, m.x);
+                mac_split(c0, c1, c2, v.y, m.y);
+            }
+            r = make_ulonglong2(fold_split(a0, a1, a2, P), fold_split(c0, c1, c2, P));
+        } else {
+            u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
+#pragma unroll 4
+            for (int t = t0; t < t1; t++) {
+                const ulonglong2 v = vsm[(size_t)pg.tsrc[t] * kGmacThreads + tid];
+                const ulonglong2 m = msm[t * pp_n + pp];
+                mac128(hi0, lo0, v.x, m.x);
+                mac128(hi1, lo1, v.y, m.y);
+            }
+            r = make_ulonglong2(redc(reduce_word(hi0, P), lo0, P), redc(reduce_word(hi1, P), lo1, P));
+        }
         if (pg.accumulate) {
-            const ulonglong2 b = *o;
             r.x = add_mod(r.x, b.x, q);
             r.y = add_mod(r.y, b.y, q);
         }
@@ -1458,7 +1521,7 @@ void rotate_mac(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int nco
     case B:                                                                                 \
         k_ks_ip<B><<<g1, 256, 0, ctx->stream>>>(key.d, KL, lane, ls, digits, ncol, level, E, \
                                                 ctx->alpha, ctx->nq, key.galois, ctx->log_n, \
-                                                u, ctx->d_primes);                          \
+                                                u, ctx->d_primes, nullptr);                 \
         break;
     switch (beta) {
         FG_KS_CASE(1) FG_KS_CASE(2) FG_KS_CASE(3) FG_KS_CASE(4) FG_KS_CASE(5) FG_KS_CASE(6)
@@ -1556,7 +1619,6 @@ void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vec
     for (size_t s = 0; s < srcs.size(); s++) {
         pg.su[s] = srcs[s].u;
         pg.slane[s] = srcs[s].lane;
-        pg.sg[s] = srcs[s].galois;
         for (int t = srcs[s].t0; t < srcs[s].t1; t++) src_of[t] = (int)s;
     }
     int n = 0;
@@ -1576,8 +1638,10 @@ void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vec
     const int pp_n = kGmacThreads / npoly;
     dim3 g((N / 2 + pp_n - 1) / pp_n, E);
     const size_t sm = (size_t)pg.nsrc * kGmacThreads * 16 + (size_t)pg.nterm * pp_n * 16;
+    double src_limbs = 0;
+    for (const auto &gs : srcs) src_limbs += gs.u ? E : level + 1;
     KTimer kt(ctx, "group_mac",
-              ((double)srcs.size() * npoly * E + (double)pg.nterm * E +
+              (src_limbs * npoly + (double)pg.nterm * E +
                (double)X * npoly * E * (accumulate ? 2 : 1)) * N * 8);
     if (sm > 48 * 1024)
         CUDA_TRY(cudaFuncSetAttribute(k_group_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -1592,12 +1656,12 @@ void ks_only(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int ncol, 
     const int N = ctx->n, E = ctx->ext(level), beta = ctx->n_digits(level);
     const int KL = ctx->nq + ctx->np;
     dim3 g1((N / 2 + 255) / 256, E);
-    KTimer kt(ctx, "ks_ip", ((double)ncol * beta * E + 2.0 * beta * E + 2.0 * ncol * E) * N * 8);
+    KTimer kt(ctx, "ks_ip", ((double)ncol * beta * E + 2.0 * beta * E + 2.0 * ncol * E + (double)ncol * (level + 1)) * N * 8);
 #define FG_KS_CASE(B)                                                                       \
     case B:                                                                                 \
         k_ks_ip<B><<<g1, 256, 0, ctx->stream>>>(key.d, KL, lane, ls, digits, ncol, level, E, \
                                                 ctx->alpha, ctx->nq, key.galois, ctx->log_n, \
-                                                u, ctx->d_primes);                          \
+                                                u, ctx->d_primes, ctx->d_pmodq);            \
         break;
     switch (beta) {
         FG_KS_CASE(1) FG_KS_CASE(2) FG_KS_CASE(3) FG_KS_CASE(4) FG_KS_CASE(5) FG_KS_CASE(6)
