@@ -252,6 +252,25 @@ const u64 *fg_ctx::pinv_tab(int level)
     return d;
 }
 
+const u64 *fg_ctx::moddown_rescale_tab(int level)
+{
+    auto it = mdr_tabs.find(level);
+    if (it != mdr_tabs.end()) return it->second;
+    std::vector<u64> h(2 * std::max(level, 1));
+    for (int i = 0; i < level; i++) {
+        const u64 q = primes[i];
+        u64 Pq = primes[level] % q;
+        for (int k = 0; k < np; k++) Pq = hm::mulmod(Pq, primes[nq + k] % q, q);
+        h[2 * i] = hm::invmod(Pq, q);
+        h[2 * i + 1] = hm::shoup(h[2 * i], q);
+    }
+    u64 *d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, h.size() * 8));
+    CUDA_TRY(cudaMemcpy(d, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
+    mdr_tabs[level] = d;
+    return d;
+}
+
 const KeyDev &fg_keys::get(int32_t amount) const
 {
     auto it = keys.find(amount);
@@ -465,6 +484,7 @@ int fg_ctx_destroy(fg_ctx *ctx)
     for (auto &kv : ctx->conv_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->rescale_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->pinv_tabs) cudaFree(kv.second);
+    for (auto &kv : ctx->mdr_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->ws) cudaFree(kv.second.first);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     auto s = g_sk.find(ctx);

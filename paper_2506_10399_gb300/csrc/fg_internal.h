@@ -104,6 +104,7 @@ struct fg_ctx {
     std::map<std::tuple<int, int, int>, ConvTab *> conv_tabs;
     std::map<int, u64 *> rescale_tabs;   // level -> [level][2] q_l^-1 mod q_i + Shoup
     std::map<int, u64 *> pinv_tabs;      // level -> [level+1][2] P^-1 mod q_i + Shoup
+    std::map<int, u64 *> mdr_tabs;       // level -> [level][2] (P q_l)^-1 mod q_i + Shoup
 
     // instrumentation: kernel launch count, and CUDA-event timing of every
     // launch of one kernel class with its algorithmic bytes
@@ -132,6 +133,7 @@ struct fg_ctx {
     const ConvTab *moddown_tab(int level);
     const u64 *rescale_tab(int level);
     const u64 *pinv_tab(int level);
+    const u64 *moddown_rescale_tab(int level);
 };
 
 struct KeyDev {
@@ -250,7 +252,9 @@ void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vec
 void ks_only(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int ncol, int level,
              const u64 *digits, u64 *u);
 // ModDown of an extended-basis batch [ncol][2][E][N] into lane limbs 0..level (stride ls)
-void moddown_to_lane(fg_ctx *ctx, u64 *ext, int ncol, int level, u64 *out, int ls);
+// ModDown of an extended-basis sum to Q, then the rescale by q_level, into a
+// lane (limbs 0..level-1); ext is scratch and is overwritten
+void moddown_rescale_to_lane(fg_ctx *ctx, u64 *ext, int ncol, int level, u64 *out, int ls);
 // residues mod the special primes from limb 0 (centred): out [np][N]
 void lift_special(fg_ctx *ctx, const u64 *limb0, u64 *out);
 void stay_mac(fg_ctx *ctx, const u64 *lane, int ls, int ncol, int level,

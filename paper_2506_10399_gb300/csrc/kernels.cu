@@ -80,10 +80,11 @@ __device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, const ulonglong2 w, u64 
 // log N = 16: radix-16 rounds.  Every thread holds 16 elements in registers
 // for four stages, so each pass makes two shared-memory round trips
 // (N = 256 x 256; pass A on columns, pass B on rows).  For primes below
-// 2^47 the butterflies skip every conditional reduction: forward values
-// grow by at most 2q per stage (< 33q after 16 stages), inverse values
-// double per stage (< 2^16 q), both far below 2^64; one reduction at the
-// end restores [0, q).  Larger primes keep Harvey's bounds (< 4q, < 2q).
+// 2^47 the butterflies skip every conditional reduction and use the
+// three-product quotient (shoup_lazy3, products in [0, 3q)): forward values
+// grow by at most 3q per stage (< 49q after 16 stages); inverse values are
+// below 3 2^(k-1) q after k stages (< 2^64 for q < 2^47); one reduction at
+// the end restores [0, q).  Larger primes keep Harvey's bounds (< 4q, < 2q).
 // ------------------------------------------------------------------------
 template <bool LAZY>
 __device__ __forceinline__ void ct16(u64 (&v)[16], const ulonglong2 (&w)[15], u64 q, u64 q2)
@@ -96,10 +97,16 @@ __device__ __forceinline__ void ct16(u64 (&v)[16], const ulonglong2 (&w)[15], u6
             if ((m & h) == 0) {
                 const ulonglong2 tw = w[(1 << st) - 1 + (m >> (4 - st))];
                 u64 X = v[m], Y = v[m + h];
-                if (!LAZY) X = X >= q2 ? X - q2 : X;
-                const u64 T = shoup_lazy(Y, tw.x, tw.y, q);
-                v[m + h] = X - T + q2;
-                v[m] = X + T;
+                if (LAZY) {
+                    const u64 T = shoup_lazy3(Y, tw.x, tw.y, q);
+                    v[m + h] = X - T + 3 * q;
+                    v[m] = X + T;
+                } else {
+                    X = X >= q2 ? X - q2 : X;
+                    const u64 T = shoup_lazy(Y, tw.x, tw.y, q);
+                    v[m + h] = X - T + q2;
+                    v[m] = X + T;
+                }
             }
         }
     }
@@ -112,7 +119,7 @@ __device__ __forceinline__ void gs16(u64 (&v)[16], const ulonglong2 (&w)[15], u6
 #pragma unroll
     for (int st = 3; st >= 0; st--) {
         const int h = 8 >> st;
-        const u64 qb = LAZY ? (q << (k0 + 3 - st)) : q2;
+        const u64 qb = LAZY ? (q << (k0 + 4 - st)) : q2;   // above the bound of V
 #pragma unroll
         for (int m = 0; m < 16; m++) {
             if ((m & h) == 0) {
@@ -120,7 +127,8 @@ __device__ __forceinline__ void gs16(u64 (&v)[16], const ulonglong2 (&w)[15], u6
                 const u64 U = v[m], V = v[m + h];
                 const u64 S = U + V;
                 v[m] = LAZY ? S : (S >= q2 ? S - q2 : S);
-                v[m + h] = shoup_lazy(U - V + qb, tw.x, tw.y, q);
+                v[m + h] = LAZY ? shoup_lazy3(U - V + qb, tw.x, tw.y, q)
+                                : shoup_lazy(U - V + qb, tw.x, tw.y, q);
             }
         }
     }
@@ -156,7 +164,7 @@ __device__ __forceinline__ void fwd_a16_body(const u64 *s, u64 *d, const ulonglo
     for (int m = 0; m < 16; m++) d[(size_t)(16 * r + m) * N2 + c] = v[m];   // lazy
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 ntt16_fwd_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ tw)
 {
     const int limb = blockIdx.y;
@@ -213,7 +221,7 @@ __device__ __forceinline__ void fwd_b16_body(u64 *d, const ulonglong2 *twp, int 
                         : make_ulonglong2(reduce4(v[m], q), reduce4(v[m + 1], q));
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 ntt16_fwd_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ tw)
 {
     const int limb = blockIdx.y;
@@ -265,10 +273,10 @@ __device__ __forceinline__ void inv_b16_body(const u64 *s, u64 *d, const ulonglo
     gs16<LAZY>(v, w, q, q2, 4);
     u64 *drow = d + (size_t)r * 256;
 #pragma unroll
-    for (int m = 0; m < 16; m++) drow[j + 16 * m] = v[m];   // lazy (< 2^8 q or < 2q)
+    for (int m = 0; m < 16; m++) drow[j + 16 * m] = v[m];   // lazy (< 2^9 q or < 2q)
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 ntt16_inv_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ itw)
 {
     const int limb = blockIdx.y;
@@ -313,7 +321,7 @@ __device__ __forceinline__ void inv_a16_body(u64 *d, const ulonglong2 *stw, u64 
     for (int m = 0; m < 16; m++) d[(size_t)(r + 16 * m) * N2 + c] = shoup_mul(v[m], ni, nis, q);
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 ntt16_inv_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ itw,
             const u64 *__restrict__ ninv)
 {
@@ -712,10 +720,11 @@ __global__ void k_copy_limbs(const u64 *src, int src_ls, u64 *dst, int dst_ls, i
 
 // ------------------------------------------------------------------------
 // combination: Z[j][p][i] = sum_f c[i][f][j] * X[f][p][i]   (coefficient domain)
-// constants in Montgomery form; 128-bit accumulation, high word folded mod q
-// every 128 terms, one Montgomery reduction at the end.
+// constants in Montgomery form, one Montgomery reduction at the end.  For
+// primes below 2^46 the products are 23-bit split sums (mac_split); for the
+// others 128-bit sums with the high word folded mod q every chunk.
 // ------------------------------------------------------------------------
-constexpr int kCombJ = 16;
+constexpr int kCombJ = 8;
 constexpr int kCombChunk = 128;
 
 __global__ void __launch_bounds__(256)
@@ -727,34 +736,44 @@ k_comb(const u64 *__restrict__ X, int F, int Fp, int j0, int level,
     const int i = blockIdx.y, p = blockIdx.z;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const PrimeC P = primes[i];
+    const bool split = P.q < (1ull << 46);
     const int nl = level + 1;
-    u64 hi[kCombJ], lo[kCombJ];
+    u64 a0[kCombJ], a1[kCombJ], a2[kCombJ];   // split: A0, A1, A2; else lo, hi, unused
 #pragma unroll
-    for (int j = 0; j < kCombJ; j++) hi[j] = lo[j] = 0;
+    for (int j = 0; j < kCombJ; j++) a0[j] = a1[j] = a2[j] = 0;
     for (int f0 = 0; f0 < F; f0 += kCombChunk) {
         const int fc = min(kCombChunk, F - f0);
         __syncthreads();
         for (int idx = threadIdx.x; idx < kCombChunk * kCombJ; idx += blockDim.x) {
             int ff = idx / kCombJ, jj = idx % kCombJ;
-            cs[ff][jj] = (ff < fc && j0 + jj < Fp)
-                             ? consts[((size_t)i * F + f0 + ff) * Fp + j0 + jj] : 0;
+            const u64 c = (ff < fc && j0 + jj < Fp) ? consts[((size_t)i * F + f0 + ff) * Fp + j0 + jj] : 0;
+            cs[ff][jj] = split ? split23(c) : c;
         }
         __syncthreads();
         if (x < N) {
-            for (int ff = 0; ff < fc; ff++) {
-                const u64 xv = X[(((size_t)(f0 + ff) * 2 + p) * nl + i) * N + x];
+            if (split) {
+                for (int ff = 0; ff < fc; ff++) {
+                    const u64 xv = split23(X[(((size_t)(f0 + ff) * 2 + p) * nl + i) * N + x]);
 #pragma unroll
-                for (int j = 0; j < kCombJ; j++) mac128(hi[j], lo[j], xv, cs[ff][j]);
+                    for (int j = 0; j < kCombJ; j++) mac_split(a0[j], a1[j], a2[j], xv, cs[ff][j]);
+                }
+            } else {
+                for (int ff = 0; ff < fc; ff++) {
+                    const u64 xv = X[(((size_t)(f0 + ff) * 2 + p) * nl + i) * N + x];
+#pragma unroll
+                    for (int j = 0; j < kCombJ; j++) mac128(a1[j], a0[j], xv, cs[ff][j]);
+                }
+#pragma unroll
+                for (int j = 0; j < kCombJ; j++) a1[j] = reduce_word(a1[j], P);
             }
-#pragma unroll
-            for (int j = 0; j < kCombJ; j++) hi[j] = reduce_word(hi[j], P);
         }
     }
     if (x < N) {
 #pragma unroll
         for (int j = 0; j < kCombJ; j++)
             if (j0 + j < Fp)
-                Z[(((size_t)(j0 + j) * 2 + p) * z_ls + i) * N + x] = redc(hi[j], lo[j], P);
+                Z[(((size_t)(j0 + j) * 2 + p) * z_ls + i) * N + x] =
+                    split ? fold_split(a0[j], a1[j], a2[j], P) : redc(a1[j], a0[j], P);
     }
 }
 
@@ -811,15 +830,32 @@ __global__ void k_rescale_finish(u64 *ct, int ls, const u64 *rr, int level,
 // two words below 2^61 accumulate below p * 2^64, so one Montgomery
 // reduction gives the exact residue.
 // ------------------------------------------------------------------------
+// NMAX bounds T.n_in at compile time, so that y stays in registers.
+template <int NMAX>
 __device__ __forceinline__ u64 conv_point(const ConvTab &T, const u64 *y, int t, const PrimeC &P)
 {
     u64 hi = 0, lo = 0;
-    for (int k = 0; k < T.n_in; k++) mac128(hi, lo, y[k], T.hmod[k][t]);
+#pragma unroll
+    for (int k = 0; k < NMAX; k++)
+        if (k < T.n_in) mac128(hi, lo, y[k], T.hmod[k][t]);
     return redc(hi, lo, P);
+}
+
+template <int NMAX>
+__device__ __forceinline__ void conv_inputs(const ConvTab &T, const u64 *src, size_t limb_stride,
+                                            u64 *y, const PrimeC *__restrict__ primes)
+{
+#pragma unroll
+    for (int k = 0; k < NMAX; k++)
+        if (k < T.n_in) {
+            const u64 v = src[(size_t)T.in_l[k] * limb_stride];
+            y[k] = shoup_mul(v, T.hinv[k], T.hinv_s[k], primes[T.in_p[k]].q);
+        }
 }
 
 // ModUp conversion.  c1c: [ncol][nl][N] coefficient domain (nl = level+1);
 // digits: [ncol][beta][E][N]; writes every limb outside digit dg.
+template <int NMAX>
 __global__ void __launch_bounds__(256)
 k_modup_conv(const u64 *__restrict__ c1c, int nl, u64 *digits, int beta, int E,
              const ConvTab *__restrict__ tabs, const PrimeC *__restrict__ primes, int N)
@@ -828,21 +864,18 @@ k_modup_conv(const u64 *__restrict__ c1c, int nl, u64 *digits, int beta, int E,
     const ConvTab &T = tabs[dg];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= N) return;
-    u64 y[8];
-    for (int k = 0; k < T.n_in; k++) {
-        const int pi = T.in_p[k];
-        const u64 v = c1c[((size_t)f * nl + T.in_l[k]) * N + x];
-        y[k] = shoup_mul(v, T.hinv[k], T.hinv_s[k], primes[pi].q);
-    }
+    u64 y[NMAX];
+    conv_inputs<NMAX>(T, c1c + (size_t)f * nl * N + x, N, y, primes);
     u64 *out = digits + ((size_t)f * beta + dg) * E * N;
     for (int t = 0; t < T.n_out; t++) {
         const PrimeC P = primes[T.out_p[t]];
-        out[(size_t)T.out_l[t] * N + x] = conv_point(T, y, t, P);
+        out[(size_t)T.out_l[t] * N + x] = conv_point<NMAX>(T, y, t, P);
     }
 }
 
 // ModDown conversion P -> q_0..q_level.  u: [npoly][E][N] (P limbs in the
 // coefficient domain at positions level+1..), conv: [npoly][level+1][N].
+template <int NMAX>
 __global__ void __launch_bounds__(256)
 k_moddown_conv(const u64 *__restrict__ u, int E, u64 *conv, int nl,
                const ConvTab *__restrict__ tab, const PrimeC *__restrict__ primes, int N)
@@ -851,14 +884,11 @@ k_moddown_conv(const u64 *__restrict__ u, int E, u64 *conv, int nl,
     const ConvTab &T = *tab;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= N) return;
-    u64 y[8];
-    for (int k = 0; k < T.n_in; k++) {
-        const u64 v = u[((size_t)poly * E + T.in_l[k]) * N + x];
-        y[k] = shoup_mul(v, T.hinv[k], T.hinv_s[k], primes[T.in_p[k]].q);
-    }
+    u64 y[NMAX];
+    conv_inputs<NMAX>(T, u + (size_t)poly * E * N + x, N, y, primes);
     for (int t = 0; t < T.n_out; t++) {
         const PrimeC P = primes[T.out_p[t]];
-        conv[((size_t)poly * nl + T.out_l[t]) * N + x] = conv_point(T, y, t, P);
+        conv[((size_t)poly * nl + T.out_l[t]) * N + x] = conv_point<NMAX>(T, y, t, P);
     }
 }
 
@@ -885,7 +915,7 @@ __device__ __forceinline__ ulonglong2 gather_pair(const u64 *limb, int m2, bool 
 // (P mod q_i and its Shoup companion at pmodq[2i], pmodq[2i+1]), so that
 // ModDown of u is Rot(c) itself: ModDown(A + P B) = ModDown(A) + B exactly.
 template <int BETA>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, BETA <= 4 ? 3 : 2)
 k_ks_ip(const u64 *__restrict__ key, int KL, const u64 *__restrict__ lane, int ls,
         const u64 *__restrict__ digits, int ncol, int level, int E, int alpha, int nq,
         uint32_t g, int log_n, u64 *u, const PrimeC *__restrict__ primes,
@@ -906,6 +936,7 @@ k_ks_ip(const u64 *__restrict__ key, int KL, const u64 *__restrict__ lane, int l
         kb[d] = *reinterpret_cast<const ulonglong2 *>(key + (((size_t)d * 2 + 0) * KL + pi) * N + x);
         ka[d] = *reinterpret_cast<const ulonglong2 *>(key + (((size_t)d * 2 + 1) * KL + pi) * N + x);
     }
+#pragma unroll 2
     for (int f = 0; f < ncol; f++) {
         u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0, h2 = 0, l2 = 0, h3 = 0, l3 = 0;
 #pragma unroll
@@ -1073,7 +1104,7 @@ struct GProg {
     int nsrc, nterm, X, accumulate;
     const u64 *su[kGmacSrc];      // rotation: key-switch output; kept lane: nullptr
     const u64 *slane[kGmacSrc];   // kept lane
-    int tsrc[kGmacTerms];         // terms sorted by output
+    u32 tvoff[kGmacTerms];        // terms sorted by output: byte offset of the source's row in vsm
     const u64 *tmask[kGmacTerms];
     int dfirst[kGmacOut + 1];
     u64 *outs[kGmacOut];
@@ -1090,28 +1121,13 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-__device__ __forceinline__ u64 split23(u64 v) { return (v & 0x7FFFFF) | ((v >> 23) << 32); }
-
-__device__ __forceinline__ void mac_split(u64 &a0, u64 &a1, u64 &a2, u64 v, u64 m)
+// 16-byte shared-memory load by 32-bit shared address (volatile: it must
+// stay after the barrier that publishes the staged words)
+__device__ __forceinline__ ulonglong2 lds128(u32 addr)
 {
-    const u32 v0 = (u32)v, v1 = (u32)(v >> 32), m0 = (u32)m, m1 = (u32)(m >> 32);
-    a0 += (u64)v0 * m0;
-    a1 += (u64)v0 * m1;
-    a1 += (u64)v1 * m0;
-    a2 += (u64)v1 * m1;
-}
-
-// (A0 + A1 2^23 + A2 2^46) R^-1 mod q
-__device__ __forceinline__ u64 fold_split(u64 a0, u64 a1, u64 a2, const PrimeC &P)
-{
-    u64 lo = a0, hi = (a1 >> 41) + (a2 >> 18);
-    u64 t = a1 << 23;
-    lo += t;
-    hi += lo < t;
-    t = a2 << 46;
-    lo += t;
-    hi += lo < t;
-    return redc(reduce_word(hi, P), lo, P);
+    ulonglong2 v;
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"(addr));
+    return v;
 }
 
 __global__ void __launch_bounds__(kGmacThreads)
@@ -1135,13 +1151,13 @@ k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
     const u64 q = P.q;
     const bool split = q < (1ull << 46);
     const size_t ext_off = ((size_t)poly * E + i) * N + x;
-    // 1. asynchronous copies
-    for (int e = tid; e < nterm * pp_n; e += kGmacThreads) {
-        const int t = e / pp_n, k = e - t * pp_n;
-        const int xx = 2 * (blockIdx.x * pp_n + k);
-        if (xx < N) cp_async16(msm + e, pg.tmask[t] + (size_t)i * N + xx);
-        else msm[e] = make_ulonglong2(0, 0);
-    }
+    // 1. asynchronous copies; thread (poly, pp) copies the masks of terms
+    // poly, poly + npoly, ... at its own slot pair
+    if (poly < npoly)
+        for (int t = poly; t < nterm; t += npoly) {
+            if (x < N) cp_async16(msm + t * pp_n + pp, pg.tmask[t] + (size_t)i * N + x);
+            else msm[t * pp_n + pp] = make_ulonglong2(0, 0);
+        }
     if (act) {
         for (int s = 0; s < nsrc; s++) {
             ulonglong2 *dst = vsm + (size_t)s * kGmacThreads + tid;
@@ -1152,10 +1168,10 @@ k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
     }
     cp_async_wait_all();
     // 2. in place, each thread on the words it copied
-    if (split)
-        for (int e = tid; e < nterm * pp_n; e += kGmacThreads) {
-            const ulonglong2 m = msm[e];
-            msm[e] = make_ulonglong2(split23(m.x), split23(m.y));
+    if (split && poly < npoly)
+        for (int t = poly; t < nterm; t += npoly) {
+            const ulonglong2 m = msm[t * pp_n + pp];
+            msm[t * pp_n + pp] = make_ulonglong2(split23(m.x), split23(m.y));
         }
     if (act && (split || isq)) {
         const u64 pw = isq ? pmodq[2 * i] : 0, pws = isq ? pmodq[2 * i + 1] : 0;
@@ -1177,7 +1193,12 @@ k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
     }
     __syncthreads();
     if (!act) return;
-    // 3. outputs
+    // 3. outputs.  Shared-memory reads by 32-bit address: the source row of a
+    // term is a constant offset from this thread's slot, the mask row steps
+    // by pp_n words per term.
+    const u32 vbase = (u32)__cvta_generic_to_shared(vsm + tid);
+    u32 maddr = (u32)__cvta_generic_to_shared(msm + pp);
+    const u32 mstep = (u32)pp_n * 16;
     for (int d = 0; d < pg.X; d++) {
         ulonglong2 *o = reinterpret_cast<ulonglong2 *>(pg.outs[d] + ext_off);
         const ulonglong2 b = pg.accumulate ? *o : make_ulonglong2(0, 0);
@@ -1185,20 +1206,18 @@ k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
         ulonglong2 r;
         if (split) {
             u64 a0 = 0, a1 = 0, a2 = 0, c0 = 0, c1 = 0, c2 = 0;
-#pragma unroll 4
-            for (int t = t0; t < t1; t++) {
-                const ulonglong2 v = vsm[(size_t)pg.tsrc[t] * kGmacThreads + tid];
-                const ulonglong2 m = msm[t * pp_n + pp];
+            for (int t = t0; t < t1; t++, maddr += mstep) {
+                const ulonglong2 v = lds128(vbase + pg.tvoff[t]);
+                const ulonglong2 m = lds128(maddr);
                 mac_split(a0, a1, a2, v.x, m.x);
                 mac_split(c0, c1, c2, v.y, m.y);
             }
             r = make_ulonglong2(fold_split(a0, a1, a2, P), fold_split(c0, c1, c2, P));
         } else {
             u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
-#pragma unroll 4
-            for (int t = t0; t < t1; t++) {
-                const ulonglong2 v = vsm[(size_t)pg.tsrc[t] * kGmacThreads + tid];
-                const ulonglong2 m = msm[t * pp_n + pp];
+            for (int t = t0; t < t1; t++, maddr += mstep) {
+                const ulonglong2 v = lds128(vbase + pg.tvoff[t]);
+                const ulonglong2 m = lds128(maddr);
                 mac128(hi0, lo0, v.x, m.x);
                 mac128(hi1, lo1, v.y, m.y);
             }
@@ -1212,23 +1231,54 @@ k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
     }
 }
 
-// ModDown finish into a lane: out_i = (ext_i - conv_i) * P^-1 for i <= level
+// ModDown followed by the rescale by q_l, equal word for word to the two
+// done in turn.  With conv_i the base conversion of the special limbs and
+// o_l = (ext_l - conv_l) P^-1 mod q_l (coefficient domain: the limb the
+// rescale drops), the rescaled limbs are
+//   ((ext_i - conv_i) P^-1 - [o_l]_{q_i}) q_l^-1 = (ext_i - (conv_i + P o_l)) (P q_l)^-1,
+// so one forward NTT of w_i = conv_i + P o_l mod q_i per kept limb replaces
+// the NTT of conv_i and the rescale's NTT of [o_l]_{q_i}.
+// ext: [npoly][E][N], limbs l and l+1.. in the coefficient domain;
+// w: [npoly][l][N] coefficient domain.
+template <int NMAX>
 __global__ void __launch_bounds__(256)
-k_moddown_store(const u64 *__restrict__ ext, int E, const u64 *__restrict__ conv, u64 *out, int ls,
-                int npoly, int level, const u64 *__restrict__ pinv, const PrimeC *__restrict__ primes,
-                int N)
+k_moddown_rescale_conv(const u64 *__restrict__ ext, int E, u64 *w, int l,
+                       const ConvTab *__restrict__ tab, const u64 *__restrict__ pinv,
+                       const u64 *__restrict__ pmodq, const PrimeC *__restrict__ primes, int N)
+{
+    const int poly = blockIdx.y;
+    const ConvTab &T = *tab;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    u64 y[NMAX];
+    conv_inputs<NMAX>(T, ext + (size_t)poly * E * N + x, N, y, primes);
+    const PrimeC Pl = primes[l];
+    const u64 el = ext[((size_t)poly * E + l) * N + x];
+    const u64 ol = shoup_mul(sub_mod(el, conv_point<NMAX>(T, y, l, Pl), Pl.q), pinv[2 * l],
+                             pinv[2 * l + 1], Pl.q);
+    for (int t = 0; t < l; t++) {
+        const PrimeC P = primes[t];
+        w[((size_t)poly * l + t) * N + x] =
+            add_mod(conv_point<NMAX>(T, y, t, P), shoup_mul(ol, pmodq[2 * t], pmodq[2 * t + 1], P.q), P.q);
+    }
+}
+
+// out_i = (ext_i - w_i) (P q_l)^-1 for i < l (NTT domain)
+__global__ void __launch_bounds__(256)
+k_moddown_rescale_finish(const u64 *__restrict__ ext, int E, const u64 *__restrict__ w, u64 *out,
+                         int ls, int npoly, int l, const u64 *__restrict__ tab,
+                         const PrimeC *__restrict__ primes, int N)
 {
     const int i = blockIdx.y;
     const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (x >= N) return;
-    const u64 q = primes[i].q, pv = pinv[2 * i], pvs = pinv[2 * i + 1];
-    const int nl = level + 1;
+    const u64 q = primes[i].q, c = tab[2 * i], cs = tab[2 * i + 1];
     for (int poly = 0; poly < npoly; poly++) {
         const ulonglong2 e = *reinterpret_cast<const ulonglong2 *>(ext + ((size_t)poly * E + i) * N + x);
-        const ulonglong2 c = *reinterpret_cast<const ulonglong2 *>(conv + ((size_t)poly * nl + i) * N + x);
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(w + ((size_t)poly * l + i) * N + x);
         *reinterpret_cast<ulonglong2 *>(out + ((size_t)poly * ls + i) * N + x) =
-            make_ulonglong2(shoup_mul(sub_mod(e.x, c.x, q), pv, pvs, q),
-                            shoup_mul(sub_mod(e.y, c.y, q), pv, pvs, q));
+            make_ulonglong2(shoup_mul(sub_mod(e.x, v.x, q), c, cs, q),
+                            shoup_mul(sub_mod(e.y, v.y, q), c, cs, q));
     }
 }
 
@@ -1257,6 +1307,20 @@ __global__ void k_lift_special(const u64 *limb0, u64 q0, u64 *out, int np, int n
 // ========================================================================
 // host wrappers
 // ========================================================================
+// launch a kernel templated on the number of base-conversion inputs
+#define FG_NIN_DISPATCH(n, LAUNCH)                                               \
+    switch (n) {                                                                 \
+    case 1: LAUNCH(1); break;                                                    \
+    case 2: LAUNCH(2); break;                                                    \
+    case 3: LAUNCH(3); break;                                                    \
+    case 4: LAUNCH(4); break;                                                    \
+    case 5: LAUNCH(5); break;                                                    \
+    case 6: LAUNCH(6); break;                                                    \
+    case 7: LAUNCH(7); break;                                                    \
+    case 8: LAUNCH(8); break;                                                    \
+    default: throw fg_error(FG_EINVAL, "base conversion with more than 8 inputs"); \
+    }
+
 namespace kern {
 
 KTimer::KTimer(fg_ctx *c, const char *cls, double alg_bytes) : ctx(c), bytes(alg_bytes)
@@ -1437,6 +1501,8 @@ void copy_limbs(fg_ctx *ctx, const u64 *src, int src_ls, u64 *dst, int dst_ls, i
 void comb_const_mac(fg_ctx *ctx, const u64 *X, int F, int Fp, int level, const u64 *consts, u64 *Z,
                     int z_ls)
 {
+    // split partial sums stay below 2^64 for up to 2^16 terms
+    FG_CHECK(F < (1 << 16), FG_EINVAL, "combination over more than 2^16 input columns");
     for (int j0 = 0; j0 < Fp; j0 += kCombJ) {
         const int jn = std::min(kCombJ, Fp - j0);
         KTimer kt(ctx, "comb", ((double)F + jn) * 2 * (level + 1) * ctx->n * 8);
@@ -1495,8 +1561,11 @@ void modup(fg_ctx *ctx, const u64 *lane, int ls, int ncol, int level, u64 *digit
     dim3 g((N + 255) / 256, 1, ncol * beta);
     {
     KTimer kt(ctx, "modup_conv", (double)ncol * (nl + (double)beta * E - nl) * N * 8);
-    k_modup_conv<<<g, 256, 0, ctx->stream>>>(c1c, nl, digits, beta, E, ctx->modup_tabs(level),
-                                             ctx->d_primes, N);
+#define FG_LAUNCH(M)                                                                       \
+    k_modup_conv<M><<<g, 256, 0, ctx->stream>>>(c1c, nl, digits, beta, E, ctx->modup_tabs(level), \
+                                                ctx->d_primes, N)
+    FG_NIN_DISPATCH(std::min(ctx->alpha, nl), FG_LAUNCH)
+#undef FG_LAUNCH
     check_launch("modup_conv");
     }
     std::vector<int> dp(beta * E);
@@ -1540,8 +1609,11 @@ void rotate_mac(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int nco
     dim3 g2((N + 255) / 256, 2 * ncol);
     {
     KTimer kt(ctx, "moddown_conv", (double)2 * ncol * (ctx->np + nl) * N * 8);
-    k_moddown_conv<<<g2, 256, 0, ctx->stream>>>(u, E, conv, nl, ctx->moddown_tab(level),
-                                                ctx->d_primes, N);
+#define FG_LAUNCH(M)                                                                       \
+    k_moddown_conv<M><<<g2, 256, 0, ctx->stream>>>(u, E, conv, nl, ctx->moddown_tab(level),   \
+                                                   ctx->d_primes, N)
+    FG_NIN_DISPATCH(ctx->np, FG_LAUNCH)
+#undef FG_LAUNCH
     check_launch("moddown_conv");
     }
     std::vector<int> pq(nl);
@@ -1627,7 +1699,7 @@ void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vec
         pg.outs[d] = outs[d];
         for (size_t t = 0; t < terms_in.size(); t++)
             if (term_dest[t] == d) {
-                pg.tsrc[n] = src_of[t];
+                pg.tvoff[n] = (u32)src_of[t] * kGmacThreads * 16;
                 pg.tmask[n] = terms_in[t].mask;
                 n++;
             }
@@ -1673,30 +1745,37 @@ void ks_only(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int ncol, 
     check_launch("ks_ip");
 }
 
-void moddown_to_lane(fg_ctx *ctx, u64 *ext, int ncol, int level, u64 *out, int ls)
+void moddown_rescale_to_lane(fg_ctx *ctx, u64 *ext, int ncol, int level, u64 *out, int ls)
 {
-    const int N = ctx->n, nl = level + 1, E = ctx->ext(level);
-    std::vector<int> pp(E);
-    for (int i = 0; i < E; i++) pp[i] = i <= level ? -1 : ctx->ext_prime(level, i);
-    LimbSet us{ext, E, E, 2 * ncol, pp};
+    FG_CHECK(level >= 1, FG_ELEVEL, "rescale needs level >= 1");
+    const int N = ctx->n, l = level, E = ctx->ext(level), npoly = 2 * ncol;
+    std::vector<int> pp(E, -1);
+    pp[l] = l;
+    for (int i = l + 1; i < E; i++) pp[i] = ctx->ext_prime(level, i);
+    LimbSet us{ext, E, E, npoly, pp};
     ntt_inv(ctx, us, us);
-    u64 *conv = (u64 *)ctx->buf("ks_conv", (size_t)ncol * 2 * nl * N * 8);
+    u64 *w = (u64 *)ctx->buf("ks_conv", (size_t)npoly * l * N * 8);
     {
-        KTimer kt(ctx, "moddown_conv", (double)2 * ncol * (ctx->np + nl) * N * 8);
-        dim3 g2((N + 255) / 256, 2 * ncol);
-        k_moddown_conv<<<g2, 256, 0, ctx->stream>>>(ext, E, conv, nl, ctx->moddown_tab(level),
-                                                    ctx->d_primes, N);
-        check_launch("moddown_conv");
+        KTimer kt(ctx, "moddown_conv", (double)npoly * (ctx->np + 1 + l) * N * 8);
+        dim3 g2((N + 255) / 256, npoly);
+#define FG_LAUNCH(M)                                                                        \
+        k_moddown_rescale_conv<M><<<g2, 256, 0, ctx->stream>>>(ext, E, w, l, ctx->moddown_tab(level), \
+                                                               ctx->pinv_tab(level), ctx->d_pmodq,  \
+                                                               ctx->d_primes, N)
+        FG_NIN_DISPATCH(ctx->np, FG_LAUNCH)
+#undef FG_LAUNCH
+        check_launch("moddown_rescale_conv");
     }
-    std::vector<int> pq(nl);
-    for (int i = 0; i < nl; i++) pq[i] = i;
-    LimbSet cs{conv, nl, nl, 2 * ncol, pq};
-    ntt_fwd(ctx, cs, cs);
-    KTimer kt(ctx, "moddown_store", (double)2 * ncol * nl * 3 * N * 8);
-    dim3 g3((N / 2 + 255) / 256, nl);
-    k_moddown_store<<<g3, 256, 0, ctx->stream>>>(ext, E, conv, out, ls, 2 * ncol, level,
-                                                 ctx->pinv_tab(level), ctx->d_primes, N);
-    check_launch("moddown_store");
+    std::vector<int> pq(l);
+    for (int i = 0; i < l; i++) pq[i] = i;
+    LimbSet ws{w, l, l, npoly, pq};
+    ntt_fwd(ctx, ws, ws);
+    KTimer kt(ctx, "moddown_store", (double)npoly * l * 3 * N * 8);
+    dim3 g3((N / 2 + 255) / 256, l);
+    k_moddown_rescale_finish<<<g3, 256, 0, ctx->stream>>>(ext, E, w, out, ls, npoly, l,
+                                                          ctx->moddown_rescale_tab(level),
+                                                          ctx->d_primes, N);
+    check_launch("moddown_rescale_finish");
 }
 
 }  // namespace kern

@@ -458,13 +458,10 @@ int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, const 
             }
             flush();
             // one ModDown per output, then the rescale that closes the group
-            for (int x = 0; x < g.n_out; x++) {
-                kern::moddown_to_lane(ctx, ext[x], Fp, level, (*outb)[x], LS);
-                kern::rescale_ntt(ctx, (*outb)[x], LS, Fp * 2, level);
-            }
+            for (int x = 0; x < g.n_out; x++)
+                kern::moddown_rescale_to_lane(ctx, ext[x], Fp, level, (*outb)[x], LS);
             if (any_acc) {
-                kern::moddown_to_lane(ctx, ext[g.n_out], Fp, level, acc_new, LS);
-                kern::rescale_ntt(ctx, acc_new, LS, Fp * 2, level);
+                kern::moddown_rescale_to_lane(ctx, ext[g.n_out], Fp, level, acc_new, LS);
                 if (have_acc) {
                     std::vector<int> pidx(LS, -1);
                     for (int i = 0; i < level; i++) pidx[i] = i;

@@ -69,10 +69,64 @@ __device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) { return reduce2(a +
 __device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
 
 // 128-bit accumulator: (hi, lo) += a * b
+// (one carry-chained multiply-add pair, so no compare is needed for the carry)
 __device__ __forceinline__ void mac128(u64 &hi, u64 &lo, u64 a, u64 b)
 {
-    u64 p_lo = a * b;
-    u64 p_hi = mulhi64(a, b);
-    lo += p_lo;
-    hi += p_hi + (lo < p_lo);
+    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\t"
+        "madc.hi.u64 %1, %2, %3, %1;"
+        : "+l"(lo), "+l"(hi)
+        : "l"(a), "l"(b));
+}
+
+// Products of factors below 2^46 on 32-bit multipliers.  A factor is
+// stored split into 23-bit halves, v0 | v1 << 32 (v = v0 + v1 2^23), and a
+// sum of products is kept as three 64-bit partial sums
+//   A0 = sum v0 m0,  A1 = sum (v0 m1 + v1 m0),  A2 = sum v1 m1,
+// each term below 2^47, so up to 2^16 terms cannot overflow.  Four
+// 32 x 32 -> 64-bit multiply-adds per product replace the 64 x 64 -> 128-bit
+// product of mac128.
+__device__ __forceinline__ u64 split23(u64 v) { return (v & 0x7FFFFF) | ((v >> 23) << 32); }
+
+__device__ __forceinline__ void mac_split(u64 &a0, u64 &a1, u64 &a2, u64 v, u64 m)
+{
+    const u32 v0 = (u32)v, v1 = (u32)(v >> 32), m0 = (u32)m, m1 = (u32)(m >> 32);
+    asm("mad.wide.u32 %0, %3, %5, %0;\n\t"
+        "mad.wide.u32 %1, %3, %6, %1;\n\t"
+        "mad.wide.u32 %1, %4, %5, %1;\n\t"
+        "mad.wide.u32 %2, %4, %6, %2;"
+        : "+l"(a0), "+l"(a1), "+l"(a2)
+        : "r"(v0), "r"(v1), "r"(m0), "r"(m1));
+}
+
+// (A0 + A1 2^23 + A2 2^46) R^-1 mod q for partial sums that have not wrapped
+__device__ __forceinline__ u64 fold_split(u64 a0, u64 a1, u64 a2, const PrimeC &P)
+{
+    u64 lo = a0, hi = (a1 >> 41) + (a2 >> 18);
+    u64 t = a1 << 23;
+    lo += t;
+    hi += lo < t;
+    t = a2 << 46;
+    lo += t;
+    hi += lo < t;
+    return redc(reduce_word(hi, P), lo, P);
+}
+
+
+// Shoup product with a cheaper quotient: y * w mod q in [0, 3q) for any
+// y < 2^64 (q < 2^62).  The quotient floor(y w' / 2^64) is computed from the
+// three 32 x 32-bit partial products that reach the high word, leaving out
+// y_lo w'_lo: with s = lo(y_lo w'_hi) + y_hi w'_lo,
+//   y w' = y_lo w'_lo + lo(s) 2^32 + (hi(s) + hi(y_lo w'_hi) + y_hi w'_hi) 2^64,
+// and the first two terms sum to less than 2^65, so the estimate is the true
+// quotient or one less; Shoup's own estimate is within one of floor(y w / q).
+__device__ __forceinline__ u64 shoup_lazy3(u64 y, u64 w, u64 ws, u64 q)
+{
+    const u32 y0 = (u32)y, y1 = (u32)(y >> 32);
+    const u32 s0 = (u32)ws, s1 = (u32)(ws >> 32);
+    u64 t, s, h;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(t) : "r"(y0), "r"(s1));
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(s) : "r"(y1), "r"(s0), "l"(t & 0xFFFFFFFFull));
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(h) : "r"(y1), "r"(s1), "l"(t >> 32));
+    h += s >> 32;
+    return y * w - h * q;
 }

@@ -69,14 +69,21 @@ def test_poly_mul_matches_oracle(fg, name, level):
         np.testing.assert_array_equal(got[i], _ref.negacyclic_mul(a[i], b[i], q, P.psi(q)))
 
 
-@pytest.mark.parametrize("log_n", [15, 16])
-def test_poly_mul_large_n(fg, log_n):
+@pytest.mark.parametrize("log_n,pattern", [(15, "random"), (16, "random"), (16, "max")])
+def test_poly_mul_large_n(fg, log_n, pattern):
+    """N = 2^15 and 2^16 (the radix-16 path, lazy butterflies for the 45-bit
+    primes); "max" sets every coefficient to q - 1, the largest inputs the
+    lazy bounds must absorb."""
     p = dict(log_n=log_n, q_bits=[60, 45, 45], p_bits=[60], alpha=1, log_scale=45)
     ctx = fg.Context(**p)
     P = ckks.Params(log_n, p["q_bits"], p["p_bits"], 1, 45)
     rng = np.random.default_rng(log_n)
-    a = rand_res(rng, P.q, P.n)
-    b = rand_res(rng, P.q, P.n)
+    if pattern == "max":
+        a = np.stack([np.full(P.n, q - 1, dtype=np.uint64) for q in P.q])
+        b = a.copy()
+    else:
+        a = rand_res(rng, P.q, P.n)
+        b = rand_res(rng, P.q, P.n)
     got = fg.poly_mul(ctx, a, b, 2)
     for i in (0, 2):
         q = P.q[i]
