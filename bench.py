@@ -125,6 +125,14 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of the ranks' values (every rank gets it)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------ CPU oracle sample
 def oracle_sample(plan_counts, budget_s=25.0):
     """Time the oracle on bounded pieces of the workload (one hoisted rotation
@@ -193,11 +201,20 @@ def oracle_plan_counts():
 
 
 def run_reference(args):
+    """The oracle as the reference arm: W untimed and K timed bounded samples
+    of the layer (each about 6 s of host work), the layer time of each
+    extrapolated from the plan's operation counts; the line reports the mean
+    of the K.  Under torchrun only rank 0 works."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     counts = oracle_plan_counts()
-    base = oracle_sample(counts)
+    for _ in range(args.warmup):
+        oracle_sample(counts)
+    samples = [oracle_sample(counts) for _ in range(max(1, args.steps))]
+    base = dict(samples[-1])
+    base["value"] = statistics.mean(s["value"] for s in samples)
+    base["sample"] = "%d timed samples (after %d untimed) of: %s" % (len(samples), args.warmup, base["sample"])
     line = {"impl": "reference", "metric": METRIC, "value": round(base["value"], 3), "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(base["value"], 3), "higher_is_better": False, "scaling": "weak",
@@ -365,9 +382,7 @@ def run_ours(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
 
     # ---- end to end through the C ABI with host buffers (copies inside)
     in_host = in_dev.cpu().pin_memory()
@@ -382,6 +397,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    if dist is not None:
+        e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
     h2d = in_host.numel() * 8
     d2h = out_host.numel() * 8
 

@@ -248,10 +248,10 @@ struct GroupSource {
 void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vector<Dest> &terms,
                const std::vector<int> &term_dest, const std::vector<u64 *> &outs, bool accumulate,
                int ncol, int level, int ls);
-// key-switching inner product only: u [ncol][2][E][N] (extended basis, NTT domain)
-void ks_only(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int ncol, int level,
-             const u64 *digits, u64 *u);
-// ModDown of an extended-basis batch [ncol][2][E][N] into lane limbs 0..level (stride ls)
+// key-switch outputs u_r = sum_d D_d(sigma_r) evk_r + P phi_r(c0) of several
+// rotations r of one lane (extended basis, NTT domain, [ncol][2][E][N] each)
+void ks_multi(fg_ctx *ctx, const std::vector<const KeyDev *> &keys, const std::vector<u64 *> &us,
+              const u64 *lane, int ls, int ncol, int level, const u64 *digits);
 // ModDown of an extended-basis sum to Q, then the rescale by q_level, into a
 // lane (limbs 0..level-1); ext is scratch and is overwritten
 void moddown_rescale_to_lane(fg_ctx *ctx, u64 *ext, int ncol, int level, u64 *out, int ls);

@@ -911,23 +911,36 @@ __device__ __forceinline__ ulonglong2 gather_pair(const u64 *limb, int m2, bool 
     return swap ? make_ulonglong2(v.y, v.x) : v;
 }
 
+// Several rotations of one lane in one launch: blockIdx.y picks the rotation
+// and blockIdx.z the limb, so the CTAs of one limb run together and the
+// lane's digits of that limb (ncol * beta limbs) are read from HBM once and
+// gathered again from L2 by the other rotations.
+constexpr int kKsMulti = 24;
+struct KsSet {
+    int n;
+    const u64 *key[kKsMulti];
+    uint32_t g[kKsMulti];
+    u64 *u[kKsMulti];
+};
+
 // With pmodq given, part 0 also receives P phi_g(c0) on the limbs of Q
 // (P mod q_i and its Shoup companion at pmodq[2i], pmodq[2i+1]), so that
 // ModDown of u is Rot(c) itself: ModDown(A + P B) = ModDown(A) + B exactly.
 template <int BETA>
 __global__ void __launch_bounds__(256, BETA <= 4 ? 3 : 2)
-k_ks_ip(const u64 *__restrict__ key, int KL, const u64 *__restrict__ lane, int ls,
+k_ks_ip(const KsSet ks, int KL, const u64 *__restrict__ lane, int ls,
         const u64 *__restrict__ digits, int ncol, int level, int E, int alpha, int nq,
-        uint32_t g, int log_n, u64 *u, const PrimeC *__restrict__ primes,
-        const u64 *__restrict__ pmodq)
+        int log_n, const PrimeC *__restrict__ primes, const u64 *__restrict__ pmodq)
 {
     const int N = 1 << log_n;
-    const int i = blockIdx.y;
+    const int rot = blockIdx.y, i = blockIdx.z;
     const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (x >= N) return;
+    const u64 *key = ks.key[rot];
+    u64 *u = ks.u[rot];
     const int pi = i <= level ? i : nq + (i - level - 1);
     const PrimeC P = primes[pi];
-    const int sx = auto_src(x, g, log_n);
+    const int sx = auto_src(x, ks.g[rot], log_n);
     const bool swap = sx & 1;
     const int own = i <= level ? i / alpha : -1;
     ulonglong2 kb[BETA], ka[BETA];
@@ -950,6 +963,7 @@ k_ks_ip(const u64 *__restrict__ key, int KL, const u64 *__restrict__ lane, int l
             mac128(h3, l3, v.y, ka[d].y);
         }
         ulonglong2 r0 = make_ulonglong2(redc(h0, l0, P), redc(h1, l1, P));
+        const ulonglong2 r1 = make_ulonglong2(redc(h2, l2, P), redc(h3, l3, P));
         if (pmodq && i <= level) {
             const ulonglong2 c0 = gather_pair(lane + (((size_t)f * 2) * ls + i) * N, sx, swap);
             const u64 pw = pmodq[2 * i], pws = pmodq[2 * i + 1];
@@ -957,8 +971,7 @@ k_ks_ip(const u64 *__restrict__ key, int KL, const u64 *__restrict__ lane, int l
             r0.y = add_mod(r0.y, shoup_mul(c0.y, pw, pws, P.q), P.q);
         }
         *reinterpret_cast<ulonglong2 *>(u + (((size_t)f * 2 + 0) * E + i) * N + x) = r0;
-        *reinterpret_cast<ulonglong2 *>(u + (((size_t)f * 2 + 1) * E + i) * N + x) =
-            make_ulonglong2(redc(h2, l2, P), redc(h3, l3, P));
+        *reinterpret_cast<ulonglong2 *>(u + (((size_t)f * 2 + 1) * E + i) * N + x) = r1;
     }
 }
 
@@ -1576,21 +1589,34 @@ void modup(fg_ctx *ctx, const u64 *lane, int ls, int ncol, int level, u64 *digit
     ntt_fwd(ctx, ds, ds);
 }
 
-void rotate_mac(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int ncol, int level,
-                const u64 *digits, const std::vector<Dest> &dests, int out_ls)
+// key-switch inner products of up to kKsMulti rotations of one lane (with
+// P phi(c0) folded in when add_c0 is set)
+static void ks_launch(fg_ctx *ctx, const std::vector<const KeyDev *> &keys, const std::vector<u64 *> &us,
+                      const u64 *lane, int ls, int ncol, int level, const u64 *digits, bool add_c0)
 {
-    const int N = ctx->n, nl = level + 1, E = ctx->ext(level), beta = ctx->n_digits(level);
+    const int N = ctx->n, E = ctx->ext(level), beta = ctx->n_digits(level);
     FG_CHECK(beta <= kMaxBeta, FG_EINVAL, "too many key-switching digits");
+    FG_CHECK(!keys.empty() && keys.size() <= (size_t)kKsMulti && keys.size() == us.size(), FG_EINVAL,
+             "ks_launch: 1 to 24 rotations");
     const int KL = ctx->nq + ctx->np;
-    u64 *u = (u64 *)ctx->buf("ks_u", (size_t)ncol * 2 * E * N * 8);
-    dim3 g1((N / 2 + 255) / 256, E);
-    {
-    KTimer kt(ctx, "ks_ip", ((double)ncol * beta * E + 2.0 * beta * E + 2.0 * ncol * E) * N * 8);
-#define FG_KS_CASE(B)                                                                       \
-    case B:                                                                                 \
-        k_ks_ip<B><<<g1, 256, 0, ctx->stream>>>(key.d, KL, lane, ls, digits, ncol, level, E, \
-                                                ctx->alpha, ctx->nq, key.galois, ctx->log_n, \
-                                                u, ctx->d_primes, nullptr);                 \
+    KsSet ks;
+    memset(&ks, 0, sizeof(ks));
+    ks.n = (int)keys.size();
+    for (int r = 0; r < ks.n; r++) {
+        ks.key[r] = keys[r]->d;
+        ks.g[r] = keys[r]->galois;
+        ks.u[r] = us[r];
+    }
+    const u64 *pmodq = add_c0 ? ctx->d_pmodq : nullptr;
+    dim3 g1((N / 2 + 255) / 256, ks.n, E);
+    // digits and c0 once per launch, keys and outputs once per rotation
+    KTimer kt(ctx, "ks_ip", ((double)ncol * beta * E + (add_c0 ? (double)ncol * (level + 1) : 0) +
+                             (double)ks.n * (2.0 * beta * E + 2.0 * ncol * E)) * N * 8);
+#define FG_KS_CASE(B)                                                                          \
+    case B:                                                                                    \
+        k_ks_ip<B><<<g1, 256, 0, ctx->stream>>>(ks, KL, lane, ls, digits, ncol, level, E,      \
+                                                ctx->alpha, ctx->nq, ctx->log_n, ctx->d_primes, \
+                                                pmodq);                                        \
         break;
     switch (beta) {
         FG_KS_CASE(1) FG_KS_CASE(2) FG_KS_CASE(3) FG_KS_CASE(4) FG_KS_CASE(5) FG_KS_CASE(6)
@@ -1600,7 +1626,16 @@ void rotate_mac(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int nco
     }
 #undef FG_KS_CASE
     check_launch("ks_ip");
-    }
+}
+
+void rotate_mac(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int ncol, int level,
+                const u64 *digits, const std::vector<Dest> &dests, int out_ls)
+{
+    const int N = ctx->n, nl = level + 1, E = ctx->ext(level), beta = ctx->n_digits(level);
+    FG_CHECK(beta <= kMaxBeta, FG_EINVAL, "too many key-switching digits");
+    const int KL = ctx->nq + ctx->np;
+    u64 *u = (u64 *)ctx->buf("ks_u", (size_t)ncol * 2 * E * N * 8);
+    ks_launch(ctx, {&key}, {u}, lane, ls, ncol, level, digits, false);
     std::vector<int> pp(E);
     for (int i = 0; i < E; i++) pp[i] = i <= level ? -1 : ctx->ext_prime(level, i);
     LimbSet us{u, E, E, 2 * ncol, pp};
@@ -1722,27 +1757,15 @@ void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vec
     check_launch("group_mac");
 }
 
-void ks_only(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int ncol, int level,
-             const u64 *digits, u64 *u)
+void ks_multi(fg_ctx *ctx, const std::vector<const KeyDev *> &keys, const std::vector<u64 *> &us,
+              const u64 *lane, int ls, int ncol, int level, const u64 *digits)
 {
-    const int N = ctx->n, E = ctx->ext(level), beta = ctx->n_digits(level);
-    const int KL = ctx->nq + ctx->np;
-    dim3 g1((N / 2 + 255) / 256, E);
-    KTimer kt(ctx, "ks_ip", ((double)ncol * beta * E + 2.0 * beta * E + 2.0 * ncol * E + (double)ncol * (level + 1)) * N * 8);
-#define FG_KS_CASE(B)                                                                       \
-    case B:                                                                                 \
-        k_ks_ip<B><<<g1, 256, 0, ctx->stream>>>(key.d, KL, lane, ls, digits, ncol, level, E, \
-                                                ctx->alpha, ctx->nq, key.galois, ctx->log_n, \
-                                                u, ctx->d_primes, ctx->d_pmodq);            \
-        break;
-    switch (beta) {
-        FG_KS_CASE(1) FG_KS_CASE(2) FG_KS_CASE(3) FG_KS_CASE(4) FG_KS_CASE(5) FG_KS_CASE(6)
-        FG_KS_CASE(7) FG_KS_CASE(8) FG_KS_CASE(9) FG_KS_CASE(10) FG_KS_CASE(11) FG_KS_CASE(12)
-        FG_KS_CASE(13) FG_KS_CASE(14) FG_KS_CASE(15) FG_KS_CASE(16)
-    default: throw fg_error(FG_EINVAL, "too many key-switching digits");
+    for (size_t r0 = 0; r0 < keys.size(); r0 += kKsMulti) {
+        const size_t r1 = std::min(keys.size(), r0 + kKsMulti);
+        ks_launch(ctx, std::vector<const KeyDev *>(keys.begin() + r0, keys.begin() + r1),
+                  std::vector<u64 *>(us.begin() + r0, us.begin() + r1), lane, ls, ncol, level, digits,
+                  true);
     }
-#undef FG_KS_CASE
-    check_launch("ks_ip");
 }
 
 void moddown_rescale_to_lane(fg_ctx *ctx, u64 *ext, int ncol, int level, u64 *out, int ls)

@@ -393,7 +393,19 @@ int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, const 
                 gs.t1 = (int)terms.size();
                 srcs.push_back(gs);
             };
+            // key switches of the current lane not yet launched (one launch per
+            // lane and pool, see ks_multi)
+            std::vector<const KeyDev *> pend_keys;
+            std::vector<u64 *> pend_u;
+            const u64 *pend_lane = nullptr;
+            auto issue_pending = [&]() {
+                if (!pend_keys.empty())
+                    kern::ks_multi(ctx, pend_keys, pend_u, pend_lane, LS, Fp, level, digits);
+                pend_keys.clear();
+                pend_u.clear();
+            };
             auto flush = [&]() {
+                issue_pending();
                 if (srcs.empty()) return;
                 // outputs in slices of at most 20 (shared-memory partial sums)
                 for (int x0 = 0; x0 < X; x0 += 64) {
@@ -446,13 +458,16 @@ int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, const 
                     used = 0;
                 }
                 if (a != cur) {
+                    issue_pending();   // the ModUp below overwrites the digits
                     kern::modup(ctx, (*in)[a], LS, Fp, level, digits);
                     cur = a;
                 }
                 if ((int)upool.size() <= used)
                     upool.push_back((u64 *)ctx->buf("upool" + std::to_string(used), ext_w * 8));
                 const KeyDev &key = keys->get(((k % M) + M) % M);
-                kern::ks_only(ctx, key, (*in)[a], LS, Fp, level, digits, upool[used]);
+                pend_keys.push_back(&key);
+                pend_u.push_back(upool[used]);
+                pend_lane = (*in)[a];
                 add_source(upool[used], (*in)[a], key.galois, it->second);
                 used++;
             }

@@ -98,7 +98,10 @@ __device__ __forceinline__ void mac_split(u64 &a0, u64 &a1, u64 &a2, u64 v, u64 
         : "r"(v0), "r"(v1), "r"(m0), "r"(m1));
 }
 
-// (A0 + A1 2^23 + A2 2^46) R^-1 mod q for partial sums that have not wrapped
+// (A0 + A1 2^23 + A2 2^46) R^-1 mod q.  The sum S = A0 + A1 2^23 + A2 2^46
+// of T < 2^16 products of reduced factors is below T q^2, so its high word
+// is below T q (q / 2^64) < q / 4 for q < 2^46: Montgomery's condition
+// S < q 2^64 holds without reducing the high word first.
 __device__ __forceinline__ u64 fold_split(u64 a0, u64 a1, u64 a2, const PrimeC &P)
 {
     u64 lo = a0, hi = (a1 >> 41) + (a2 >> 18);
@@ -108,7 +111,7 @@ __device__ __forceinline__ u64 fold_split(u64 a0, u64 a1, u64 a2, const PrimeC &
     t = a2 << 46;
     lo += t;
     hi += lo < t;
-    return redc(reduce_word(hi, P), lo, P);
+    return redc(hi, lo, P);
 }
 
 
