@@ -193,8 +193,12 @@ typedef struct {
 int fg_plan_info(const fg_plan *plan, fg_plan_info_t *info);
 /* The distinct rotation amounts (mod M) the plan needs keys for. */
 int fg_plan_rotation_amounts(const fg_plan *plan, int32_t *out, int cap, int *n);
-/* The plan's structure as int64 records (format in the design doc terms:
- * header, perm, combination, groups, masks with slot/value-bit pairs).
+/* The plan's structure as int64 records: [N, M, t, B, V, F, Fp, in_level,
+ * out_level, radix_bits, aoo, n_groups, n_masks], perm[V], the combination
+ * (t == 1: F*Fp integer constants; t > 1: nb*Fp mask ids, n_rots, rots),
+ * per group [bit_lo, n_bits, level, n_in, n_out, n_rots, (src, k)*,
+ * n_terms, (src, k, dst, mask)*] (dst -1 = the accumulator), per mask
+ * [level, n_slots, (slot, IEEE-754 bits of the value)*].
  * With out == NULL only *len is set. */
 int fg_plan_describe(const fg_plan *plan, int64_t *out, size_t cap, size_t *len);
 /* Host-only planning (no device, no context): the records fg_plan_describe
@@ -205,6 +209,19 @@ int fg_plan_dry_run(const fg_params *params, const int32_t *row_ptr, const int32
                     const double *val, int V, const double *W, int F, int Fp,
                     const int32_t *perm, const fg_plan_opts *opts, int64_t *out, size_t cap,
                     size_t *len);
+/* Node order optimisation (paper Sec. 3.4, Alg. 1), host only: perm_out[v]
+ * receives the slot in [0, M) of node v of the graph A-hat (CSR row_ptr[V+1],
+ * col; values not needed).  Regions of at most TH nodes found by a
+ * breadth-first search over siblings (nodes with a common aggregation
+ * target) from the highest-degree unplaced node; regions interleaved one
+ * slot per turn, blanks taking the turns of exhausted regions while any of
+ * the M - V remain; inside a region, nodes placed greedily at the free slot
+ * with the fewest rotation steps (set bits of the index distances) to their
+ * placed neighbours, ties to the lowest index.  *n_regions (may be NULL)
+ * receives the number of regions.  FG_EINVAL for V < 1, M < V, TH < 1, or a
+ * malformed CSR. */
+int fg_node_order(const int32_t *row_ptr, const int32_t *col, int V, int M, int TH,
+                  int32_t *perm_out, int *n_regions);
 /* Replace the encoding of mask `mask` by caller-given coefficients
  * [level+1][N] (host or device), e.g. an independent encoder's output. */
 int fg_plan_set_plaintext(fg_plan *plan, int mask, const uint64_t *coeffs);

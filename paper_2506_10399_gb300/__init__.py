@@ -307,6 +307,21 @@ def plan_build(ctx, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=True, min
     return Plan(ctx, h)
 
 
+def node_order(row_ptr, col, slots, th):
+    """(perm node -> slot, number of regions) by node order optimisation."""
+    nat = _lib()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    V = row_ptr.size - 1
+    perm = np.empty(V, np.int32)
+    nr = ctypes.c_int()
+    rc = nat.lib.fg_node_order(ctypes.c_void_p(row_ptr.ctypes.data), ctypes.c_void_p(col.ctypes.data),
+                               V, int(slots), int(th), ctypes.c_void_p(perm.ctypes.data), ctypes.byref(nr))
+    if rc != 0:
+        raise FicgcnError(rc, "node order failed")
+    return perm, nr.value
+
+
 def plan_dry_run(params, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=True,
                  min_out_level=0, n_sampled=0):
     """Plan records (as Plan.describe()) computed on the host only, no device."""

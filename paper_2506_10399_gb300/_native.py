@@ -66,6 +66,7 @@ SIGS = {
     "fg_plan_set_plaintext": (c_int, [c_void_p, c_int, c_void_p]),
     "fg_plan_dry_run": (c_int, [P(Params), c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_int,
                                 c_void_p, P(PlanOpts), c_void_p, c_size, P(c_size)]),
+    "fg_node_order": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, P(c_int)]),
     "fg_gcn_layer_axw": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int,
                                  P(c_int), P(c_double)]),
     "fg_rotate": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),

@@ -12,7 +12,7 @@ OUT = os.path.join(HERE, "libficgcn.so")
 BUILD = os.path.join(HERE, "_build")
 
 CUDA_SRCS = ["kernels.cu", "api.cu", "layer.cu", "noalloc.cu"]
-HOST_SRCS = ["host_math.cpp", "planner.cpp"]
+HOST_SRCS = ["host_math.cpp", "planner.cpp", "noo.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
