@@ -234,6 +234,25 @@ int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *plan,
                      const uint64_t *in_cts, int n_in, uint64_t *out_cts, int n_out,
                      int *out_level, double *out_scale);
 
+/* Batched layers (many queries, e.g. several graphs of one client, sharing
+ * ctx and keys; the keys must hold every plan's rotations).  Query q runs
+ * plans[q] on in_cts[q] (device, fg_pack_features layout) into out_cts[q]
+ * (device, [Fp][2][out_l+1][N]); out_levels[q] receives its level (the scale
+ * is ctx's Delta).  Up to opts->streams layers are in flight at once, each on
+ * its own stream and workspace; opts->streams = 0 picks the count by timing
+ * 8, 4, 2 and 1 on the first call (*streams_used, may be NULL, receives it).
+ * With opts->graph = 1 the batch is captured into a CUDA graph on the first
+ * call and replayed by later calls with the same plans and buffers.  Every
+ * query runs exactly the kernels of fg_gcn_layer_axw, so the outputs are
+ * the same word for word.  opts NULL = {0, 1}.  Host buffers: FG_EINVAL. */
+typedef struct {
+    int streams;   /* 1..16 layers in flight, 0 = chosen by timing */
+    int graph;     /* 1 = capture once, replay while the arguments repeat */
+} fg_batch_opts;
+int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *plans, int n,
+                       const uint64_t *const *in_cts, uint64_t *const *out_cts,
+                       const fg_batch_opts *opts, int *out_levels, int *streams_used);
+
 /* One rotation Rot(ct, k) (paper Sec. 2.1) with hybrid key switching,
  * ModUp taken before the automorphism (the hoisted order the layer uses).
  * ct, out: [2][level+1][N] (out may alias ct). */

@@ -365,6 +365,23 @@ def gcn_layer_axw(ctx, keys, plan, in_cts, out=None):
     return out, lvl.value, sc.value
 
 
+def gcn_layer_batch(ctx, keys, plans, ins, outs, streams=0, graph=True):
+    """Several layers at once (device tensors only): query q runs plans[q] on
+    ins[q] into outs[q].  Returns (output levels, streams used)."""
+    nat = _lib()
+    n = len(plans)
+    assert len(ins) == n and len(outs) == n
+    P = (ctypes.c_void_p * n)(*[p._h.value if isinstance(p._h, ctypes.c_void_p) else p._h for p in plans])
+    I = (ctypes.c_void_p * n)(*[_ptr(x).value for x in ins])
+    O = (ctypes.c_void_p * n)(*[_ptr(x).value for x in outs])
+    lv = (ctypes.c_int * n)()
+    su = ctypes.c_int()
+    o = nat.BatchOpts(int(streams), 1 if graph else 0)
+    _check(ctx, nat.lib.fg_gcn_layer_batch(ctx._h, keys._h, P, n, I, O, ctypes.byref(o), lv,
+                                           ctypes.byref(su)))
+    return list(lv), su.value
+
+
 def rotate(ctx, keys, ct, level, k, out=None):
     if out is None:
         out = _like(ct, (2, level + 1, ctx.n))

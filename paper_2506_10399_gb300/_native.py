@@ -30,6 +30,10 @@ class PlanOpts(ctypes.Structure):
                 ("n_sampled", c_int)]
 
 
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("streams", c_int), ("graph", c_int)]
+
+
 class PlanInfo(ctypes.Structure):
     _fields_ = [("t", c_int), ("B", c_int), ("n_in", c_int), ("n_out", c_int), ("in_level", c_int),
                 ("out_level", c_int), ("n_groups", c_int), ("n_masks", c_int), ("n_keys", c_int),
@@ -67,6 +71,8 @@ SIGS = {
     "fg_plan_dry_run": (c_int, [P(Params), c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_int,
                                 c_void_p, P(PlanOpts), c_void_p, c_size, P(c_size)]),
     "fg_node_order": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, P(c_int)]),
+    "fg_gcn_layer_batch": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
+                                   P(BatchOpts), c_void_p, P(c_int)]),
     "fg_gcn_layer_axw": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int,
                                  P(c_int), P(c_double)]),
     "fg_rotate": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),

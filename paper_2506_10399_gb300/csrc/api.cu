@@ -107,12 +107,13 @@ void *blob_copy(const std::vector<uint8_t> &b)
 }  // namespace
 
 // ====================================================================== context
-void *fg_ctx::buf(const std::string &name, size_t bytes)
+void *fg_ctx::buf(const std::string &name0, size_t bytes)
 {
+    const std::string name = ws_prefix + name0;
     auto it = ws.find(name);
     if (it != ws.end() && it->second.second >= bytes) return it->second.first;
     if (it != ws.end()) {
-        CUDA_TRY(cudaStreamSynchronize(stream));
+        CUDA_TRY(cudaDeviceSynchronize());   // any stream may still use it
         CUDA_TRY(cudaFree(it->second.first));
         ws.erase(it);
     }
@@ -477,6 +478,8 @@ int fg_ctx_destroy(fg_ctx *ctx)
 {
     if (!ctx) return FG_OK;
     cudaStreamSynchronize(ctx->stream);
+    for (cudaStream_t st : ctx->pool) cudaStreamSynchronize(st);
+    if (ctx->batch_stream) cudaStreamSynchronize(ctx->batch_stream);
     cudaFree(ctx->d_primes);
     cudaFree(ctx->d_fwd);
     cudaFree(ctx->d_inv);
@@ -487,6 +490,10 @@ int fg_ctx_destroy(fg_ctx *ctx)
     for (auto &kv : ctx->mdr_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->ws) cudaFree(kv.second.first);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->batch.exec) cudaGraphExecDestroy(ctx->batch.exec);
+    for (cudaStream_t st : ctx->pool) cudaStreamDestroy(st);
+    if (ctx->batch_stream) cudaStreamDestroy(ctx->batch_stream);
+    for (cudaEvent_t e : ctx->pool_events) cudaEventDestroy(e);
     auto s = g_sk.find(ctx);
     if (s != g_sk.end()) {
         cudaFree(s->second.d);

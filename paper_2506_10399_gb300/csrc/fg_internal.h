@@ -119,9 +119,23 @@ struct fg_ctx {
     size_t ev_next = 0;
     cudaEvent_t event();
 
-    // workspace (grow-only arena of named device buffers)
+    // workspace (grow-only arena of named device buffers); names are
+    // prefixed with ws_prefix, which batched execution sets per stream
     std::map<std::string, std::pair<void *, size_t>> ws;
+    std::string ws_prefix;
     size_t table_bytes = 0;
+
+    // batched execution: streams for layers in flight at once, fork/join
+    // events, and the CUDA graph of the last batch with its arguments
+    std::vector<cudaStream_t> pool;
+    std::vector<cudaEvent_t> pool_events;
+    cudaStream_t batch_stream = nullptr;   // the batch's own origin (capturable)
+    struct BatchGraph {
+        std::vector<const void *> args;   // plans, inputs, outputs
+        int streams = 0;
+        cudaGraphExec_t exec = nullptr;
+        int64_t launches = 0;
+    } batch;
 
     int L() const { return nq - 1; }
     int ext(int level) const { return level + 1 + np; }

@@ -1750,8 +1750,13 @@ void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vec
     KTimer kt(ctx, "group_mac",
               (src_limbs * npoly + (double)pg.nterm * E +
                (double)X * npoly * E * (accumulate ? 2 : 1)) * N * 8);
-    if (sm > 48 * 1024)
+    // raised once per process and size (not a stream operation, and kept out
+    // of the launches a CUDA graph capture records)
+    static size_t sm_set = 48 * 1024;
+    if (sm > sm_set) {
         CUDA_TRY(cudaFuncSetAttribute(k_group_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        sm_set = sm;
+    }
     k_group_mac<<<g, kGmacThreads, sm, ctx->stream>>>(pg, ncol, level, E, ls, ctx->log_n,
                                                       ctx->d_pmodq, ctx->d_primes, ctx->nq);
     check_launch("group_mac");

@@ -287,12 +287,15 @@ int fg_plan_set_plaintext(fg_plan *pl, int mask, const uint64_t *coeffs)
     return FG_OK;
 }
 
+}  // extern "C"
+
 // ------------------------------------------------------------------ the layer
-int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, const uint64_t *in_cts,
-                     int n_in, uint64_t *out_cts, int n_out, int *out_level, double *out_scale)
+// Enqueues one layer on ctx->stream with the workspace names prefixed by
+// ctx->ws_prefix; waits for it only when sync is set (host buffers need it).
+static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, const uint64_t *in_cts,
+                       int n_in, uint64_t *out_cts, int n_out, bool sync, int *out_level)
 {
-    if (!ctx) return FG_EINVAL;
-    try {
+    {
         FG_CHECK(keys && pl && in_cts && out_cts, FG_EINVAL, "null argument");
         FG_CHECK(pl->ctx == ctx && keys->ctx == ctx, FG_EINVAL, "plan or keys of another context");
         const int N = ctx->n, M = ctx->slots, Fp = pl->Fp, F = pl->F, t = pl->t;
@@ -503,8 +506,184 @@ int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, const 
         kern::copy_limbs(ctx, acc, LS, o, nlo, Fp * 2, nlo);
         if (o != out_cts)
             CUDA_TRY(cudaMemcpyAsync(out_cts, o, out_w * 8, cudaMemcpyDeviceToHost, ctx->stream));
-        CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        if (sync) CUDA_TRY(cudaStreamSynchronize(ctx->stream));
         if (out_level) *out_level = level;
+    }
+}
+
+// ------------------------------------------------------------------ batched layers
+// Several layers (queries with their own plans) in flight at once: query q
+// runs on stream q mod S with its own workspace, between a fork and a join
+// on the context's stream.  Every query runs exactly the kernels it would
+// run alone, so the results do not depend on S or on the graph.
+static void batch_pass(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *plans, int n,
+                       const uint64_t *const *in_cts, uint64_t *const *out_cts, int S,
+                       int *levels)
+{
+    while ((int)ctx->pool.size() < S) {
+        cudaStream_t st;
+        CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        ctx->pool.push_back(st);
+    }
+    while ((int)ctx->pool_events.size() < S + 1) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->pool_events.push_back(e);
+    }
+    cudaStream_t origin = ctx->stream;
+    CUDA_TRY(cudaEventRecord(ctx->pool_events[S], origin));
+    for (int s = 0; s < S; s++) CUDA_TRY(cudaStreamWaitEvent(ctx->pool[s], ctx->pool_events[S], 0));
+    try {
+        for (int q = 0; q < n; q++) {
+            const fg_plan *pl = plans[q];
+            ctx->stream = ctx->pool[q % S];
+            ctx->ws_prefix = "b" + std::to_string(q % S) + "/";
+            const int nb = pl->t == 1 ? pl->F : (pl->F + pl->t - 1) / pl->t;
+            layer_exec(ctx, keys, pl, in_cts[q], nb, out_cts[q], pl->Fp, false, &levels[q]);
+        }
+    } catch (...) {
+        ctx->stream = origin;
+        ctx->ws_prefix.clear();
+        throw;
+    }
+    ctx->stream = origin;
+    ctx->ws_prefix.clear();
+    for (int s = 0; s < S; s++) {
+        CUDA_TRY(cudaEventRecord(ctx->pool_events[s], ctx->pool[s]));
+        CUDA_TRY(cudaStreamWaitEvent(origin, ctx->pool_events[s], 0));
+    }
+}
+
+static double time_pass(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *plans, int n,
+                        const uint64_t *const *in_cts, uint64_t *const *out_cts, int S, int *levels)
+{
+    cudaEvent_t a, b;
+    CUDA_TRY(cudaEventCreate(&a));
+    CUDA_TRY(cudaEventCreate(&b));
+    CUDA_TRY(cudaEventRecord(a, ctx->stream));
+    batch_pass(ctx, keys, plans, n, in_cts, out_cts, S, levels);
+    CUDA_TRY(cudaEventRecord(b, ctx->stream));
+    CUDA_TRY(cudaEventSynchronize(b));
+    float ms = 0;
+    CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+}
+
+// the batch runs from ctx->batch_stream (a non-blocking stream that can be
+// captured, which the legacy default stream cannot), joined to ctx->stream
+// before and after
+static void batch_body(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *plans, int n,
+                       const uint64_t *const *in_cts, uint64_t *const *out_cts, const fg_batch_opts &o,
+                       const std::vector<const void *> &args, int *out_levels, int *streams_used)
+{
+    // replay the captured batch when the arguments are the same
+    if (o.graph && ctx->batch.exec && ctx->batch.args == args &&
+        (o.streams == 0 || o.streams == ctx->batch.streams)) {
+        CUDA_TRY(cudaGraphLaunch(ctx->batch.exec, ctx->stream));
+        ctx->launches += ctx->batch.launches;
+        for (int q = 0; q < n; q++) out_levels[q] = plans[q]->out_level;
+        if (streams_used) *streams_used = ctx->batch.streams;
+        return;
+    }
+    // first call: one pass with every workspace allocated (this pass gives
+    // the results), then the stream count, then the capture
+    int S = o.streams ? std::min(o.streams, n) : 1;
+    if (o.streams == 0) {
+        // the largest candidate first, so that every workspace exists
+        // before the timed passes
+        const int cand[4] = {8, 4, 2, 1};
+        batch_pass(ctx, keys, plans, n, in_cts, out_cts, std::min(8, n), out_levels);
+        CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        double best = 0;
+        for (int c : cand) {
+            if (c > n) continue;
+            const double ms = time_pass(ctx, keys, plans, n, in_cts, out_cts, c, out_levels);
+            if (best == 0 || ms < best) {
+                best = ms;
+                S = c;
+            }
+        }
+    } else {
+        batch_pass(ctx, keys, plans, n, in_cts, out_cts, S, out_levels);
+    }
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (o.graph) {
+        if (ctx->batch.exec) {
+            cudaGraphExecDestroy(ctx->batch.exec);
+            ctx->batch.exec = nullptr;
+        }
+        const int64_t l0 = ctx->launches;
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed));
+        try {
+            batch_pass(ctx, keys, plans, n, in_cts, out_cts, S, out_levels);
+        } catch (...) {
+            cudaStreamEndCapture(ctx->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        CUDA_TRY(cudaStreamEndCapture(ctx->stream, &g));
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) throw fg_error(FG_ECUDA, std::string("graph: ") + cudaGetErrorString(e));
+        ctx->batch.exec = ex;
+        ctx->batch.args = args;
+        ctx->batch.streams = S;
+        ctx->batch.launches = ctx->launches - l0;
+        ctx->launches = l0;
+    }
+    if (streams_used) *streams_used = S;
+}
+
+extern "C" int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *plans, int n,
+                                  const uint64_t *const *in_cts, uint64_t *const *out_cts,
+                                  const fg_batch_opts *opts, int *out_levels, int *streams_used)
+{
+    if (!ctx) return FG_EINVAL;
+    cudaStream_t home = ctx->stream;
+    try {
+        FG_CHECK(keys && plans && in_cts && out_cts && out_levels && n >= 1, FG_EINVAL, "null argument");
+        fg_batch_opts o{0, 1};
+        if (opts) o = *opts;
+        FG_CHECK(o.streams >= 0 && o.streams <= 16, FG_EINVAL, "streams must be 0..16");
+        std::vector<const void *> args;
+        for (int q = 0; q < n; q++) {
+            FG_CHECK(plans[q] && plans[q]->ctx == ctx && keys->ctx == ctx, FG_EINVAL,
+                     "plan or keys of another context");
+            FG_CHECK(in_cts[q] && out_cts[q] && is_dev(in_cts[q]) && is_dev(out_cts[q]), FG_EINVAL,
+                     "batched layers take device buffers");
+            args.insert(args.end(), {plans[q], in_cts[q], out_cts[q]});
+        }
+        if (!ctx->batch_stream)
+            CUDA_TRY(cudaStreamCreateWithFlags(&ctx->batch_stream, cudaStreamNonBlocking));
+        CUDA_TRY(cudaStreamSynchronize(home));   // inputs written on the caller's stream
+        ctx->stream = ctx->batch_stream;
+        batch_body(ctx, keys, plans, n, in_cts, out_cts, o, args, out_levels, streams_used);
+        CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        ctx->stream = home;
+    } catch (const fg_error &e) {
+        ctx->stream = home;
+        ctx->err = e.what();
+        return e.code;
+    } catch (const std::exception &e) {
+        ctx->stream = home;
+        ctx->err = e.what();
+        return FG_EOOM;
+    }
+    return FG_OK;
+}
+
+extern "C" {
+
+int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, const uint64_t *in_cts,
+                     int n_in, uint64_t *out_cts, int n_out, int *out_level, double *out_scale)
+{
+    if (!ctx) return FG_EINVAL;
+    try {
+        layer_exec(ctx, keys, pl, in_cts, n_in, out_cts, n_out, true, out_level);
         if (out_scale) *out_scale = ctx->scale;
     } catch (const fg_error &e) {
         ctx->err = e.what();

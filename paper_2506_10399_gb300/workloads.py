@@ -44,6 +44,28 @@ CONFIGS = {
 }
 
 
+# batched form: many single-layer queries of uneven size sharing one
+# parameter set (N = 2^16, scale 2^45, 14 primes, dnum 4: 4 primes per
+# digit, 4 special); each query's graph, features and weights come from
+# batch_queries below
+BATCH_PARAMS = dict(log_n=16, q_bits=[60] + [45] * 13, p_bits=[60] * 4, alpha=4, log_scale=45)
+
+
+def batch_queries(n=32, first_seed=0):
+    """n query workloads, seeds first_seed.. : power-law graphs of
+    V ~ U{500..4000} nodes (mean degree 4) with exponent ~ U[2.1, 3.0],
+    TF-IDF-like features F ~ U{64..512}, F' = 16, Glorot weights."""
+    out = []
+    for s in range(first_seed, first_seed + n):
+        rng = np.random.default_rng(s)
+        V = int(rng.integers(500, 4001))
+        gamma = float(rng.uniform(2.1, 3.0))
+        F = int(rng.integers(64, 513))
+        out.append(make_workload(graph="chung_lu", V=V, deg=4.0, gamma=gamma, F=F, Fp=16,
+                                 x="tfidf", w="glorot", seed=s))
+    return out
+
+
 @dataclass
 class Workload:
     V: int

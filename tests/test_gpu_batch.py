@@ -1,0 +1,94 @@
+"""Batched layers: several queries of uneven size in flight at once (one
+stream and workspace each), optionally captured into one CUDA graph, must
+give the same ciphertexts word for word as running them one at a time; the
+one-at-a-time path is itself bit-exact against the oracle (test_gpu_parity)."""
+import numpy as np
+import pytest
+
+from paper_2506_10399_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+PARAMS = dict(log_n=13, q_bits=[60] + [45] * 7, p_bits=[60] * 3, alpha=3, log_scale=45)
+QUERIES = [
+    dict(graph="chung_lu", V=500, deg=4.0, gamma=2.1, F=64, Fp=4, x="tfidf", w="glorot", seed=0),
+    dict(graph="chung_lu", V=1200, deg=3.5, gamma=2.7, F=24, Fp=4, x="binary", w="glorot", seed=1),
+    dict(graph="er", V=300, deg=4.0, F=40, Fp=4, seed=2),
+    dict(graph="chung_lu", V=2000, deg=4.5, gamma=3.0, F=16, Fp=4, x="tfidf", w="glorot", seed=3),
+    dict(graph="chung_lu", V=800, deg=5.0, gamma=2.4, F=48, Fp=4, x="uniform", w="normal16", seed=4),
+]
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    fg = __graft_entry__.build()
+    ctx = fg.Context(**PARAMS)
+    qs = []
+    amounts = set()
+    for i, wk in enumerate(QUERIES):
+        w = wl.make_workload(**wk)
+        t = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, wl.identity_order(w.V)).info()["t"]
+        perm = wl.random_order(w.V, ctx.slots // t, 100 + i)
+        plan = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=t)
+        amounts.update(plan.rotation_amounts())
+        qs.append((w, perm, plan, t))
+    sk, evk = fg.keygen(ctx, 9, sorted(amounts))   # one key set for every query
+    keys = fg.load_evk(ctx, evk)
+    data = []
+    for i, (w, perm, plan, t) in enumerate(qs):
+        info = plan.info()
+        cin = torch.from_numpy(fg.pack_features(ctx, sk, 50 + i, w.X, perm, t).view(np.int64)).cuda()
+        out = torch.empty((info["n_out"], 2, info["out_level"] + 1, ctx.n), dtype=torch.int64, device="cuda")
+        data.append((cin, out))
+    return fg, ctx, sk, keys, qs, data
+
+
+def _one_at_a_time(fg, ctx, keys, qs, data):
+    import torch
+    res = []
+    for (w, perm, plan, t), (cin, _) in zip(qs, data):
+        out, lvl, _ = fg.gcn_layer_axw(ctx, keys, plan, cin)
+        res.append((out.clone(), lvl))
+    torch.cuda.synchronize()
+    return res
+
+
+@pytest.mark.parametrize("streams,graph", [(0, True), (2, False), (3, True)])
+def test_batch_equals_one_at_a_time(env, streams, graph):
+    fg, ctx, sk, keys, qs, data = env
+    want = _one_at_a_time(fg, ctx, keys, qs, data)
+    plans = [q[2] for q in qs]
+    ins = [d[0] for d in data]
+    outs = [d[1] for d in data]
+    for rep in range(2):   # the second call replays the graph when one was captured
+        for o in outs:
+            o.zero_()
+        lv, used = fg.gcn_layer_batch(ctx, keys, plans, ins, outs, streams=streams, graph=graph)
+        assert 1 <= used <= max(streams, 8)
+        if streams:
+            assert used == min(streams, len(plans))
+        for (o_w, l_w), o, l in zip(want, outs, lv):
+            assert l == l_w
+            assert bool((o == o_w).all())
+
+
+def test_batch_decrypts_to_fp64(env):
+    fg, ctx, sk, keys, qs, data = env
+    plans = [q[2] for q in qs]
+    lv, _ = fg.gcn_layer_batch(ctx, keys, plans, [d[0] for d in data], [d[1] for d in data])
+    for (w, perm, plan, t), (cin, out), l in zip(qs, data, lv):
+        ref = w.reference_output()
+        for j in (0, w.W.shape[1] - 1):
+            d = fg.decrypt_decode(ctx, sk, out[j].contiguous(), l, ctx.scale)
+            assert np.max(np.abs(d[perm] - ref[:, j])) < 2 ** -20
+
+
+def test_batch_rejects_host_buffers(env):
+    fg, ctx, sk, keys, qs, data = env
+    with pytest.raises(fg.FicgcnError) as e:
+        fg.gcn_layer_batch(ctx, keys, [qs[0][2]], [data[0][0].cpu()], [data[0][1]])
+    assert e.value.code == -1
