@@ -441,6 +441,85 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------ two layers
+def run_two_layer(args):
+    """Two-layer encrypted GCN on the benchmark workload: layer 1 (F -> F'),
+    the x^2 activation (CMult + relinearisation + rescale), layer 2
+    (F' -> C), inputs resident in HBM; decrypted against FP64
+    A-hat (A-hat X W1)^2 W2."""
+    import torch
+    import __graft_entry__
+    fg = __graft_entry__.build()
+    from paper_2506_10399_gb300 import workloads as wl
+    c = dict(wl.CONFIGS[WORKLOAD])
+    w = wl.config_workload(WORKLOAD)
+    W2 = wl.second_layer_weights(WORKLOAD)
+    t_setup = time.perf_counter()
+    ctx = fg.Context(**c)
+    perm = wl.random_order(w.V, ctx.slots, SEED)
+    plan1 = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=1, radix_bits=RADIX_BITS,
+                          min_out_level=MIN_OUT_LEVEL)
+    l1 = plan1.info()["out_level"]
+    plan2 = fg.plan_build(ctx, w.row_ptr, w.col, w.val, W2, perm, t=1, radix_bits=RADIX_BITS,
+                          in_level=l1 - 1)
+    amounts = sorted(set(plan1.rotation_amounts()) | set(plan2.rotation_amounts()))
+    sk, evk = fg.keygen(ctx, SEED, amounts, relin=True)
+    keys = fg.load_evk(ctx, evk)
+    del evk
+    F, Fp, N = w.X.shape[1], w.W.shape[1], ctx.n
+    x = torch.empty((F, 2, ctx.nq, N), dtype=torch.int64, device="cuda")
+    fg.pack_features(ctx, sk, SEED, w.X, perm, 1, out=x)
+    h1 = torch.empty((Fp, 2, l1 + 1, N), dtype=torch.int64, device="cuda")
+    a1 = torch.empty((Fp, 2, l1, N), dtype=torch.int64, device="cuda")
+    i2 = plan2.info()
+    out = torch.empty((i2["n_out"], 2, i2["out_level"] + 1, N), dtype=torch.int64, device="cuda")
+    setup_s = time.perf_counter() - t_setup
+
+    def step():
+        _, la, sc = fg.gcn_layer_axw(ctx, keys, plan1, x, out=h1)
+        fg.mul_relin_rescale(ctx, keys, h1, h1, la, out=a1)
+        _, lb, _ = fg.gcn_layer_axw(ctx, keys, plan2, a1, out=out)
+        return la, lb, sc
+
+    la, lb, sc = step()
+    torch.cuda.synchronize()
+    scale = sc * sc / ctx.q[la]
+    ref = wl.two_layer_reference(w, W2)
+    err = 0.0
+    for j in range(W2.shape[1]):
+        d = fg.decrypt_decode(ctx, sk, out[j].contiguous(), lb, scale)
+        err = max(err, float(np.max(np.abs(d[perm] - ref[:, j]))))
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    parts = {}
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    n0 = ctx.launch_count()
+    tot = 0.0
+    for _ in range(args.steps):
+        e[0].record()
+        fg.gcn_layer_axw(ctx, keys, plan1, x, out=h1)
+        e[1].record()
+        fg.mul_relin_rescale(ctx, keys, h1, h1, la, out=a1)
+        e[2].record()
+        fg.gcn_layer_axw(ctx, keys, plan2, a1, out=out)
+        e[3].record()
+        torch.cuda.synchronize()
+        for k, (a, b) in enumerate(((0, 1), (1, 2), (2, 3))):
+            parts[k] = parts.get(k, 0.0) + e[a].elapsed_time(e[b]) / args.steps
+        tot += e[0].elapsed_time(e[3]) / args.steps
+    line = {"metric": "encrypted two-layer GCN latency (ms) at N=2^16", "value": round(tot, 3),
+            "unit": "ms/inference", "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+            "layer1_ms": round(parts[0], 3), "square_ms": round(parts[1], 3), "layer2_ms": round(parts[2], 3),
+            "levels": {"layer1_out": la, "square_out": la - 1, "layer2_out": lb},
+            "rotations": plan1.info()["rotations"] + i2["rotations"],
+            "decrypt_max_abs_err_vs_fp64": err, "gpu_launches": (ctx.launch_count() - n0) // args.steps,
+            "setup_s": round(setup_s, 1),
+            "config": {"workload": config_desc()["workload"] + "; second layer W2 16x3 Glorot, x^2 between"}}
+    print(json.dumps(line))
+    return 0
+
+
 # ------------------------------------------------------------------ batched form
 def run_batched(args):
     """Many single-layer queries of uneven size (the batch recipe of
@@ -548,11 +627,14 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="batched form: many queries one at a time vs all at once")
     ap.add_argument("--queries", type=int, default=16, help="queries in the batched form")
+    ap.add_argument("--two-layer", action="store_true", help="two-layer GCN with x^2 between")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.batched:
         return run_batched(args)
+    if args.two_layer:
+        return run_two_layer(args)
     return run_ours(args)
 
 

@@ -118,8 +118,14 @@ int fg_ctx_launch_count(const fg_ctx *ctx, int64_t *launches);
  * digit D_j, b_j = -a_j s + e_j + P [q_i in D_j] phi_g(s) mod q_i and
  * b_j = -a_j s + e_j mod p_k.  Blobs (host memory, free with fg_free) are
  * versioned, checksummed and hold keys in the coefficient domain. */
-int fg_keygen(fg_ctx *ctx, uint64_t seed, const int32_t *rot_amounts, int n_rot,
+int fg_keygen(fg_ctx *ctx, uint64_t seed, const int32_t *rot_amounts, int n_rot, int relin,
               void **sk_blob, size_t *sk_len, void **evk_blob, size_t *evk_len);
+/* With relin = 1 fg_keygen also makes the relinearisation key (for the
+ * ciphertext product CMult of Sec. 2.1): the same construction switching
+ * s^2 -> s, sampled with stream index 0 (Galois elements, the indices of the
+ * rotation keys, are odd).  It is stored in the evk blob as amount FG_RELIN
+ * with Galois element 1. */
+#define FG_RELIN (-1)
 
 /* CKKS encoding (canonical embedding, paper Sec. 2.1): real slot values
  * z_0..z_{n_slots-1} (missing slots are 0) -> coefficients m with
@@ -160,8 +166,9 @@ int fg_decrypt_decode(fg_ctx *ctx, const void *sk_blob, size_t sk_len, const uin
  * checking its magic, parameters and checksum (FG_EKEY otherwise). */
 int fg_load_evk(fg_ctx *ctx, const void *evk_blob, size_t len, fg_keys **out);
 int fg_keys_destroy(fg_keys *keys);
-/* Coefficient-domain copy of key `amount`'s digit j: b and a as [L+1+K][N]
- * (host or device buffers).  FG_EKEY if the amount has no key. */
+/* Coefficient-domain copy of key `amount`'s digit j (amount FG_RELIN: the
+ * relinearisation key): b and a as [L+1+K][N] (host or device buffers).
+ * FG_EKEY if the amount has no key. */
 int fg_keys_export(const fg_keys *keys, int32_t amount, int digit, uint64_t *b_out,
                    uint64_t *a_out);
 
@@ -171,6 +178,7 @@ typedef struct {
     int aoo;            /* 1 = shortest cyclic shift (AOO), 0 = shift in [0, M) */
     int min_out_level;  /* lowest level the output may reach */
     int n_sampled;      /* n in J(t;F,n); 0 = mean row length of A-hat, rounded */
+    int in_level;       /* level of the input ciphertexts; 0 = the top level L */
 } fg_plan_opts;
 
 /* Plan of one layer (paper Sec. 3.2-3.3): packing t, combination constants,
@@ -252,6 +260,15 @@ typedef struct {
 int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *plans, int n,
                        const uint64_t *const *in_cts, uint64_t *const *out_cts,
                        const fg_batch_opts *opts, int *out_levels, int *streams_used);
+
+/* Ciphertext products (paper Sec. 2.1 CMult; the x^2 activation between
+ * GCN layers multiplies a ciphertext by itself): for each of n pairs,
+ * out = Rescale((a0 b0, a0 b1 + a1 b0) + KS_relin(a1 b1)), with the
+ * relinearisation key of fg_keygen (FG_EKEY without it).  a, b: [n][2][level+1][N]
+ * coefficient domain (b may equal a); out: [n][2][level][N]; host or device.
+ * The scale becomes scale_a * scale_b / q_level.  FG_ELEVEL for level < 1. */
+int fg_mul_relin_rescale(fg_ctx *ctx, const fg_keys *keys, const uint64_t *a, const uint64_t *b,
+                         int n, int level, uint64_t *out);
 
 /* One rotation Rot(ct, k) (paper Sec. 2.1) with hybrid key switching,
  * ModUp taken before the automorphism (the hoisted order the layer uses).

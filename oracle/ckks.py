@@ -251,6 +251,64 @@ def keygen_rotation(params, seed, s, k):
     return keygen_switch(params, seed, s, automorphism_small(s, g, params.n), g)
 
 
+def secret_square(params, s):
+    """s^2 in R = Z[X]/(X^N+1) as integers (|coefficient| <= N): the
+    negacyclic product mod q_0, read as a centred integer."""
+    q = params.q[0]
+    r = small_to_res(s, [q])[0]
+    sq = _ref.negacyclic_mul(r, r, q, params.psi(q))
+    return np.where(sq > q // 2, sq.astype(object) - q, sq.astype(object)).astype(np.int64)
+
+
+def keygen_relin(params, seed, s):
+    """Relinearisation key: switches s^2 -> s (the key of Sec. 2.1's CMult),
+    the same hybrid construction as a rotation key with stream index 0 (no
+    rotation key uses 0: Galois elements are odd)."""
+    return keygen_switch(params, seed, s, secret_square(params, s), 0)
+
+
+def mul_ct(params, a, b):
+    """Tensor product of two ciphertexts at one level:
+    (d0, d1, d2) = (a0 b0, a0 b1 + a1 b0, a1 b1), so that
+    d0 + d1 s + d2 s^2 = (a0 + a1 s)(b0 + b1 s)."""
+    nl = a.shape[1]
+    primes = params.q[:nl]
+    d0 = poly_mul(params, a[0], b[0], primes)
+    d1 = add_res(poly_mul(params, a[0], b[1], primes), poly_mul(params, a[1], b[0], primes), primes)
+    d2 = poly_mul(params, a[1], b[1], primes)
+    return d0, d1, d2
+
+
+def relinearize(params, d0, d1, d2, key):
+    """(d0, d1) + KS(d2) with the relinearisation key: ModUp of d2, inner
+    product with the key's digits over q_0..q_l, p.., ModDown of both sums
+    (hybrid key switching as in rotate, without an automorphism)."""
+    level = d0.shape[0] - 1
+    ext = params.ext_primes(level)
+    digits = modup(params, d2, level)
+    u0 = np.zeros((len(ext), params.n), dtype=np.uint64)
+    u1 = np.zeros((len(ext), params.n), dtype=np.uint64)
+    for j, dj in enumerate(digits):
+        kb, ka = key[j]
+        for i, pr in enumerate(ext):
+            kl = params.key_limb(level, i)
+            psi = params.psi(pr)
+            t0 = _ref.negacyclic_mul(dj[i], kb[kl], pr, psi)
+            t1 = _ref.negacyclic_mul(dj[i], ka[kl], pr, psi)
+            u0[i] = add_res(u0[i:i + 1], t0[None], [pr])[0]
+            u1[i] = add_res(u1[i:i + 1], t1[None], [pr])[0]
+    qs = params.q[:level + 1]
+    r0 = _ref.moddown(u0, qs, params.p)
+    r1 = _ref.moddown(u1, qs, params.p)
+    return np.stack([add_res(d0, r0, qs), add_res(d1, r1, qs)])
+
+
+def mul_relin_rescale(params, a, b, key):
+    """CMult (Sec. 2.1): tensor product, relinearisation, rescale by q_l.
+    The scale becomes scale_a * scale_b / q_l."""
+    return rescale_ct(params, relinearize(params, *mul_ct(params, a, b), key))
+
+
 def encrypt(params, seed, index, pt, s, level):
     """Secret-key encryption c = (-a*s + m + e, a) over q_0..q_l.
     Streams: a from (seed, 4, index), e from (seed, 5, index)."""

@@ -164,13 +164,17 @@ class Keys:
             pass
 
 
-def keygen(ctx, seed, rot_amounts):
-    """(secret-key blob as bytes, evaluation-key blob as a numpy uint8 array)."""
+RELIN = -1   # evk entry of the relinearisation key
+
+
+def keygen(ctx, seed, rot_amounts, relin=False):
+    """(secret-key blob as bytes, evaluation-key blob as a numpy uint8 array);
+    relin=True adds the relinearisation key for mul_relin_rescale."""
     nat = _lib()
     am = np.ascontiguousarray(np.array(list(rot_amounts), dtype=np.int32))
     skb, skl, evb, evl = ctypes.c_void_p(), ctypes.c_size_t(), ctypes.c_void_p(), ctypes.c_size_t()
     _check(ctx, nat.lib.fg_keygen(ctx._h, int(seed), am.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                  len(am), ctypes.byref(skb), ctypes.byref(skl),
+                                  len(am), 1 if relin else 0, ctypes.byref(skb), ctypes.byref(skl),
                                   ctypes.byref(evb), ctypes.byref(evl)))
     sk = _copy_blob(skb, skl.value).tobytes()
     evk = _copy_blob(evb, evl.value)
@@ -289,7 +293,7 @@ class Plan:
 
 
 def plan_build(ctx, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=True, min_out_level=0,
-               n_sampled=0):
+               n_sampled=0, in_level=0):
     nat = _lib()
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
     col = np.ascontiguousarray(col, dtype=np.int32)
@@ -298,7 +302,8 @@ def plan_build(ctx, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=True, min
     perm = np.ascontiguousarray(perm, dtype=np.int32)
     V = row_ptr.size - 1
     F, Fp = W.shape
-    o = nat.PlanOpts(int(t), int(radix_bits), 1 if aoo else 0, int(min_out_level), int(n_sampled))
+    o = nat.PlanOpts(int(t), int(radix_bits), 1 if aoo else 0, int(min_out_level), int(n_sampled),
+                     int(in_level))
     h = ctypes.c_void_p()
     _check(ctx, nat.lib.fg_plan_build(ctx._h, ctypes.c_void_p(row_ptr.ctypes.data),
                                       ctypes.c_void_p(col.ctypes.data), _ptr(val), V, _ptr(W), F, Fp,
@@ -323,7 +328,7 @@ def node_order(row_ptr, col, slots, th):
 
 
 def plan_dry_run(params, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=True,
-                 min_out_level=0, n_sampled=0):
+                 min_out_level=0, n_sampled=0, in_level=0):
     """Plan records (as Plan.describe()) computed on the host only, no device."""
     nat = _lib()
     q_bits, p_bits = params["q_bits"], params["p_bits"]
@@ -337,7 +342,8 @@ def plan_dry_run(params, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=True
     W = np.ascontiguousarray(W, dtype=np.float64)
     perm = np.ascontiguousarray(perm, dtype=np.int32)
     F, Fp = W.shape
-    o = nat.PlanOpts(int(t), int(radix_bits), 1 if aoo else 0, int(min_out_level), int(n_sampled))
+    o = nat.PlanOpts(int(t), int(radix_bits), 1 if aoo else 0, int(min_out_level), int(n_sampled),
+                     int(in_level))
     args = [ctypes.byref(prm), ctypes.c_void_p(row_ptr.ctypes.data), ctypes.c_void_p(col.ctypes.data),
             _ptr(val), row_ptr.size - 1, _ptr(W), F, Fp, ctypes.c_void_p(perm.ctypes.data),
             ctypes.byref(o)]
@@ -357,7 +363,8 @@ def gcn_layer_axw(ctx, keys, plan, in_cts, out=None):
     info = plan.info()
     if out is None:
         out = _like(in_cts, (info["n_out"], 2, info["out_level"] + 1, ctx.n))
-    assert int(in_cts.shape[-1]) == ctx.n and int(in_cts.shape[-2]) == ctx.nq, "inputs must be [n][2][L+1][N]"
+    assert int(in_cts.shape[-1]) == ctx.n and int(in_cts.shape[-2]) == info["in_level"] + 1, \
+        "inputs must be [n][2][in_level+1][N]"
     lvl, sc = ctypes.c_int(), ctypes.c_double()
     _check(ctx, _lib().lib.fg_gcn_layer_axw(ctx._h, keys._h, plan._h, _ptr(in_cts), int(in_cts.shape[0]),
                                             _ptr(out), info["n_out"], ctypes.byref(lvl),
@@ -380,6 +387,18 @@ def gcn_layer_batch(ctx, keys, plans, ins, outs, streams=0, graph=True):
     _check(ctx, nat.lib.fg_gcn_layer_batch(ctx._h, keys._h, P, n, I, O, ctypes.byref(o), lv,
                                            ctypes.byref(su)))
     return list(lv), su.value
+
+
+def mul_relin_rescale(ctx, keys, a, b, level, out=None):
+    """CMult of each pair: a, b [n][2][level+1][N] (or [2][level+1][N]) ->
+    [n][2][level][N]; b may be a itself (the x^2 activation)."""
+    single = len(a.shape) == 3
+    n = 1 if single else int(a.shape[0])
+    if out is None:
+        out = _like(a, (2, level, ctx.n) if single else (n, 2, level, ctx.n))
+    _check(ctx, _lib().lib.fg_mul_relin_rescale(ctx._h, keys._h, _ptr(a), _ptr(b), n, int(level),
+                                                _ptr(out)))
+    return out
 
 
 def rotate(ctx, keys, ct, level, k, out=None):

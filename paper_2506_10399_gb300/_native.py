@@ -27,7 +27,7 @@ class Params(ctypes.Structure):
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("t", c_int), ("radix_bits", c_int), ("aoo", c_int), ("min_out_level", c_int),
-                ("n_sampled", c_int)]
+                ("n_sampled", c_int), ("in_level", c_int)]
 
 
 class BatchOpts(ctypes.Structure):
@@ -50,7 +50,7 @@ SIGS = {
     "fg_ctx_time_kernels": (c_int, [c_void_p, ctypes.c_char_p]),
     "fg_ctx_kernel_times": (c_int, [c_void_p, P(c_double), P(ctypes.c_int64), P(c_double)]),
     "fg_ctx_launch_count": (c_int, [c_void_p, P(ctypes.c_int64)]),
-    "fg_keygen": (c_int, [c_void_p, c_u64, P(ctypes.c_int32), c_int, P(c_void_p), P(c_size),
+    "fg_keygen": (c_int, [c_void_p, c_u64, P(ctypes.c_int32), c_int, c_int, P(c_void_p), P(c_size),
                           P(c_void_p), P(c_size)]),
     "fg_encode_plain": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p]),
     "fg_encrypt": (c_int, [c_void_p, c_void_p, c_size, c_u64, c_u64, c_void_p, c_int, c_void_p]),
@@ -71,6 +71,7 @@ SIGS = {
     "fg_plan_dry_run": (c_int, [P(Params), c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_int,
                                 c_void_p, P(PlanOpts), c_void_p, c_size, P(c_size)]),
     "fg_node_order": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, P(c_int)]),
+    "fg_mul_relin_rescale": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "fg_gcn_layer_batch": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
                                    P(BatchOpts), c_void_p, P(c_int)]),
     "fg_gcn_layer_axw": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int,

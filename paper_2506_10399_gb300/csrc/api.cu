@@ -573,8 +573,8 @@ int fg_ctx_launch_count(const fg_ctx *ctx, int64_t *launches)
 }
 
 // ---------------------------------------------------------------- client side
-int fg_keygen(fg_ctx *ctx, uint64_t seed, const int32_t *rot_amounts, int n_rot, void **sk_blob,
-              size_t *sk_len, void **evk_blob, size_t *evk_len)
+int fg_keygen(fg_ctx *ctx, uint64_t seed, const int32_t *rot_amounts, int n_rot, int relin,
+              void **sk_blob, size_t *sk_len, void **evk_blob, size_t *evk_len)
 {
     if (!ctx) return FG_EINVAL;
     API_TRY
@@ -597,6 +597,7 @@ int fg_keygen(fg_ctx *ctx, uint64_t seed, const int32_t *rot_amounts, int n_rot,
     std::sort(am.begin(), am.end());
     am.erase(std::unique(am.begin(), am.end()), am.end());
     am.erase(std::remove(am.begin(), am.end(), 0), am.end());
+    if (relin) am.push_back(FG_RELIN);   // last entry: the relinearisation key
     const int beta = ctx->n_digits(L);
     const size_t limb_w = (size_t)N, key_w = (size_t)beta * 2 * KL * N;
     Writer ew;
@@ -610,7 +611,7 @@ int fg_keygen(fg_ctx *ctx, uint64_t seed, const int32_t *rot_amounts, int n_rot,
     for (u64 p : ctx->primes) ew.put<u64>(p);
     std::vector<uint32_t> gal(am.size());
     for (size_t i = 0; i < am.size(); i++) {
-        gal[i] = (uint32_t)hm::powmod(5, am[i], 2 * (u64)N);
+        gal[i] = am[i] == FG_RELIN ? 1u : (uint32_t)hm::powmod(5, am[i], 2 * (u64)N);
         ew.put<int32_t>(am[i]);
         ew.put<uint32_t>(gal[i]);
     }
@@ -628,9 +629,11 @@ int fg_keygen(fg_ctx *ctx, uint64_t seed, const int32_t *rot_amounts, int n_rot,
     kern::LimbSet As{A, KL, KL, 1, all}, Bs{Bv, KL, KL, 1, all}, Es{Er, KL, KL, 1, all};
     for (size_t ki = 0; ki < am.size(); ki++) {
         const uint32_t g = gal[ki];
-        kern::automorphism(ctx, S, Sg, KL, g);
+        const bool rl = am[ki] == FG_RELIN;
+        if (rl) kern::pointwise(ctx, S, S, Sg, KL, all);   // s^2 (NTT domain)
+        else kern::automorphism(ctx, S, Sg, KL, g);        // phi_g(s)
         for (int j = 0; j < beta; j++) {
-            const u64 idx = ((u64)g << 8) | (u64)j;
+            const u64 idx = ((u64)(rl ? 0 : g) << 8) | (u64)j;
             hm::sample_uniform(seed, 2, idx, ctx->primes.data(), KL, N, ha.data());
             hm::sample_cbd(seed, 3, idx, N, he.data());
             CUDA_TRY(cudaMemcpyAsync(A, ha.data(), ha.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
@@ -842,9 +845,10 @@ int fg_load_evk(fg_ctx *ctx, const void *evk_blob, size_t len, fg_keys **out)
     for (uint32_t i = 0; i < nk; i++) {
         ids[i].first = r.get<int32_t>();
         ids[i].second = r.get<uint32_t>();
-        FG_CHECK(ids[i].first > 0 && ids[i].first < ctx->slots &&
-                     ids[i].second == (uint32_t)hm::powmod(5, ids[i].first, 2 * (u64)N),
-                 FG_EKEY, "evk rotation entry inconsistent");
+        FG_CHECK((ids[i].first == FG_RELIN && ids[i].second == 1u) ||
+                     (ids[i].first > 0 && ids[i].first < ctx->slots &&
+                      ids[i].second == (uint32_t)hm::powmod(5, ids[i].first, 2 * (u64)N)),
+                 FG_EKEY, "evk key entry inconsistent");
     }
     FG_CHECK(r.off + nk * key_w * 8 == r.len, FG_EKEY, "evk size mismatch");
     keys = new fg_keys;
@@ -895,7 +899,8 @@ int fg_keys_export(const fg_keys *keys, int32_t amount, int digit, uint64_t *b_o
     API_TRY
     const int N = ctx->n, KL = ctx->nq + ctx->np, beta = ctx->n_digits(ctx->L());
     FG_CHECK(digit >= 0 && digit < beta && b_out && a_out, FG_EINVAL, "bad digit");
-    const KeyDev &k = keys->get(((amount % ctx->slots) + ctx->slots) % ctx->slots);
+    const KeyDev &k = keys->get(amount == FG_RELIN ? FG_RELIN
+                                                   : ((amount % ctx->slots) + ctx->slots) % ctx->slots);
     u64 *t = (u64 *)ctx->buf("kx", (size_t)2 * KL * N * 8);
     CUDA_TRY(cudaMemcpyAsync(t, k.d + (size_t)digit * 2 * KL * N, (size_t)2 * KL * N * 8,
                              cudaMemcpyDeviceToDevice, ctx->stream));
@@ -959,6 +964,67 @@ int fg_rescale(fg_ctx *ctx, const uint64_t *ct, int level, uint64_t *out)
     FG_CHECK(o != d, FG_EINVAL, "rescale output must not alias its input");
     kern::rescale_coef(ctx, d, level + 1, o, level, 2, level);
     stage_out(ctx, out, o, (size_t)2 * level * N);
+    sync(ctx);
+    API_CATCH(ctx)
+}
+
+int fg_mul_relin_rescale(fg_ctx *ctx, const fg_keys *keys, const uint64_t *a, const uint64_t *b,
+                         int n, int level, uint64_t *out)
+{
+    if (!ctx || !keys) return FG_EINVAL;
+    API_TRY
+    FG_CHECK(a && b && out && n >= 1, FG_EINVAL, "null argument");
+    FG_CHECK(level >= 1 && level < ctx->nq, FG_ELEVEL, "CMult needs a level >= 1");
+    const KeyDev &rk = keys->get(FG_RELIN);
+    const int N = ctx->n, nl = level + 1, E = ctx->ext(level), beta = ctx->n_digits(level);
+    const size_t w = (size_t)n * 2 * nl * N, pw = (size_t)nl * N;
+    const u64 *da = stage_in(ctx, a, w, "mul_a");
+    const u64 *db = b == a ? da : stage_in(ctx, b, w, "mul_b");
+    const std::vector<int> pid = iota(nl);
+    u64 *A = (u64 *)ctx->buf("mul_an", w * 8);
+    kern::LimbSet as{const_cast<u64 *>(da), nl, nl, 2 * n, pid}, an{A, nl, nl, 2 * n, pid};
+    kern::ntt_fwd(ctx, as, an);
+    u64 *B = A;
+    if (b != a) {
+        B = (u64 *)ctx->buf("mul_bn", w * 8);
+        kern::LimbSet bs{const_cast<u64 *>(db), nl, nl, 2 * n, pid}, bn{B, nl, nl, 2 * n, pid};
+        kern::ntt_fwd(ctx, bs, bn);
+    }
+    // lane (d0, d2) per pair, d1 aside (NTT domain)
+    u64 *Ln = (u64 *)ctx->buf("mul_lane", w * 8);
+    u64 *D1 = (u64 *)ctx->buf("mul_d1", (size_t)n * pw * 8);
+    u64 *T = (u64 *)ctx->buf("mul_t", (size_t)n * pw * 8);
+    for (int c = 0; c < n; c++) {
+        const u64 *a0 = A + (size_t)c * 2 * pw, *a1 = a0 + pw;
+        const u64 *b0 = B + (size_t)c * 2 * pw, *b1 = b0 + pw;
+        u64 *l0 = Ln + (size_t)c * 2 * pw;
+        kern::pointwise(ctx, a0, b0, l0, nl, pid);
+        kern::pointwise(ctx, a1, b1, l0 + pw, nl, pid);
+        kern::pointwise(ctx, a0, b1, D1 + (size_t)c * pw, nl, pid);
+        kern::pointwise(ctx, a1, b0, T + (size_t)c * pw, nl, pid);
+    }
+    kern::add(ctx, D1, T, D1, n * nl, pid);
+    // u = KS(d2) + P d0 (part 0), then + P d1 (part 1): ModDown gives
+    // (d0, d1) + KS(d2) exactly, and the rescale is fused into it
+    u64 *digits = (u64 *)ctx->buf("mul_digits", (size_t)n * beta * E * N * 8);
+    kern::modup(ctx, Ln, nl, n, level, digits);
+    u64 *u = (u64 *)ctx->buf("mul_u", (size_t)n * 2 * E * N * 8);
+    kern::ks_multi(ctx, {&rk}, {u}, Ln, nl, n, level, digits);
+    kern::scalar(ctx, D1, T, n * nl, pid, ctx->d_pmodq);
+    for (int c = 0; c < n; c++) {
+        u64 *u1 = u + ((size_t)c * 2 + 1) * E * N;
+        kern::add(ctx, u1, T + (size_t)c * pw, u1, nl, pid);
+    }
+    u64 *R = (u64 *)ctx->buf("mul_r", w * 8);
+    kern::moddown_rescale_to_lane(ctx, u, n, level, R, nl);
+    std::vector<int> top(nl, -1);
+    for (int i = 0; i < level; i++) top[i] = i;
+    kern::LimbSet rs{R, nl, nl, 2 * n, top};
+    kern::ntt_inv(ctx, rs, rs);
+    const size_t ow = (size_t)n * 2 * level * N;
+    u64 *O = is_device_ptr(out) ? out : (u64 *)ctx->buf("mul_o", ow * 8);
+    kern::copy_limbs(ctx, R, nl, O, level, 2 * n, level);
+    if (O != out) stage_out(ctx, out, O, ow);
     sync(ctx);
     API_CATCH(ctx)
 }

@@ -82,7 +82,7 @@ int fg_plan_build(fg_ctx *ctx, const int32_t *row_ptr, const int32_t *col, const
     try {
         FG_CHECK(row_ptr && (col || V == 0) && W && perm && out, FG_EINVAL, "null argument");
         *out = nullptr;
-        fg_plan_opts o{0, 0, 1, 0, 0};
+        fg_plan_opts o{0, 0, 1, 0, 0, 0};
         if (opts) o = *opts;
         pl = new fg_plan;
         pl->ctx = ctx;
@@ -260,7 +260,7 @@ int fg_plan_dry_run(const fg_params *prm, const int32_t *row_ptr, const int32_t 
         std::vector<int> bits(prm->q_bits, prm->q_bits + prm->n_q);
         bits.insert(bits.end(), prm->p_bits, prm->p_bits + prm->n_p);
         c.primes = hm::gen_primes(c.log_n, bits);
-        fg_plan_opts o{0, 0, 1, 0, 0};
+        fg_plan_opts o{0, 0, 1, 0, 0, 0};
         if (opts) o = *opts;
         fg_plan pl;
         planner::build(pl, c, row_ptr, col, val, V, W, F, Fp, perm, o);

@@ -121,7 +121,8 @@ void build(fg_plan &pl, const fg_ctx &ctx, const int32_t *row_ptr, const int32_t
     pl.V = V;
     pl.F = F;
     pl.Fp = Fp;
-    pl.in_level = ctx.nq - 1;
+    FG_CHECK(o.in_level >= 0 && o.in_level < ctx.nq, FG_ELEVEL, "input level out of range");
+    pl.in_level = o.in_level > 0 ? o.in_level : ctx.nq - 1;
     pl.aoo = o.aoo ? 1 : 0;
     pl.perm.assign(perm, perm + V);
 

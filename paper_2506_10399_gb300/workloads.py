@@ -175,6 +175,28 @@ def config_workload(name, **over):
     return make_workload(**cfg)
 
 
+# output classes of the second GCN layer (W2 is F' x C)
+SECOND_LAYER_CLASSES = {"toy": 4, "cora_like": 7, "pubmed_like": 3}
+
+
+def second_layer_weights(name, seed=None):
+    """W2 (F' x C, Glorot-uniform) of a two-layer GCN on configuration name."""
+    cfg = CONFIGS[name]
+    rng = np.random.default_rng((cfg["seed"] if seed is None else seed) + 1)
+    return weights("glorot", cfg["Fp"], SECOND_LAYER_CLASSES[name], rng)
+
+
+def two_layer_reference(w, W2):
+    """FP64 A-hat (A-hat X W1)^2 W2 (square taken elementwise)."""
+    h = w.reference_output() ** 2
+    XW = h @ W2
+    out = np.zeros((w.V, W2.shape[1]))
+    for v in range(w.V):
+        s, e = w.row_ptr[v], w.row_ptr[v + 1]
+        out[v] = w.val[s:e] @ XW[w.col[s:e]]
+    return out
+
+
 def random_order(V, size, seed):
     """A seeded injection of V nodes into [0, size)."""
     rng = np.random.default_rng(seed + 7919)

@@ -542,3 +542,104 @@ def test_moddown_of_p_multiple_is_exact(nq, npr):
     lhs = _ref.moddown(APB, qs, ps)
     rhs = ckks.add_res(_ref.moddown(A, qs, ps), B, qs)
     np.testing.assert_array_equal(lhs, rhs)
+
+
+# ---------------------------------------------------------------- CMult (x^2)
+def test_secret_square_is_the_integer_negacyclic_square():
+    P = ckks.Params(10, [60, 40], [60], 1, 40)
+    s = ckks.keygen_secret(P, 4).astype(np.int64)
+    full = np.convolve(s, s)                      # integer product, then X^N = -1
+    want = full[:P.n].copy()
+    want[:P.n - 1] -= full[P.n:]
+    np.testing.assert_array_equal(ckks.secret_square(P, ckks.keygen_secret(P, 4)), want)
+
+
+def test_tensor_product_decrypts_to_the_product_bigint():
+    """d0 + d1 s + d2 s^2 == (a0 + a1 s)(b0 + b1 s) mod Q, checked on CRT-lifted
+    big integers with schoolbook products (N = 16)."""
+    P = ckks.Params(4, [50, 40, 40], [60], 1, 30)
+    rng = np.random.default_rng(2)
+    s = ckks.keygen_secret(P, 2)
+    a = np.stack([np.stack([rng.integers(0, q, P.n, dtype=np.uint64) for q in P.q]) for _ in range(2)])
+    b = np.stack([np.stack([rng.integers(0, q, P.n, dtype=np.uint64) for q in P.q]) for _ in range(2)])
+    d0, d1, d2 = ckks.mul_ct(P, a, b)
+    Q = 1
+    for q in P.q:
+        Q *= q
+
+    def lift(res):
+        return [int(v) for v in ckks.crt_centered(P, res)]
+
+    def nmul(x, y):
+        out = [0] * P.n
+        for i in range(P.n):
+            for j in range(P.n):
+                k = i + j
+                if k < P.n:
+                    out[k] += x[i] * y[j]
+                else:
+                    out[k - P.n] -= x[i] * y[j]
+        return out
+
+    si = [int(v) for v in s]
+    s2 = nmul(si, si)
+    lhs = [x + y + z for x, y, z in zip(lift(d0), nmul(lift(d1), si), nmul(lift(d2), s2))]
+    da = [x + y for x, y in zip(lift(a[0]), nmul(lift(a[1]), si))]
+    db = [x + y for x, y in zip(lift(b[0]), nmul(lift(b[1]), si))]
+    rhs = nmul(da, db)
+    assert all((x - y) % Q == 0 for x, y in zip(lhs, rhs))
+
+
+def test_relinearisation_keeps_the_decryption_up_to_small_noise():
+    """Dec(relinearize(d)) - (d0 + d1 s + d2 s^2) is the key-switching noise:
+    small against the scale (bigint check at N = 1024)."""
+    P = ckks.Params(10, [60, 40, 40, 40], [60, 60], 2, 40)
+    s = ckks.keygen_secret(P, 6)
+    key = ckks.keygen_relin(P, 6, s)
+    rng = np.random.default_rng(3)
+    lvl = 3
+    z = rng.uniform(-1, 1, P.slots)
+    ct = ckks.encrypt(P, 6, 0, ckks.encode(P, z, P.scale, lvl), s, lvl)
+    d0, d1, d2 = ckks.mul_ct(P, ct, ct)
+    r = ckks.relinearize(P, d0, d1, d2, key)
+    s_res = ckks.small_to_res(s, P.q[:lvl + 1])
+    s2_res = ckks.small_to_res(ckks.secret_square(P, s), P.q[:lvl + 1])
+    qs = P.q[:lvl + 1]
+    want = ckks.add_res(ckks.add_res(d0, ckks.poly_mul(P, d1, s_res, qs), qs),
+                        ckks.poly_mul(P, d2, s2_res, qs), qs)
+    got = ckks.decrypt(P, r, s)
+    diff = [abs(int(v)) for v in ckks.crt_centered(P, ckks.sub_res(got, want, qs))]
+    assert max(diff) < 2 ** 30 and max(diff) > 0
+
+
+def test_cmult_decodes_to_the_product():
+    P = ckks.Params(11, [60, 40, 40, 40], [60, 60], 2, 40)
+    s = ckks.keygen_secret(P, 8)
+    key = ckks.keygen_relin(P, 8, s)
+    rng = np.random.default_rng(4)
+    z1, z2 = rng.uniform(-1, 1, P.slots), rng.uniform(-1, 1, P.slots)
+    lvl = 3
+    c1 = ckks.encrypt(P, 8, 0, ckks.encode(P, z1, P.scale, lvl), s, lvl)
+    c2 = ckks.encrypt(P, 8, 1, ckks.encode(P, z2, P.scale, lvl), s, lvl)
+    out = ckks.mul_relin_rescale(P, c1, c2, key)
+    assert out.shape[1] == lvl
+    d = ckks.decode(P, ckks.decrypt(P, out, s), P.scale * P.scale / P.q[lvl])
+    assert np.max(np.abs(d - z1 * z2)) < 2 ** -20
+
+
+def test_planted_cmult_mistakes_are_caught(monkeypatch):
+    """A dropped cross term in the tensor product, and s in place of s^2 in
+    the relinearisation key, each fail a CMult pin."""
+    orig = ckks.mul_ct
+
+    def dropped(params, a, b):
+        d0, d1, d2 = orig(params, a, b)
+        primes = params.q[:a.shape[1]]
+        return d0, ckks.poly_mul(params, a[0], b[1], primes), d2
+    monkeypatch.setattr(ckks, "mul_ct", dropped)
+    with pytest.raises(AssertionError):
+        test_tensor_product_decrypts_to_the_product_bigint()
+    monkeypatch.undo()
+    monkeypatch.setattr(ckks, "secret_square", lambda params, s: np.asarray(s, np.int64))
+    with pytest.raises(AssertionError):
+        test_cmult_decodes_to_the_product()

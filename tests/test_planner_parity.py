@@ -45,6 +45,20 @@ def test_library_planner_matches_oracle_planner(ci):
     np.testing.assert_array_equal(got, want)
 
 
+@pytest.mark.parametrize("in_level,t", [(9, 1), (5, 4)])
+def test_planner_from_a_lower_input_level(in_level, t):
+    """A second layer starts below the top level (after the first layer and
+    the x^2 activation): both planners take the input level."""
+    prm = dict(log_n=11, q_bits=[60] + [40] * 12, p_bits=[60, 60], alpha=2, log_scale=40)
+    P = ckks.Params(prm["log_n"], prm["q_bits"], prm["p_bits"], prm["alpha"], prm["log_scale"])
+    w = wl.make_workload(graph="chung_lu", V=200, deg=4.0, gamma=2.5, F=16, Fp=3, seed=5)
+    perm = wl.random_order(w.V, P.slots // t, 5)
+    op = planner.build_plan(P, in_level, w.row_ptr, w.col, w.val, w.V, w.W, perm, t, 3, True)
+    got = fg.plan_dry_run(prm, w.row_ptr, w.col, w.val, w.W, perm, t=t, radix_bits=3, in_level=in_level)
+    np.testing.assert_array_equal(got, oracle_records(op))
+    assert got[7] == in_level
+
+
 def test_packing_rule_matches_oracle():
     prm = dict(log_n=12, q_bits=[60, 40, 40], p_bits=[60], alpha=1, log_scale=40)
     w = wl.config_workload("toy")
