@@ -520,6 +520,60 @@ def run_two_layer(args):
     return 0
 
 
+# ------------------------------------------------------------------ Inter-CA
+def run_inter(args):
+    """The benchmark layer in Inter-CA mode (the paper's first-layer mode):
+    the client sends one copy of X per neighbour slot (GraphSage: the node
+    and 4 sampled neighbours, MEAN weights), the server aggregates by PMult
+    and Add with no rotation.  Copies resident in HBM; decrypted against
+    FP64 sum_k w_k X[nbr_k] W."""
+    import torch
+    import __graft_entry__
+    fg = __graft_entry__.build()
+    from paper_2506_10399_gb300 import workloads as wl
+    c = dict(wl.CONFIGS[WORKLOAD])
+    w = wl.config_workload(WORKLOAD)
+    nbr, wts = wl.sample_neighbors(w, 4, SEED)
+    t_setup = time.perf_counter()
+    ctx = fg.Context(**c)
+    perm = wl.random_order(w.V, ctx.slots, SEED)
+    plan = fg.plan_build_inter(ctx, nbr, wts, w.W, perm)
+    info = plan.info()
+    sk, evk = fg.keygen(ctx, SEED, [])
+    keys = fg.load_evk(ctx, evk)
+    x = torch.empty((info["n_in"], 2, ctx.nq, ctx.n), dtype=torch.int64, device="cuda")
+    fg.pack_neighbor_copies(ctx, sk, SEED, w.X, nbr, perm, out=x)
+    out = torch.empty((info["n_out"], 2, info["out_level"] + 1, ctx.n), dtype=torch.int64, device="cuda")
+    setup_s = time.perf_counter() - t_setup
+    _, lvl, sc = fg.gcn_layer_axw(ctx, keys, plan, x, out=out)
+    ref = wl.neighbor_reference(w, nbr, wts)
+    err = 0.0
+    for j in (0, info["n_out"] - 1):
+        d = fg.decrypt_decode(ctx, sk, out[j].contiguous(), lvl, sc)
+        err = max(err, float(np.max(np.abs(d[perm] - ref[:, j]))))
+    for _ in range(args.warmup):
+        fg.gcn_layer_axw(ctx, keys, plan, x, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = ctx.launch_count()
+    e0.record()
+    for _ in range(args.steps):
+        fg.gcn_layer_axw(ctx, keys, plan, x, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"metric": "encrypted A.X.W layer latency (ms) at N=2^16, Inter-CA mode",
+                      "value": round(ms, 3), "unit": "ms/layer", "higher_is_better": False,
+                      "copies": int(nbr.shape[1]), "input_ciphertexts": info["n_in"],
+                      "input_bytes": int(x.numel() * 8), "rotations": 0, "out_level": lvl,
+                      "decrypt_max_abs_err_vs_fp64": err,
+                      "gpu_launches": (ctx.launch_count() - n0) // args.steps,
+                      "steps": args.steps, "warmup": args.warmup, "setup_s": round(setup_s, 1),
+                      "config": {"workload": config_desc()["workload"] +
+                                 "; GraphSage neighbourhoods: the node and 4 sampled neighbours, MEAN"}}))
+    return 0
+
+
 # ------------------------------------------------------------------ batched form
 def run_batched(args):
     """Many single-layer queries of uneven size (the batch recipe of
@@ -628,6 +682,7 @@ def main():
                     help="batched form: many queries one at a time vs all at once")
     ap.add_argument("--queries", type=int, default=16, help="queries in the batched form")
     ap.add_argument("--two-layer", action="store_true", help="two-layer GCN with x^2 between")
+    ap.add_argument("--inter", action="store_true", help="the layer in Inter-CA mode")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -635,6 +690,8 @@ def main():
         return run_batched(args)
     if args.two_layer:
         return run_two_layer(args)
+    if args.inter:
+        return run_inter(args)
     return run_ours(args)
 
 

@@ -230,6 +230,53 @@ int fg_plan_dry_run(const fg_params *params, const int32_t *row_ptr, const int32
  * malformed CSR. */
 int fg_node_order(const int32_t *row_ptr, const int32_t *col, int V, int M, int TH,
                   int32_t *perm_out, int *n_regions);
+/* Inter-CA plan (paper Sec. 3.1, Table 1; the first-layer mode): the client
+ * sends n copies of X, copy k holding row nbr[v][k] of X at node v's slot
+ * (fg_pack_features of the gathered rows; nbr -1: no neighbour), and the
+ * server computes out_j = sum_k wts[.][k] (x) (X_k W)_j by PMult and Add
+ * only (no rotation): the combination of every copy (constants at q_l),
+ * a rescale, the masked sum over k (masks at q_{l-1}), a rescale.  nbr and
+ * wts are [V][n] row-major; t = 1; the layer takes n*F input ciphertexts
+ * (copy-major) and returns Fp at level in_level - 2.  GraphSage's MEAN over
+ * {v} and n sampled neighbours is nbr[v] = (v, u_1, .., u_n), wts = 1/(n+1). */
+int fg_plan_build_inter(fg_ctx *ctx, const int32_t *nbr, const double *wts, int V, int n,
+                        const double *W, int F, int Fp, const int32_t *perm,
+                        const fg_plan_opts *opts, fg_plan **out);
+
+/* Plan statistics for the learned planner (host only, like
+ * fg_plan_dry_run): feat[FG_PLAN_FEATURES] = log2 V, log2 F, mean row
+ * length of A-hat, log2(1 + max row length), log2 t, radix bits, mean bit
+ * length of the node shifts |pi(u) - pi(v)| (AOO), groups, log2(1 +
+ * rotations), log2(1 + masked terms), most lanes in a group, log2(1 + sum of
+ * rotations x extended limbs), log2(1 + sum of terms x extended limbs),
+ * log2(F (in_level + 1)), in_level. */
+#define FG_PLAN_FEATURES 15
+int fg_plan_features(const fg_params *params, const int32_t *row_ptr, const int32_t *col,
+                     const double *val, int V, const double *W, int F, int Fp,
+                     const int32_t *perm, const fg_plan_opts *opts, float *feat);
+
+/* The learned planner's latency model (the paper's packing and ordering
+ * choices, Sec. 3.2 and 3.4, made by a model instead of a search): a
+ * three-layer perceptron y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 in FP32
+ * on the GPU (current device), trained by full-batch Adam on the mean
+ * squared error.  Parameters (host, float) are packed W1 [n_in][hidden],
+ * b1 [hidden], W2 [hidden][hidden], b2 [hidden], W3 [hidden][1], b3 [1].
+ * X is [n][n_in] row-major, y [n], all host memory.  fg_mlp_grad gives the
+ * loss and its gradient in the packed order; fg_mlp_train runs `steps` Adam
+ * steps (beta 0.9, 0.999, eps 1e-8) and writes the loss before each step
+ * into losses (may be NULL).  fg_plan_choose scores n_cand feature rows and
+ * returns the index of the lowest prediction.  Errors: FG_EINVAL, FG_ECUDA,
+ * FG_EOOM; the message is fg_last_error(NULL). */
+typedef struct fg_mlp fg_mlp;
+int fg_mlp_create(int n_in, int hidden, const float *params, fg_mlp **out);
+int fg_mlp_destroy(fg_mlp *mlp);
+int fg_mlp_params(const fg_mlp *mlp, float *out);
+int fg_mlp_forward(fg_mlp *mlp, const float *X, int n, float *y);
+int fg_mlp_grad(fg_mlp *mlp, const float *X, const float *y, int n, float *loss, float *grad);
+int fg_mlp_train(fg_mlp *mlp, const float *X, const float *y, int n, int steps, float lr,
+                 float *losses);
+int fg_plan_choose(fg_mlp *mlp, const float *features, int n_cand, float *pred, int *best);
+
 /* Replace the encoding of mask `mask` by caller-given coefficients
  * [level+1][N] (host or device), e.g. an independent encoder's output. */
 int fg_plan_set_plaintext(fg_plan *plan, int mask, const uint64_t *coeffs);

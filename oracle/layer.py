@@ -100,3 +100,21 @@ def layer_axw(params, plan, cts_in, keys, pts, columns=None):
     cols = range(plan.Fp) if columns is None else columns
     return [aggregation(params, plan, combination(params, plan, cts_in, keys, pts, j),
                         keys, pts) for j in cols]
+
+
+def inter_ca_layer(params, plan, copies, pts, columns=None):
+    """Inter-CA layer: for each output column j,
+    Rescale(sum_k mask_k (x) Rescale(sum_f c_{f,j} X_{k,f})), the copies
+    given copy-major (copies[k * F + f])."""
+    cols = range(plan.Fp) if columns is None else columns
+    F = plan.F
+    out = []
+    for j in cols:
+        acc = None
+        for k in range(plan.n_copies):
+            z = combination(params, plan, copies[k * F:(k + 1) * F], None, pts, j)
+            prod = ckks.pmult(params, pts[k], z)
+            acc = prod if acc is None else np.stack(
+                [ckks.add_res(acc[p], prod[p], params.q[:prod.shape[1]]) for p in range(2)])
+        out.append(ckks.rescale_ct(params, acc))
+    return out

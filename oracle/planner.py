@@ -120,6 +120,7 @@ class Plan:
     out_level: int = 0
     radix_bits: int = 0
     aoo: bool = True
+    n_copies: int = 0          # Inter-CA: one mask per neighbour copy (masks 0..n_copies-1)
 
     def rotation_amounts(self):
         ks = set()
@@ -333,3 +334,32 @@ def simulate_combination(plan, X, W):
                 z = z + np.roll(z, -k)
         Z.append(z)
     return Z
+
+
+def build_inter_plan(params, in_level, nbr, wts, V, W, perm):
+    """Inter-CA plan (Sec. 3.1, Table 1: aggregation by PMult and Add over n
+    node arrangements the client encrypts).  Copy k of the input holds row
+    nbr[v][k] of X at slot perm[v]; the layer computes Z_k = X_k W (the
+    combination of App. B.1 on every copy, constants at q_l) and then
+    sum_k mask_k (x) Z_k with mask_k holding wts[v][k] at perm[v] (scale
+    q_{l-1}); two rescales.  The records mark it with radix_bits = -n."""
+    M = params.slots
+    F, Fp = W.shape
+    nbr = np.asarray(nbr)
+    n = nbr.shape[1]
+    perm = np.asarray(perm, dtype=np.int64)
+    if perm.shape[0] != V or len(set(perm.tolist())) != V or perm.min() < 0 or perm.max() >= M:
+        raise ValueError("perm must be an injection of the V nodes into [0, M)")
+    plan = Plan(n=params.n, M=M, t=1, B=M, V=V, F=F, Fp=Fp, perm=perm, in_level=in_level,
+                radix_bits=-n, aoo=True, n_copies=n)
+    ql = params.q[in_level]
+    plan.comb_consts = [[int(_round_half_away(float(W[f, j]) * float(ql))) for j in range(Fp)]
+                        for f in range(F)]
+    for k in range(n):
+        vals = np.zeros(M)
+        for v in range(V):
+            if nbr[v, k] >= 0:
+                vals[perm[v]] = wts[v, k]
+        plan.masks.append(Mask(level=in_level - 1, values=vals))
+    plan.out_level = in_level - 2
+    return plan

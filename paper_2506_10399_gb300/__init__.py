@@ -292,6 +292,41 @@ class Plan:
             pass
 
 
+def plan_build_inter(ctx, nbr, wts, W, perm, min_out_level=0, in_level=0):
+    """Inter-CA plan: nbr, wts [V][n] (neighbour index or -1, its weight)."""
+    nat = _lib()
+    nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+    wts = np.ascontiguousarray(wts, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    V, n = nbr.shape
+    F, Fp = W.shape
+    o = nat.PlanOpts(1, 0, 1, int(min_out_level), 0, int(in_level))
+    h = ctypes.c_void_p()
+    _check(ctx, nat.lib.fg_plan_build_inter(ctx._h, ctypes.c_void_p(nbr.ctypes.data), _ptr(wts), V, n,
+                                            _ptr(W), F, Fp, ctypes.c_void_p(perm.ctypes.data),
+                                            ctypes.byref(o), ctypes.byref(h)))
+    return Plan(ctx, h)
+
+
+def pack_neighbor_copies(ctx, sk, seed, X, nbr, perm, out=None):
+    """The client's Inter-CA input: for every neighbour slot k, the rows
+    nbr[:, k] of X (zero where nbr is -1) packed as fg_pack_features does,
+    copy k encrypted under seed + k; [n*F][2][L+1][N], copy-major."""
+    X = np.asarray(X, dtype=np.float64)
+    nbr = np.asarray(nbr)
+    V, n = nbr.shape
+    F = X.shape[1]
+    parts = []
+    for k in range(n):
+        Xk = np.where((nbr[:, k] >= 0)[:, None], X[np.maximum(nbr[:, k], 0)], 0.0)
+        if out is not None:
+            pack_features(ctx, sk, seed + k, Xk, perm, 1, out=out[k * F:(k + 1) * F])
+        else:
+            parts.append(pack_features(ctx, sk, seed + k, Xk, perm, 1))
+    return out if out is not None else np.concatenate(parts)
+
+
 def plan_build(ctx, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=True, min_out_level=0,
                n_sampled=0, in_level=0):
     nat = _lib()
@@ -387,6 +422,106 @@ def gcn_layer_batch(ctx, keys, plans, ins, outs, streams=0, graph=True):
     _check(ctx, nat.lib.fg_gcn_layer_batch(ctx._h, keys._h, P, n, I, O, ctypes.byref(o), lv,
                                            ctypes.byref(su)))
     return list(lv), su.value
+
+
+N_PLAN_FEATURES = 15
+
+
+def plan_features(params, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=True, min_out_level=0,
+                  n_sampled=0, in_level=0):
+    """The learned planner's statistics of one candidate plan (host only)."""
+    nat = _lib()
+    q_bits, p_bits = params["q_bits"], params["p_bits"]
+    qb = (ctypes.c_int * len(q_bits))(*q_bits)
+    pb = (ctypes.c_int * len(p_bits))(*p_bits)
+    prm = nat.Params(params["log_n"], len(q_bits), qb, len(p_bits), pb, params["alpha"],
+                     float(params["log_scale"]))
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    F, Fp = W.shape
+    o = nat.PlanOpts(int(t), int(radix_bits), 1 if aoo else 0, int(min_out_level), int(n_sampled),
+                     int(in_level))
+    out = np.zeros(N_PLAN_FEATURES, np.float32)
+    rc = nat.lib.fg_plan_features(ctypes.byref(prm), ctypes.c_void_p(row_ptr.ctypes.data),
+                                  ctypes.c_void_p(col.ctypes.data), ctypes.c_void_p(val.ctypes.data),
+                                  row_ptr.size - 1, ctypes.c_void_p(W.ctypes.data), F, Fp,
+                                  ctypes.c_void_p(perm.ctypes.data), ctypes.byref(o),
+                                  ctypes.c_void_p(out.ctypes.data))
+    if rc != 0:
+        raise FicgcnError(rc, "plan features failed")
+    return out
+
+
+class Mlp:
+    """The learned planner's latency model on the GPU (fg_mlp_*)."""
+
+    def __init__(self, n_in, hidden, params):
+        nat = _lib()
+        self.n_in, self.hidden = int(n_in), int(hidden)
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        h = ctypes.c_void_p()
+        rc = nat.lib.fg_mlp_create(self.n_in, self.hidden, ctypes.c_void_p(p.ctypes.data), ctypes.byref(h))
+        if rc != 0:
+            raise FicgcnError(rc, (nat.lib.fg_last_error(None) or b"").decode())
+        self._h = h
+        self.n_params = p.size
+
+    def _rc(self, rc):
+        if rc != 0:
+            raise FicgcnError(rc, (_lib().lib.fg_last_error(None) or b"").decode())
+
+    def params(self):
+        out = np.zeros(self.n_params, np.float32)
+        self._rc(_lib().lib.fg_mlp_params(self._h, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def forward(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.zeros(X.shape[0], np.float32)
+        self._rc(_lib().lib.fg_mlp_forward(self._h, ctypes.c_void_p(X.ctypes.data), X.shape[0],
+                                            ctypes.c_void_p(y.ctypes.data)))
+        return y
+
+    def grad(self, X, y):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        loss = ctypes.c_float()
+        g = np.zeros(self.n_params, np.float32)
+        self._rc(_lib().lib.fg_mlp_grad(self._h, ctypes.c_void_p(X.ctypes.data),
+                                         ctypes.c_void_p(y.ctypes.data), X.shape[0], ctypes.byref(loss),
+                                         ctypes.c_void_p(g.ctypes.data)))
+        return loss.value, g
+
+    def train(self, X, y, steps, lr):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        losses = np.zeros(max(1, steps), np.float32)
+        self._rc(_lib().lib.fg_mlp_train(self._h, ctypes.c_void_p(X.ctypes.data),
+                                          ctypes.c_void_p(y.ctypes.data), X.shape[0], int(steps),
+                                          ctypes.c_float(lr), ctypes.c_void_p(losses.ctypes.data)))
+        return losses[:steps]
+
+    def choose(self, features):
+        F = np.ascontiguousarray(features, dtype=np.float32)
+        pred = np.zeros(F.shape[0], np.float32)
+        best = ctypes.c_int()
+        self._rc(_lib().lib.fg_plan_choose(self._h, ctypes.c_void_p(F.ctypes.data), F.shape[0],
+                                            ctypes.c_void_p(pred.ctypes.data), ctypes.byref(best)))
+        return best.value, pred
+
+    def close(self):
+        if self._h is not None:
+            _lib().lib.fg_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mul_relin_rescale(ctx, keys, a, b, level, out=None):

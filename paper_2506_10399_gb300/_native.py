@@ -71,6 +71,17 @@ SIGS = {
     "fg_plan_dry_run": (c_int, [P(Params), c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_int,
                                 c_void_p, P(PlanOpts), c_void_p, c_size, P(c_size)]),
     "fg_node_order": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, P(c_int)]),
+    "fg_plan_build_inter": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p, c_int, c_int,
+                                    c_void_p, P(PlanOpts), P(c_void_p)]),
+    "fg_plan_features": (c_int, [P(Params), c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_int,
+                                 c_void_p, P(PlanOpts), c_void_p]),
+    "fg_mlp_create": (c_int, [c_int, c_int, c_void_p, P(c_void_p)]),
+    "fg_mlp_destroy": (c_int, [c_void_p]),
+    "fg_mlp_params": (c_int, [c_void_p, c_void_p]),
+    "fg_mlp_forward": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
+    "fg_mlp_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
+    "fg_mlp_train": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, ctypes.c_float, c_void_p]),
+    "fg_plan_choose": (c_int, [c_void_p, c_void_p, c_int, c_void_p, P(c_int)]),
     "fg_mul_relin_rescale": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "fg_gcn_layer_batch": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
                                    P(BatchOpts), c_void_p, P(c_int)]),

@@ -12,10 +12,12 @@
 #include "modarith.cuh"
 
 // ====================================================================== helpers
+// message of the last failed call that has no context (fg_last_error(NULL))
+std::string g_create_err = "no context";
+
 namespace {
 
 constexpr int kMaxQ = 60, kMaxP = 8;
-std::string g_create_err = "no context";
 
 bool is_device_ptr(const void *p)
 {

@@ -190,6 +190,7 @@ struct fg_plan {
     std::vector<MaskC> masks;
     u64 *d_comb = nullptr;                 // t == 1: [in_level+1][F][Fp] Montgomery constants
     int max_lanes = 1;
+    int n_copies = 0;                      // Inter-CA: neighbour copies (masks 0..n_copies-1)
 };
 
 // ------------------------------------------------------------------ kernels
@@ -281,4 +282,8 @@ int choose_t(int F, int n, int V, int Fp, int M);
 void build(fg_plan &pl, const fg_ctx &ctx, const int32_t *row_ptr, const int32_t *col,
            const double *val, int V, const double *W, int F, int Fp, const int32_t *perm,
            const fg_plan_opts &opts);
+// Inter-CA plan: combination constants of W, then one mask per neighbour
+// copy k holding wts[v][k] at slot perm[v]
+void build_inter(fg_plan &pl, const fg_ctx &ctx, const int32_t *nbr, const double *wts, int V,
+                 int n, const double *W, int F, int Fp, const int32_t *perm, const fg_plan_opts &opts);
 }  // namespace planner

@@ -1095,8 +1095,8 @@ k_stay_mac(const u64 *__restrict__ lane, int ls, int ncol, int level, const Dest
 // (below 2^55 for 255 terms): four 32 x 32 -> 64-bit multiply-adds per
 // product instead of a 64 x 64 -> 128-bit one.  The halves are stored as
 // v0 | v1 << 32, so each factor is a register pair read without shifts.
-// Other primes (q_0 and the special primes, up to 60 bits) use the
-// 128-bit sum.
+// Other primes (q_0 and the special primes, up to 60 bits) are split into
+// 30-bit halves and folded into a 128-bit sum every 8 terms.
 //
 // Thread = one polynomial (column, part) at one slot pair; a CTA covers the
 // npoly polynomials of 128 / npoly slot pairs of one limb, neighbouring
@@ -1180,28 +1180,26 @@ k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
         }
     }
     cp_async_wait_all();
-    // 2. in place, each thread on the words it copied
-    if (split && poly < npoly)
+    // 2. in place, each thread on the words it copied: kept lanes times P,
+    // every word split into halves (23 bits below 2^46, else 30 bits)
+    if (poly < npoly)
         for (int t = poly; t < nterm; t += npoly) {
             const ulonglong2 m = msm[t * pp_n + pp];
-            msm[t * pp_n + pp] = make_ulonglong2(split23(m.x), split23(m.y));
+            msm[t * pp_n + pp] = split ? make_ulonglong2(split23(m.x), split23(m.y))
+                                       : make_ulonglong2(split30(m.x), split30(m.y));
         }
-    if (act && (split || isq)) {
+    if (act) {
         const u64 pw = isq ? pmodq[2 * i] : 0, pws = isq ? pmodq[2 * i + 1] : 0;
         for (int s = 0; s < nsrc; s++) {
             const bool kept = isq && !pg.su[s];
-            if (!split && !kept) continue;
             ulonglong2 *dst = vsm + (size_t)s * kGmacThreads + tid;
             ulonglong2 v = *dst;
             if (kept) {
                 v.x = shoup_mul(v.x, pw, pws, q);
                 v.y = shoup_mul(v.y, pw, pws, q);
             }
-            if (split) {
-                v.x = split23(v.x);
-                v.y = split23(v.y);
-            }
-            *dst = v;
+            *dst = split ? make_ulonglong2(split23(v.x), split23(v.y))
+                         : make_ulonglong2(split30(v.x), split30(v.y));
         }
     }
     __syncthreads();
@@ -1227,12 +1225,19 @@ k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
             }
             r = make_ulonglong2(fold_split(a0, a1, a2, P), fold_split(c0, c1, c2, P));
         } else {
+            // 30-bit halves: partial sums folded into 128 bits every 8 terms
             u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
-            for (int t = t0; t < t1; t++, maddr += mstep) {
-                const ulonglong2 v = lds128(vbase + pg.tvoff[t]);
-                const ulonglong2 m = lds128(maddr);
-                mac128(hi0, lo0, v.x, m.x);
-                mac128(hi1, lo1, v.y, m.y);
+            for (int t = t0; t < t1;) {
+                const int te = min(t + 8, t1);
+                u64 a0 = 0, a1 = 0, a2 = 0, c0 = 0, c1 = 0, c2 = 0;
+                for (; t < te; t++, maddr += mstep) {
+                    const ulonglong2 v = lds128(vbase + pg.tvoff[t]);
+                    const ulonglong2 m = lds128(maddr);
+                    mac_split(a0, a1, a2, v.x, m.x);
+                    mac_split(c0, c1, c2, v.y, m.y);
+                }
+                fold30(hi0, lo0, a0, a1, a2);
+                fold30(hi1, lo1, c0, c1, c2);
             }
             r = make_ulonglong2(redc(reduce_word(hi0, P), lo0, P), redc(reduce_word(hi1, P), lo1, P));
         }

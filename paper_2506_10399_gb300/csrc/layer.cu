@@ -73,6 +73,51 @@ void encode_mask(const fg_ctx *ctx, const MaskC &m, u64 *out)
 
 extern "C" {
 
+}  // extern "C"
+
+// masks encoded on the host (all cores), uploaded, NTT, Montgomery form;
+// the combination constants in Montgomery form for every limb
+static void finish_plan(fg_ctx *ctx, fg_plan *pl)
+{
+    const int N = ctx->n, F = pl->F, Fp = pl->Fp;
+    const int nm = (int)pl->masks.size();
+    const int chunk = 32;
+    std::vector<std::vector<u64>> enc(chunk);
+    for (int m0 = 0; m0 < nm; m0 += chunk) {
+        const int cn = std::min(chunk, nm - m0);
+        int bad = 0;
+#pragma omp parallel for schedule(dynamic) reduction(| : bad)
+        for (int c = 0; c < cn; c++) {
+            const MaskC &m = pl->masks[m0 + c];
+            enc[c].resize((size_t)(m.level + 1) * N);
+            try {
+                encode_mask(ctx, m, enc[c].data());
+            } catch (...) {
+                bad = 1;
+            }
+        }
+        FG_CHECK(!bad, FG_EINVAL, "mask cannot be encoded");
+        for (int c = 0; c < cn; c++) upload_mask(ctx, pl->masks[m0 + c], enc[c].data());
+        CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    if (pl->t == 1) {
+        const int l0 = pl->in_level, nl = l0 + 1;
+        std::vector<u64> h((size_t)nl * F * Fp);
+        for (int i = 0; i < nl; i++) {
+            const u64 q = ctx->primes[i];
+            for (size_t e = 0; e < (size_t)F * Fp; e++) {
+                const i64 c = pl->comb_consts[e];
+                const u64 r = c >= 0 ? (u64)c % q : (q - ((u64)(-(c + 1)) % q + 1) % q) % q;
+                h[(size_t)i * F * Fp + e] = hm::to_mont(r, q);
+            }
+        }
+        CUDA_TRY(cudaMalloc(&pl->d_comb, h.size() * 8));
+        CUDA_TRY(cudaMemcpy(pl->d_comb, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
+    }
+}
+
+extern "C" {
+
 int fg_plan_build(fg_ctx *ctx, const int32_t *row_ptr, const int32_t *col, const double *val,
                   int V, const double *W, int F, int Fp, const int32_t *perm,
                   const fg_plan_opts *opts, fg_plan **out)
@@ -87,42 +132,35 @@ int fg_plan_build(fg_ctx *ctx, const int32_t *row_ptr, const int32_t *col, const
         pl = new fg_plan;
         pl->ctx = ctx;
         planner::build(*pl, *ctx, row_ptr, col, val, V, W, F, Fp, perm, o);
-        // masks: encode on the host (all cores), upload, NTT, Montgomery form
-        const int N = ctx->n;
-        const int nm = (int)pl->masks.size();
-        const int chunk = 32;
-        std::vector<std::vector<u64>> enc(chunk);
-        for (int m0 = 0; m0 < nm; m0 += chunk) {
-            const int cn = std::min(chunk, nm - m0);
-            int bad = 0;
-#pragma omp parallel for schedule(dynamic) reduction(| : bad)
-            for (int c = 0; c < cn; c++) {
-                const MaskC &m = pl->masks[m0 + c];
-                enc[c].resize((size_t)(m.level + 1) * N);
-                try {
-                    encode_mask(ctx, m, enc[c].data());
-                } catch (...) {
-                    bad = 1;
-                }
-            }
-            FG_CHECK(!bad, FG_EINVAL, "mask cannot be encoded");
-            for (int c = 0; c < cn; c++) upload_mask(ctx, pl->masks[m0 + c], enc[c].data());
-            CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-        }
-        if (pl->t == 1) {
-            const int l0 = pl->in_level, nl = l0 + 1;
-            std::vector<u64> h((size_t)nl * F * Fp);
-            for (int i = 0; i < nl; i++) {
-                const u64 q = ctx->primes[i];
-                for (size_t e = 0; e < (size_t)F * Fp; e++) {
-                    const i64 c = pl->comb_consts[e];
-                    const u64 r = c >= 0 ? (u64)c % q : (q - ((u64)(-(c + 1)) % q + 1) % q) % q;
-                    h[(size_t)i * F * Fp + e] = hm::to_mont(r, q);
-                }
-            }
-            CUDA_TRY(cudaMalloc(&pl->d_comb, h.size() * 8));
-            CUDA_TRY(cudaMemcpy(pl->d_comb, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
-        }
+        finish_plan(ctx, pl);
+        *out = pl;
+        return FG_OK;
+    } catch (const fg_error &e) {
+        ctx->err = e.what();
+        fg_plan_destroy(pl);
+        return e.code;
+    } catch (const std::exception &e) {
+        ctx->err = e.what();
+        fg_plan_destroy(pl);
+        return FG_EOOM;
+    }
+}
+
+int fg_plan_build_inter(fg_ctx *ctx, const int32_t *nbr, const double *wts, int V, int n,
+                        const double *W, int F, int Fp, const int32_t *perm,
+                        const fg_plan_opts *opts, fg_plan **out)
+{
+    if (!ctx) return FG_EINVAL;
+    fg_plan *pl = nullptr;
+    try {
+        FG_CHECK(nbr && wts && W && perm && out, FG_EINVAL, "null argument");
+        *out = nullptr;
+        fg_plan_opts o{0, 0, 1, 0, 0, 0};
+        if (opts) o = *opts;
+        pl = new fg_plan;
+        pl->ctx = ctx;
+        planner::build_inter(*pl, *ctx, nbr, wts, V, n, W, F, Fp, perm, o);
+        finish_plan(ctx, pl);
         *out = pl;
         return FG_OK;
     } catch (const fg_error &e) {
@@ -152,7 +190,7 @@ int fg_plan_info(const fg_plan *pl, fg_plan_info_t *info)
     memset(info, 0, sizeof(*info));
     info->t = pl->t;
     info->B = pl->B;
-    info->n_in = pl->t == 1 ? pl->F : (pl->F + pl->t - 1) / pl->t;
+    info->n_in = pl->n_copies ? pl->n_copies * pl->F : pl->t == 1 ? pl->F : (pl->F + pl->t - 1) / pl->t;
     info->n_out = pl->Fp;
     info->in_level = pl->in_level;
     info->out_level = pl->out_level;
@@ -241,35 +279,98 @@ int fg_plan_describe(const fg_plan *pl, int64_t *out, size_t cap, size_t *len)
     return copy_records(describe_records(pl), out, cap, len);
 }
 
+}  // extern "C"
+
+// host-only planning: a context with the primes and sizes, no device tables
+static void host_plan(const fg_params *prm, const int32_t *row_ptr, const int32_t *col,
+                      const double *val, int V, const double *W, int F, int Fp, const int32_t *perm,
+                      const fg_plan_opts *opts, fg_ctx &c, fg_plan &pl)
+{
+    FG_CHECK(prm->log_n >= 10 && prm->log_n <= 16 && prm->n_q >= 2 && prm->n_q <= 60 &&
+                 prm->n_p >= 1 && prm->n_p <= 8 && prm->q_bits && prm->p_bits,
+             FG_EINVAL, "bad parameters");
+    c.log_n = prm->log_n;
+    c.n = 1 << prm->log_n;
+    c.slots = c.n / 2;
+    c.nq = prm->n_q;
+    c.np = prm->n_p;
+    c.alpha = prm->alpha;
+    std::vector<int> bits(prm->q_bits, prm->q_bits + prm->n_q);
+    bits.insert(bits.end(), prm->p_bits, prm->p_bits + prm->n_p);
+    c.primes = hm::gen_primes(c.log_n, bits);
+    fg_plan_opts o{0, 0, 1, 0, 0, 0};
+    if (opts) o = *opts;
+    planner::build(pl, c, row_ptr, col, val, V, W, F, Fp, perm, o);
+}
+
+extern "C" {
+
 int fg_plan_dry_run(const fg_params *prm, const int32_t *row_ptr, const int32_t *col,
                     const double *val, int V, const double *W, int F, int Fp, const int32_t *perm,
                     const fg_plan_opts *opts, int64_t *out, size_t cap, size_t *len)
 {
     if (!prm || !row_ptr || !W || !perm || !len) return FG_EINVAL;
     try {
-        FG_CHECK(prm->log_n >= 10 && prm->log_n <= 16 && prm->n_q >= 2 && prm->n_q <= 60 &&
-                     prm->n_p >= 1 && prm->n_p <= 8 && prm->q_bits && prm->p_bits,
-                 FG_EINVAL, "bad parameters");
-        fg_ctx c;   // host-only: primes and sizes, no device tables
-        c.log_n = prm->log_n;
-        c.n = 1 << prm->log_n;
-        c.slots = c.n / 2;
-        c.nq = prm->n_q;
-        c.np = prm->n_p;
-        c.alpha = prm->alpha;
-        std::vector<int> bits(prm->q_bits, prm->q_bits + prm->n_q);
-        bits.insert(bits.end(), prm->p_bits, prm->p_bits + prm->n_p);
-        c.primes = hm::gen_primes(c.log_n, bits);
-        fg_plan_opts o{0, 0, 1, 0, 0, 0};
-        if (opts) o = *opts;
+        fg_ctx c;
         fg_plan pl;
-        planner::build(pl, c, row_ptr, col, val, V, W, F, Fp, perm, o);
+        host_plan(prm, row_ptr, col, val, V, W, F, Fp, perm, opts, c, pl);
         return copy_records(describe_records(&pl), out, cap, len);
     } catch (const fg_error &e) {
         return e.code;
     } catch (const std::exception &) {
         return FG_EOOM;
     }
+}
+
+int fg_plan_features(const fg_params *prm, const int32_t *row_ptr, const int32_t *col,
+                     const double *val, int V, const double *W, int F, int Fp, const int32_t *perm,
+                     const fg_plan_opts *opts, float *feat)
+{
+    if (!prm || !row_ptr || !col || !W || !perm || !feat) return FG_EINVAL;
+    try {
+        fg_ctx c;
+        fg_plan pl;
+        host_plan(prm, row_ptr, col, val, V, W, F, Fp, perm, opts, c, pl);
+        const int M = c.slots, B = pl.B;
+        int maxdeg = 0;
+        double shift_bits = 0;
+        long long edges = 0;
+        for (int v = 0; v < V; v++) {
+            maxdeg = std::max(maxdeg, row_ptr[v + 1] - row_ptr[v]);
+            for (int e = row_ptr[v]; e < row_ptr[v + 1]; e++) {
+                const int u = col[e];
+                if (u == v) continue;
+                int d = ((perm[u] - perm[v]) % B + B) % B;
+                if (d > B / 2) d -= B;
+                shift_bits += 32 - __builtin_clz((unsigned)std::abs(d) | 1u);
+                edges++;
+            }
+        }
+        double rots = 0, terms = 0, ks_work = 0, mac_work = 0;
+        int lanes = 1;
+        for (const GroupC &g : pl.groups) {
+            rots += (double)g.rots.size();
+            terms += (double)g.terms.size();
+            ks_work += (double)g.rots.size() * (g.level + 1 + c.np);
+            mac_work += (double)g.terms.size() * (g.level + 1 + c.np);
+            lanes = std::max(lanes, g.n_out);
+        }
+        const float f[FG_PLAN_FEATURES] = {
+            (float)std::log2((double)V), (float)std::log2((double)F),
+            (float)((double)row_ptr[V] / V), (float)std::log2(1.0 + maxdeg),
+            (float)std::log2((double)pl.t), (float)pl.radix_bits,
+            (float)(edges ? shift_bits / edges : 0.0), (float)pl.groups.size(),
+            (float)std::log2(1.0 + rots), (float)std::log2(1.0 + terms), (float)lanes,
+            (float)std::log2(1.0 + ks_work), (float)std::log2(1.0 + mac_work),
+            (float)std::log2((double)F * (pl.in_level + 1)), (float)pl.in_level};
+        (void)M;
+        for (int i = 0; i < FG_PLAN_FEATURES; i++) feat[i] = f[i];
+    } catch (const fg_error &e) {
+        return e.code;
+    } catch (const std::exception &) {
+        return FG_EOOM;
+    }
+    return FG_OK;
 }
 
 int fg_plan_set_plaintext(fg_plan *pl, int mask, const uint64_t *coeffs)
@@ -300,7 +401,7 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
         FG_CHECK(pl->ctx == ctx && keys->ctx == ctx, FG_EINVAL, "plan or keys of another context");
         const int N = ctx->n, M = ctx->slots, Fp = pl->Fp, F = pl->F, t = pl->t;
         const int l0 = pl->in_level, nl0 = l0 + 1;
-        const int nb = t == 1 ? F : (F + t - 1) / t;
+        const int nb = pl->n_copies ? pl->n_copies * F : t == 1 ? F : (F + t - 1) / t;
         FG_CHECK(n_in == nb, FG_EINVAL, "number of input ciphertexts does not match the plan");
         FG_CHECK(n_out == Fp, FG_EINVAL, "number of output ciphertexts does not match the plan");
         // every rotation key the plan needs must be present before any work
@@ -325,6 +426,36 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
         }
         u64 *acc = (u64 *)ctx->buf("acc", lane_w * 8);
         u64 *acc_new = (u64 *)ctx->buf("acc_new", lane_w * 8);
+
+        // ---- Inter-CA (the client sent one copy of X per neighbour slot k):
+        // Z_k = X_k W for every copy, then out = sum_k mask_k (x) Z_k, rescale
+        if (pl->n_copies) {
+            const std::vector<int> pid_l1 = iota(LS);
+            u64 *Zc = (u64 *)ctx->buf("comb_z", (size_t)Fp * 2 * nl0 * N * 8);
+            CUDA_TRY(cudaMemsetAsync(acc, 0, lane_w * 8, ctx->stream));
+            for (int k = 0; k < pl->n_copies; k++) {
+                kern::comb_const_mac(ctx, X + (size_t)k * F * 2 * nl0 * N, F, Fp, l0, pl->d_comb, Zc, nl0);
+                kern::rescale_coef(ctx, Zc, nl0, bufA[0], LS, Fp * 2, l0);
+                kern::LimbSet z{bufA[0], LS, LS, Fp * 2, pid_l1};
+                kern::ntt_fwd(ctx, z, z);
+                kern::stay_mac(ctx, bufA[0], LS, Fp, l1, {{acc, pl->masks[k].d}}, LS);
+            }
+            kern::rescale_ntt(ctx, acc, LS, Fp * 2, l1);
+            const int level = l1 - 1, nlo = level + 1;
+            FG_CHECK(level == pl->out_level, FG_ELEVEL, "plan output level mismatch");
+            std::vector<int> pidx(LS, -1);
+            for (int i = 0; i < nlo; i++) pidx[i] = i;
+            kern::LimbSet as{acc, LS, LS, Fp * 2, pidx};
+            kern::ntt_inv(ctx, as, as);
+            const size_t out_w = (size_t)Fp * 2 * nlo * N;
+            u64 *o = is_dev(out_cts) ? out_cts : (u64 *)ctx->buf("layer_out", out_w * 8);
+            kern::copy_limbs(ctx, acc, LS, o, nlo, Fp * 2, nlo);
+            if (o != out_cts)
+                CUDA_TRY(cudaMemcpyAsync(out_cts, o, out_w * 8, cudaMemcpyDeviceToHost, ctx->stream));
+            if (sync) CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+            if (out_level) *out_level = level;
+            return;
+        }
 
         // ---- 1. combination
         const std::vector<int> pid_l1 = iota(LS);
@@ -538,7 +669,7 @@ static void batch_pass(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
             const fg_plan *pl = plans[q];
             ctx->stream = ctx->pool[q % S];
             ctx->ws_prefix = "b" + std::to_string(q % S) + "/";
-            const int nb = pl->t == 1 ? pl->F : (pl->F + pl->t - 1) / pl->t;
+            const int nb = pl->n_copies ? pl->n_copies * pl->F : pl->t == 1 ? pl->F : (pl->F + pl->t - 1) / pl->t;
             layer_exec(ctx, keys, pl, in_cts[q], nb, out_cts[q], pl->Fp, false, &levels[q]);
         }
     } catch (...) {

@@ -133,3 +133,22 @@ __device__ __forceinline__ u64 shoup_lazy3(u64 y, u64 w, u64 ws, u64 q)
     h += s >> 32;
     return y * w - h * q;
 }
+
+// Factors below 2^60 split into 30-bit halves, v0 | v1 << 32 (v = v0 + v1
+// 2^30): the same three partial sums, each product below 2^60, so they hold
+// 8 terms (A1 takes two products a term) before they are folded into a
+// 128-bit total.
+__device__ __forceinline__ u64 split30(u64 v) { return (v & 0x3FFFFFFF) | ((v >> 30) << 32); }
+
+// (hi, lo) += A0 + A1 2^30 + A2 2^60
+__device__ __forceinline__ void fold30(u64 &hi, u64 &lo, u64 a0, u64 a1, u64 a2)
+{
+    lo += a0;
+    hi += lo < a0;
+    u64 t = a1 << 30;
+    lo += t;
+    hi += (lo < t) + (a1 >> 34);
+    t = a2 << 60;
+    lo += t;
+    hi += (lo < t) + (a2 >> 4);
+}

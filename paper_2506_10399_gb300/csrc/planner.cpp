@@ -323,4 +323,55 @@ void build(fg_plan &pl, const fg_ctx &ctx, const int32_t *row_ptr, const int32_t
     pl.out_level = level;
 }
 
+
+void build_inter(fg_plan &pl, const fg_ctx &ctx, const int32_t *nbr, const double *wts, int V,
+                 int n, const double *W, int F, int Fp, const int32_t *perm, const fg_plan_opts &o)
+{
+    const int M = ctx.slots;
+    FG_CHECK(V >= 1 && n >= 1 && F >= 1 && Fp >= 1, FG_EINVAL, "empty layer");
+    FG_CHECK(V <= M, FG_EINVAL, "V nodes do not fit the slots");
+    std::vector<char> seen(M, 0);
+    for (int v = 0; v < V; v++) {
+        FG_CHECK(perm[v] >= 0 && perm[v] < M && !seen[perm[v]], FG_EINVAL,
+                 "perm must be an injection of the nodes into [0, M)");
+        seen[perm[v]] = 1;
+        for (int k = 0; k < n; k++) {
+            const int u = nbr[(size_t)v * n + k];
+            FG_CHECK(u >= -1 && u < V && std::isfinite(wts[(size_t)v * n + k]), FG_EINVAL,
+                     "bad neighbour entry");
+        }
+    }
+    for (i64 e = 0; e < (i64)F * Fp; e++) FG_CHECK(std::isfinite(W[e]), FG_EINVAL, "W not finite");
+    FG_CHECK(o.in_level >= 0 && o.in_level < ctx.nq, FG_ELEVEL, "input level out of range");
+    pl.N = ctx.n;
+    pl.M = M;
+    pl.t = 1;
+    pl.B = M;
+    pl.V = V;
+    pl.F = F;
+    pl.Fp = Fp;
+    pl.in_level = o.in_level > 0 ? o.in_level : ctx.nq - 1;
+    pl.aoo = 1;
+    pl.perm.assign(perm, perm + V);
+    pl.n_copies = n;
+    pl.radix_bits = -n;   // marks an Inter-CA plan in the records
+    const int l0 = pl.in_level;
+    FG_CHECK(l0 - 2 >= o.min_out_level && l0 >= 2, FG_ELEVEL, "Inter-CA needs two levels");
+    const double ql = (double)ctx.primes[l0];
+    pl.comb_consts.resize((size_t)F * Fp);
+    for (i64 e = 0; e < (i64)F * Fp; e++) {
+        double c = std::round(W[e] * ql);
+        FG_CHECK(std::fabs(c) < 9.2e18, FG_EINVAL, "weight too large for the scale");
+        pl.comb_consts[e] = (i64)c;
+    }
+    for (int k = 0; k < n; k++) {
+        std::vector<std::pair<int, double>> vals;
+        for (int v = 0; v < V; v++)
+            if (nbr[(size_t)v * n + k] >= 0) vals.push_back({perm[v], wts[(size_t)v * n + k]});
+        push_mask(pl, l0 - 1, std::move(vals));
+    }
+    pl.out_level = l0 - 2;
+    pl.max_lanes = 1;
+}
+
 }  // namespace planner

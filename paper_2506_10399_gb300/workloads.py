@@ -66,6 +66,22 @@ def batch_queries(n=32, first_seed=0):
     return out
 
 
+def planner_graphs(seeds):
+    """Workloads for training and judging the learned planner, one per seed:
+    power-law graphs of V ~ U{1000..20000} nodes (mean degree 4) with
+    exponent ~ U[2.1, 3.0], TF-IDF-like features F ~ U{128..1024}, F' = 16,
+    Glorot weights (parameters: BATCH_PARAMS)."""
+    out = []
+    for s in seeds:
+        rng = np.random.default_rng(s)
+        V = int(rng.integers(1000, 20001))
+        gamma = float(rng.uniform(2.1, 3.0))
+        F = int(rng.integers(128, 1025))
+        out.append(make_workload(graph="chung_lu", V=V, deg=4.0, gamma=gamma, F=F, Fp=16,
+                                 x="tfidf", w="glorot", seed=s))
+    return out
+
+
 @dataclass
 class Workload:
     V: int
@@ -194,6 +210,45 @@ def two_layer_reference(w, W2):
     for v in range(w.V):
         s, e = w.row_ptr[v], w.row_ptr[v + 1]
         out[v] = w.val[s:e] @ XW[w.col[s:e]]
+    return out
+
+
+def sample_neighbors(w, n, seed):
+    """GraphSage-style neighbourhoods for Inter-CA: node v itself, then up to
+    n of its neighbours drawn without replacement; weights 1/(1 + drawn)
+    (the MEAN aggregator).  Returns nbr [V][n+1] (-1 = none) and wts."""
+    rng = np.random.default_rng(seed)
+    nbr = np.full((w.V, n + 1), -1, dtype=np.int32)
+    wts = np.zeros((w.V, n + 1))
+    for v in range(w.V):
+        nb = [int(u) for u in w.col[w.row_ptr[v]:w.row_ptr[v + 1]] if int(u) != v]
+        pick = list(rng.choice(nb, size=min(n, len(nb)), replace=False)) if nb else []
+        row = [v] + pick
+        nbr[v, :len(row)] = row
+        wts[v, :len(row)] = 1.0 / len(row)
+    return nbr, wts
+
+
+def full_neighbors(w):
+    """Every neighbourhood of A-hat as Inter-CA copies: nbr [V][max row
+    length] with the A-hat weights (the exact layer)."""
+    n = w.max_degree()
+    nbr = np.full((w.V, n), -1, dtype=np.int32)
+    wts = np.zeros((w.V, n))
+    for v in range(w.V):
+        s, e = w.row_ptr[v], w.row_ptr[v + 1]
+        nbr[v, :e - s] = w.col[s:e]
+        wts[v, :e - s] = w.val[s:e]
+    return nbr, wts
+
+
+def neighbor_reference(w, nbr, wts):
+    """FP64 sum_k wts[v][k] X[nbr[v][k]] W."""
+    XW = w.X @ w.W
+    out = np.zeros((w.V, w.W.shape[1]))
+    for k in range(nbr.shape[1]):
+        ok = nbr[:, k] >= 0
+        out[ok] += wts[ok, k][:, None] * XW[nbr[ok, k]]
     return out
 
 

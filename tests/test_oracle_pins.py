@@ -643,3 +643,62 @@ def test_planted_cmult_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(ckks, "secret_square", lambda params, s: np.asarray(s, np.int64))
     with pytest.raises(AssertionError):
         test_cmult_decodes_to_the_product()
+
+
+# ------------------------------------------------ learned planner's latency model
+def _mlp_case(seed=0, n=40, n_in=5, h=7):
+    from oracle import mlp
+    rng = np.random.default_rng(seed)
+    params = [rng.normal(0, 0.5, s) for s in mlp.sizes(n_in, h)]
+    X = rng.normal(0, 1, (n, n_in))
+    y = rng.normal(0, 1, n)
+    return mlp, params, X, y
+
+
+def test_mlp_gradient_matches_finite_differences():
+    mlp, params, X, y = _mlp_case()
+    loss, grads = mlp.loss_and_grads(params, X, y)
+    flat = mlp.pack(params)
+    g = mlp.pack(grads)
+    eps = 1e-6
+    for i in range(flat.size):
+        up, dn = flat.copy(), flat.copy()
+        up[i] += eps
+        dn[i] -= eps
+        lu, _ = mlp.loss_and_grads(mlp.unpack(up, 5, 7), X, y)
+        ld, _ = mlp.loss_and_grads(mlp.unpack(dn, 5, 7), X, y)
+        assert abs((lu - ld) / (2 * eps) - g[i]) < 1e-6 * max(1.0, abs(g[i]))
+
+
+def test_mlp_adam_fits_a_linear_target():
+    """With a linear target the network can fit exactly; full-batch Adam
+    drives the error far below the target's variance."""
+    from oracle import mlp
+    rng = np.random.default_rng(1)
+    X = rng.uniform(0, 1, (200, 4))
+    y = X @ np.array([1.0, -2.0, 0.5, 3.0]) + 0.25
+    params = [rng.normal(0, 0.3, s) for s in mlp.sizes(4, 16)]
+    _, losses = mlp.adam(params, X, y, 1500, 0.01)
+    assert losses[-1] < 1e-3 * np.var(y) and losses[-1] < losses[0]
+
+
+def test_planted_mlp_mistake_is_caught(monkeypatch):
+    """A transposed weight in the backward pass fails the finite-difference
+    pin."""
+    from oracle import mlp
+    orig = mlp.loss_and_grads
+
+    def transposed(params, X, y):
+        loss, g = orig(params, X, y)
+        W1, b1, W2, b2, W3, b3 = params
+        f, (z1, a1, z2, a2) = mlp.forward(params, X)
+        n = X.shape[0]
+        d3 = (2.0 / n) * (f - y)[:, None]
+        d2 = (d3 @ W3.T) * (z2 > 0)
+        d1 = (d2 @ W2) * (z1 > 0)          # W2 instead of W2^T
+        g[0] = X.T @ d1
+        g[1] = d1.sum(axis=0)
+        return loss, g
+    monkeypatch.setattr(mlp, "loss_and_grads", transposed)
+    with pytest.raises(AssertionError):
+        test_mlp_gradient_matches_finite_differences()
