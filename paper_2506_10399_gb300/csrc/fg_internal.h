@@ -130,6 +130,10 @@ struct fg_ctx {
     std::vector<cudaStream_t> pool;
     std::vector<cudaEvent_t> pool_events;
     cudaStream_t batch_stream = nullptr;   // the batch's own origin (capturable)
+    // host inputs: copied in chunks on their own stream, each chunk's part of
+    // the combination starting when the chunk has arrived
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> copy_events;
     struct BatchGraph {
         std::vector<const void *> args;   // plans, inputs, outputs
         int streams = 0;
@@ -235,7 +239,7 @@ void copy_limbs(fg_ctx *ctx, const u64 *src, int src_ls, u64 *dst, int dst_ls, i
 // combination: Z[j][p][i] = sum_f c[i][f][j] X[f][p][i], coefficient domain;
 // X: [F][2][level+1][N], consts: [level+1][F][Fp] Montgomery form, Z limb stride z_ls
 void comb_const_mac(fg_ctx *ctx, const u64 *X, int F, int Fp, int level, const u64 *consts,
-                    u64 *Z, int z_ls);
+                    u64 *Z, int z_ls, int fb = 0, int fe = -1, bool accumulate = false);
 // rescale by q_level, coefficient domain, npoly polys with limb strides
 void rescale_coef(fg_ctx *ctx, const u64 *in, int in_ls, u64 *out, int out_ls, int npoly,
                   int level);

@@ -727,8 +727,9 @@ __global__ void k_copy_limbs(const u64 *src, int src_ls, u64 *dst, int dst_ls, i
 constexpr int kCombJ = 8;
 constexpr int kCombChunk = 128;
 
+// Columns fb..fe-1 of X; with accumulate set, the result is added to Z.
 __global__ void __launch_bounds__(256)
-k_comb(const u64 *__restrict__ X, int F, int Fp, int j0, int level,
+k_comb(const u64 *__restrict__ X, int F, int fb, int fe, int accumulate, int Fp, int j0, int level,
        const u64 *__restrict__ consts, u64 *Z, int z_ls, const PrimeC *__restrict__ primes,
        int N)
 {
@@ -741,8 +742,8 @@ k_comb(const u64 *__restrict__ X, int F, int Fp, int j0, int level,
     u64 a0[kCombJ], a1[kCombJ], a2[kCombJ];   // split: A0, A1, A2; else lo, hi, unused
 #pragma unroll
     for (int j = 0; j < kCombJ; j++) a0[j] = a1[j] = a2[j] = 0;
-    for (int f0 = 0; f0 < F; f0 += kCombChunk) {
-        const int fc = min(kCombChunk, F - f0);
+    for (int f0 = fb; f0 < fe; f0 += kCombChunk) {
+        const int fc = min(kCombChunk, fe - f0);
         __syncthreads();
         for (int idx = threadIdx.x; idx < kCombChunk * kCombJ; idx += blockDim.x) {
             int ff = idx / kCombJ, jj = idx % kCombJ;
@@ -771,9 +772,11 @@ k_comb(const u64 *__restrict__ X, int F, int Fp, int j0, int level,
     if (x < N) {
 #pragma unroll
         for (int j = 0; j < kCombJ; j++)
-            if (j0 + j < Fp)
-                Z[(((size_t)(j0 + j) * 2 + p) * z_ls + i) * N + x] =
-                    split ? fold_split(a0[j], a1[j], a2[j], P) : redc(a1[j], a0[j], P);
+            if (j0 + j < Fp) {
+                u64 *z = Z + (((size_t)(j0 + j) * 2 + p) * z_ls + i) * N + x;
+                const u64 r = split ? fold_split(a0[j], a1[j], a2[j], P) : redc(a1[j], a0[j], P);
+                *z = accumulate ? add_mod(*z, r, P.q) : r;
+            }
     }
 }
 
@@ -1517,16 +1520,18 @@ void copy_limbs(fg_ctx *ctx, const u64 *src, int src_ls, u64 *dst, int dst_ls, i
 }
 
 void comb_const_mac(fg_ctx *ctx, const u64 *X, int F, int Fp, int level, const u64 *consts, u64 *Z,
-                    int z_ls)
+                    int z_ls, int fb, int fe, bool accumulate)
 {
     // split partial sums stay below 2^64 for up to 2^16 terms
     FG_CHECK(F < (1 << 16), FG_EINVAL, "combination over more than 2^16 input columns");
+    if (fe < 0) fe = F;
+    FG_CHECK(0 <= fb && fb < fe && fe <= F, FG_EINVAL, "combination column range");
     for (int j0 = 0; j0 < Fp; j0 += kCombJ) {
         const int jn = std::min(kCombJ, Fp - j0);
-        KTimer kt(ctx, "comb", ((double)F + jn) * 2 * (level + 1) * ctx->n * 8);
+        KTimer kt(ctx, "comb", ((double)(fe - fb) + jn * (accumulate ? 2 : 1)) * 2 * (level + 1) * ctx->n * 8);
         dim3 g((ctx->n + 255) / 256, level + 1, 2);
-        k_comb<<<g, 256, 0, ctx->stream>>>(X, F, Fp, j0, level, consts, Z, z_ls, ctx->d_primes,
-                                           ctx->n);
+        k_comb<<<g, 256, 0, ctx->stream>>>(X, F, fb, fe, accumulate ? 1 : 0, Fp, j0, level, consts, Z,
+                                           z_ls, ctx->d_primes, ctx->n);
         check_launch("comb");
     }
 }

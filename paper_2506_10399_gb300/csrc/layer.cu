@@ -411,9 +411,33 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
 
         const size_t in_w = (size_t)nb * 2 * nl0 * N;
         const u64 *X = in_cts;
+        // host inputs of a t = 1 layer: copied in chunks of columns on a side
+        // stream, the combination of each chunk starting when it has arrived
+        const bool chunked = !is_dev(in_cts) && t == 1 && !pl->n_copies;
+        const int kChunk = 64, n_chunks = (F + kChunk - 1) / kChunk;
         if (!is_dev(in_cts)) {
             u64 *d = (u64 *)ctx->buf("layer_in", in_w * 8);
-            CUDA_TRY(cudaMemcpyAsync(d, in_cts, in_w * 8, cudaMemcpyHostToDevice, ctx->stream));
+            if (chunked) {
+                if (!ctx->copy_stream)
+                    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+                while ((int)ctx->copy_events.size() < n_chunks + 1) {
+                    cudaEvent_t e;
+                    CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                    ctx->copy_events.push_back(e);
+                }
+                // the buffer is free once the work queued before this layer is done
+                CUDA_TRY(cudaEventRecord(ctx->copy_events[n_chunks], ctx->stream));
+                CUDA_TRY(cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_events[n_chunks], 0));
+                const size_t ct_w = (size_t)2 * nl0 * N;
+                for (int c = 0; c < n_chunks; c++) {
+                    const int fb = c * kChunk, fn = std::min(kChunk, F - fb);
+                    CUDA_TRY(cudaMemcpyAsync(d + fb * ct_w, in_cts + fb * ct_w, fn * ct_w * 8,
+                                             cudaMemcpyHostToDevice, ctx->copy_stream));
+                    CUDA_TRY(cudaEventRecord(ctx->copy_events[c], ctx->copy_stream));
+                }
+            } else {
+                CUDA_TRY(cudaMemcpyAsync(d, in_cts, in_w * 8, cudaMemcpyHostToDevice, ctx->stream));
+            }
             X = d;
         }
         const int l1 = l0 - 1, LS = l1 + 1;           // lanes keep a fixed limb stride
@@ -461,7 +485,15 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
         const std::vector<int> pid_l1 = iota(LS);
         if (t == 1) {
             u64 *Zc = (u64 *)ctx->buf("comb_z", (size_t)Fp * 2 * nl0 * N * 8);
-            kern::comb_const_mac(ctx, X, F, Fp, l0, pl->d_comb, Zc, nl0);
+            if (chunked) {
+                for (int c = 0; c < n_chunks; c++) {
+                    CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->copy_events[c], 0));
+                    kern::comb_const_mac(ctx, X, F, Fp, l0, pl->d_comb, Zc, nl0, c * kChunk,
+                                         std::min(F, (c + 1) * kChunk), c > 0);
+                }
+            } else {
+                kern::comb_const_mac(ctx, X, F, Fp, l0, pl->d_comb, Zc, nl0);
+            }
             kern::rescale_coef(ctx, Zc, nl0, bufA[0], LS, Fp * 2, l0);
             kern::LimbSet z{bufA[0], LS, LS, Fp * 2, pid_l1};
             kern::ntt_fwd(ctx, z, z);

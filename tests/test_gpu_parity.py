@@ -306,3 +306,24 @@ def test_layer_argument_errors(fg):
     with pytest.raises(fg.FicgcnError) as e:
         fg.gcn_layer_axw(ctx, keys, plan, np.ascontiguousarray(cts[:2]))
     assert e.value.code == -1
+
+
+def test_layer_host_inputs_arrive_in_chunks(fg):
+    """Host inputs of a t = 1 layer are copied in chunks of 64 columns, each
+    chunk's combination starting when it arrives: the result equals the
+    layer on the same inputs already in device memory."""
+    import torch
+    ctx, P = setup(fg, "multi")
+    w = wl.make_workload(graph="er", V=50, deg=3.0, F=150, Fp=3, seed=21)
+    perm = wl.random_order(w.V, P.slots, 21)
+    plan = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=1, radix_bits=2)
+    sk, evk = fg.keygen(ctx, 21, plan.rotation_amounts())
+    keys = fg.load_evk(ctx, evk)
+    cts = fg.pack_features(ctx, sk, 21, w.X, perm, 1)
+    host_out, lvl, scale = fg.gcn_layer_axw(ctx, keys, plan, cts)
+    dev = torch.from_numpy(cts.view(np.int64)).cuda()
+    dev_out, _, _ = fg.gcn_layer_axw(ctx, keys, plan, dev)
+    np.testing.assert_array_equal(host_out, dev_out.cpu().numpy().view(np.uint64))
+    ref = w.reference_output()
+    d = fg.decrypt_decode(ctx, sk, np.ascontiguousarray(host_out[0]), lvl, scale)
+    assert np.max(np.abs(d[perm] - ref[:, 0])) < 2 ** -20
