@@ -157,7 +157,8 @@ static ConvTab make_conv(const fg_ctx &c, const std::vector<int> &in_p, const st
             u64 hp = 1;   // (B / b_k) mod p
             for (int j = 0; j < T.n_in; j++)
                 if (j != k) hp = hm::mulmod(hp, c.primes[in_p[j]] % p, p);
-            T.hmod[k][t] = hm::to_mont(hp, p);
+            const u64 hm_ = hm::to_mont(hp, p);
+            T.hmod[k][t] = (hm_ & 0x3FFFFFFFull) | ((hm_ >> 30) << 32);   // 30-bit halves
         }
     }
     for (int t = 0; t < T.n_out; t++) {

@@ -79,7 +79,7 @@ struct ConvTab {
     int in_p[8], in_l[8];     // prime index and limb position of each input
     int out_p[72], out_l[72]; // prime index and limb position of each output
     u64 hinv[8], hinv_s[8];   // (B/b_k)^-1 mod b_k and its Shoup companion
-    u64 hmod[8][72];          // (B/b_k) mod out prime, Montgomery form
+    u64 hmod[8][72];          // (B/b_k) mod out prime, Montgomery form, 30-bit halves (lo | hi << 32)
 };
 
 struct fg_ctx {

@@ -833,14 +833,19 @@ __global__ void k_rescale_finish(u64 *ct, int ls, const u64 *rr, int level,
 // two words below 2^61 accumulate below p * 2^64, so one Montgomery
 // reduction gives the exact residue.
 // ------------------------------------------------------------------------
-// NMAX bounds T.n_in at compile time, so that y stays in registers.
+// NMAX bounds T.n_in at compile time, so that y stays in registers.  y and
+// the table hold 30-bit halves: at most 8 products per partial sum, and the
+// total below 8 2^60 p keeps its high word below p for the Montgomery step.
 template <int NMAX>
 __device__ __forceinline__ u64 conv_point(const ConvTab &T, const u64 *y, int t, const PrimeC &P)
 {
-    u64 hi = 0, lo = 0;
+    static_assert(NMAX <= 8, "at most 8 inputs per conversion");
+    u64 a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
     for (int k = 0; k < NMAX; k++)
-        if (k < T.n_in) mac128(hi, lo, y[k], T.hmod[k][t]);
+        if (k < T.n_in) mac_split(a0, a1, a2, y[k], T.hmod[k][t]);
+    u64 hi = 0, lo = 0;
+    fold30(hi, lo, a0, a1, a2);
     return redc(hi, lo, P);
 }
 
@@ -852,7 +857,7 @@ __device__ __forceinline__ void conv_inputs(const ConvTab &T, const u64 *src, si
     for (int k = 0; k < NMAX; k++)
         if (k < T.n_in) {
             const u64 v = src[(size_t)T.in_l[k] * limb_stride];
-            y[k] = shoup_mul(v, T.hinv[k], T.hinv_s[k], primes[T.in_p[k]].q);
+            y[k] = split30(shoup_mul(v, T.hinv[k], T.hinv_s[k], primes[T.in_p[k]].q));
         }
 }
 
@@ -946,27 +951,57 @@ k_ks_ip(const KsSet ks, int KL, const u64 *__restrict__ lane, int ls,
     const int sx = auto_src(x, ks.g[rot], log_n);
     const bool swap = sx & 1;
     const int own = i <= level ? i / alpha : -1;
+    // Sums of BETA products of words below 2^60: with 30-bit halves (keys
+    // split once per thread, each gathered digit word once for its two
+    // products) the three 64-bit partial sums hold up to 8 products per
+    // term; more digits take the 128-bit sums.  The total, below
+    // BETA 2^60 q, keeps its high word below q for the Montgomery step.
+    constexpr bool SPLIT = BETA <= 8;
     ulonglong2 kb[BETA], ka[BETA];
 #pragma unroll
     for (int d = 0; d < BETA; d++) {
         kb[d] = *reinterpret_cast<const ulonglong2 *>(key + (((size_t)d * 2 + 0) * KL + pi) * N + x);
         ka[d] = *reinterpret_cast<const ulonglong2 *>(key + (((size_t)d * 2 + 1) * KL + pi) * N + x);
-    }
-#pragma unroll 2
-    for (int f = 0; f < ncol; f++) {
-        u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0, h2 = 0, l2 = 0, h3 = 0, l3 = 0;
-#pragma unroll
-        for (int d = 0; d < BETA; d++) {
-            const u64 *limb = d == own ? lane + (((size_t)f * 2 + 1) * ls + i) * N
-                                       : digits + (((size_t)f * BETA + d) * E + i) * N;
-            const ulonglong2 v = gather_pair(limb, sx, swap);
-            mac128(h0, l0, v.x, kb[d].x);
-            mac128(h1, l1, v.y, kb[d].y);
-            mac128(h2, l2, v.x, ka[d].x);
-            mac128(h3, l3, v.y, ka[d].y);
+        if (SPLIT) {
+            kb[d] = make_ulonglong2(split30(kb[d].x), split30(kb[d].y));
+            ka[d] = make_ulonglong2(split30(ka[d].x), split30(ka[d].y));
         }
-        ulonglong2 r0 = make_ulonglong2(redc(h0, l0, P), redc(h1, l1, P));
-        const ulonglong2 r1 = make_ulonglong2(redc(h2, l2, P), redc(h3, l3, P));
+    }
+    for (int f = 0; f < ncol; f++) {
+        ulonglong2 r0, r1;
+        if (SPLIT) {
+            u64 a[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+            for (int d = 0; d < BETA; d++) {
+                const u64 *limb = d == own ? lane + (((size_t)f * 2 + 1) * ls + i) * N
+                                           : digits + (((size_t)f * BETA + d) * E + i) * N;
+                ulonglong2 v = gather_pair(limb, sx, swap);
+                v = make_ulonglong2(split30(v.x), split30(v.y));
+                mac_split(a[0], a[1], a[2], v.x, kb[d].x);
+                mac_split(a[3], a[4], a[5], v.y, kb[d].y);
+                mac_split(a[6], a[7], a[8], v.x, ka[d].x);
+                mac_split(a[9], a[10], a[11], v.y, ka[d].y);
+            }
+            u64 h[4] = {0, 0, 0, 0}, l[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int c = 0; c < 4; c++) fold30(h[c], l[c], a[3 * c], a[3 * c + 1], a[3 * c + 2]);
+            r0 = make_ulonglong2(redc(h[0], l[0], P), redc(h[1], l[1], P));
+            r1 = make_ulonglong2(redc(h[2], l[2], P), redc(h[3], l[3], P));
+        } else {
+            u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0, h2 = 0, l2 = 0, h3 = 0, l3 = 0;
+#pragma unroll
+            for (int d = 0; d < BETA; d++) {
+                const u64 *limb = d == own ? lane + (((size_t)f * 2 + 1) * ls + i) * N
+                                           : digits + (((size_t)f * BETA + d) * E + i) * N;
+                const ulonglong2 v = gather_pair(limb, sx, swap);
+                mac128(h0, l0, v.x, kb[d].x);
+                mac128(h1, l1, v.y, kb[d].y);
+                mac128(h2, l2, v.x, ka[d].x);
+                mac128(h3, l3, v.y, ka[d].y);
+            }
+            r0 = make_ulonglong2(redc(h0, l0, P), redc(h1, l1, P));
+            r1 = make_ulonglong2(redc(h2, l2, P), redc(h3, l3, P));
+        }
         if (pmodq && i <= level) {
             const ulonglong2 c0 = gather_pair(lane + (((size_t)f * 2) * ls + i) * N, sx, swap);
             const u64 pw = pmodq[2 * i], pws = pmodq[2 * i + 1];
