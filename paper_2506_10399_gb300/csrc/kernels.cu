@@ -81,10 +81,11 @@ __device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, const ulonglong2 w, u64 
 // for four stages, so each pass makes two shared-memory round trips
 // (N = 256 x 256; pass A on columns, pass B on rows).  For primes below
 // 2^47 the butterflies skip every conditional reduction and use the
-// three-product quotient (shoup_lazy3, products in [0, 3q)): forward values
-// grow by at most 3q per stage (< 49q after 16 stages); inverse values are
-// below 3 2^(k-1) q after k stages (< 2^64 for q < 2^47); one reduction at
-// the end restores [0, q).  Larger primes keep Harvey's bounds (< 4q, < 2q).
+// three-product quotient without carries (shoup_lazy4, products in
+// [0, 4q)): forward values grow by at most 4q per stage (< 65q after 16
+// stages); inverse values are below 2^(k+1) q after k stages (< 2^64 for
+// q < 2^47); one reduction at the end restores [0, q).  Larger primes keep
+// Harvey's bounds (< 4q, < 2q).
 // ------------------------------------------------------------------------
 template <bool LAZY>
 __device__ __forceinline__ void ct16(u64 (&v)[16], const ulonglong2 (&w)[15], u64 q, u64 q2)
@@ -98,8 +99,8 @@ __device__ __forceinline__ void ct16(u64 (&v)[16], const ulonglong2 (&w)[15], u6
                 const ulonglong2 tw = w[(1 << st) - 1 + (m >> (4 - st))];
                 u64 X = v[m], Y = v[m + h];
                 if (LAZY) {
-                    const u64 T = shoup_lazy3(Y, tw.x, tw.y, q);
-                    v[m + h] = X - T + 3 * q;
+                    const u64 T = shoup_lazy4(Y, tw.x, tw.y, q);
+                    v[m + h] = X - T + 4 * q;
                     v[m] = X + T;
                 } else {
                     X = X >= q2 ? X - q2 : X;
@@ -127,7 +128,7 @@ __device__ __forceinline__ void gs16(u64 (&v)[16], const ulonglong2 (&w)[15], u6
                 const u64 U = v[m], V = v[m + h];
                 const u64 S = U + V;
                 v[m] = LAZY ? S : (S >= q2 ? S - q2 : S);
-                v[m + h] = LAZY ? shoup_lazy3(U - V + qb, tw.x, tw.y, q)
+                v[m + h] = LAZY ? shoup_lazy4(U - V + qb, tw.x, tw.y, q)
                                 : shoup_lazy(U - V + qb, tw.x, tw.y, q);
             }
         }

@@ -115,24 +115,6 @@ __device__ __forceinline__ u64 fold_split(u64 a0, u64 a1, u64 a2, const PrimeC &
 }
 
 
-// Shoup product with a cheaper quotient: y * w mod q in [0, 3q) for any
-// y < 2^64 (q < 2^62).  The quotient floor(y w' / 2^64) is computed from the
-// three 32 x 32-bit partial products that reach the high word, leaving out
-// y_lo w'_lo: with s = lo(y_lo w'_hi) + y_hi w'_lo,
-//   y w' = y_lo w'_lo + lo(s) 2^32 + (hi(s) + hi(y_lo w'_hi) + y_hi w'_hi) 2^64,
-// and the first two terms sum to less than 2^65, so the estimate is the true
-// quotient or one less; Shoup's own estimate is within one of floor(y w / q).
-__device__ __forceinline__ u64 shoup_lazy3(u64 y, u64 w, u64 ws, u64 q)
-{
-    const u32 y0 = (u32)y, y1 = (u32)(y >> 32);
-    const u32 s0 = (u32)ws, s1 = (u32)(ws >> 32);
-    u64 t, s, h;
-    asm("mul.wide.u32 %0, %1, %2;" : "=l"(t) : "r"(y0), "r"(s1));
-    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(s) : "r"(y1), "r"(s0), "l"(t & 0xFFFFFFFFull));
-    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(h) : "r"(y1), "r"(s1), "l"(t >> 32));
-    h += s >> 32;
-    return y * w - h * q;
-}
 
 // Factors below 2^60 split into 30-bit halves, v0 | v1 << 32 (v = v0 + v1
 // 2^30): the same three partial sums, each product below 2^60, so they hold
@@ -151,4 +133,19 @@ __device__ __forceinline__ void fold30(u64 &hi, u64 &lo, u64 a0, u64 a1, u64 a2)
     t = a2 << 60;
     lo += t;
     hi += (lo < t) + (a2 >> 4);
+}
+
+// Shoup product with a three-product quotient that skips the carries of the
+// low partial products: h = y_hi w'_hi + hi(y_lo w'_hi) + hi(y_hi w'_lo)
+// leaves out y_lo w'_lo and the low halves of the cross products, three
+// terms below 2^64 each, so h is floor(y w' / 2^64) or up to two less and
+// y w - h q lies in [0, 4q) for any y < 2^64 (q < 2^61).
+__device__ __forceinline__ u64 shoup_lazy4(u64 y, u64 w, u64 ws, u64 q)
+{
+    const u32 y0 = (u32)y, y1 = (u32)(y >> 32);
+    const u32 s0 = (u32)ws, s1 = (u32)(ws >> 32);
+    const u64 c = (u64)__umulhi(y0, s1) + __umulhi(y1, s0);
+    u64 h;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(h) : "r"(y1), "r"(s1), "l"(c));
+    return y * w - h * q;
 }
