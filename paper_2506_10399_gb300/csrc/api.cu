@@ -444,6 +444,28 @@ int fg_ctx_create(const fg_params *prm, void *cuda_stream, fg_ctx **out)
         CUDA_TRY(cudaMemcpy(ctx->d_inv, inv.data(), sizeof(ulonglong2) * KL * N, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(ctx->d_ninv, ninv.data(), 16 * KL, cudaMemcpyHostToDevice));
         ctx->table_bytes = sizeof(PrimeC) * KL + 2 * sizeof(ulonglong2) * KL * N + 16 * KL;
+        if (ctx->log_n == 16) {
+            // row-stage twiddles for the radix-16 row pass: entry (row r,
+            // stage st, group g, column j) = table[2^(12+st) + (r << (4+st)) + (j << st) + g]
+            const size_t per = (size_t)256 * 15 * 16;
+            std::vector<ulonglong2> fr(KL * per), ir(KL * per);
+            for (int k = 0; k < KL; k++)
+                for (int r = 0; r < 256; r++)
+                    for (int st = 0; st < 4; st++)
+                        for (int g = 0; g < (1 << st); g++)
+                            for (int j = 0; j < 16; j++) {
+                                const size_t src = (size_t)k * N + (1u << (12 + st)) + ((size_t)r << (4 + st)) +
+                                                   ((size_t)j << st) + g;
+                                const size_t dst = (size_t)k * per + ((size_t)r * 15 + (1 << st) - 1 + g) * 16 + j;
+                                fr[dst] = fwd[src];
+                                ir[dst] = inv[src];
+                            }
+            CUDA_TRY(cudaMalloc(&ctx->d_fwd_rows, sizeof(ulonglong2) * KL * per));
+            CUDA_TRY(cudaMalloc(&ctx->d_inv_rows, sizeof(ulonglong2) * KL * per));
+            CUDA_TRY(cudaMemcpy(ctx->d_fwd_rows, fr.data(), sizeof(ulonglong2) * KL * per, cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(ctx->d_inv_rows, ir.data(), sizeof(ulonglong2) * KL * per, cudaMemcpyHostToDevice));
+            ctx->table_bytes += 2 * sizeof(ulonglong2) * KL * per;
+        }
         // P mod q_i (Shoup) and the identity prime-index list
         std::vector<u64> pm(2 * ctx->nq);
         for (int i = 0; i < ctx->nq; i++) {
@@ -487,6 +509,8 @@ int fg_ctx_destroy(fg_ctx *ctx)
     cudaFree(ctx->d_primes);
     cudaFree(ctx->d_fwd);
     cudaFree(ctx->d_inv);
+    cudaFree(ctx->d_fwd_rows);
+    cudaFree(ctx->d_inv_rows);
     cudaFree(ctx->d_ninv);
     for (auto &kv : ctx->conv_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->rescale_tabs) cudaFree(kv.second);

@@ -96,6 +96,11 @@ struct fg_ctx {
     PrimeC *d_primes = nullptr;       // [nq+np]
     void *d_fwd = nullptr;            // ulonglong2 [nq+np][N] (psi^brv(i), Shoup)
     void *d_inv = nullptr;            // ulonglong2 [nq+np][N]
+    // N = 2^16: the twiddles of the row stages 12..15 (forward) and of the
+    // inverse's first four row stages, laid out [row][stage group][column]
+    // so that the 16 threads of a row read 16 consecutive entries
+    void *d_fwd_rows = nullptr;       // ulonglong2 [nq+np][256][15][16]
+    void *d_inv_rows = nullptr;
     u64 *d_ninv = nullptr;            // [nq+np][2] N^-1 and Shoup
     u64 *d_pmodq = nullptr;           // [nq][2] P mod q_i and Shoup
     std::vector<u64> h_qneg, h_r2, h_ones;

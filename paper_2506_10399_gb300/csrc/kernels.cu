@@ -186,8 +186,8 @@ ntt16_fwd_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 
 }
 
 template <bool LAZY>
-__device__ __forceinline__ void fwd_b16_body(u64 *d, const ulonglong2 *twp, int row0, const PrimeC &P,
-                                             u64 *sm)
+__device__ __forceinline__ void fwd_b16_body(u64 *d, const ulonglong2 *twp, const ulonglong2 *rows,
+                                             int row0, const PrimeC &P, u64 *sm)
 {
     const int t = threadIdx.x, j = t & 15, r = t >> 4;
     constexpr int S1 = 8;
@@ -209,11 +209,9 @@ __device__ __forceinline__ void fwd_b16_body(u64 *d, const ulonglong2 *twp, int 
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < 16; m++) v[m] = srow[pad16(16 * j + m)];
+    // row stages 12..15 from the row-blocked table (consecutive per row)
 #pragma unroll
-    for (int st = 0; st < 4; st++)
-#pragma unroll
-        for (int g = 0; g < (1 << st); g++)
-            w[(1 << st) - 1 + g] = twp[(1 << (S1 + 4 + st)) + (grow << (4 + st)) + (j << st) + g];
+    for (int k = 0; k < 15; k++) w[k] = rows[((size_t)grow * 15 + k) * 16 + j];
     ct16<LAZY>(v, w, q, q2);
     ulonglong2 *o = reinterpret_cast<ulonglong2 *>(drow + 16 * j);
 #pragma unroll
@@ -223,7 +221,8 @@ __device__ __forceinline__ void fwd_b16_body(u64 *d, const ulonglong2 *twp, int 
 }
 
 __global__ void __launch_bounds__(256, 3)
-ntt16_fwd_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ tw)
+ntt16_fwd_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ tw,
+            const ulonglong2 *__restrict__ tw_rows)
 {
     const int limb = blockIdx.y;
     const int col = limb % bt.per_row, row = limb / bt.per_row;
@@ -234,13 +233,14 @@ ntt16_fwd_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 
     const ulonglong2 *twp = tw + (size_t)pi * 65536;
     const int row0 = blockIdx.x * 16;
     u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * 65536 + (size_t)row0 * 256;
-    if (P.q < (1ull << 47)) fwd_b16_body<true>(d, twp, row0, P, sm);
-    else fwd_b16_body<false>(d, twp, row0, P, sm);
+    const ulonglong2 *rows = tw_rows + (size_t)pi * 256 * 15 * 16;
+    if (P.q < (1ull << 47)) fwd_b16_body<true>(d, twp, rows, row0, P, sm);
+    else fwd_b16_body<false>(d, twp, rows, row0, P, sm);
 }
 
 template <bool LAZY>
-__device__ __forceinline__ void inv_b16_body(const u64 *s, u64 *d, const ulonglong2 *twp, int row0,
-                                             u64 q, u64 *sm)
+__device__ __forceinline__ void inv_b16_body(const u64 *s, u64 *d, const ulonglong2 *twp,
+                                             const ulonglong2 *rows, int row0, u64 q, u64 *sm)
 {
     const int t = threadIdx.x, j = t & 15, r = t >> 4;
     constexpr int S1 = 8;
@@ -256,10 +256,7 @@ __device__ __forceinline__ void inv_b16_body(const u64 *s, u64 *d, const ulonglo
         v[m + 1] = a.y;
     }
 #pragma unroll
-    for (int st = 0; st < 4; st++)
-#pragma unroll
-        for (int g = 0; g < (1 << st); g++)
-            w[(1 << st) - 1 + g] = twp[(1 << (S1 + 4 + st)) + (grow << (4 + st)) + (j << st) + g];
+    for (int k = 0; k < 15; k++) w[k] = rows[((size_t)grow * 15 + k) * 16 + j];
     gs16<LAZY>(v, w, q, q2, 0);
     u64 *srow = sm + r * kR16Row;
 #pragma unroll
@@ -278,7 +275,8 @@ __device__ __forceinline__ void inv_b16_body(const u64 *s, u64 *d, const ulonglo
 }
 
 __global__ void __launch_bounds__(256, 3)
-ntt16_inv_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ itw)
+ntt16_inv_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ itw,
+            const ulonglong2 *__restrict__ itw_rows)
 {
     const int limb = blockIdx.y;
     const int col = limb % bt.per_row, row = limb / bt.per_row;
@@ -290,8 +288,9 @@ ntt16_inv_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 
     const int row0 = blockIdx.x * 16;
     const u64 *s = bt.src + ((size_t)row * bt.src_stride + col) * 65536 + (size_t)row0 * 256;
     u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * 65536 + (size_t)row0 * 256;
-    if (q < (1ull << 47)) inv_b16_body<true>(s, d, twp, row0, q, sm);
-    else inv_b16_body<false>(s, d, twp, row0, q, sm);
+    const ulonglong2 *rows = itw_rows + (size_t)pi * 256 * 15 * 16;
+    if (q < (1ull << 47)) inv_b16_body<true>(s, d, twp, rows, row0, q, sm);
+    else inv_b16_body<false>(s, d, twp, rows, row0, q, sm);
 }
 
 template <bool LAZY>
@@ -1410,9 +1409,11 @@ static void ntt16_launch(fg_ctx *ctx, const Batch &bt, int count, bool inverse)
     b2.src_stride = b2.dst_stride;
     if (!inverse) {
         ntt16_fwd_a<<<gA, 256, 0, ctx->stream>>>(bt, ctx->d_primes, fwd);
-        ntt16_fwd_b<<<gB, 256, 0, ctx->stream>>>(b2, ctx->d_primes, fwd);
+        ntt16_fwd_b<<<gB, 256, 0, ctx->stream>>>(b2, ctx->d_primes, fwd,
+                                                 (const ulonglong2 *)ctx->d_fwd_rows);
     } else {
-        ntt16_inv_b<<<gB, 256, 0, ctx->stream>>>(bt, ctx->d_primes, inv);
+        ntt16_inv_b<<<gB, 256, 0, ctx->stream>>>(bt, ctx->d_primes, inv,
+                                                 (const ulonglong2 *)ctx->d_inv_rows);
         ntt16_inv_a<<<gA, 256, 0, ctx->stream>>>(b2, ctx->d_primes, inv, ctx->d_ninv);
     }
 }
