@@ -268,7 +268,10 @@ struct GroupSource {
     uint32_t galois;
     int t0, t1;        // its terms (indices into the term list)
 };
-// one SpIntra-CA group's outputs in the extended basis (see k_group_mac)
+// one SpIntra-CA group's outputs in the extended basis (see k_group_mac);
+// a launch takes at most kGmacSrc sources and kGmacTerms terms
+constexpr int kGmacSrc = 36;
+constexpr int kGmacTerms = 300;
 void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vector<Dest> &terms,
                const std::vector<int> &term_dest, const std::vector<u64 *> &outs, bool accumulate,
                int ncol, int level, int ls);

@@ -1115,9 +1115,7 @@ k_stay_mac(const u64 *__restrict__ lane, int ls, int ncol, int level, const Dest
 // P phi_r(c0)) + sum over its kept sources of mask (x) P lane, in the
 // extended basis q_0..q_l, p_0..p_{K-1} (the P terms vanish mod p_k).
 // ModDown(ext_d) is then exactly the sum of mask (x) Rot and mask (x) lane,
-// since ModDown(A + P B) = ModDown(A) + B.  Thread = one polynomial (column
-// and part) at one slot pair; the CTA's threads of one slot pair read the
-// same mask words; partial sums stay in shared memory until the end.
+// since ModDown(A + P B) = ModDown(A) + B.
 // ------------------------------------------------------------------------
 
 // Partial sums are products v * m~ (m~ = mask R mod q, its Montgomery form)
@@ -1136,27 +1134,34 @@ k_stay_mac(const u64 *__restrict__ lane, int ls, int ncol, int level, const Dest
 // Other primes (q_0 and the special primes, up to 60 bits) are split into
 // 30-bit halves and folded into a 128-bit sum every 8 terms.
 //
-// Thread = one polynomial (column, part) at one slot pair; a CTA covers the
-// npoly polynomials of 128 / npoly slot pairs of one limb, neighbouring
-// threads on neighbouring pairs of one polynomial.  Phase 1 copies every
-// source value of the thread (the key-switch output, which already holds
-// u + P phi(c0), or the kept lane) and the CTA's mask words into shared
-// memory with asynchronous copies, all in flight at once; phase 2 turns
-// kept lanes into P lane and splits words in place; phase 3 walks the
+// Tiling.  A tile is PPC polynomials (column, part) times PPN neighbouring
+// slot pairs of one limb, thread = one polynomial at one slot pair (PPC =
+// min(npoly, 16), PPN = min(128 / PPC, 16): for 32 polynomials two tiles of
+// 16 x 8, 128-byte runs per polynomial).  A CTA holds one tile and
+// kGmacGroups thread groups that share its staged words: every group copies
+// and splits a share of the sources and masks, then computes its own
+// contiguous slice of the outputs (balanced by term count on the host), so
+// the CTA has three times the warps for the same shared memory.  Phase 1
+// copies the sources (the key-switch output, which already holds u +
+// P phi(c0), or the kept lane) and the tile's mask words into shared memory
+// with asynchronous copies, all in flight at once; phase 2 turns kept lanes
+// into P lane and splits words in place; phase 3 walks the group's
 // outputs, each a register sum over its terms.
-constexpr int kGmacThreads = 128;
-constexpr int kGmacSrc = 24;      // sources per launch
-constexpr int kGmacTerms = 192;   // terms per launch
+constexpr int kGmacTile = 128;    // threads per group: PPC x PPN (idle ones when npoly < 8)
+constexpr int kGmacGroups = 3;    // output groups per CTA
+constexpr int kGmacThreads = kGmacTile * kGmacGroups;
 constexpr int kGmacOut = 64;      // outputs per launch
 
 // the launch's program, passed by value (kernel parameters sit in the
 // constant bank: uniform reads need no global loads)
 struct GProg {
     int nsrc, nterm, X, accumulate;
-    const u64 *su[kGmacSrc];      // rotation: key-switch output; kept lane: nullptr
-    const u64 *slane[kGmacSrc];   // kept lane
-    u32 tvoff[kGmacTerms];        // terms sorted by output: byte offset of the source's row in vsm
-    const u64 *tmask[kGmacTerms];
+    int ppc, ppn;                       // tile: polynomials x slot pairs
+    int gfirst[kGmacGroups + 1];        // first output of each thread group
+    const u64 *su[kern::kGmacSrc];      // rotation: key-switch output; kept lane: nullptr
+    const u64 *slane[kern::kGmacSrc];   // kept lane
+    u32 tvoff[kern::kGmacTerms];        // terms sorted by output: byte offset of the source's row in vsm
+    const u64 *tmask[kern::kGmacTerms];
     int dfirst[kGmacOut + 1];
     u64 *outs[kGmacOut];
 };
@@ -1181,37 +1186,39 @@ __device__ __forceinline__ ulonglong2 lds128(u32 addr)
     return v;
 }
 
-__global__ void __launch_bounds__(kGmacThreads)
+__global__ void __launch_bounds__(kGmacThreads, 2)
 k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
             const u64 *__restrict__ pmodq, const PrimeC *__restrict__ primes, int nq)
 {
     extern __shared__ __align__(16) unsigned char gsm[];
-    const int npoly = 2 * ncol;
-    const int pp_n = kGmacThreads / npoly;          // slot pairs per CTA
+    const int npoly = 2 * ncol, PPC = pg.ppc, PPN = pg.ppn;
+    const int npg = (npoly + PPC - 1) / PPC;
     const int nsrc = pg.nsrc, nterm = pg.nterm;
-    ulonglong2 *vsm = reinterpret_cast<ulonglong2 *>(gsm);                  // [nsrc][threads]
-    ulonglong2 *msm = vsm + (size_t)nsrc * kGmacThreads;                    // [nterm][pp_n]
+    ulonglong2 *vsm = reinterpret_cast<ulonglong2 *>(gsm);                  // [nsrc][kGmacTile]
+    ulonglong2 *msm = vsm + (size_t)nsrc * kGmacTile;                       // [nterm][PPN]
     const int N = 1 << log_n;
-    const int tid = threadIdx.x;
-    const int poly = tid / pp_n, pp = tid - poly * pp_n;
-    const int x = 2 * (blockIdx.x * pp_n + pp);
-    const bool act = poly < npoly && x < N;
+    const int grp = threadIdx.x / kGmacTile, lt = threadIdx.x % kGmacTile;
+    const int pl = lt / PPN, pp = lt - pl * PPN;
+    const int pgi = blockIdx.x % npg, blk = blockIdx.x / npg;
+    const int poly = pgi * PPC + pl;
+    const int x = 2 * (blk * PPN + pp);
+    const bool xin = pl < PPC && x < N;          // a slot pair of the tile
+    const bool act = xin && poly < npoly;        // ... of an existing polynomial
     const int i = blockIdx.y;
     const bool isq = i <= level;
     const PrimeC P = primes[isq ? i : nq + (i - level - 1)];
     const u64 q = P.q;
     const bool split = q < (1ull << 46);
     const size_t ext_off = ((size_t)poly * E + i) * N + x;
-    // 1. asynchronous copies; thread (poly, pp) copies the masks of terms
-    // poly, poly + npoly, ... at its own slot pair
-    if (poly < npoly)
-        for (int t = poly; t < nterm; t += npoly) {
-            if (x < N) cp_async16(msm + t * pp_n + pp, pg.tmask[t] + (size_t)i * N + x);
-            else msm[t * pp_n + pp] = make_ulonglong2(0, 0);
-        }
+    constexpr int G = kGmacGroups;
+    // 1. asynchronous copies: the masks of terms grp PPC + pl (step G PPC)
+    // at this slot pair, the sources grp, grp + G, ... of this thread's slot
+    if (xin)
+        for (int t = grp * PPC + pl; t < nterm; t += G * PPC)
+            cp_async16(msm + t * PPN + pp, pg.tmask[t] + (size_t)i * N + x);
     if (act) {
-        for (int s = 0; s < nsrc; s++) {
-            ulonglong2 *dst = vsm + (size_t)s * kGmacThreads + tid;
+        for (int s = grp; s < nsrc; s += G) {
+            ulonglong2 *dst = vsm + (size_t)s * kGmacTile + lt;
             if (pg.su[s]) cp_async16(dst, pg.su[s] + ext_off);
             else if (isq) cp_async16(dst, pg.slane[s] + ((size_t)poly * ls + i) * N + x);
             else *dst = make_ulonglong2(0, 0);   // P lane vanishes mod the special primes
@@ -1220,17 +1227,17 @@ k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
     cp_async_wait_all();
     // 2. in place, each thread on the words it copied: kept lanes times P,
     // every word split into halves (23 bits below 2^46, else 30 bits)
-    if (poly < npoly)
-        for (int t = poly; t < nterm; t += npoly) {
-            const ulonglong2 m = msm[t * pp_n + pp];
-            msm[t * pp_n + pp] = split ? make_ulonglong2(split23(m.x), split23(m.y))
-                                       : make_ulonglong2(split30(m.x), split30(m.y));
+    if (xin)
+        for (int t = grp * PPC + pl; t < nterm; t += G * PPC) {
+            const ulonglong2 m = msm[t * PPN + pp];
+            msm[t * PPN + pp] = split ? make_ulonglong2(split23(m.x), split23(m.y))
+                                      : make_ulonglong2(split30(m.x), split30(m.y));
         }
     if (act) {
         const u64 pw = isq ? pmodq[2 * i] : 0, pws = isq ? pmodq[2 * i + 1] : 0;
-        for (int s = 0; s < nsrc; s++) {
+        for (int s = grp; s < nsrc; s += G) {
             const bool kept = isq && !pg.su[s];
-            ulonglong2 *dst = vsm + (size_t)s * kGmacThreads + tid;
+            ulonglong2 *dst = vsm + (size_t)s * kGmacTile + lt;
             ulonglong2 v = *dst;
             if (kept) {
                 v.x = shoup_mul(v.x, pw, pws, q);
@@ -1242,13 +1249,14 @@ k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
     }
     __syncthreads();
     if (!act) return;
-    // 3. outputs.  Shared-memory reads by 32-bit address: the source row of a
-    // term is a constant offset from this thread's slot, the mask row steps
-    // by pp_n words per term.
-    const u32 vbase = (u32)__cvta_generic_to_shared(vsm + tid);
-    u32 maddr = (u32)__cvta_generic_to_shared(msm + pp);
-    const u32 mstep = (u32)pp_n * 16;
-    for (int d = 0; d < pg.X; d++) {
+    // 3. this group's outputs.  Shared-memory reads by 32-bit address: the
+    // source row of a term is a constant offset from this thread's slot, the
+    // mask row steps by PPN words per term.
+    const int d0 = pg.gfirst[grp], d1 = pg.gfirst[grp + 1];
+    const u32 vbase = (u32)__cvta_generic_to_shared(vsm + lt);
+    const u32 mstep = (u32)PPN * 16;
+    u32 maddr = (u32)__cvta_generic_to_shared(msm + pp) + (u32)pg.dfirst[d0] * mstep;
+    for (int d = d0; d < d1; d++) {
         ulonglong2 *o = reinterpret_cast<ulonglong2 *>(pg.outs[d] + ext_off);
         const ulonglong2 b = pg.accumulate ? *o : make_ulonglong2(0, 0);
         const int t0 = pg.dfirst[d], t1 = pg.dfirst[d + 1];
@@ -1781,17 +1789,26 @@ void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vec
         pg.outs[d] = outs[d];
         for (size_t t = 0; t < terms_in.size(); t++)
             if (term_dest[t] == d) {
-                pg.tvoff[n] = (u32)src_of[t] * kGmacThreads * 16;
+                pg.tvoff[n] = (u32)src_of[t] * kGmacTile * 16;
                 pg.tmask[n] = terms_in[t].mask;
                 n++;
             }
     }
     pg.dfirst[X] = n;
+    // output slices of the thread groups, cut where the running term count
+    // passes k / kGmacGroups of the total
+    pg.gfirst[0] = 0;
+    int k = 1;
+    for (int d = 0; d < X && k < kGmacGroups; d++)
+        while (k < kGmacGroups && (int64_t)pg.dfirst[d + 1] * kGmacGroups >= (int64_t)k * n) pg.gfirst[k++] = d + 1;
+    for (; k <= kGmacGroups; k++) pg.gfirst[k] = X;
     const int npoly = 2 * ncol;
-    FG_CHECK(npoly <= kGmacThreads, FG_EINVAL, "group_mac: too many columns");
-    const int pp_n = kGmacThreads / npoly;
-    dim3 g((N / 2 + pp_n - 1) / pp_n, E);
-    const size_t sm = (size_t)pg.nsrc * kGmacThreads * 16 + (size_t)pg.nterm * pp_n * 16;
+    pg.ppc = std::min(npoly, 16);
+    pg.ppn = std::min(kGmacTile / pg.ppc, 16);
+    const int npg = (npoly + pg.ppc - 1) / pg.ppc;
+    dim3 g(((N / 2 + pg.ppn - 1) / pg.ppn) * npg, E);
+    FG_CHECK(g.x < (1u << 31), FG_EINVAL, "group_mac: grid too large");
+    const size_t sm = (size_t)pg.nsrc * kGmacTile * 16 + (size_t)pg.nterm * pg.ppn * 16;
     double src_limbs = 0;
     for (const auto &gs : srcs) src_limbs += gs.u ? E : level + 1;
     KTimer kt(ctx, "group_mac",

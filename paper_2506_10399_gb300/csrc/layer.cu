@@ -527,7 +527,6 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
         bool have_acc = false;
         int level = l1;
         const size_t ext_w = (size_t)Fp * 2 * ctx->ext(l1) * N;
-        const int pool_cap = 24;   // key-switch outputs held at once (sources per group_mac)
         std::vector<u64 *> upool;
         for (const GroupC &g : pl->groups) {
             FG_CHECK(g.level == level, FG_ELEVEL, "plan level mismatch");
@@ -541,6 +540,13 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
             // terms by source: (lane, k) in plan order of the rotations, kept lanes after
             std::map<std::pair<int, int>, std::vector<const TermC *>> by_src;
             for (const TermC &tm : g.terms) by_src[{tm.src, tm.k}].push_back(&tm);
+            // sources per launch: the group's sources split evenly over the
+            // fewest launches within the program limits of k_group_mac (the
+            // key-switch outputs of one launch are held at once)
+            const int n_src = (int)by_src.size();
+            const int n_launch = std::max({1, (n_src + kern::kGmacSrc - 1) / kern::kGmacSrc,
+                                           ((int)g.terms.size() + kern::kGmacTerms - 1) / kern::kGmacTerms});
+            const int per_launch = (n_src + n_launch - 1) / n_launch;
             u64 *digits = (u64 *)ctx->buf("digits",
                                           (size_t)Fp * ctx->n_digits(level) * ctx->ext(level) * N * 8);
             std::vector<kern::GroupSource> srcs;
@@ -573,7 +579,7 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
             auto flush = [&]() {
                 issue_pending();
                 if (srcs.empty()) return;
-                // outputs in slices of at most 20 (shared-memory partial sums)
+                // outputs in slices of at most 64 (the program's output table)
                 for (int x0 = 0; x0 < X; x0 += 64) {
                     const int xn = std::min(64, X - x0);
                     std::vector<kern::GroupSource> ss;
@@ -604,7 +610,8 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
                 std::fill(dest_terms.begin(), dest_terms.end(), 0);
             };
             auto needs_flush = [&](const std::vector<const TermC *> &ts) {
-                bool full = (int)srcs.size() >= 24 || terms.size() + ts.size() > 192;
+                bool full = (int)srcs.size() >= per_launch ||
+                            (int)(terms.size() + ts.size()) > kern::kGmacTerms;
                 for (const TermC *tm : ts) full |= dest_terms[out_index(tm->dst)] >= 255;
                 return full;
             };
@@ -619,7 +626,7 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
                 const int a = rk.first, k = rk.second;
                 auto it = by_src.find({a, k});
                 if (it == by_src.end()) continue;
-                if (used == pool_cap || needs_flush(it->second)) {
+                if (needs_flush(it->second)) {
                     flush();
                     used = 0;
                 }
