@@ -1137,18 +1137,21 @@ k_stay_mac(const u64 *__restrict__ lane, int ls, int ncol, int level, const Dest
 // Tiling.  A tile is PPC polynomials (column, part) times PPN neighbouring
 // slot pairs of one limb, thread = one polynomial at one slot pair (PPC =
 // min(npoly, 16), PPN = min(128 / PPC, 16): for 32 polynomials two tiles of
-// 16 x 8, 128-byte runs per polynomial).  A CTA holds one tile and
-// kGmacGroups thread groups that share its staged words: every group copies
-// and splits a share of the sources and masks, then computes its own
-// contiguous slice of the outputs (balanced by term count on the host), so
-// the CTA has three times the warps for the same shared memory.  Phase 1
+// 16 x 8, 128-byte runs per polynomial).  A CTA holds one tile and G thread
+// groups that share its staged words: every group copies and splits a share
+// of the sources and masks, then computes its own contiguous slice of the
+// outputs (balanced by term count on the host).  With seven or more outputs
+// G = 3: the CTA gets three times the warps for the same shared memory
+// (measured on a 66-source, 12-output group: 9% faster than one group);
+// with fewer, the per-thread setup of extra groups costs more than it
+// hides (6 outputs: one group 20% faster than three), so G = 1.  Phase 1
 // copies the sources (the key-switch output, which already holds u +
 // P phi(c0), or the kept lane) and the tile's mask words into shared memory
 // with asynchronous copies, all in flight at once; phase 2 turns kept lanes
 // into P lane and splits words in place; phase 3 walks the group's
 // outputs, each a register sum over its terms.
 constexpr int kGmacTile = 128;    // threads per group: PPC x PPN (idle ones when npoly < 8)
-constexpr int kGmacGroups = 3;    // output groups per CTA
+constexpr int kGmacGroups = 3;    // most output groups per CTA
 constexpr int kGmacThreads = kGmacTile * kGmacGroups;
 constexpr int kGmacOut = 64;      // outputs per launch
 
@@ -1157,6 +1160,7 @@ constexpr int kGmacOut = 64;      // outputs per launch
 struct GProg {
     int nsrc, nterm, X, accumulate;
     int ppc, ppn;                       // tile: polynomials x slot pairs
+    int groups;                         // thread groups (blockDim = groups x kGmacTile)
     int gfirst[kGmacGroups + 1];        // first output of each thread group
     const u64 *su[kern::kGmacSrc];      // rotation: key-switch output; kept lane: nullptr
     const u64 *slane[kern::kGmacSrc];   // kept lane
@@ -1210,7 +1214,7 @@ k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
     const u64 q = P.q;
     const bool split = q < (1ull << 46);
     const size_t ext_off = ((size_t)poly * E + i) * N + x;
-    constexpr int G = kGmacGroups;
+    const int G = pg.groups;
     // 1. asynchronous copies: the masks of terms grp PPC + pl (step G PPC)
     // at this slot pair, the sources grp, grp + G, ... of this thread's slot
     if (xin)
@@ -1795,12 +1799,14 @@ void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vec
             }
     }
     pg.dfirst[X] = n;
-    // output slices of the thread groups, cut where the running term count
-    // passes k / kGmacGroups of the total
+    // thread groups and their output slices, cut where the running term
+    // count passes k / G of the total
+    const int G = X >= 7 ? kGmacGroups : 1;
+    pg.groups = G;
     pg.gfirst[0] = 0;
     int k = 1;
-    for (int d = 0; d < X && k < kGmacGroups; d++)
-        while (k < kGmacGroups && (int64_t)pg.dfirst[d + 1] * kGmacGroups >= (int64_t)k * n) pg.gfirst[k++] = d + 1;
+    for (int d = 0; d < X && k < G; d++)
+        while (k < G && (int64_t)pg.dfirst[d + 1] * G >= (int64_t)k * n) pg.gfirst[k++] = d + 1;
     for (; k <= kGmacGroups; k++) pg.gfirst[k] = X;
     const int npoly = 2 * ncol;
     pg.ppc = std::min(npoly, 16);
@@ -1821,7 +1827,7 @@ void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vec
         CUDA_TRY(cudaFuncSetAttribute(k_group_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         sm_set = sm;
     }
-    k_group_mac<<<g, kGmacThreads, sm, ctx->stream>>>(pg, ncol, level, E, ls, ctx->log_n,
+    k_group_mac<<<g, G * kGmacTile, sm, ctx->stream>>>(pg, ncol, level, E, ls, ctx->log_n,
                                                       ctx->d_pmodq, ctx->d_primes, ctx->nq);
     check_launch("group_mac");
 }
