@@ -225,6 +225,9 @@ LAYERS = [
                    w="glorot", seed=3), 1, 3, True, [0, 1]),
     ("multi", dict(graph="er", V=30, deg=3.0, F=7, Fp=3, seed=4), 4, 3, True, [0, 2]),
     ("toy", dict(graph="er", V=64, deg=4.0, F=16, Fp=8, seed=0), 4, 11, True, [0, 7]),
+    # groups of 8 and 11 outputs (three thread groups per group-MAC CTA) and of
+    # 39 and 60 sources, 279 and 331 terms (each split over two launches)
+    ("multi", dict(graph="er", V=1000, deg=4.0, F=4, Fp=2, seed=5), 1, 2, True, [0, 1]),
 ]
 
 
