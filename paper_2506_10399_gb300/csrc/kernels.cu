@@ -935,7 +935,7 @@ struct KsSet {
 // (P mod q_i and its Shoup companion at pmodq[2i], pmodq[2i+1]), so that
 // ModDown of u is Rot(c) itself: ModDown(A + P B) = ModDown(A) + B exactly.
 template <int BETA>
-__global__ void __launch_bounds__(256, BETA <= 5 ? 3 : 2)
+__global__ void __launch_bounds__(256, BETA <= 4 ? 4 : BETA <= 5 ? 3 : 2)
 k_ks_ip(const KsSet ks, int KL, const u64 *__restrict__ lane, int ls,
         const u64 *__restrict__ digits, int ncol, int level, int E, int alpha, int nq,
         int log_n, const PrimeC *__restrict__ primes, const u64 *__restrict__ pmodq)
