@@ -443,32 +443,45 @@ def run_ours(args):
 
 # ------------------------------------------------------------------ two layers
 def run_two_layer(args):
-    """Two-layer encrypted GCN on the benchmark workload: layer 1 (F -> F'),
-    the x^2 activation (CMult + relinearisation + rescale), layer 2
-    (F' -> C), inputs resident in HBM; decrypted against FP64
-    A-hat (A-hat X W1)^2 W2."""
+    """Two-layer encrypted GCN: layer 1 (F -> F'), the x^2 activation (CMult
+    + relinearisation + rescale), layer 2 (F' -> C), inputs resident in HBM;
+    decrypted against FP64 A-hat (H1)^2 W2.  On the benchmark workload both
+    layers are SpIntra-CA (H1 = A-hat X W1).  On cora_like (N = 2^15, ten
+    primes: no room for two SpIntra-CA layers) the first layer runs in
+    Inter-CA mode as in the paper's models (the node and 4 sampled
+    neighbours, MEAN; H1 = sum_k w_k X[nbr_k] W1) and the second at radix 16."""
     import torch
     import __graft_entry__
     fg = __graft_entry__.build()
     from paper_2506_10399_gb300 import workloads as wl
-    c = dict(wl.CONFIGS[WORKLOAD])
-    w = wl.config_workload(WORKLOAD)
-    W2 = wl.second_layer_weights(WORKLOAD)
+    name = args.workload
+    c = dict(wl.CONFIGS[name])
+    w = wl.config_workload(name)
+    W2 = wl.second_layer_weights(name)
+    inter = name == "cora_like"
     t_setup = time.perf_counter()
     ctx = fg.Context(**c)
     perm = wl.random_order(w.V, ctx.slots, SEED)
-    plan1 = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=1, radix_bits=RADIX_BITS,
-                          min_out_level=MIN_OUT_LEVEL)
-    l1 = plan1.info()["out_level"]
-    plan2 = fg.plan_build(ctx, w.row_ptr, w.col, w.val, W2, perm, t=1, radix_bits=RADIX_BITS,
-                          in_level=l1 - 1)
+    if inter:
+        nbr, wts = wl.sample_neighbors(w, 4, SEED)
+        plan1 = fg.plan_build_inter(ctx, nbr, wts, w.W, perm)
+    else:
+        plan1 = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=1, radix_bits=RADIX_BITS,
+                              min_out_level=MIN_OUT_LEVEL)
+    i1 = plan1.info()
+    l1 = i1["out_level"]
+    plan2 = fg.plan_build(ctx, w.row_ptr, w.col, w.val, W2, perm, t=1,
+                          radix_bits=4 if inter else RADIX_BITS, in_level=l1 - 1)
     amounts = sorted(set(plan1.rotation_amounts()) | set(plan2.rotation_amounts()))
     sk, evk = fg.keygen(ctx, SEED, amounts, relin=True)
     keys = fg.load_evk(ctx, evk)
     del evk
-    F, Fp, N = w.X.shape[1], w.W.shape[1], ctx.n
-    x = torch.empty((F, 2, ctx.nq, N), dtype=torch.int64, device="cuda")
-    fg.pack_features(ctx, sk, SEED, w.X, perm, 1, out=x)
+    Fp, N = w.W.shape[1], ctx.n
+    x = torch.empty((i1["n_in"], 2, ctx.nq, N), dtype=torch.int64, device="cuda")
+    if inter:
+        fg.pack_neighbor_copies(ctx, sk, SEED, w.X, nbr, perm, out=x)
+    else:
+        fg.pack_features(ctx, sk, SEED, w.X, perm, 1, out=x)
     h1 = torch.empty((Fp, 2, l1 + 1, N), dtype=torch.int64, device="cuda")
     a1 = torch.empty((Fp, 2, l1, N), dtype=torch.int64, device="cuda")
     i2 = plan2.info()
@@ -484,7 +497,7 @@ def run_two_layer(args):
     la, lb, sc = step()
     torch.cuda.synchronize()
     scale = sc * sc / ctx.q[la]
-    ref = wl.two_layer_reference(w, W2)
+    ref = wl.two_layer_reference(w, W2, first=wl.neighbor_reference(w, nbr, wts) if inter else None)
     err = 0.0
     for j in range(W2.shape[1]):
         d = fg.decrypt_decode(ctx, sk, out[j].contiguous(), lb, scale)
@@ -508,14 +521,20 @@ def run_two_layer(args):
         for k, (a, b) in enumerate(((0, 1), (1, 2), (2, 3))):
             parts[k] = parts.get(k, 0.0) + e[a].elapsed_time(e[b]) / args.steps
         tot += e[0].elapsed_time(e[3]) / args.steps
-    line = {"metric": "encrypted two-layer GCN latency (ms) at N=2^16", "value": round(tot, 3),
+    if inter:
+        desc = ("two-layer GCN, synthetic Cora-like graph (power law 2.5, V=2708, mean degree 3.9, "
+                "F=1433 binary 1.3%, F'=16, 7 classes), CKKS N=2^15, 10 primes 60+9x40 bit, K=4 special, "
+                "dnum=3; layer 1 Inter-CA (node + 4 sampled neighbours, MEAN), x^2, layer 2 radix-16 "
+                "SpIntra-CA; seeded random node order")
+    else:
+        desc = config_desc()["workload"] + "; second layer W2 16x3 Glorot, x^2 between"
+    line = {"metric": "encrypted two-layer GCN latency (ms) at N=2^%d" % c["log_n"], "value": round(tot, 3),
             "unit": "ms/inference", "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
             "layer1_ms": round(parts[0], 3), "square_ms": round(parts[1], 3), "layer2_ms": round(parts[2], 3),
             "levels": {"layer1_out": la, "square_out": la - 1, "layer2_out": lb},
-            "rotations": plan1.info()["rotations"] + i2["rotations"],
+            "rotations": i1["rotations"] + i2["rotations"],
             "decrypt_max_abs_err_vs_fp64": err, "gpu_launches": (ctx.launch_count() - n0) // args.steps,
-            "setup_s": round(setup_s, 1),
-            "config": {"workload": config_desc()["workload"] + "; second layer W2 16x3 Glorot, x^2 between"}}
+            "setup_s": round(setup_s, 1), "config": {"workload": desc}}
     print(json.dumps(line))
     return 0
 
@@ -682,6 +701,8 @@ def main():
                     help="batched form: many queries one at a time vs all at once")
     ap.add_argument("--queries", type=int, default=16, help="queries in the batched form")
     ap.add_argument("--two-layer", action="store_true", help="two-layer GCN with x^2 between")
+    ap.add_argument("--workload", default="pubmed_like", choices=["pubmed_like", "cora_like"],
+                    help="workload of --two-layer")
     ap.add_argument("--inter", action="store_true", help="the layer in Inter-CA mode")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -346,7 +346,7 @@ def drop_ct(ct):
 
 
 def rescale_ct(params, ct):
-    """Divide by the top prime q_l (floor convention), both parts."""
+    """Divide by the top prime q_l, rounding to the nearest integer, both parts."""
     primes = params.q[:ct.shape[1]]
     return np.stack([_ref.rescale(ct[0], primes), _ref.rescale(ct[1], primes)])
 

@@ -258,42 +258,69 @@ void ref_base_convert(const u64 *in, int n_in, const u64 *b_primes,
 /* rescale and ModDown                                                 */
 /* ------------------------------------------------------------------ */
 
-/* Rescale by the last prime (the level drop that follows a product):
- * c_i <- (c_i - r) * q_l^-1 mod q_i for i < l, with r = [c]_{q_l} in
- * [0, q_l) taken as an integer (floor convention).  in: [l+1][n] over
- * q_0..q_l, out: [l][n]. */
+/* Rescale by the last prime (the level drop that follows a product),
+ * rounding to the nearest integer: c <- floor((c + h) / q_l) with
+ * h = (q_l - 1) / 2, i.e. per limb
+ *   c_i <- (c_i + [h]_{q_i} - [r]_{q_i}) * q_l^-1 mod q_i,  r = [c_l + h]_{q_l}
+ * (r in [0, q_l) taken as an integer).  Rounding keeps the error of each
+ * coefficient centred; a floor (h = 0) biases every coefficient of both
+ * parts by -1/2, and that constant bias, multiplied by s at decryption,
+ * is amplified at the slots whose evaluation points lie near 1.
+ * in: [l+1][n] over q_0..q_l, out: [l][n]. */
 void ref_rescale(const u64 *in, int n_limbs, const u64 *primes, u64 *out, int n)
 {
     int l = n_limbs - 1;
     u64 ql = primes[l];
-    const u64 *r = in + (size_t)l * n;
+    u64 h = (ql - 1) / 2;
+    const u64 *c = in + (size_t)l * n;
     for (int i = 0; i < l; i++) {
         u64 qi = primes[i];
         u64 inv = invmod(ql % qi, qi);
+        u64 hi = h % qi;
         for (int x = 0; x < n; x++) {
-            u64 d = submod(in[(size_t)i * n + x], r[x] % qi, qi);
+            u64 r = addmod(c[x], h, ql);
+            u64 d = submod(addmod(in[(size_t)i * n + x], hi, qi), r % qi, qi);
             out[(size_t)i * n + x] = mulmod(d, inv, qi);
         }
     }
 }
 
-/* ModDown: (u - Conv_{P->Q}([u]_P)) * P^-1 mod q_i.  in: [nq + np][n] with
- * the q-limbs first, out: [nq][n]. */
+/* [(P - 1) / 2]_m for P = prod of the primes ps (all odd, m odd):
+ * (P - 1) 2^-1 mod m */
+static u64 half_mod(const u64 *ps, int np, u64 m)
+{
+    u64 P = 1;
+    for (int k = 0; k < np; k++) P = mulmod(P, ps[k] % m, m);
+    return mulmod(submod(P, 1 % m, m), invmod(2, m), m);
+}
+
+/* ModDown, rounding: floor((u + H) / P) with H = (P - 1) / 2, up to the
+ * multiple of P that the fast base conversion may add:
+ *   u~ = u + [H] on every limb,  out_i = (u~_i - Conv_{P->Q}([u~]_P)_i) * P^-1.
+ * in: [nq + np][n] with the q-limbs first, out: [nq][n]. */
 void ref_moddown(const u64 *in, int nq, const u64 *q_primes, int np,
                  const u64 *p_primes, u64 *out, int n)
 {
     u64 *conv = (u64 *)malloc(sizeof(u64) * (size_t)nq * (size_t)n);
-    ref_base_convert(in + (size_t)nq * n, np, p_primes, conv, nq, q_primes, n);
+    u64 *up = (u64 *)malloc(sizeof(u64) * (size_t)np * (size_t)n);
+    for (int k = 0; k < np; k++) {
+        u64 pk = p_primes[k], hk = half_mod(p_primes, np, pk);
+        for (int x = 0; x < n; x++)
+            up[(size_t)k * n + x] = addmod(in[(size_t)(nq + k) * n + x], hk, pk);
+    }
+    ref_base_convert(up, np, p_primes, conv, nq, q_primes, n);
     for (int i = 0; i < nq; i++) {
         u64 qi = q_primes[i];
         u64 P = 1;
         for (int k = 0; k < np; k++) P = mulmod(P, p_primes[k] % qi, qi);
         u64 pinv = invmod(P, qi);
+        u64 hi = half_mod(p_primes, np, qi);
         for (int x = 0; x < n; x++) {
-            u64 d = submod(in[(size_t)i * n + x], conv[(size_t)i * n + x], qi);
+            u64 d = submod(addmod(in[(size_t)i * n + x], hi, qi), conv[(size_t)i * n + x], qi);
             out[(size_t)i * n + x] = mulmod(d, pinv, qi);
         }
     }
+    free(up);
     free(conv);
 }
 

@@ -275,6 +275,28 @@ const u64 *fg_ctx::moddown_rescale_tab(int level)
     return d;
 }
 
+// the offset of the rounded ModDown-then-rescale, H = (P - 1) / 2 +
+// P (q_l - 1) / 2, mod q_0..q_l
+const u64 *fg_ctx::moddown_rescale_half_tab(int level)
+{
+    auto it = mdr_half_tabs.find(level);
+    if (it != mdr_half_tabs.end()) return it->second;
+    std::vector<u64> h(level + 1);
+    const u64 hl = (primes[level] - 1) / 2;
+    for (int i = 0; i <= level; i++) {
+        const u64 q = primes[i];
+        u64 P = 1;
+        for (int k = 0; k < np; k++) P = hm::mulmod(P, primes[nq + k] % q, q);
+        const u64 hp = hm::mulmod((P + q - 1) % q, hm::invmod(2, q), q);
+        h[i] = (hp + hm::mulmod(P, hl % q, q)) % q;
+    }
+    u64 *d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, h.size() * 8));
+    CUDA_TRY(cudaMemcpy(d, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
+    mdr_half_tabs[level] = d;
+    return d;
+}
+
 const KeyDev &fg_keys::get(int32_t amount) const
 {
     auto it = keys.find(amount);
@@ -480,6 +502,17 @@ int fg_ctx_create(const fg_params *prm, void *cuda_stream, fg_ctx **out)
         CUDA_TRY(cudaMemcpy(dpm, pm.data(), pm.size() * 8, cudaMemcpyHostToDevice));
         g_pmodq[ctx] = dpm;
         ctx->d_pmodq = dpm;
+        // (P - 1) / 2 mod every prime: the offset that makes ModDown round
+        // (P is odd: (P - 1) / 2 = (P - 1) 2^-1 mod m)
+        std::vector<u64> hp(KL);
+        for (int j = 0; j < KL; j++) {
+            const u64 m = ctx->primes[j];
+            u64 P = 1;
+            for (int k = 0; k < ctx->np; k++) P = hm::mulmod(P, ctx->primes[ctx->nq + k] % m, m);
+            hp[j] = hm::mulmod((P + m - 1) % m, hm::invmod(2, m), m);
+        }
+        CUDA_TRY(cudaMalloc(&ctx->d_halfp, hp.size() * 8));
+        CUDA_TRY(cudaMemcpy(ctx->d_halfp, hp.data(), hp.size() * 8, cudaMemcpyHostToDevice));
         std::vector<int> ids = iota(KL);
         int *dpi = nullptr;
         CUDA_TRY(cudaMalloc(&dpi, ids.size() * sizeof(int)));
@@ -512,10 +545,12 @@ int fg_ctx_destroy(fg_ctx *ctx)
     cudaFree(ctx->d_fwd_rows);
     cudaFree(ctx->d_inv_rows);
     cudaFree(ctx->d_ninv);
+    cudaFree(ctx->d_halfp);
     for (auto &kv : ctx->conv_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->rescale_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->pinv_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->mdr_tabs) cudaFree(kv.second);
+    for (auto &kv : ctx->mdr_half_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->ws) cudaFree(kv.second.first);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->batch.exec) cudaGraphExecDestroy(ctx->batch.exec);

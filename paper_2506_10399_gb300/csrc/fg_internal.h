@@ -103,6 +103,7 @@ struct fg_ctx {
     void *d_inv_rows = nullptr;
     u64 *d_ninv = nullptr;            // [nq+np][2] N^-1 and Shoup
     u64 *d_pmodq = nullptr;           // [nq][2] P mod q_i and Shoup
+    u64 *d_halfp = nullptr;           // [nq + np] ((P - 1) / 2) mod each prime (rounded ModDown)
     std::vector<u64> h_qneg, h_r2, h_ones;
 
     // cached RNS constant tables, keyed by (kind, level, digit)
@@ -110,6 +111,7 @@ struct fg_ctx {
     std::map<int, u64 *> rescale_tabs;   // level -> [level][2] q_l^-1 mod q_i + Shoup
     std::map<int, u64 *> pinv_tabs;      // level -> [level+1][2] P^-1 mod q_i + Shoup
     std::map<int, u64 *> mdr_tabs;       // level -> [level][2] (P q_l)^-1 mod q_i + Shoup
+    std::map<int, u64 *> mdr_half_tabs;  // level -> [level+1] H mod q_i, H = (P-1)/2 + P (q_l-1)/2
 
     // instrumentation: kernel launch count, and CUDA-event timing of every
     // launch of one kernel class with its algorithmic bytes
@@ -157,6 +159,7 @@ struct fg_ctx {
     const u64 *rescale_tab(int level);
     const u64 *pinv_tab(int level);
     const u64 *moddown_rescale_tab(int level);
+    const u64 *moddown_rescale_half_tab(int level);
 };
 
 struct KeyDev {

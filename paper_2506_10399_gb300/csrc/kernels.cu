@@ -783,33 +783,43 @@ k_comb(const u64 *__restrict__ X, int F, int fb, int fe, int accumulate, int Fp,
 // ------------------------------------------------------------------------
 // rescale
 // ------------------------------------------------------------------------
-// coefficient domain: out_i = (in_i - [in_l]_{q_i}) * q_l^-1 mod q_i
+// Rescale rounds: c <- floor((c + h) / q_l), h = (q_l - 1) / 2, so the
+// error of every coefficient is centred (a floor biases all of them by -1/2,
+// and decryption amplifies that bias at the slots near 1).  Per limb:
+//   out_i = (in_i + [h]_{q_i} - [r]_{q_i}) * q_l^-1,  r = [in_l + h]_{q_l}.
+// coefficient domain
 __global__ void k_rescale_coef(const u64 *in, int in_ls, u64 *out, int out_ls, int level,
                                const PrimeC *__restrict__ primes, const u64 *__restrict__ tab,
                                int N)
 {
     const int i = blockIdx.y, poly = blockIdx.z;
-    const PrimeC P = primes[i];
+    const PrimeC P = primes[i], Pl = primes[level];
     const u64 inv = tab[2 * i], invs = tab[2 * i + 1];
+    const u64 h = Pl.q >> 1, hi = reduce_word(h, P);
     const u64 *top = in + ((size_t)poly * in_ls + level) * N;
     const u64 *src = in + ((size_t)poly * in_ls + i) * N;
     u64 *dst = out + ((size_t)poly * out_ls + i) * N;
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
-        u64 r = reduce_word(top[x], P);
-        dst[x] = shoup_mul(sub_mod(src[x], r, P.q), inv, invs, P.q);
+        const u64 r = reduce_word(reduce_word(top[x], Pl) + h, Pl);
+        dst[x] = shoup_mul(sub_mod(add_mod(src[x], hi, P.q), reduce_word(r, P), P.q), inv, invs, P.q);
     }
 }
 
-// r (coefficient domain, one limb per poly) -> its residues mod q_0..q_{level-1}
+// the top limb l (coefficient domain, one per poly) -> [r]_{q_i} - [h]_{q_i}
+// for i < level, r = [c_l + h]_{q_l}: what the rounded rescale subtracts
+// (after its NTT) from limb i
 __global__ void k_bcast_reduce(const u64 *r, int r_ls, int r_limb, u64 *out, int level,
                                const PrimeC *__restrict__ primes, int N)
 {
     const int i = blockIdx.y, poly = blockIdx.z;
-    const PrimeC P = primes[i];
+    const PrimeC P = primes[i], Pl = primes[r_limb];
+    const u64 h = Pl.q >> 1, hi = reduce_word(h, P);
     const u64 *src = r + ((size_t)poly * r_ls + r_limb) * N;
     u64 *dst = out + ((size_t)poly * level + i) * N;
-    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x)
-        dst[x] = reduce_word(src[x], P);
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
+        const u64 t = reduce_word(reduce_word(src[x], Pl) + h, Pl);
+        dst[x] = sub_mod(reduce_word(t, P), hi, P.q);
+    }
 }
 
 // NTT domain finish: ct_i = (ct_i - r_i) * q_l^-1
@@ -849,14 +859,18 @@ __device__ __forceinline__ u64 conv_point(const ConvTab &T, const u64 *y, int t,
     return redc(hi, lo, P);
 }
 
+// off (optional, by prime index): a constant added to every input residue
+// first (ModDown adds (P - 1) / 2 there so that it rounds)
 template <int NMAX>
 __device__ __forceinline__ void conv_inputs(const ConvTab &T, const u64 *src, size_t limb_stride,
-                                            u64 *y, const PrimeC *__restrict__ primes)
+                                            u64 *y, const PrimeC *__restrict__ primes,
+                                            const u64 *__restrict__ off = nullptr)
 {
 #pragma unroll
     for (int k = 0; k < NMAX; k++)
         if (k < T.n_in) {
-            const u64 v = src[(size_t)T.in_l[k] * limb_stride];
+            u64 v = src[(size_t)T.in_l[k] * limb_stride];
+            if (off) v += off[T.in_p[k]];   // v < 2^62 + 2^60: Shoup's lazy product takes any word
             y[k] = split30(shoup_mul(v, T.hinv[k], T.hinv_s[k], primes[T.in_p[k]].q));
         }
 }
@@ -883,20 +897,25 @@ k_modup_conv(const u64 *__restrict__ c1c, int nl, u64 *digits, int beta, int E,
 
 // ModDown conversion P -> q_0..q_level.  u: [npoly][E][N] (P limbs in the
 // coefficient domain at positions level+1..), conv: [npoly][level+1][N].
+// The ModDown rounds: floor((u + H) / P), H = (P - 1) / 2.  H is added to
+// the special limbs before the conversion and, on the limbs of Q, folded
+// into what the finish subtracts: conv_i - [H]_{q_i}.
 template <int NMAX>
 __global__ void __launch_bounds__(256)
 k_moddown_conv(const u64 *__restrict__ u, int E, u64 *conv, int nl,
-               const ConvTab *__restrict__ tab, const PrimeC *__restrict__ primes, int N)
+               const ConvTab *__restrict__ tab, const u64 *__restrict__ halfp,
+               const PrimeC *__restrict__ primes, int N)
 {
     const int poly = blockIdx.y;
     const ConvTab &T = *tab;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= N) return;
     u64 y[NMAX];
-    conv_inputs<NMAX>(T, u + (size_t)poly * E * N + x, N, y, primes);
+    conv_inputs<NMAX>(T, u + (size_t)poly * E * N + x, N, y, primes, halfp);
     for (int t = 0; t < T.n_out; t++) {
         const PrimeC P = primes[T.out_p[t]];
-        conv[((size_t)poly * nl + T.out_l[t]) * N + x] = conv_point<NMAX>(T, y, t, P);
+        conv[((size_t)poly * nl + T.out_l[t]) * N + x] =
+            sub_mod(conv_point<NMAX>(T, y, t, P), halfp[T.out_p[t]], P.q);
     }
 }
 
@@ -1305,29 +1324,35 @@ k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
 // rescale drops), the rescaled limbs are
 //   ((ext_i - conv_i) P^-1 - [o_l]_{q_i}) q_l^-1 = (ext_i - (conv_i + P o_l)) (P q_l)^-1,
 // so one forward NTT of w_i = conv_i + P o_l mod q_i per kept limb replaces
-// the NTT of conv_i and the rescale's NTT of [o_l]_{q_i}.
+// the NTT of conv_i and the rescale's NTT of [o_l]_{q_i}.  Both steps round
+// (ModDown adds (P - 1) / 2, the rescale (q_l - 1) / 2): the pair adds
+// H = (P - 1) / 2 + P (q_l - 1) / 2 to ext, which reaches the special limbs
+// as (P - 1) / 2, limb l through o_l, and the kept limbs as w_i - [H]_{q_i}.
 // ext: [npoly][E][N], limbs l and l+1.. in the coefficient domain;
 // w: [npoly][l][N] coefficient domain.
 template <int NMAX>
 __global__ void __launch_bounds__(256)
 k_moddown_rescale_conv(const u64 *__restrict__ ext, int E, u64 *w, int l,
                        const ConvTab *__restrict__ tab, const u64 *__restrict__ pinv,
-                       const u64 *__restrict__ pmodq, const PrimeC *__restrict__ primes, int N)
+                       const u64 *__restrict__ pmodq, const u64 *__restrict__ halfp,
+                       const u64 *__restrict__ hq, const PrimeC *__restrict__ primes, int N)
 {
     const int poly = blockIdx.y;
     const ConvTab &T = *tab;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= N) return;
     u64 y[NMAX];
-    conv_inputs<NMAX>(T, ext + (size_t)poly * E * N + x, N, y, primes);
+    conv_inputs<NMAX>(T, ext + (size_t)poly * E * N + x, N, y, primes, halfp);
     const PrimeC Pl = primes[l];
-    const u64 el = ext[((size_t)poly * E + l) * N + x];
+    // hq[i] = [H]_{q_i}, H = (P - 1) / 2 + P (q_l - 1) / 2
+    const u64 el = add_mod(ext[((size_t)poly * E + l) * N + x], hq[l], Pl.q);
     const u64 ol = shoup_mul(sub_mod(el, conv_point<NMAX>(T, y, l, Pl), Pl.q), pinv[2 * l],
                              pinv[2 * l + 1], Pl.q);
     for (int t = 0; t < l; t++) {
         const PrimeC P = primes[t];
         w[((size_t)poly * l + t) * N + x] =
-            add_mod(conv_point<NMAX>(T, y, t, P), shoup_mul(ol, pmodq[2 * t], pmodq[2 * t + 1], P.q), P.q);
+            sub_mod(add_mod(conv_point<NMAX>(T, y, t, P), shoup_mul(ol, pmodq[2 * t], pmodq[2 * t + 1], P.q),
+                            P.q), hq[t], P.q);
     }
 }
 
@@ -1705,7 +1730,7 @@ void rotate_mac(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int nco
     KTimer kt(ctx, "moddown_conv", (double)2 * ncol * (ctx->np + nl) * N * 8);
 #define FG_LAUNCH(M)                                                                       \
     k_moddown_conv<M><<<g2, 256, 0, ctx->stream>>>(u, E, conv, nl, ctx->moddown_tab(level),   \
-                                                   ctx->d_primes, N)
+                                                   ctx->d_halfp, ctx->d_primes, N)
     FG_NIN_DISPATCH(ctx->np, FG_LAUNCH)
 #undef FG_LAUNCH
     check_launch("moddown_conv");
@@ -1859,6 +1884,8 @@ void moddown_rescale_to_lane(fg_ctx *ctx, u64 *ext, int ncol, int level, u64 *ou
 #define FG_LAUNCH(M)                                                                        \
         k_moddown_rescale_conv<M><<<g2, 256, 0, ctx->stream>>>(ext, E, w, l, ctx->moddown_tab(level), \
                                                                ctx->pinv_tab(level), ctx->d_pmodq,  \
+                                                               ctx->d_halfp,                        \
+                                                               ctx->moddown_rescale_half_tab(level), \
                                                                ctx->d_primes, N)
         FG_NIN_DISPATCH(ctx->np, FG_LAUNCH)
 #undef FG_LAUNCH

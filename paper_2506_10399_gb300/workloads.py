@@ -202,9 +202,11 @@ def second_layer_weights(name, seed=None):
     return weights("glorot", cfg["Fp"], SECOND_LAYER_CLASSES[name], rng)
 
 
-def two_layer_reference(w, W2):
-    """FP64 A-hat (A-hat X W1)^2 W2 (square taken elementwise)."""
-    h = w.reference_output() ** 2
+def two_layer_reference(w, W2, first=None):
+    """FP64 A-hat (H1)^2 W2 (square taken elementwise), H1 = A-hat X W1 unless
+    the first layer's FP64 output is given (e.g. an Inter-CA layer's
+    sum_k w_k X[nbr_k] W1)."""
+    h = (w.reference_output() if first is None else first) ** 2
     XW = h @ W2
     out = np.zeros((w.V, W2.shape[1]))
     for v in range(w.V):

@@ -65,3 +65,50 @@ def test_fullsize_layer_decrypts_to_fp64(env):
     for j in (0, 7, 15):
         d = fg.decrypt_decode(ctx, sk, out[j].contiguous(), lvl, scale)
         assert np.max(np.abs(d[perm] - ref[:, j])) < 2 ** -20
+
+
+def test_cora_like_two_layer_decrypts_to_fp64():
+    """The two-layer configuration at its full sizes (N = 2^15, 10 + 4 primes,
+    dnum 3; V = 2708, F = 1433, F' = 16, 7 classes): ten primes leave no room
+    for two SpIntra-CA layers (each takes the combination's level and one per
+    group), so the first layer runs in Inter-CA mode as in the paper's
+    models (the node and 4 sampled neighbours, MEAN weights; 2 levels), then
+    x^2 (CMult, relinearisation, rescale), then SpIntra-CA at radix 16 (4
+    groups).  Every output column decrypts within 2^-20 of FP64
+    A-hat (sum_k w_k X[nbr_k] W1)^2 W2."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    fg = __graft_entry__.build()
+    cfg = wl.CONFIGS["cora_like"]
+    ctx = fg.Context(**cfg)
+    w = wl.config_workload("cora_like")
+    W2 = wl.second_layer_weights("cora_like")
+    perm = wl.random_order(w.V, ctx.slots, 5)
+    nbr, wts = wl.sample_neighbors(w, 4, 5)
+    plan1 = fg.plan_build_inter(ctx, nbr, wts, w.W, perm)
+    i1 = plan1.info()
+    assert i1["out_level"] == 7
+    plan2 = fg.plan_build(ctx, w.row_ptr, w.col, w.val, W2, perm, t=1, radix_bits=4,
+                          in_level=i1["out_level"] - 1)
+    i2 = plan2.info()
+    assert i2["out_level"] == 1 and i2["n_out"] == 7
+    sk, evk = fg.keygen(ctx, 5, plan2.rotation_amounts(), relin=True)
+    keys = fg.load_evk(ctx, evk)
+    del evk
+    x = torch.empty((i1["n_in"], 2, ctx.nq, ctx.n), dtype=torch.int64, device="cuda")
+    fg.pack_neighbor_copies(ctx, sk, 5, w.X, nbr, perm, out=x)
+    h1 = torch.empty((i1["n_out"], 2, i1["out_level"] + 1, ctx.n), dtype=torch.int64, device="cuda")
+    _, la, sc = fg.gcn_layer_axw(ctx, keys, plan1, x, out=h1)
+    del x
+    a1 = torch.empty((i1["n_out"], 2, la, ctx.n), dtype=torch.int64, device="cuda")
+    fg.mul_relin_rescale(ctx, keys, h1, h1, la, out=a1)
+    out = torch.empty((i2["n_out"], 2, i2["out_level"] + 1, ctx.n), dtype=torch.int64, device="cuda")
+    _, lb, _ = fg.gcn_layer_axw(ctx, keys, plan2, a1, out=out)
+    assert lb == 1
+    scale = sc * sc / ctx.q[la]
+    ref = wl.two_layer_reference(w, W2, first=wl.neighbor_reference(w, nbr, wts))
+    for j in range(W2.shape[1]):
+        d = fg.decrypt_decode(ctx, sk, out[j].contiguous(), lb, scale)
+        assert np.max(np.abs(d[perm] - ref[:, j])) < 2 ** -20

@@ -11,6 +11,7 @@ import json
 import math
 import os
 import random
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -186,7 +187,9 @@ def test_base_convert_is_x_plus_small_multiple(n_in):
 
 
 @pytest.mark.parametrize("nq,npr", [(2, 1), (3, 2), (5, 4)])
-def test_moddown_is_floor_division_by_p(nq, npr):
+def test_moddown_is_rounded_division_by_p(nq, npr):
+    """ModDown rounds u / P to the nearest integer (floor((u + (P-1)/2) / P)),
+    up to the multiple e < K of P that the fast base conversion may add."""
     primes = _ref.gen_primes(3, [45] * nq + [60] * npr)
     qs, ps = primes[:nq], primes[nq:]
     rng = random.Random(nq * 10 + npr)
@@ -197,13 +200,14 @@ def test_moddown_is_floor_division_by_p(nq, npr):
         P *= p
     for c in range(8):
         X, _ = crt(u[:, c], qs + ps)
-        base = X // P
+        base = (X + (P - 1) // 2) // P
         es = [e for e in range(npr) if all(int(out[i, c]) == (base - e) % q for i, q in enumerate(qs))]
         assert len(es) == 1
 
 
 @pytest.mark.parametrize("nl", [2, 3, 6])
-def test_rescale_exact_floor_division(nl):
+def test_rescale_exact_rounded_division(nl):
+    """Rescale by q_l is the nearest integer to X / q_l (q_l odd: no ties)."""
     primes = _ref.gen_primes(3, [60] + [40] * (nl - 1))
     rng = random.Random(nl)
     x = rand_res(rng, primes, 8)
@@ -211,9 +215,31 @@ def test_rescale_exact_floor_division(nl):
     ql = primes[-1]
     for c in range(8):
         X, _ = crt(x[:, c], primes)
-        want = (X - X % ql) // ql
+        want = (X + (ql - 1) // 2) // ql
+        assert abs(Fraction(X, ql) - want) < Fraction(1, 2)
         for i, q in enumerate(primes[:-1]):
             assert int(out[i, c]) == want % q
+
+
+def test_rescale_error_stays_small_at_low_frequency_slots():
+    """The reason rescale rounds: a constant multiplied into a fresh
+    ciphertext, then one rescale, at N = 2^15, scale 2^40.  With rounding
+    the error is the centred rounding noise e0 + e1 s (4.0e-8 here, about
+    4.5 standard deviations of sqrt(N/18) sqrt(N) / 2^40); a floor rescale
+    biases every coefficient of both parts by -1/2, and decryption
+    multiplies that bias by s and amplifies it at the slots near 1
+    (measured: 1.7e-6 with floor)."""
+    P = ckks.Params(15, [60] + [40] * 9, [60] * 4, 4, 40)
+    s = ckks.keygen_secret(P, 3)
+    rng = np.random.default_rng(1)
+    z = rng.uniform(-0.05, 0.05, P.slots)
+    ct = ckks.encrypt(P, 3, 0, ckks.encode(P, z, P.scale, P.L), s, P.L)
+    qL = P.q[P.L]
+    acc = np.zeros_like(ct)
+    ckks.const_mac(P, acc, ct, int(round(0.06 * qL)))
+    r = ckks.rescale_ct(P, acc)
+    d = ckks.decode(P, ckks.decrypt(P, r, s), P.scale)
+    assert np.max(np.abs(d - 0.06 * z)) < 1e-7
 
 
 # ---------------------------------------------------------------- encoding
