@@ -327,8 +327,8 @@ int fg_rotate(fg_ctx *ctx, const fg_keys *keys, const uint64_t *ct, int level, i
  * level drops by one), rounding each coefficient to the nearest integer:
  * out = floor((c + h) / q_l), h = (q_l - 1) / 2, i.e.
  * out_i = (c_i + [h]_{q_i} - [r]_{q_i}) q_l^-1 mod q_i with r = [c_l + h]_{q_l}
- * in [0, q_l).  Every key switch's ModDown rounds the same way (offset
- * (P - 1) / 2).  ct: [2][level+1][N], out: [2][level][N]. */
+ * in [0, q_l).  Every key switch's ModDown uses the centred base conversion
+ * (error of mean zero).  ct: [2][level+1][N], out: [2][level][N]. */
 int fg_rescale(fg_ctx *ctx, const uint64_t *ct, int level, uint64_t *out);
 
 /* Negacyclic product c = a * b mod (X^N + 1, q_i) for i <= level through the

@@ -285,42 +285,40 @@ void ref_rescale(const u64 *in, int n_limbs, const u64 *primes, u64 *out, int n)
     }
 }
 
-/* [(P - 1) / 2]_m for P = prod of the primes ps (all odd, m odd):
- * (P - 1) 2^-1 mod m */
-static u64 half_mod(const u64 *ps, int np, u64 m)
-{
-    u64 P = 1;
-    for (int k = 0; k < np; k++) P = mulmod(P, ps[k] % m, m);
-    return mulmod(submod(P, 1 % m, m), invmod(2, m), m);
-}
-
-/* ModDown, rounding: floor((u + H) / P) with H = (P - 1) / 2, up to the
- * multiple of P that the fast base conversion may add:
- *   u~ = u + [H] on every limb,  out_i = (u~_i - Conv_{P->Q}([u~]_P)_i) * P^-1.
+/* ModDown with the centred fast base conversion: with
+ *   y_k = [u_k (P/p_k)^-1]_{p_k} taken in (-p_k/2, p_k/2],
+ *   Conv'(u)_i = sum_k y_k (P/p_k) mod q_i   (= [u]_P + e P, |e| <= K/2),
+ * out_i = (u_i - Conv'(u)_i) * P^-1 mod q_i.  As integers out = (u - Conv')/P,
+ * whose distance to u/P is minus S = sum_k y_k / p_k: centred, so the error
+ * has mean zero (the plain conversion, y_k in [0, p_k), gives mean -K/2,
+ * and that constant bias in c1 is amplified at decryption at the slots near
+ * 1).  Conv' is the plain conversion minus c P, c = #{k : y_k > p_k/2}.
  * in: [nq + np][n] with the q-limbs first, out: [nq][n]. */
 void ref_moddown(const u64 *in, int nq, const u64 *q_primes, int np,
                  const u64 *p_primes, u64 *out, int n)
 {
     u64 *conv = (u64 *)malloc(sizeof(u64) * (size_t)nq * (size_t)n);
-    u64 *up = (u64 *)malloc(sizeof(u64) * (size_t)np * (size_t)n);
+    int *c = (int *)calloc((size_t)n, sizeof(int));
+    ref_base_convert(in + (size_t)nq * n, np, p_primes, conv, nq, q_primes, n);
     for (int k = 0; k < np; k++) {
-        u64 pk = p_primes[k], hk = half_mod(p_primes, np, pk);
+        u64 pk = p_primes[k], h = 1;
+        for (int j = 0; j < np; j++) if (j != k) h = mulmod(h, p_primes[j] % pk, pk);
+        u64 hinv = invmod(h, pk);
         for (int x = 0; x < n; x++)
-            up[(size_t)k * n + x] = addmod(in[(size_t)(nq + k) * n + x], hk, pk);
+            if (mulmod(in[(size_t)(nq + k) * n + x], hinv, pk) > pk / 2) c[x]++;
     }
-    ref_base_convert(up, np, p_primes, conv, nq, q_primes, n);
     for (int i = 0; i < nq; i++) {
         u64 qi = q_primes[i];
         u64 P = 1;
         for (int k = 0; k < np; k++) P = mulmod(P, p_primes[k] % qi, qi);
         u64 pinv = invmod(P, qi);
-        u64 hi = half_mod(p_primes, np, qi);
         for (int x = 0; x < n; x++) {
-            u64 d = submod(addmod(in[(size_t)i * n + x], hi, qi), conv[(size_t)i * n + x], qi);
+            u64 cv = submod(conv[(size_t)i * n + x], mulmod((u64)c[x], P, qi), qi);
+            u64 d = submod(in[(size_t)i * n + x], cv, qi);
             out[(size_t)i * n + x] = mulmod(d, pinv, qi);
         }
     }
-    free(up);
+    free(c);
     free(conv);
 }
 

@@ -164,6 +164,11 @@ static ConvTab make_conv(const fg_ctx &c, const std::vector<int> &in_p, const st
     for (int t = 0; t < T.n_out; t++) {
         T.out_p[t] = out_p[t];
         T.out_l[t] = out_l[t];
+        const u64 p = c.primes[out_p[t]];
+        u64 B = 1;   // B mod p
+        for (int j = 0; j < T.n_in; j++) B = hm::mulmod(B, c.primes[in_p[j]] % p, p);
+        const u64 nb = hm::to_mont((p - B) % p, p);
+        T.negb[t] = (nb & 0x3FFFFFFFull) | ((nb >> 30) << 32);
     }
     return T;
 }
@@ -210,6 +215,8 @@ const ConvTab *fg_ctx::moddown_tab(int level)
         op.push_back(i);
         ol.push_back(i);
     }
+    // the centred conversion adds one product (c times -P) to the K inputs
+    FG_CHECK(np <= 7, FG_EINVAL, "ModDown conversion: at most 7 special primes");
     ConvTab h = make_conv(*this, ip, il, op, ol);
     ConvTab *d = nullptr;
     CUDA_TRY(cudaMalloc(&d, sizeof(ConvTab)));
@@ -275,8 +282,8 @@ const u64 *fg_ctx::moddown_rescale_tab(int level)
     return d;
 }
 
-// the offset of the rounded ModDown-then-rescale, H = (P - 1) / 2 +
-// P (q_l - 1) / 2, mod q_0..q_l
+// the offset of the rounded rescale that follows a ModDown, seen before the
+// division by P: H = P (q_l - 1) / 2, mod q_0..q_l
 const u64 *fg_ctx::moddown_rescale_half_tab(int level)
 {
     auto it = mdr_half_tabs.find(level);
@@ -287,8 +294,7 @@ const u64 *fg_ctx::moddown_rescale_half_tab(int level)
         const u64 q = primes[i];
         u64 P = 1;
         for (int k = 0; k < np; k++) P = hm::mulmod(P, primes[nq + k] % q, q);
-        const u64 hp = hm::mulmod((P + q - 1) % q, hm::invmod(2, q), q);
-        h[i] = (hp + hm::mulmod(P, hl % q, q)) % q;
+        h[i] = hm::mulmod(P, hl % q, q);
     }
     u64 *d = nullptr;
     CUDA_TRY(cudaMalloc(&d, h.size() * 8));
@@ -502,17 +508,6 @@ int fg_ctx_create(const fg_params *prm, void *cuda_stream, fg_ctx **out)
         CUDA_TRY(cudaMemcpy(dpm, pm.data(), pm.size() * 8, cudaMemcpyHostToDevice));
         g_pmodq[ctx] = dpm;
         ctx->d_pmodq = dpm;
-        // (P - 1) / 2 mod every prime: the offset that makes ModDown round
-        // (P is odd: (P - 1) / 2 = (P - 1) 2^-1 mod m)
-        std::vector<u64> hp(KL);
-        for (int j = 0; j < KL; j++) {
-            const u64 m = ctx->primes[j];
-            u64 P = 1;
-            for (int k = 0; k < ctx->np; k++) P = hm::mulmod(P, ctx->primes[ctx->nq + k] % m, m);
-            hp[j] = hm::mulmod((P + m - 1) % m, hm::invmod(2, m), m);
-        }
-        CUDA_TRY(cudaMalloc(&ctx->d_halfp, hp.size() * 8));
-        CUDA_TRY(cudaMemcpy(ctx->d_halfp, hp.data(), hp.size() * 8, cudaMemcpyHostToDevice));
         std::vector<int> ids = iota(KL);
         int *dpi = nullptr;
         CUDA_TRY(cudaMalloc(&dpi, ids.size() * sizeof(int)));
@@ -545,7 +540,6 @@ int fg_ctx_destroy(fg_ctx *ctx)
     cudaFree(ctx->d_fwd_rows);
     cudaFree(ctx->d_inv_rows);
     cudaFree(ctx->d_ninv);
-    cudaFree(ctx->d_halfp);
     for (auto &kv : ctx->conv_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->rescale_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->pinv_tabs) cudaFree(kv.second);

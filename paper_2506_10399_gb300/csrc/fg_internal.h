@@ -80,6 +80,7 @@ struct ConvTab {
     int out_p[72], out_l[72]; // prime index and limb position of each output
     u64 hinv[8], hinv_s[8];   // (B/b_k)^-1 mod b_k and its Shoup companion
     u64 hmod[8][72];          // (B/b_k) mod out prime, Montgomery form, 30-bit halves (lo | hi << 32)
+    u64 negb[72];             // -B mod out prime, same form (the centred conversion's correction)
 };
 
 struct fg_ctx {
@@ -103,7 +104,6 @@ struct fg_ctx {
     void *d_inv_rows = nullptr;
     u64 *d_ninv = nullptr;            // [nq+np][2] N^-1 and Shoup
     u64 *d_pmodq = nullptr;           // [nq][2] P mod q_i and Shoup
-    u64 *d_halfp = nullptr;           // [nq + np] ((P - 1) / 2) mod each prime (rounded ModDown)
     std::vector<u64> h_qneg, h_r2, h_ones;
 
     // cached RNS constant tables, keyed by (kind, level, digit)
@@ -111,7 +111,7 @@ struct fg_ctx {
     std::map<int, u64 *> rescale_tabs;   // level -> [level][2] q_l^-1 mod q_i + Shoup
     std::map<int, u64 *> pinv_tabs;      // level -> [level+1][2] P^-1 mod q_i + Shoup
     std::map<int, u64 *> mdr_tabs;       // level -> [level][2] (P q_l)^-1 mod q_i + Shoup
-    std::map<int, u64 *> mdr_half_tabs;  // level -> [level+1] H mod q_i, H = (P-1)/2 + P (q_l-1)/2
+    std::map<int, u64 *> mdr_half_tabs;  // level -> [level+1] P (q_l - 1)/2 mod q_i (rounded rescale)
 
     // instrumentation: kernel launch count, and CUDA-event timing of every
     // launch of one kernel class with its algorithmic bytes

@@ -847,32 +847,39 @@ __global__ void k_rescale_finish(u64 *ct, int ls, const u64 *rr, int level,
 // the table hold 30-bit halves: at most 8 products per partial sum, and the
 // total below 8 2^60 p keeps its high word below p for the Montgomery step.
 template <int NMAX>
-__device__ __forceinline__ u64 conv_point(const ConvTab &T, const u64 *y, int t, const PrimeC &P)
+__device__ __forceinline__ u64 conv_point(const ConvTab &T, const u64 *y, int t, const PrimeC &P,
+                                          int c = 0)
 {
     static_assert(NMAX <= 8, "at most 8 inputs per conversion");
     u64 a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
     for (int k = 0; k < NMAX; k++)
         if (k < T.n_in) mac_split(a0, a1, a2, y[k], T.hmod[k][t]);
+    // centred conversion: c B subtracted (c <= 7: the product adds below
+    // 2^34 to the partial sums, within the 8-term bound for K <= 7)
+    if (c) mac_split(a0, a1, a2, (u64)c, T.negb[t]);
     u64 hi = 0, lo = 0;
     fold30(hi, lo, a0, a1, a2);
     return redc(hi, lo, P);
 }
 
-// off (optional, by prime index): a constant added to every input residue
-// first (ModDown adds (P - 1) / 2 there so that it rounds)
+// returns the number of inputs y_k above b_k / 2: taking those as y_k - b_k
+// centres the conversion (see k_moddown_conv)
 template <int NMAX>
-__device__ __forceinline__ void conv_inputs(const ConvTab &T, const u64 *src, size_t limb_stride,
-                                            u64 *y, const PrimeC *__restrict__ primes,
-                                            const u64 *__restrict__ off = nullptr)
+__device__ __forceinline__ int conv_inputs(const ConvTab &T, const u64 *src, size_t limb_stride,
+                                           u64 *y, const PrimeC *__restrict__ primes)
 {
+    int c = 0;
 #pragma unroll
     for (int k = 0; k < NMAX; k++)
         if (k < T.n_in) {
-            u64 v = src[(size_t)T.in_l[k] * limb_stride];
-            if (off) v += off[T.in_p[k]];   // v < 2^62 + 2^60: Shoup's lazy product takes any word
-            y[k] = split30(shoup_mul(v, T.hinv[k], T.hinv_s[k], primes[T.in_p[k]].q));
+            const u64 v = src[(size_t)T.in_l[k] * limb_stride];
+            const u64 b = primes[T.in_p[k]].q;
+            const u64 yk = shoup_mul(v, T.hinv[k], T.hinv_s[k], b);
+            c += yk > (b >> 1);
+            y[k] = split30(yk);
         }
+    return c;
 }
 
 // ModUp conversion.  c1c: [ncol][nl][N] coefficient domain (nl = level+1);
@@ -897,25 +904,26 @@ k_modup_conv(const u64 *__restrict__ c1c, int nl, u64 *digits, int beta, int E,
 
 // ModDown conversion P -> q_0..q_level.  u: [npoly][E][N] (P limbs in the
 // coefficient domain at positions level+1..), conv: [npoly][level+1][N].
-// The ModDown rounds: floor((u + H) / P), H = (P - 1) / 2.  H is added to
-// the special limbs before the conversion and, on the limbs of Q, folded
-// into what the finish subtracts: conv_i - [H]_{q_i}.
+// The ModDown's conversion is centred: y_k = [u_k (P/p_k)^-1]_{p_k} taken
+// in (-p_k/2, p_k/2], i.e. the plain conversion minus c P with c the number
+// of y_k above p_k/2.  Then (u - Conv)/P differs from u/P by minus
+// sum_k y_k / p_k, which has mean zero; the plain conversion (y_k in
+// [0, p_k)) biases every coefficient by -K/2, and in c1 decryption
+// multiplies that bias by s and amplifies it at the slots near 1.
 template <int NMAX>
 __global__ void __launch_bounds__(256)
 k_moddown_conv(const u64 *__restrict__ u, int E, u64 *conv, int nl,
-               const ConvTab *__restrict__ tab, const u64 *__restrict__ halfp,
-               const PrimeC *__restrict__ primes, int N)
+               const ConvTab *__restrict__ tab, const PrimeC *__restrict__ primes, int N)
 {
     const int poly = blockIdx.y;
     const ConvTab &T = *tab;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= N) return;
     u64 y[NMAX];
-    conv_inputs<NMAX>(T, u + (size_t)poly * E * N + x, N, y, primes, halfp);
+    const int c = conv_inputs<NMAX>(T, u + (size_t)poly * E * N + x, N, y, primes);
     for (int t = 0; t < T.n_out; t++) {
         const PrimeC P = primes[T.out_p[t]];
-        conv[((size_t)poly * nl + T.out_l[t]) * N + x] =
-            sub_mod(conv_point<NMAX>(T, y, t, P), halfp[T.out_p[t]], P.q);
+        conv[((size_t)poly * nl + T.out_l[t]) * N + x] = conv_point<NMAX>(T, y, t, P, c);
     }
 }
 
@@ -1324,34 +1332,35 @@ k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
 // rescale drops), the rescaled limbs are
 //   ((ext_i - conv_i) P^-1 - [o_l]_{q_i}) q_l^-1 = (ext_i - (conv_i + P o_l)) (P q_l)^-1,
 // so one forward NTT of w_i = conv_i + P o_l mod q_i per kept limb replaces
-// the NTT of conv_i and the rescale's NTT of [o_l]_{q_i}.  Both steps round
-// (ModDown adds (P - 1) / 2, the rescale (q_l - 1) / 2): the pair adds
-// H = (P - 1) / 2 + P (q_l - 1) / 2 to ext, which reaches the special limbs
-// as (P - 1) / 2, limb l through o_l, and the kept limbs as w_i - [H]_{q_i}.
+// the NTT of conv_i and the rescale's NTT of [o_l]_{q_i}.  The conversion
+// is centred (see k_moddown_conv) and the rescale rounds: its offset
+// (q_l - 1) / 2, seen before the division by P, is H = P (q_l - 1) / 2,
+// which vanishes on the special limbs, enters limb l through o_l and the
+// kept limbs as w_i - [H]_{q_i}.
 // ext: [npoly][E][N], limbs l and l+1.. in the coefficient domain;
 // w: [npoly][l][N] coefficient domain.
 template <int NMAX>
 __global__ void __launch_bounds__(256)
 k_moddown_rescale_conv(const u64 *__restrict__ ext, int E, u64 *w, int l,
                        const ConvTab *__restrict__ tab, const u64 *__restrict__ pinv,
-                       const u64 *__restrict__ pmodq, const u64 *__restrict__ halfp,
-                       const u64 *__restrict__ hq, const PrimeC *__restrict__ primes, int N)
+                       const u64 *__restrict__ pmodq, const u64 *__restrict__ hq,
+                       const PrimeC *__restrict__ primes, int N)
 {
     const int poly = blockIdx.y;
     const ConvTab &T = *tab;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= N) return;
     u64 y[NMAX];
-    conv_inputs<NMAX>(T, ext + (size_t)poly * E * N + x, N, y, primes, halfp);
+    const int c = conv_inputs<NMAX>(T, ext + (size_t)poly * E * N + x, N, y, primes);
     const PrimeC Pl = primes[l];
-    // hq[i] = [H]_{q_i}, H = (P - 1) / 2 + P (q_l - 1) / 2
+    // hq[i] = [H]_{q_i}, H = P (q_l - 1) / 2
     const u64 el = add_mod(ext[((size_t)poly * E + l) * N + x], hq[l], Pl.q);
-    const u64 ol = shoup_mul(sub_mod(el, conv_point<NMAX>(T, y, l, Pl), Pl.q), pinv[2 * l],
+    const u64 ol = shoup_mul(sub_mod(el, conv_point<NMAX>(T, y, l, Pl, c), Pl.q), pinv[2 * l],
                              pinv[2 * l + 1], Pl.q);
     for (int t = 0; t < l; t++) {
         const PrimeC P = primes[t];
         w[((size_t)poly * l + t) * N + x] =
-            sub_mod(add_mod(conv_point<NMAX>(T, y, t, P), shoup_mul(ol, pmodq[2 * t], pmodq[2 * t + 1], P.q),
+            sub_mod(add_mod(conv_point<NMAX>(T, y, t, P, c), shoup_mul(ol, pmodq[2 * t], pmodq[2 * t + 1], P.q),
                             P.q), hq[t], P.q);
     }
 }
@@ -1730,7 +1739,7 @@ void rotate_mac(fg_ctx *ctx, const KeyDev &key, const u64 *lane, int ls, int nco
     KTimer kt(ctx, "moddown_conv", (double)2 * ncol * (ctx->np + nl) * N * 8);
 #define FG_LAUNCH(M)                                                                       \
     k_moddown_conv<M><<<g2, 256, 0, ctx->stream>>>(u, E, conv, nl, ctx->moddown_tab(level),   \
-                                                   ctx->d_halfp, ctx->d_primes, N)
+                                                   ctx->d_primes, N)
     FG_NIN_DISPATCH(ctx->np, FG_LAUNCH)
 #undef FG_LAUNCH
     check_launch("moddown_conv");
@@ -1884,7 +1893,6 @@ void moddown_rescale_to_lane(fg_ctx *ctx, u64 *ext, int ncol, int level, u64 *ou
 #define FG_LAUNCH(M)                                                                        \
         k_moddown_rescale_conv<M><<<g2, 256, 0, ctx->stream>>>(ext, E, w, l, ctx->moddown_tab(level), \
                                                                ctx->pinv_tab(level), ctx->d_pmodq,  \
-                                                               ctx->d_halfp,                        \
                                                                ctx->moddown_rescale_half_tab(level), \
                                                                ctx->d_primes, N)
         FG_NIN_DISPATCH(ctx->np, FG_LAUNCH)
