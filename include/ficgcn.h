@@ -68,7 +68,7 @@ typedef struct fg_plan fg_plan;
  * Primes: for each bit size, in the order q_bits then p_bits, the largest
  * prime below 2^bits that is 1 mod 2N and not taken before.  alpha primes
  * form one key-switching digit (hybrid key switching).  10 <= log_n <= 16,
- * 2 <= n_q <= 60, 1 <= n_p <= 8, bit sizes in [log_n + 2, 60], at most 16
+ * 2 <= n_q <= 60, 1 <= n_p <= 7, bit sizes in [log_n + 2, 60], at most 16
  * digits (ceil(n_q / alpha)). */
 typedef struct {
     int log_n;
@@ -337,18 +337,20 @@ int fg_poly_mul(fg_ctx *ctx, const uint64_t *a, const uint64_t *b, int level, ui
 
 /* The same product as fg_poly_mul, for callers that cannot allocate device
  * memory during the call: serving threads that must not block on or fail
- * in cudaMalloc, code whose device memory is owned by a host framework or
- * pool, and code running while a stream is captured (where cudaMalloc and
- * cudaFree are not allowed).  The paper has no counterpart; this is a
- * deployment aid.  a, b, c: DEVICE buffers [level+1][N] (host pointers are
- * rejected with FG_EINVAL); requires (level+1) * N <= 2^18 words
- * (FG_EINVAL otherwise).  Scratch comes from one 4 MiB array compiled into
- * the library, resident on every GPU that loads it until the process exits;
- * no cudaMalloc, cudaFree or other allocating routine is called.  The first
- * call on each device looks up that array's device address (make that first
- * call before any stream capture).  Every call shares the array, so calls
- * that overlap on the GPU (other streams, other threads) race; nothing in it
- * needs clearing, since each call writes all the scratch it reads. */
+ * in cudaMalloc (it can synchronise the device and run out of memory at any
+ * time), and code whose device memory is owned and accounted by a host
+ * framework or pool.  The paper has no counterpart; this is a deployment
+ * aid.  a, b, c: DEVICE buffers [level+1][N] on the context's GPU (host
+ * pointers and other GPUs' memory are rejected with FG_EINVAL); requires
+ * (level+1) * N <= 2^18 words (FG_EINVAL otherwise).  Scratch comes from
+ * one 4 MiB array compiled into the library, resident on every GPU that
+ * loads it until the process exits; no cudaMalloc, cudaFree or other
+ * allocating routine is called.  The first call for a context's GPU looks
+ * up that array's device address on that GPU (make that first call before
+ * any stream capture).  The call returns when c holds the product, like
+ * fg_poly_mul.  Every call shares the array, so calls that overlap on the
+ * GPU (other streams, other threads) race; nothing in it needs clearing,
+ * since each call writes all the scratch it reads. */
 int fg_poly_mul_noalloc(fg_ctx *ctx, const uint64_t *a, const uint64_t *b, int level,
                         uint64_t *c);
 

@@ -11,11 +11,14 @@ Modules
   _ref      ctypes binding of the exact-integer core (ckks_ref.c)
   ckks      parameters, encode/decode, keys, encryption, rotation, rescale
   planner   latency-aware packing, AOO shifts, SpIntra-CA lanes and masks
-  layer     the encrypted A.X.W layer executed step by step on a plan
+  layer     the encrypted A.X.W layer executed step by step on a plan, in
+            the paper's step order and in the double-hoisted form
+  noo       node order optimisation (Alg. 1)
+  mlp       the learned planner's latency model in FP64
 
-Parity status: every function is pinned by tests/test_oracle_*.py except the
-NOO region reordering, which the oracle does not implement (its output, a
-node order, is an input to parity, never a parity target).
+Parity status: every function is pinned by tests/test_oracle_*.py and
+tests/test_noo.py; the NOO heuristic's output (a node order) is an input to
+parity, never a parity target.
 """
 import os
 import subprocess

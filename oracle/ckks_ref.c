@@ -4,7 +4,7 @@
  * This is the oracle's exact-integer core: plain, slow and meant to be read
  * against the definitions.  Nothing in the library links or calls it; only
  * the tests, the smoke check and the CPU-baseline leg of the benchmark load
- * it (through ctypes, see ckks_oracle.py).
+ * it (through ctypes, see _ref.py).
  *
  * Conventions
  *   - A polynomial over a list of primes is stored limb-major:

@@ -17,7 +17,7 @@ std::string g_create_err = "no context";
 
 namespace {
 
-constexpr int kMaxQ = 60, kMaxP = 8;
+constexpr int kMaxQ = 60, kMaxP = 7;   // the centred ModDown conversion takes one extra product term
 
 bool is_device_ptr(const void *p)
 {
@@ -421,7 +421,7 @@ int fg_ctx_create(const fg_params *prm, void *cuda_stream, fg_ctx **out)
     try {
         FG_CHECK(prm->log_n >= 10 && prm->log_n <= 16, FG_EINVAL, "log_n must be in [10, 16]");
         FG_CHECK(prm->n_q >= 2 && prm->n_q <= kMaxQ && prm->q_bits, FG_EINVAL, "n_q must be in [2, 60]");
-        FG_CHECK(prm->n_p >= 1 && prm->n_p <= kMaxP && prm->p_bits, FG_EINVAL, "n_p must be in [1, 8]");
+        FG_CHECK(prm->n_p >= 1 && prm->n_p <= kMaxP && prm->p_bits, FG_EINVAL, "n_p must be in [1, 7]");
         FG_CHECK(prm->alpha >= 1 && prm->alpha <= 8, FG_EINVAL, "alpha must be in [1, 8]");
         FG_CHECK(prm->log_scale > 0 && prm->log_scale < 62, FG_EINVAL, "bad log_scale");
         ctx->log_n = prm->log_n;

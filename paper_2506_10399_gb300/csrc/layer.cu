@@ -287,7 +287,7 @@ static void host_plan(const fg_params *prm, const int32_t *row_ptr, const int32_
                       const fg_plan_opts *opts, fg_ctx &c, fg_plan &pl)
 {
     FG_CHECK(prm->log_n >= 10 && prm->log_n <= 16 && prm->n_q >= 2 && prm->n_q <= 60 &&
-                 prm->n_p >= 1 && prm->n_p <= 8 && prm->q_bits && prm->p_bits,
+                 prm->n_p >= 1 && prm->n_p <= 7 && prm->q_bits && prm->p_bits,
              FG_EINVAL, "bad parameters");
     c.log_n = prm->log_n;
     c.n = 1 << prm->log_n;

@@ -3,12 +3,12 @@
 // Some callers cannot allocate device memory at the moment they call into
 // the library: a serving thread that must not block or fail on cudaMalloc
 // (cudaMalloc may synchronise the device and can run out of memory at any
-// time), code whose device memory is owned and accounted by a host framework
-// or pool, and code that runs while a stream is being captured, where
-// cudaMalloc/cudaFree are not allowed.  fg_poly_mul needs scratch for the
-// transformed operands and takes it from the context's workspace, which
-// grows with cudaMalloc on first use.  fg_poly_mul_noalloc does the same
-// product with its scratch in a fixed array compiled into the library.
+// time), and code whose device memory is owned and accounted by a host
+// framework or pool that forbids allocations behind its back.  fg_poly_mul
+// needs scratch for the transformed operands and takes it from the
+// context's workspace, which grows with cudaMalloc on first use.
+// fg_poly_mul_noalloc does the same product with its scratch in a fixed
+// array compiled into the library.
 //
 // The array below lives in every GPU that loads the library, for as long as
 // the process runs.  Host code cannot use its name as a device address (the
@@ -31,15 +31,20 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 u64 *g_noalloc_ptr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device.  The first
-// call on a device does the lookup; later calls reuse it.
+// Device address of the scratch array on `device`.  The first call for a
+// device makes that device current, looks the address up and restores the
+// caller's device; later calls reuse the address.
 u64 *noalloc_scratch(int device)
 {
     FG_CHECK(device >= 0 && device < kMaxDevices, FG_EINVAL, "device index out of range");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_ptr[device]) {
+        int prev = 0;
+        CUDA_TRY(cudaGetDevice(&prev));
+        CUDA_TRY(cudaSetDevice(device));
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        cudaSetDevice(prev);
         if (e != cudaSuccess)
             throw fg_error(FG_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         g_noalloc_ptr[device] = (u64 *)p;
@@ -47,14 +52,15 @@ u64 *noalloc_scratch(int device)
     return g_noalloc_ptr[device];
 }
 
-bool on_device(const void *p)
+// true when p is device (or managed) memory of GPU `device`
+bool on_device(const void *p, int device)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == device;
 }
 
 }  // namespace
@@ -68,10 +74,9 @@ extern "C" int fg_poly_mul_noalloc(fg_ctx *ctx, const uint64_t *a, const uint64_
         const int N = ctx->n, nl = level + 1;
         FG_CHECK((size_t)nl * N <= kNoAllocWords, FG_EINVAL,
                  "fg_poly_mul_noalloc: (level + 1) * N exceeds 2^18 words");
-        FG_CHECK(a && b && c && on_device(a) && on_device(b) && on_device(c), FG_EINVAL,
-                 "fg_poly_mul_noalloc takes device pointers only");
-        int dev = 0;
-        CUDA_TRY(cudaGetDevice(&dev));
+        const int dev = ctx->device;
+        FG_CHECK(a && b && c && on_device(a, dev) && on_device(b, dev) && on_device(c, dev), FG_EINVAL,
+                 "fg_poly_mul_noalloc takes device pointers on the context's GPU only");
         u64 *ta = noalloc_scratch(dev);
         u64 *tb = ta + kNoAllocWords;
         // every scratch word read below is written first by the forward
