@@ -58,18 +58,28 @@ def combination(params, plan, cts_in, keys, pts, column):
     return z
 
 
-def group_step_double_hoisted(params, plan, grp, lanes, keys, pts):
+def _map(pool, fn, items):
+    """fn over items, in a thread pool when one is given (the oracle's C core
+    releases the interpreter lock); the results come back in item order."""
+    items = list(items)
+    return list(pool.map(fn, items)) if pool is not None else [fn(x) for x in items]
+
+
+def group_step_double_hoisted(params, plan, grp, lanes, keys, pts, pool=None):
     """One SpIntra-CA group in the double-hoisted form: the outputs before
     their rescale ({dst: ct at grp.level}) and the extended-basis sums
-    ({dst: [2][l+1+K][N]}) that were key-switched down."""
+    ({dst: [2][l+1+K][N]}) that were key-switched down.  pool: optional
+    executor for the independent key switches and term products (sums are
+    taken in term order either way)."""
     lv = grp.level
     assert all(ckks.level_of(c) == lv for c in lanes)
     qs = params.q[:lv + 1]
     ext_primes = params.ext_primes(lv)
     need = sorted({a for (a, _) in grp.rotations})
-    digits = {a: ckks.modup(params, lanes[a][1], lv) for a in need}
-    ks = {(a, k): ckks.keyswitch_ext(params, lanes[a], k, keys[k % plan.M], digits[a])
-          for (a, k) in grp.rotations}
+    digits = dict(zip(need, _map(pool, lambda a: ckks.modup(params, lanes[a][1], lv), need)))
+    ks = dict(zip(grp.rotations, _map(
+        pool, lambda r: ckks.keyswitch_ext(params, lanes[r[0]], r[1], keys[r[1] % plan.M], digits[r[0]]),
+        grp.rotations)))
     ext = {}    # output -> extended-basis sum of Mask (x) u
     norm = {}   # output -> sum of Mask (x) phi_g(c0) and Mask (x) kept lane
 
@@ -77,18 +87,21 @@ def group_step_double_hoisted(params, plan, grp, lanes, keys, pts):
         d[key] = val if key not in d else np.stack(
             [ckks.add_res(d[key][0], val[0], primes), ckks.add_res(d[key][1], val[1], primes)])
 
-    for tm in grp.terms:
+    def products(tm):
         m = pts[tm.mask]
         if tm.k == 0:
-            add_into(norm, tm.dst, ckks.pmult(params, m[:lv + 1], lanes[tm.src]), qs)
-        else:
-            u, c0g = ks[(tm.src, tm.k)]
-            prod = np.stack([ckks.poly_mul(params, m, u[0], ext_primes),
-                             ckks.poly_mul(params, m, u[1], ext_primes)])
-            add_into(ext, tm.dst, prod, ext_primes)
-            c0part = np.stack([ckks.poly_mul(params, m[:lv + 1], c0g, qs),
-                               np.zeros((lv + 1, params.n), dtype=np.uint64)])
-            add_into(norm, tm.dst, c0part, qs)
+            return ckks.pmult(params, m[:lv + 1], lanes[tm.src]), None
+        u, c0g = ks[(tm.src, tm.k)]
+        prod = np.stack([ckks.poly_mul(params, m, u[0], ext_primes),
+                         ckks.poly_mul(params, m, u[1], ext_primes)])
+        c0part = np.stack([ckks.poly_mul(params, m[:lv + 1], c0g, qs),
+                           np.zeros((lv + 1, params.n), dtype=np.uint64)])
+        return c0part, prod
+
+    for tm, (qpart, extpart) in zip(grp.terms, _map(pool, products, grp.terms)):
+        add_into(norm, tm.dst, qpart, qs)
+        if extpart is not None:
+            add_into(ext, tm.dst, extpart, ext_primes)
     outs = {}
     for dst in set(ext) | set(norm):
         o = ckks.moddown_ct(params, ext[dst]) if dst in ext else None
@@ -133,7 +146,7 @@ def close_group(params, grp, outs, acc):
     return lanes, acc
 
 
-def aggregation(params, plan, z, keys, pts, plain=False):
+def aggregation(params, plan, z, keys, pts, plain=False, pool=None):
     """SpIntra-CA on one column ciphertext z (step 2), double hoisted (the
     library's form) or, with plain set, in the paper's step order."""
     lanes = [z]
@@ -142,17 +155,18 @@ def aggregation(params, plan, z, keys, pts, plain=False):
         if plain:
             outs = group_step_plain(params, plan, grp, lanes, keys, pts)
         else:
-            outs, _ = group_step_double_hoisted(params, plan, grp, lanes, keys, pts)
+            outs, _ = group_step_double_hoisted(params, plan, grp, lanes, keys, pts, pool)
         lanes, acc = close_group(params, grp, outs, acc)
     return acc
 
 
-def layer_axw(params, plan, cts_in, keys, pts, columns=None, plain=False):
+def layer_axw(params, plan, cts_in, keys, pts, columns=None, plain=False, pool=None):
     """Output ciphertexts (one per output column) of the layer; plain selects
-    the paper's step order for the SpIntra-CA groups (see aggregation)."""
+    the paper's step order for the SpIntra-CA groups (see aggregation), pool
+    an optional thread pool for the double-hoisted form."""
     cols = range(plan.Fp) if columns is None else columns
     return [aggregation(params, plan, combination(params, plan, cts_in, keys, pts, j),
-                        keys, pts, plain=plain) for j in cols]
+                        keys, pts, plain=plain, pool=pool) for j in cols]
 
 
 def inter_ca_layer(params, plan, copies, pts, columns=None):

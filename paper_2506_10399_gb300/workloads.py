@@ -262,3 +262,19 @@ def random_order(V, size, seed):
 
 def identity_order(V):
     return np.arange(V, dtype=np.int64)
+
+
+def random_words(primes, n, seed):
+    """Uniform residues [len(primes)][n] (uint64), one row per prime: stand-in
+    ciphertext limbs for word-for-word comparisons, where the values need no
+    meaning.  numpy's PCG64 stream is the same on every platform."""
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.integers(0, int(q), n, dtype=np.uint64) for q in primes])
+
+
+def random_small_poly(n, bits, seed):
+    """Integer coefficients uniform in [-2^bits, 2^bits] (int64): a stand-in
+    plaintext given by its integers, so that both sides derive the same
+    residues on any platform (no floating-point encoding in between)."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(-(1 << bits), (1 << bits) + 1, n, dtype=np.int64)
