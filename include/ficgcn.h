@@ -243,6 +243,29 @@ int fg_plan_build_inter(fg_ctx *ctx, const int32_t *nbr, const double *wts, int 
                         const double *W, int F, int Fp, const int32_t *perm,
                         const fg_plan_opts *opts, fg_plan **out);
 
+/* Aggregation mode of one layer (paper Sec. 3.4 "Selecting Aggregation
+ * Mode", App. B.2, Table 1), host only like fg_plan_dry_run.  The
+ * SpIntra-CA plan of (params, A-hat, W, perm, opts) is built and its
+ * rotations R and masked terms T per output column counted; with n node
+ * arrangements (n_copies: the largest row length of A-hat for the exact
+ * layer, 1 + the sample size for GraphSage), F input columns and t columns
+ * per ciphertext, the costs per output column are
+ *   cost[0] SpIntra-CA = (ceil(F/t) + T)(L_pmult + L_add) + (ceil(log2 t) + R) L_rot,
+ *   cost[1] Inter-CA   = (n ceil(F/t) + n)(L_pmult + L_add) + ceil(log2 t) L_rot,
+ * lat = {L_rot, L_pmult, L_add} (measured; the paper assumes 20, 1, 1).
+ * The dry-run counts replace the paper's estimate 10 c n log^2 V, whose
+ * factor c it leaves open.  *mode: the first layer (layer 0) is Inter-CA
+ * (the client encrypts its copies offline) unless its input, n ceil(F/t)
+ * ciphertexts, exceeds max_inter_cts (0 = no limit); any other layer takes
+ * the cheaper mode, ties to SpIntra-CA.  counts (may be NULL) = {R, T,
+ * n ceil(F/t), ceil(log2 t)}.  FG_EINVAL / FG_ELEVEL as fg_plan_dry_run. */
+#define FG_MODE_SPINTRA 0
+#define FG_MODE_INTER 1
+int fg_select_mode(const fg_params *params, const int32_t *row_ptr, const int32_t *col,
+                   const double *val, int V, const double *W, int F, int Fp, const int32_t *perm,
+                   const fg_plan_opts *opts, int layer, int n_copies, const double lat[3],
+                   double max_inter_cts, int *mode, double cost[2], int64_t counts[4]);
+
 /* Plan statistics for the learned planner (host only, like
  * fg_plan_dry_run): feat[FG_PLAN_FEATURES] = log2 V, log2 F, mean row
  * length of A-hat, log2(1 + max row length), log2 t, radix bits, mean bit

@@ -363,3 +363,50 @@ def build_inter_plan(params, in_level, nbr, wts, V, W, perm):
         plan.masks.append(Mask(level=in_level - 1, values=vals))
     plan.out_level = in_level - 2
     return plan
+
+
+# ----------------------------------------------------------------------
+# aggregation mode of a layer (Sec. 3.4 "Selecting Aggregation Mode",
+# App. B.2, Table 1)
+# ----------------------------------------------------------------------
+SPINTRA, INTER = 0, 1
+
+
+def mode_costs(F, t, n, R, T, lat=(20.0, 1.0, 1.0)):
+    """Latency of one output column in each mode, from Table 1's operation
+    counts: Inter-CA applies the combination to each of the n node
+    arrangements (n ceil(F/t) PMult + Add), sums the n masked copies (n PMult
+    + Add) and needs ceil(log2 t) Rot for the packing; SpIntra-CA applies the
+    combination once (ceil(F/t) PMult + Add), the same ceil(log2 t) Rot, and
+    its plan's R rotations and T masked terms (PMult + Add each).
+    lat = (L_rot, L_pmult, L_add).  Returns (SpIntra-CA, Inter-CA)."""
+    l_rot, l_pm, l_add = lat
+    nb = -(-F // t)
+    lg = math.ceil(math.log2(t)) if t > 1 else 0
+    inter = (n * nb + n) * (l_pm + l_add) + lg * l_rot
+    spintra = (nb + T) * (l_pm + l_add) + (lg + R) * l_rot
+    return spintra, inter
+
+
+def paper_mode_estimates(F, t, n, V, c=1.0):
+    """The paper's estimates (Sec. 3.4): Inter-CA 2 ceil(F n / t), SpIntra-CA
+    10 c n log^2 V (V nodes; c in [0, 1] left open by the paper)."""
+    return 10.0 * c * n * math.log2(V) ** 2, 2 * (-(-F * n // t))
+
+
+def select_mode(plan, layer, n_copies, lat=(20.0, 1.0, 1.0), max_inter_cts=0):
+    """Mode of one layer given its SpIntra-CA plan: the first layer (0) is
+    Inter-CA, whose copies the client encrypts offline, unless its input
+    (n ceil(F/t) ciphertexts) exceeds max_inter_cts (0: no limit); a later
+    layer takes the cheaper mode of mode_costs, ties to SpIntra-CA.  The
+    plan's exact counts R, T stand in for the paper's 10 c n log^2 V.
+    Returns (mode, (SpIntra-CA cost, Inter-CA cost), (R, T))."""
+    R = sum(len(g.rotations) for g in plan.groups)
+    T = sum(len(g.terms) for g in plan.groups)
+    costs = mode_costs(plan.F, plan.t, n_copies, R, T, lat)
+    fits = max_inter_cts <= 0 or n_copies * (-(-plan.F // plan.t)) <= max_inter_cts
+    if layer == 0:
+        mode = INTER if fits else SPINTRA
+    else:
+        mode = INTER if (fits and costs[1] < costs[0]) else SPINTRA
+    return mode, costs, (R, T)

@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = ["Context", "Keys", "Plan", "FicgcnError", "ctx_create", "keygen", "load_evk",
            "encode_plain", "encrypt", "pack_features", "decrypt", "decrypt_decode",
-           "plan_build", "plan_dry_run", "gcn_layer_axw", "rotate", "rescale", "poly_mul", "ntt"]
+           "plan_build", "plan_dry_run", "select_mode", "gcn_layer_axw", "rotate", "rescale", "poly_mul", "ntt"]
 
 
 def _lib():
@@ -453,6 +453,47 @@ def plan_features(params, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=Tru
     if rc != 0:
         raise FicgcnError(rc, "plan features failed")
     return out
+
+
+MODE_SPINTRA, MODE_INTER = 0, 1
+
+
+def select_mode(params, row_ptr, col, val, W, perm, layer, n_copies, lat=(20.0, 1.0, 1.0),
+                max_inter_cts=0.0, t=0, radix_bits=0, aoo=True, min_out_level=0, n_sampled=0,
+                in_level=0):
+    """Aggregation mode of one layer (host only): (mode, {"spintra": cost,
+    "inter": cost}, {"rotations", "terms", "inter_inputs", "log_t"}).
+    lat = (L_rot, L_pmult, L_add)."""
+    nat = _lib()
+    q_bits, p_bits = params["q_bits"], params["p_bits"]
+    qb = (ctypes.c_int * len(q_bits))(*q_bits)
+    pb = (ctypes.c_int * len(p_bits))(*p_bits)
+    prm = nat.Params(params["log_n"], len(q_bits), qb, len(p_bits), pb, params["alpha"],
+                     float(params["log_scale"]))
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    F, Fp = W.shape
+    o = nat.PlanOpts(int(t), int(radix_bits), 1 if aoo else 0, int(min_out_level), int(n_sampled),
+                     int(in_level))
+    la = np.ascontiguousarray(lat, dtype=np.float64)
+    mode = ctypes.c_int()
+    cost = np.zeros(2, np.float64)
+    cnt = np.zeros(4, np.int64)
+    rc = nat.lib.fg_select_mode(ctypes.byref(prm), ctypes.c_void_p(row_ptr.ctypes.data),
+                                ctypes.c_void_p(col.ctypes.data), ctypes.c_void_p(val.ctypes.data),
+                                row_ptr.size - 1, ctypes.c_void_p(W.ctypes.data), F, Fp,
+                                ctypes.c_void_p(perm.ctypes.data), ctypes.byref(o), int(layer),
+                                int(n_copies), ctypes.c_void_p(la.ctypes.data), float(max_inter_cts),
+                                ctypes.byref(mode), ctypes.c_void_p(cost.ctypes.data),
+                                ctypes.c_void_p(cnt.ctypes.data))
+    if rc != 0:
+        raise FicgcnError(rc, "mode selection failed")
+    return (mode.value, {"spintra": float(cost[0]), "inter": float(cost[1])},
+            {"rotations": int(cnt[0]), "terms": int(cnt[1]), "inter_inputs": int(cnt[2]),
+             "log_t": int(cnt[3])})
 
 
 class Mlp:

@@ -75,6 +75,9 @@ SIGS = {
                                     c_void_p, P(PlanOpts), P(c_void_p)]),
     "fg_plan_features": (c_int, [P(Params), c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_int,
                                  c_void_p, P(PlanOpts), c_void_p]),
+    "fg_select_mode": (c_int, [P(Params), c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_int,
+                               c_void_p, P(PlanOpts), c_int, c_int, c_void_p, c_double, P(c_int),
+                               c_void_p, c_void_p]),
     "fg_mlp_create": (c_int, [c_int, c_int, c_void_p, P(c_void_p)]),
     "fg_mlp_destroy": (c_int, [c_void_p]),
     "fg_mlp_params": (c_int, [c_void_p, c_void_p]),

@@ -301,4 +301,7 @@ void build(fg_plan &pl, const fg_ctx &ctx, const int32_t *row_ptr, const int32_t
 // copy k holding wts[v][k] at slot perm[v]
 void build_inter(fg_plan &pl, const fg_ctx &ctx, const int32_t *nbr, const double *wts, int V,
                  int n, const double *W, int F, int Fp, const int32_t *perm, const fg_plan_opts &opts);
+// aggregation mode of one layer from the SpIntra-CA plan's counts (see planner.cpp)
+void select_mode(const fg_plan &pl, int layer, int n_copies, const double lat[3], double max_inter_cts,
+                 int *mode, double cost[2], int64_t counts[4]);
 }  // namespace planner

@@ -322,6 +322,29 @@ int fg_plan_dry_run(const fg_params *prm, const int32_t *row_ptr, const int32_t 
     }
 }
 
+int fg_select_mode(const fg_params *prm, const int32_t *row_ptr, const int32_t *col,
+                   const double *val, int V, const double *W, int F, int Fp, const int32_t *perm,
+                   const fg_plan_opts *opts, int layer, int n_copies, const double lat[3],
+                   double max_inter_cts, int *mode, double cost[2], int64_t counts[4])
+{
+    if (!prm || !row_ptr || !W || !perm || !lat || !mode || !cost) return FG_EINVAL;
+    if (layer < 0 || n_copies < 1 || !(lat[0] >= 0 && lat[1] >= 0 && lat[2] >= 0)) return FG_EINVAL;
+    try {
+        fg_ctx c;
+        fg_plan pl;
+        host_plan(prm, row_ptr, col, val, V, W, F, Fp, perm, opts, c, pl);
+        int64_t cnt[4];
+        planner::select_mode(pl, layer, n_copies, lat, max_inter_cts, mode, cost, cnt);
+        if (counts)
+            for (int i = 0; i < 4; i++) counts[i] = cnt[i];
+    } catch (const fg_error &e) {
+        return e.code;
+    } catch (const std::exception &) {
+        return FG_EOOM;
+    }
+    return FG_OK;
+}
+
 int fg_plan_features(const fg_params *prm, const int32_t *row_ptr, const int32_t *col,
                      const double *val, int V, const double *W, int F, int Fp, const int32_t *perm,
                      const fg_plan_opts *opts, float *feat)

@@ -375,3 +375,49 @@ void build_inter(fg_plan &pl, const fg_ctx &ctx, const int32_t *nbr, const doubl
 }
 
 }  // namespace planner
+
+namespace planner {
+
+// Aggregation mode of one layer (paper Sec. 3.4, "Selecting Aggregation
+// Mode"; App. B.2; Table 1's operation counts).  Both modes compute the
+// combination Z = X W; they differ in how the n node arrangements of the
+// aggregation are formed.  Per output column:
+//   Inter-CA:   n ceil(F/t) PMult + Add (the combination of every copy),
+//               n PMult + Add (the masked sum over the copies),
+//               ceil(log2 t) Rot (the packing's rotate-and-sum);
+//   SpIntra-CA: ceil(F/t) PMult + Add, ceil(log2 t) + R Rot, T PMult + Add,
+//               with R rotations and T masked terms per column counted on
+//               the plan itself (a dry run), which replaces the paper's
+//               estimate 10 c n log^2 V and its unspecified factor c.
+// Cost = sum of count x latency, latencies measured per operation (the
+// paper assumes Rot = 20 PMult = 20 Add).  The first layer is Inter-CA (its
+// copies are encrypted by the client, offline), unless the client's input,
+// n ceil(F/t) ciphertexts, exceeds max_inter_cts; every other layer takes
+// the cheaper mode (ties: SpIntra-CA).
+void select_mode(const fg_plan &pl, int layer, int n_copies, const double lat[3], double max_inter_cts,
+                 int *mode, double cost[2], int64_t counts[4])
+{
+    const double lr = lat[0], lp = lat[1], la = lat[2];
+    const i64 F = pl.F, t = pl.t, n = n_copies;
+    const i64 nb = (F + t - 1) / t;
+    i64 lg = 0;
+    while ((1ll << lg) < t) lg++;
+    i64 R = 0, T = 0;
+    for (const GroupC &g : pl.groups) {
+        R += (i64)g.rots.size();
+        T += (i64)g.terms.size();
+    }
+    const double inter = (double)(n * nb + n) * (lp + la) + (double)lg * lr;
+    const double spintra = (double)(nb + T) * (lp + la) + (double)(lg + R) * lr;
+    cost[0] = spintra;
+    cost[1] = inter;
+    counts[0] = R;
+    counts[1] = T;
+    counts[2] = n * nb;   // the client's Inter-CA input ciphertexts
+    counts[3] = lg;
+    const bool fits = max_inter_cts <= 0 || (double)(n * nb) <= max_inter_cts;
+    if (layer == 0) *mode = fits ? FG_MODE_INTER : FG_MODE_SPINTRA;
+    else *mode = (fits && inter < spintra) ? FG_MODE_INTER : FG_MODE_SPINTRA;
+}
+
+}  // namespace planner
