@@ -445,11 +445,13 @@ def run_ours(args):
 def run_two_layer(args):
     """Two-layer encrypted GCN: layer 1 (F -> F'), the x^2 activation (CMult
     + relinearisation + rescale), layer 2 (F' -> C), inputs resident in HBM;
-    decrypted against FP64 A-hat (H1)^2 W2.  On the benchmark workload both
-    layers are SpIntra-CA (H1 = A-hat X W1).  On cora_like (N = 2^15, ten
-    primes: no room for two SpIntra-CA layers) the first layer runs in
-    Inter-CA mode as in the paper's models (the node and 4 sampled
-    neighbours, MEAN; H1 = sum_k w_k X[nbr_k] W1) and the second at radix 16."""
+    decrypted against FP64 A-hat (A-hat X W1)^2 W2 on the exact A-hat.  Both
+    layers are SpIntra-CA: radix 4 with the first layer's output at level 10
+    or above on the benchmark workload; radix 32 on cora_like (N = 2^15, ten
+    primes: combination 1 + 3 groups, x^2 1, combination 1 + 3 groups = 9
+    rescales, the output at level 0).  The line also reports the paper's
+    aggregation-mode selection (Sec. 3.4) for both layers, with per-operation
+    latencies measured on the first layer."""
     import torch
     import __graft_entry__
     fg = __graft_entry__.build()
@@ -458,30 +460,23 @@ def run_two_layer(args):
     c = dict(wl.CONFIGS[name])
     w = wl.config_workload(name)
     W2 = wl.second_layer_weights(name)
-    inter = name == "cora_like"
+    radix = 5 if name == "cora_like" else RADIX_BITS
+    min_out1 = 0 if name == "cora_like" else MIN_OUT_LEVEL
     t_setup = time.perf_counter()
     ctx = fg.Context(**c)
     perm = wl.random_order(w.V, ctx.slots, SEED)
-    if inter:
-        nbr, wts = wl.sample_neighbors(w, 4, SEED)
-        plan1 = fg.plan_build_inter(ctx, nbr, wts, w.W, perm)
-    else:
-        plan1 = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=1, radix_bits=RADIX_BITS,
-                              min_out_level=MIN_OUT_LEVEL)
+    plan1 = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=1, radix_bits=radix,
+                          min_out_level=min_out1)
     i1 = plan1.info()
     l1 = i1["out_level"]
-    plan2 = fg.plan_build(ctx, w.row_ptr, w.col, w.val, W2, perm, t=1,
-                          radix_bits=4 if inter else RADIX_BITS, in_level=l1 - 1)
+    plan2 = fg.plan_build(ctx, w.row_ptr, w.col, w.val, W2, perm, t=1, radix_bits=radix, in_level=l1 - 1)
     amounts = sorted(set(plan1.rotation_amounts()) | set(plan2.rotation_amounts()))
     sk, evk = fg.keygen(ctx, SEED, amounts, relin=True)
     keys = fg.load_evk(ctx, evk)
     del evk
     Fp, N = w.W.shape[1], ctx.n
     x = torch.empty((i1["n_in"], 2, ctx.nq, N), dtype=torch.int64, device="cuda")
-    if inter:
-        fg.pack_neighbor_copies(ctx, sk, SEED, w.X, nbr, perm, out=x)
-    else:
-        fg.pack_features(ctx, sk, SEED, w.X, perm, 1, out=x)
+    fg.pack_features(ctx, sk, SEED, w.X, perm, 1, out=x)
     h1 = torch.empty((Fp, 2, l1 + 1, N), dtype=torch.int64, device="cuda")
     a1 = torch.empty((Fp, 2, l1, N), dtype=torch.int64, device="cuda")
     i2 = plan2.info()
@@ -497,7 +492,7 @@ def run_two_layer(args):
     la, lb, sc = step()
     torch.cuda.synchronize()
     scale = sc * sc / ctx.q[la]
-    ref = wl.two_layer_reference(w, W2, first=wl.neighbor_reference(w, nbr, wts) if inter else None)
+    ref = wl.two_layer_reference(w, W2)
     err = 0.0
     for j in range(W2.shape[1]):
         d = fg.decrypt_decode(ctx, sk, out[j].contiguous(), lb, scale)
@@ -521,11 +516,12 @@ def run_two_layer(args):
         for k, (a, b) in enumerate(((0, 1), (1, 2), (2, 3))):
             parts[k] = parts.get(k, 0.0) + e[a].elapsed_time(e[b]) / args.steps
         tot += e[0].elapsed_time(e[3]) / args.steps
-    if inter:
+    modes = mode_selection(fg, ctx, keys, plan1, x, h1, c, w, W2, perm, radix, min_out1, l1)
+    if name == "cora_like":
         desc = ("two-layer GCN, synthetic Cora-like graph (power law 2.5, V=2708, mean degree 3.9, "
                 "F=1433 binary 1.3%, F'=16, 7 classes), CKKS N=2^15, 10 primes 60+9x40 bit, K=4 special, "
-                "dnum=3; layer 1 Inter-CA (node + 4 sampled neighbours, MEAN), x^2, layer 2 radix-16 "
-                "SpIntra-CA; seeded random node order")
+                "dnum=3; both layers radix-32 SpIntra-CA on the exact A-hat, x^2 between; "
+                "seeded random node order")
     else:
         desc = config_desc()["workload"] + "; second layer W2 16x3 Glorot, x^2 between"
     line = {"metric": "encrypted two-layer GCN latency (ms) at N=2^%d" % c["log_n"], "value": round(tot, 3),
@@ -534,9 +530,53 @@ def run_two_layer(args):
             "levels": {"layer1_out": la, "square_out": la - 1, "layer2_out": lb},
             "rotations": i1["rotations"] + i2["rotations"],
             "decrypt_max_abs_err_vs_fp64": err, "gpu_launches": (ctx.launch_count() - n0) // args.steps,
-            "setup_s": round(setup_s, 1), "config": {"workload": desc}}
+            "setup_s": round(setup_s, 1), "mode_selection": modes, "config": {"workload": desc}}
     print(json.dumps(line))
     return 0
+
+
+def mode_selection(fg, ctx, keys, plan1, x, h1, c, w, W2, perm, radix, min_out1, l1):
+    """The paper's per-layer aggregation-mode selection (Sec. 3.4) for both
+    layers, with per-operation latencies measured on layer 1: L_pmult +
+    L_add = group-MAC time per masked product, L_rot = the rest of the
+    aggregation (ModUp, key switching, ModDown, NTTs) per rotation.  n = the
+    largest row length of A-hat (the exact layer).  Inter-CA needs n node
+    arrangements of its input: the client encrypts them for layer 1 (feasible
+    while they fit a 200 GB device budget); the server holds one arrangement
+    of H1, so layer 2 has one (max_inter_cts = 1).  Returns the costs and the
+    choices."""
+    import torch
+    info = plan1.info()
+    ctx.kernel_times()
+    fg.gcn_layer_axw(ctx, keys, plan1, x, out=h1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fg.gcn_layer_axw(ctx, keys, plan1, x, out=h1)
+    e1.record()
+    torch.cuda.synchronize()
+    total = e0.elapsed_time(e1)
+    part = {}
+    for cls in ("group_mac", "comb"):
+        ctx.time_kernels(cls)
+        fg.gcn_layer_axw(ctx, keys, plan1, x, out=h1)
+        part[cls] = ctx.kernel_times()[0]
+    ctx.time_kernels(None)
+    l_pa = part["group_mac"] / max(1, info["masked_products"])
+    l_rot = (total - part["group_mac"] - part["comb"]) / max(1, info["rotations"])
+    lat = (l_rot, l_pa / 2, l_pa / 2)
+    n = w.max_degree()
+    ct_bytes = 2 * ctx.nq * ctx.n * 8
+    out = {"latencies_ms": {"rot": l_rot, "pmult": l_pa / 2, "add": l_pa / 2}, "n_copies": n}
+    for layer, (W, in_level, cap, mo) in enumerate(((w.W, 0, 200e9 / ct_bytes, min_out1),
+                                                    (W2, l1 - 1, 1, 0))):
+        for tag, la in (("measured", lat), ("paper_20_1_1", (20.0, 1.0, 1.0))):
+            mode, cost, cnt = fg.select_mode(c, w.row_ptr, w.col, w.val, W, perm, layer, n, la, cap,
+                                             t=1, radix_bits=radix, min_out_level=mo, in_level=in_level)
+            out["layer%d_%s" % (layer + 1, tag)] = {
+                "mode": "inter" if mode == fg.MODE_INTER else "spintra", "cost_ms" if tag == "measured"
+                else "cost_units": cost, "counts": cnt}
+    return out
 
 
 # ------------------------------------------------------------------ Inter-CA

@@ -69,13 +69,12 @@ def test_fullsize_layer_decrypts_to_fp64(env):
 
 def test_cora_like_two_layer_decrypts_to_fp64():
     """The two-layer configuration at its full sizes (N = 2^15, 10 + 4 primes,
-    dnum 3; V = 2708, F = 1433, F' = 16, 7 classes): ten primes leave no room
-    for two SpIntra-CA layers (each takes the combination's level and one per
-    group), so the first layer runs in Inter-CA mode as in the paper's
-    models (the node and 4 sampled neighbours, MEAN weights; 2 levels), then
-    x^2 (CMult, relinearisation, rescale), then SpIntra-CA at radix 16 (4
-    groups).  Every output column decrypts within 2^-20 of FP64
-    A-hat (sum_k w_k X[nbr_k] W1)^2 W2."""
+    dnum 3; V = 2708, F = 1433, F' = 16, 7 classes) on the exact A-hat: both
+    layers SpIntra-CA at radix 32 (14-bit shifts in three groups), so the
+    nine rescales are combination 1 + 3 groups, x^2 1 (CMult,
+    relinearisation, rescale), combination 1 + 3 groups, and the output sits
+    at level 0.  Every output column decrypts within 2^-20 of FP64
+    A-hat (A-hat X W1)^2 W2."""
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -86,19 +85,19 @@ def test_cora_like_two_layer_decrypts_to_fp64():
     w = wl.config_workload("cora_like")
     W2 = wl.second_layer_weights("cora_like")
     perm = wl.random_order(w.V, ctx.slots, 5)
-    nbr, wts = wl.sample_neighbors(w, 4, 5)
-    plan1 = fg.plan_build_inter(ctx, nbr, wts, w.W, perm)
+    plan1 = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=1, radix_bits=5)
     i1 = plan1.info()
-    assert i1["out_level"] == 7
-    plan2 = fg.plan_build(ctx, w.row_ptr, w.col, w.val, W2, perm, t=1, radix_bits=4,
+    assert i1["out_level"] == 5 and i1["n_groups"] == 3
+    plan2 = fg.plan_build(ctx, w.row_ptr, w.col, w.val, W2, perm, t=1, radix_bits=5,
                           in_level=i1["out_level"] - 1)
     i2 = plan2.info()
-    assert i2["out_level"] == 1 and i2["n_out"] == 7
-    sk, evk = fg.keygen(ctx, 5, plan2.rotation_amounts(), relin=True)
+    assert i2["out_level"] == 0 and i2["n_out"] == 7
+    amounts = sorted(set(plan1.rotation_amounts()) | set(plan2.rotation_amounts()))
+    sk, evk = fg.keygen(ctx, 5, amounts, relin=True)
     keys = fg.load_evk(ctx, evk)
     del evk
     x = torch.empty((i1["n_in"], 2, ctx.nq, ctx.n), dtype=torch.int64, device="cuda")
-    fg.pack_neighbor_copies(ctx, sk, 5, w.X, nbr, perm, out=x)
+    fg.pack_features(ctx, sk, 5, w.X, perm, 1, out=x)
     h1 = torch.empty((i1["n_out"], 2, i1["out_level"] + 1, ctx.n), dtype=torch.int64, device="cuda")
     _, la, sc = fg.gcn_layer_axw(ctx, keys, plan1, x, out=h1)
     del x
@@ -106,9 +105,9 @@ def test_cora_like_two_layer_decrypts_to_fp64():
     fg.mul_relin_rescale(ctx, keys, h1, h1, la, out=a1)
     out = torch.empty((i2["n_out"], 2, i2["out_level"] + 1, ctx.n), dtype=torch.int64, device="cuda")
     _, lb, _ = fg.gcn_layer_axw(ctx, keys, plan2, a1, out=out)
-    assert lb == 1
+    assert lb == 0
     scale = sc * sc / ctx.q[la]
-    ref = wl.two_layer_reference(w, W2, first=wl.neighbor_reference(w, nbr, wts))
+    ref = wl.two_layer_reference(w, W2)
     for j in range(W2.shape[1]):
         d = fg.decrypt_decode(ctx, sk, out[j].contiguous(), lb, scale)
         assert np.max(np.abs(d[perm] - ref[:, j])) < 2 ** -20
