@@ -13,18 +13,28 @@ slot) is built in three stages.
    is skipped and the remaining regions alternate.
 3. Conflict-least placement inside each region.  The region's slots are
    those stage 2 gave it.  Its highest-degree node takes the first slot; the
-   others, in the order the search found them, each take the free slot of
-   lowest cost, ties to the lowest slot index.
+   others, in the order the search found them, each take the free slot i
+   that minimises the total conflict count k_n(i) = sum_j sum_rot
+   Con_j^rot (Alg. 1) of the nodes placed so far with n at i; among slots
+   of equal count, the one with the fewest rotation steps to n's placed
+   neighbours (the set bits of the index distances, one rotation per set
+   bit, Sec. 3.3.1), then the lowest index.
 
 Readings the paper leaves open (the library implements the same):
   * siblings of u: the nodes w != u with a common aggregation target v, i.e.
     u and w both in row v of A-hat (self loops ignored); enqueued in the
     order of v, then of w, both ascending;
   * degree: the number of off-diagonal entries of the row;
-  * the cost of a slot is the number of rotation steps it implies: the sum,
-    over the node's graph neighbours already placed in the region, of the
-    number of set bits of the distance between the two slot indices within
-    the region (one rotation per set bit of a shift, Sec. 3.3.1).
+  * Con_j^rot (Alg. 1; a conflict is two different values meeting at one
+    slot of one ciphertext, Sec. 3.3): within the region, positions are the
+    slot indices 0..L-1; every edge v <- u between placed nodes is a token
+    carrying u's value from p(u) to p(v), shift d = p(u) - p(v), moved bit
+    by bit from the lowest (rotation rot moves it by sign(d) 2^rot when bit
+    rot of |d| is set, so after rotation rot it sits at
+    p(u) - sign(d) (|d| mod 2^(rot+1))), for rot = 0..bitlen(L-1)-1; a token
+    that has reached p(v) is removed (it has arrived, Sec. 3.3); Con_j^rot
+    is 1 when, after rotation rot, the tokens at position j carry two or
+    more different values.
 
 Parity unpinned: NOO is a heuristic with no worked example in the paper.
 Its output is pinned only as a valid injection of the nodes into the slots,
@@ -95,6 +105,28 @@ def interleave(regions, V, M):
     return slots
 
 
+def conflict_count(pos, nb, L):
+    """sum_j sum_rot Con_j^rot for the nodes placed at pos (node -> index):
+    the tokens of every edge v <- u with both ends placed, simulated bit by
+    bit (see the module docstring)."""
+    B = max(1, (L - 1).bit_length())
+    total = 0
+    for rot in range(B):
+        at = {}
+        for v, pv in pos.items():
+            for u in nb[v]:
+                if u not in pos:
+                    continue
+                d = pos[u] - pv
+                done = abs(d) % (1 << (rot + 1))
+                if done == abs(d):
+                    continue                     # arrived: removed
+                p = pos[u] - (done if d > 0 else -done)
+                at.setdefault(p, set()).add(u)
+        total += sum(1 for vals in at.values() if len(vals) >= 2)
+    return total
+
+
 def node_order(row_ptr, col, V, M, TH):
     """pi as an int64 array: node -> slot in [0, M)."""
     regions, nb, deg = regions_bfs(row_ptr, col, V, TH)
@@ -103,9 +135,8 @@ def node_order(row_ptr, col, V, M, TH):
     for region, sl in zip(regions, slots):
         L = len(region)
         first = min(region, key=lambda v: (-deg[v], v))
-        idx = {}                      # node -> slot index within the region
+        idx = {first: 0}              # node -> slot index within the region
         free = [True] * L
-        idx[first] = 0
         free[0] = False
         for n in region:
             if n == first:
@@ -115,7 +146,8 @@ def node_order(row_ptr, col, V, M, TH):
             for i in range(L):
                 if not free[i]:
                     continue
-                cost = sum(bin(abs(i - j)).count("1") for j in placed_nb)
+                idx[n] = i
+                cost = (conflict_count(idx, nb, L), sum(bin(abs(i - j)).count("1") for j in placed_nb))
                 if best is None or cost < best:
                     best, best_i = cost, i
             idx[n] = best_i

@@ -9,10 +9,21 @@
 //    region out of nodes gives its turn to a blank slot while any of the
 //    M - V blanks remain, after that its turn is skipped.
 // 3. Inside a region: the highest-degree node takes the region's first
-//    slot; the others, in discovery order, take the free slot whose index
-//    distances to the already placed graph neighbours have the fewest set
-//    bits in total (one rotation step per set bit), ties to the lowest
-//    index.
+//    slot; the others, in discovery order, take the free slot i with the
+//    fewest conflicts k_n(i) = sum_j sum_rot Con_j^rot (Alg. 1) among the
+//    nodes placed so far and n at i; ties go to the slot with the fewest
+//    rotation steps to n's placed neighbours (set bits of the index
+//    distances, one rotation per set bit), then to the lowest index.
+//    Con_j^rot: within the region (positions 0..L-1) every edge v <- u
+//    between placed nodes is a token carrying u's value from p(u) towards
+//    p(v), shift d = p(u) - p(v) consumed bit by bit from the lowest; after
+//    rotation rot it sits at p(u) - sign(d) (|d| mod 2^(rot+1)) unless it
+//    has arrived (then it is removed); Con_j^rot = 1 when the tokens at j
+//    after rotation rot carry two or more different values (a conflict of
+//    Sec. 3.3).  The conflicts of the tokens already placed do not depend on
+//    i, so only the change that n's own tokens bring is evaluated: per
+//    rotation and position the first value seen and whether a second,
+//    different one has been seen (tokens are only ever added).
 #include <algorithm>
 #include <deque>
 #include <vector>
@@ -121,27 +132,79 @@ extern "C" int fg_node_order(const int32_t *row_ptr, const int32_t *col, int V, 
             for (int v : region)
                 if (g.deg[v] > g.deg[first] || (g.deg[v] == g.deg[first] && v < first)) first = v;
             std::vector<char> freed(L, 1);
+            int B = 1;
+            while ((1 << B) < L) B++;   // bit length of L - 1 (at least 1)
+            std::vector<int> first_val((size_t)B * L, -1);
+            std::vector<char> clash((size_t)B * L, 0);
+            // the positions of a token from a to b after each rotation (until it arrives)
+            struct Hit {
+                int step, pos, val;
+                bool operator<(const Hit &o) const
+                {
+                    return step != o.step ? step < o.step : pos != o.pos ? pos < o.pos : val < o.val;
+                }
+            };
+            std::vector<Hit> hits;
+            auto trace = [&](int a, int b, int val) {
+                const int d = a - b, ad = std::abs(d);
+                for (int st = 0; st < B; st++) {
+                    const int done = ad & ((2 << st) - 1);
+                    if (done == ad) break;   // arrived: removed
+                    hits.push_back({st, d > 0 ? a - done : a + done, val});
+                }
+            };
+            std::vector<int> placed_nb;
+            auto tokens_of = [&](int n, int i) {
+                hits.clear();
+                for (int m : g.nb[n]) {
+                    if (idx[m] < 0 || region_of[m] != (int)r) continue;
+                    trace(idx[m], i, m);   // n aggregates m
+                    trace(i, idx[m], n);   // m aggregates n
+                }
+            };
             idx[first] = 0;
             freed[0] = 0;
-            std::vector<int> placed_nb;
             for (int n : region) {
                 if (n == first) continue;
                 placed_nb.clear();
                 for (int m : g.nb[n])
                     if (idx[m] >= 0 && region_of[m] == (int)r) placed_nb.push_back(idx[m]);
                 int best = -1;
-                long long best_cost = 0;
+                long long best_con = 0, best_steps = 0;
                 for (int i = 0; i < L; i++) {
                     if (!freed[i]) continue;
-                    long long cost = 0;
-                    for (int j : placed_nb) cost += __builtin_popcount((unsigned)std::abs(i - j));
-                    if (best < 0 || cost < best_cost) {
+                    tokens_of(n, i);
+                    std::sort(hits.begin(), hits.end());
+                    long long con = 0;
+                    for (size_t a = 0; a < hits.size();) {
+                        size_t b = a;
+                        while (b < hits.size() && hits[b].step == hits[a].step && hits[b].pos == hits[a].pos) b++;
+                        const size_t cell = (size_t)hits[a].step * L + hits[a].pos;
+                        if (!clash[cell]) {
+                            const int f = first_val[cell];
+                            bool c = false;
+                            for (size_t k = a; k < b && !c; k++)
+                                c = (f >= 0 && hits[k].val != f) || hits[k].val != hits[a].val;
+                            con += c;
+                        }
+                        a = b;
+                    }
+                    long long steps = 0;
+                    for (int j : placed_nb) steps += __builtin_popcount((unsigned)std::abs(i - j));
+                    if (best < 0 || con < best_con || (con == best_con && steps < best_steps)) {
                         best = i;
-                        best_cost = cost;
+                        best_con = con;
+                        best_steps = steps;
                     }
                 }
                 idx[n] = best;
                 freed[best] = 0;
+                tokens_of(n, best);
+                for (const Hit &h : hits) {
+                    const size_t cell = (size_t)h.step * L + h.pos;
+                    if (first_val[cell] < 0) first_val[cell] = h.val;
+                    else if (first_val[cell] != h.val) clash[cell] = 1;
+                }
             }
             for (int n : region) perm_out[n] = slots[r][idx[n]];
         }

@@ -54,34 +54,76 @@ def test_regions_respect_threshold():
     assert allv == list(range(w.V))
 
 
-def test_greedy_slot_has_least_cost():
+def count_conflicts(pos, nb, L):
+    """Con summed over positions and rotations (Alg. 1), recomputed here by
+    walking every token one rotation at a time: token v <- u starts at
+    pos[u]; at rotation r, if bit r of |pos[u] - pos[v]| is set it moves
+    2^r towards pos[v]; a token at pos[v] has arrived and leaves."""
+    B = max(1, (L - 1).bit_length())
+    toks = [(u, pos[u], pos[v]) for v in pos for u in nb[v] if u in pos]
+    cur = [t[1] for t in toks]
+    total = 0
+    for r in range(B):
+        cells = {}
+        for k, (u, src, dst) in enumerate(toks):
+            if cur[k] == dst:
+                continue
+            if (abs(src - dst) >> r) & 1:
+                cur[k] += (1 << r) if dst > src else -(1 << r)
+            if cur[k] != dst:
+                cells.setdefault(cur[k], set()).add(u)
+        total += sum(len(x) >= 2 for x in cells.values())
+    return total
+
+
+def test_conflict_count_hand_worked():
+    """K4 on nodes 0..3, nodes 0, 2, 3 placed at indices 0, 1, 3 (L = 4, two
+    rotations).  Tokens 2 <- 0 and 0 <- 2 arrive at rotation 0; 3 <- 0 moves
+    0 -> 1, 0 <- 3 moves 3 -> 2, 3 <- 2 stays at 1 (bit 0 of |1 - 3| is 0),
+    2 <- 3 stays at 3: after rotation 0 index 1 holds the values of 0 and 2,
+    one conflict; after rotation 1 every token has arrived.  With node 3 at
+    index 2 instead nothing collides."""
+    nb = [[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]]
+    assert noo.conflict_count({0: 0, 2: 1, 3: 3}, nb, 4) == 1
+    assert noo.conflict_count({0: 0, 2: 1, 3: 2}, nb, 4) == 0
+    assert count_conflicts({0: 0, 2: 1, 3: 3}, nb, 4) == 1
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_greedy_slot_has_least_conflicts(seed):
     """Brute force on a small graph: each node's slot index minimises the
-    rotation-step cost among the slots free when it was placed."""
-    w = wl.make_workload(graph="chung_lu", V=120, deg=4.0, gamma=2.5, F=4, Fp=2, seed=3)
-    perm, nreg = noo.node_order(w.row_ptr, w.col, w.V, 256, TH=40)
+    conflict count (then the rotation steps, then the index) among the
+    slots free when it was placed."""
+    w = wl.make_workload(graph="chung_lu", V=90, deg=4.0, gamma=2.5, F=4, Fp=2, seed=seed)
+    perm, nreg = noo.node_order(w.row_ptr, w.col, w.V, 256, TH=30)
     assert len(set(perm.tolist())) == w.V and perm.min() >= 0 and perm.max() < 256
-    regions, nb, deg = noo.regions_bfs(w.row_ptr, w.col, w.V, 40)
+    regions, nb, deg = noo.regions_bfs(w.row_ptr, w.col, w.V, 30)
     slots = noo.interleave(regions, w.V, 256)
+    collided = 0
     for region, sl in zip(regions, slots):
+        L = len(region)
         idx = {v: sl.index(int(perm[v])) for v in region}
         first = min(region, key=lambda v: (-deg[v], v))
         assert idx[first] == 0
-        taken = {0}
-        placed = {first}
+        pos = {first: 0}
         for n in region:
             if n == first:
                 continue
-            pn = [idx[m] for m in nb[n] if m in placed]
-            cost = lambda i: sum(bin(abs(i - j)).count("1") for j in pn)
-            free = [i for i in range(len(region)) if i not in taken]
-            best = min(free, key=lambda i: (cost(i), i))
+            pn = [pos[m] for m in nb[n] if m in pos]
+            free = [i for i in range(L) if i not in pos.values()]
+
+            def key(i):
+                return (count_conflicts({**pos, n: i}, nb, L),
+                        sum(bin(abs(i - j)).count("1") for j in pn), i)
+            best = min(free, key=key)
             assert idx[n] == best
-            taken.add(idx[n])
-            placed.add(n)
+            collided += key(best)[0] > 0
+            pos[n] = idx[n]
+    assert collided > 0      # the conflict term mattered somewhere
 
 
 @pytest.mark.parametrize("case", [("er", 64, 4.0, None, 128, 16), ("chung_lu", 300, 4.0, 2.5, 512, 48),
-                                  ("chung_lu", 1000, 3.9, 2.2, 2048, 200)])
+                                  ("chung_lu", 400, 3.9, 2.2, 1024, 64)])
 def test_library_node_order_matches_oracle(case):
     import paper_2506_10399_gb300 as fg
     graph, V, d, gamma, M, TH = case
@@ -101,3 +143,25 @@ def test_library_node_order_rejects_bad_input():
     bad[0] = 99
     with pytest.raises(fg.FicgcnError):
         fg.node_order(w.row_ptr, bad, 32, 4)
+
+
+def test_planted_noo_slip_is_caught(monkeypatch):
+    """A conflict counter that also counts cells holding a single value (a
+    slip planted in the oracle) fails the hand-worked pin."""
+    def loose(pos, nb, L):
+        B = max(1, (L - 1).bit_length())
+        total = 0
+        for rot in range(B):
+            at = set()
+            for v, pv in pos.items():
+                for u in nb[v]:
+                    if u in pos:
+                        d = pos[u] - pv
+                        done = abs(d) % (1 << (rot + 1))
+                        if done != abs(d):
+                            at.add(pos[u] - (done if d > 0 else -done))
+            total += len(at)
+        return total
+    monkeypatch.setattr(noo, "conflict_count", loose)
+    with pytest.raises(AssertionError):
+        test_conflict_count_hand_worked()
