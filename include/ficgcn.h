@@ -34,8 +34,11 @@
  *     mix(seed ^ (purpose << 48) ^ index), mix being SplitMix64's output
  *     function; each draw adds 0x9E3779B97F4A7C15 to the state and returns
  *     mix(state).  Ternary coefficient: draw >> 62, redrawn while 3, minus 1.
- *     Noise coefficient: centred binomial popcount(d & 0xFFFFF) -
- *     popcount((d >> 20) & 0xFFFFF) (variance 10).  Uniform residue mod q:
+ *     Noise coefficient: the discrete Gaussian sigma = 3.2 cut at |x| <= 19,
+ *     by inversion of the table T[k] = floor(2^63 sum_{i<=k} p_i / S) over
+ *     |x| (p_0 = rho(0), p_i = 2 rho(i), rho(x) = exp(-x^2 / (2 sigma^2)),
+ *     S = sum p_i): |x| = least k with (d >> 1) < T[k], sign from bit 0 of
+ *     d (zero has no sign).  Uniform residue mod q:
  *     d & (2^bitlen(q) - 1), redrawn while >= q; limbs in prime order.
  *     Purposes: 1 secret (index 0), 2/3 key a/e (index galois << 8 | digit),
  *     4/5 encryption a/e (index = ciphertext index).  This generator is not

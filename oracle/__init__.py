@@ -34,7 +34,7 @@ def build(force=False):
             and os.path.getmtime(LIB_PATH) >= os.path.getmtime(src)):
         return LIB_PATH
     tmp = LIB_PATH + ".tmp.%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
-                           "-o", tmp, src])
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-o", tmp, src, "-lm"])
     os.replace(tmp, LIB_PATH)
     return LIB_PATH

@@ -39,7 +39,8 @@ _lib.ref_mac_scalar.argtypes = [_u64p, _u64, _u64p, _int, _u64]
 _lib.ref_splitmix_first.argtypes = [_u64, _u64, _u64, _int, _u64p]
 _lib.ref_splitmix_first.restype = _u64
 _lib.ref_sample_ternary.argtypes = [_u64, _u64, _u64, _int, _i64p]
-_lib.ref_sample_cbd.argtypes = [_u64, _u64, _u64, _int, _i64p]
+_lib.ref_sample_gauss.argtypes = [_u64, _u64, _u64, _int, _i64p]
+_lib.ref_gauss_table.argtypes = [_u64p]
 _lib.ref_sample_uniform.argtypes = [_u64, _u64, _u64, _u64p, _int, _int, _u64p]
 
 
@@ -159,10 +160,17 @@ def sample_ternary(seed, purpose, index, n):
     return out
 
 
-def sample_cbd(seed, purpose, index, n):
+def sample_gauss(seed, purpose, index, n):
+    """Discrete Gaussian noise, sigma = 3.2, |x| <= 19 (see ckks_ref.c)."""
     out = np.zeros(n, dtype=np.int64)
-    _lib.ref_sample_cbd(seed, purpose, index, n, _pi(out))
+    _lib.ref_sample_gauss(seed, purpose, index, n, _pi(out))
     return out
+
+
+def gauss_table():
+    out = np.zeros(20, dtype=np.uint64)
+    _lib.ref_gauss_table(_p(out))
+    return [int(v) for v in out]
 
 
 def sample_uniform(seed, purpose, index, primes, n):

@@ -120,9 +120,16 @@ def encode(params, z, scale, level, extended=False):
     with extended=True also the residues mod p_0..p_{K-1} ([level+1+K][N]),
     for products taken in the key-switching basis."""
     m = round_half_away(scale * embed_inverse(params, z))
-    ints = [int(v) for v in m]
     primes = params.ext_primes(level) if extended else params.q[:level + 1]
     out = np.empty((len(primes), params.n), dtype=np.uint64)
+    if np.max(np.abs(m)) < 2.0 ** 62:
+        # every coefficient is an integer-valued double below 2^62: exact as
+        # int64, and np.mod with a positive modulus returns [0, q)
+        mi = m.astype(np.int64)
+        for i, q in enumerate(primes):
+            out[i] = np.mod(mi, np.int64(q)).astype(np.uint64)
+        return out
+    ints = [int(v) for v in m]
     for i, q in enumerate(primes):
         out[i] = np.array([v % q for v in ints], dtype=np.uint64)
     return out
@@ -232,7 +239,7 @@ def keygen_switch(params, seed, s, s_from, index):
     for j, dig in enumerate(params.digits(params.L)):
         idx = (int(index) << 8) | j
         a = _ref.sample_uniform(seed, PURPOSE_KEY_A, idx, primes, n)
-        e = _ref.sample_cbd(seed, PURPOSE_KEY_E, idx, n)
+        e = _ref.sample_gauss(seed, PURPOSE_KEY_E, idx, n)
         e_res = small_to_res(e, primes)
         b = neg_res(poly_mul(params, a, s_res, primes), primes)
         b = add_res(b, e_res, primes)
@@ -314,7 +321,7 @@ def encrypt(params, seed, index, pt, s, level):
     Streams: a from (seed, 4, index), e from (seed, 5, index)."""
     primes = params.q[:level + 1]
     a = _ref.sample_uniform(seed, PURPOSE_ENC_A, index, primes, params.n)
-    e = small_to_res(_ref.sample_cbd(seed, PURPOSE_ENC_E, index, params.n), primes)
+    e = small_to_res(_ref.sample_gauss(seed, PURPOSE_ENC_E, index, params.n), primes)
     c0 = neg_res(poly_mul(params, a, small_to_res(s, primes), primes), primes)
     c0 = add_res(add_res(c0, pt[:level + 1], primes), e, primes)
     return np.stack([c0, a])

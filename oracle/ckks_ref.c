@@ -16,6 +16,7 @@
  * Parity status of each function is stated beside it; the pins live in
  * tests/test_oracle_*.py.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -386,16 +387,42 @@ void ref_sample_ternary(u64 seed, u64 purpose, u64 index, int n, i64 *out)
     }
 }
 
-/* noise: centred binomial with 20 coin pairs (variance 10, sigma ~ 3.16),
- * one draw per coefficient: popcount(r & 0xFFFFF) - popcount((r>>20) & 0xFFFFF) */
-void ref_sample_cbd(u64 seed, u64 purpose, u64 index, int n, i64 *out)
+/* noise: the discrete Gaussian D_sigma on the integers, sigma = 3.2, i.e.
+ * P(x) proportional to rho(x) = exp(-x^2 / (2 sigma^2)), cut at |x| <= 19
+ * (6 sigma), sampled by inversion of a cumulative distribution table over
+ * |x|: T[k] = floor(2^63 * sum_{i <= k} p_i / S) with p_0 = rho(0), p_i =
+ * 2 rho(i) (both signs) for i >= 1 and S = sum of all p_i (so zero is not
+ * counted twice), T[19] = 2^63.  One draw r per coefficient: |x| = the
+ * least k with (r >> 1) < T[k], and x = -|x| when bit 0 of r is set. */
+#define REF_GAUSS_TAIL 19
+
+void ref_gauss_table(u64 *T)
 {
+    const double sigma = 3.2, two_s2 = 2.0 * sigma * sigma;
+    double p[REF_GAUSS_TAIL + 1], S = 0.0, c = 0.0;
+    for (int k = 0; k <= REF_GAUSS_TAIL; k++) {
+        const double r = exp(-(double)(k * k) / two_s2);
+        p[k] = k == 0 ? r : 2.0 * r;
+        S += p[k];
+    }
+    for (int k = 0; k < REF_GAUSS_TAIL; k++) {
+        c += p[k];
+        T[k] = (u64)(c / S * 9223372036854775808.0);
+    }
+    T[REF_GAUSS_TAIL] = 1ull << 63;
+}
+
+void ref_sample_gauss(u64 seed, u64 purpose, u64 index, int n, i64 *out)
+{
+    u64 T[REF_GAUSS_TAIL + 1];
+    ref_gauss_table(T);
     sm_stream st = sm_open(seed, purpose, index);
     for (int x = 0; x < n; x++) {
         u64 r = sm_next(&st);
-        int a = __builtin_popcountll(r & 0xFFFFFull);
-        int b = __builtin_popcountll((r >> 20) & 0xFFFFFull);
-        out[x] = (i64)(a - b);
+        u64 u = r >> 1;
+        int k = 0;
+        while (u >= T[k]) k++;
+        out[x] = (r & 1) && k ? -(i64)k : (i64)k;
     }
 }
 

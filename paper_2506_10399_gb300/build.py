@@ -55,7 +55,7 @@ def build(force=False, verbose=False):
         obj = os.path.join(BUILD, s + ".o")
         objs.append(obj)
         if force or not _up_to_date(obj, [src] + headers):
-            jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-I",
+            jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-ffp-contract=off", "-I",
                          os.path.join(_cuda_home(), "include"), *inc, "-c", src, "-o", obj])
 
     def run(cmd):

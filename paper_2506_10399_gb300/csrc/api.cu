@@ -694,7 +694,7 @@ int fg_keygen(fg_ctx *ctx, uint64_t seed, const int32_t *rot_amounts, int n_rot,
         for (int j = 0; j < beta; j++) {
             const u64 idx = ((u64)(rl ? 0 : g) << 8) | (u64)j;
             hm::sample_uniform(seed, 2, idx, ctx->primes.data(), KL, N, ha.data());
-            hm::sample_cbd(seed, 3, idx, N, he.data());
+            hm::sample_gauss(seed, 3, idx, N, he.data());
             CUDA_TRY(cudaMemcpyAsync(A, ha.data(), ha.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
             CUDA_TRY(cudaMemcpyAsync(de, he.data(), N, cudaMemcpyHostToDevice, ctx->stream));
             kern::ntt_fwd(ctx, As, As);
@@ -753,7 +753,7 @@ int fg_encrypt(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t seed, u
     std::vector<u64> ha((size_t)nl * N);
     std::vector<int8_t> he(N);
     hm::sample_uniform(seed, 4, index, ctx->primes.data(), nl, N, ha.data());
-    hm::sample_cbd(seed, 5, index, N, he.data());
+    hm::sample_gauss(seed, 5, index, N, he.data());
     u64 *dout = is_device_ptr(out) ? out : (u64 *)ctx->buf("io_ct", (size_t)2 * nl * N * 8);
     encrypt_dev(ctx, S, seed, index, dpt, level, dout, ha.data(), he.data());
     stage_out(ctx, out, dout, (size_t)2 * nl * N);
@@ -800,7 +800,7 @@ int fg_pack_features(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t s
                 bad = 1;
             }
             hm::sample_uniform(seed, 4, (u64)b, ctx->primes.data(), nl, N, as[c].data());
-            hm::sample_cbd(seed, 5, (u64)b, N, es[c].data());
+            hm::sample_gauss(seed, 5, (u64)b, N, es[c].data());
         }
         FG_CHECK(!bad, FG_EINVAL, "feature value cannot be encoded");
         for (int c = 0; c < cn; c++) {

@@ -58,7 +58,7 @@ struct Stream {
     u64 next();
 };
 void sample_ternary(u64 seed, u64 purpose, u64 index, int n, int8_t *out);
-void sample_cbd(u64 seed, u64 purpose, u64 index, int n, int8_t *out);
+void sample_gauss(u64 seed, u64 purpose, u64 index, int n, int8_t *out);
 void sample_uniform(u64 seed, u64 purpose, u64 index, const u64 *primes, int n_limbs,
                     int n, u64 *out);
 

@@ -125,13 +125,39 @@ void sample_ternary(u64 seed, u64 purpose, u64 index, int n, int8_t *out)
     }
 }
 
-void sample_cbd(u64 seed, u64 purpose, u64 index, int n, int8_t *out)
+// Noise: the discrete Gaussian D_sigma, sigma = 3.2 (P(x) proportional to
+// exp(-x^2 / (2 sigma^2))), cut at |x| <= 19 (6 sigma).  Inversion of a
+// cumulative table over |x|: T[k] = floor(2^63 sum_{i<=k} p_i / S), p_0 =
+// rho(0), p_i = 2 rho(i) for i >= 1 (both signs; zero counted once), S the
+// sum of all p_i, T[19] = 2^63.  One stream word r per coefficient: |x| =
+// the least k with (r >> 1) < T[k], negative when bit 0 of r is set.
+static void gauss_table(u64 *T)
 {
+    const int tail = 19;
+    const double sigma = 3.2, two_s2 = 2.0 * sigma * sigma;
+    double p[20], S = 0.0, c = 0.0;
+    for (int k = 0; k <= tail; k++) {
+        const double r = std::exp(-(double)(k * k) / two_s2);
+        p[k] = k == 0 ? r : 2.0 * r;
+        S += p[k];
+    }
+    for (int k = 0; k < tail; k++) {
+        c += p[k];
+        T[k] = (u64)(c / S * 9223372036854775808.0);
+    }
+    T[tail] = 1ull << 63;
+}
+
+void sample_gauss(u64 seed, u64 purpose, u64 index, int n, int8_t *out)
+{
+    u64 T[20];
+    gauss_table(T);
     Stream st(seed, purpose, index);
     for (int i = 0; i < n; i++) {
-        u64 r = st.next();
-        out[i] = (int8_t)(__builtin_popcountll(r & 0xFFFFFull) -
-                          __builtin_popcountll((r >> 20) & 0xFFFFFull));
+        const u64 r = st.next(), u = r >> 1;
+        int k = 0;
+        while (u >= T[k]) k++;
+        out[i] = (int8_t)((r & 1) && k ? -k : k);
     }
 }
 

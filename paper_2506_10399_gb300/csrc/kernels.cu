@@ -728,14 +728,19 @@ constexpr int kCombJ = 8;
 constexpr int kCombChunk = 128;
 
 // Columns fb..fe-1 of X; with accumulate set, the result is added to Z.
+// The nj = ceil(Fp / kCombJ) output blocks of one slot range are
+// neighbouring CTAs (blockIdx.x = slot block * nj + output block), so they
+// run together and the later ones find the input words in L2: X is read from
+// HBM once for all F' outputs.
 __global__ void __launch_bounds__(256)
-k_comb(const u64 *__restrict__ X, int F, int fb, int fe, int accumulate, int Fp, int j0, int level,
+k_comb(const u64 *__restrict__ X, int F, int fb, int fe, int accumulate, int Fp, int nj, int level,
        const u64 *__restrict__ consts, u64 *Z, int z_ls, const PrimeC *__restrict__ primes,
        int N)
 {
     __shared__ u64 cs[kCombChunk][kCombJ];
     const int i = blockIdx.y, p = blockIdx.z;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j0 = (blockIdx.x % nj) * kCombJ;
+    const int x = (blockIdx.x / nj) * blockDim.x + threadIdx.x;
     const PrimeC P = primes[i];
     const bool split = P.q < (1ull << 46);
     const int nl = level + 1;
@@ -1609,14 +1614,13 @@ void comb_const_mac(fg_ctx *ctx, const u64 *X, int F, int Fp, int level, const u
     FG_CHECK(F < (1 << 16), FG_EINVAL, "combination over more than 2^16 input columns");
     if (fe < 0) fe = F;
     FG_CHECK(0 <= fb && fb < fe && fe <= F, FG_EINVAL, "combination column range");
-    for (int j0 = 0; j0 < Fp; j0 += kCombJ) {
-        const int jn = std::min(kCombJ, Fp - j0);
-        KTimer kt(ctx, "comb", ((double)(fe - fb) + jn * (accumulate ? 2 : 1)) * 2 * (level + 1) * ctx->n * 8);
-        dim3 g((ctx->n + 255) / 256, level + 1, 2);
-        k_comb<<<g, 256, 0, ctx->stream>>>(X, F, fb, fe, accumulate ? 1 : 0, Fp, j0, level, consts, Z,
-                                           z_ls, ctx->d_primes, ctx->n);
-        check_launch("comb");
-    }
+    const int nj = (Fp + kCombJ - 1) / kCombJ;
+    // inputs read once, outputs written once (read too when accumulating)
+    KTimer kt(ctx, "comb", ((double)(fe - fb) + Fp * (accumulate ? 2 : 1)) * 2 * (level + 1) * ctx->n * 8);
+    dim3 g(((ctx->n + 255) / 256) * nj, level + 1, 2);
+    k_comb<<<g, 256, 0, ctx->stream>>>(X, F, fb, fe, accumulate ? 1 : 0, Fp, nj, level, consts, Z, z_ls,
+                                       ctx->d_primes, ctx->n);
+    check_launch("comb");
 }
 
 void rescale_coef(fg_ctx *ctx, const u64 *in, int in_ls, u64 *out, int out_ls, int npoly, int level)

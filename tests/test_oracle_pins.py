@@ -319,8 +319,8 @@ def ctx10():
 def test_samplers_ranges_and_determinism():
     t = _ref.sample_ternary(3, 1, 0, 4096)
     assert set(np.unique(t)) <= {-1, 0, 1} and abs(np.mean(t == 0) - 1 / 3) < 0.05
-    e = _ref.sample_cbd(3, 5, 0, 20000)
-    assert e.min() >= -20 and e.max() <= 20 and abs(np.var(e) - 10) < 0.6
+    e = _ref.sample_gauss(3, 5, 0, 20000)
+    assert e.min() >= -19 and e.max() <= 19
     q = _ref.gen_primes(10, [40])
     u = _ref.sample_uniform(3, 4, 0, q, 4096)
     assert u.max() < q[0]
@@ -341,6 +341,25 @@ def test_samplers_ranges_and_determinism():
         s = (s + 0x9E3779B97F4A7C15) & M64
         want.append(mix(s))
     assert [int(v) for v in _ref.splitmix(seed, purpose, index, 4)] == want
+
+
+def test_noise_is_the_discrete_gaussian():
+    """The noise sampler against the definition of D_sigma (sigma = 3.2,
+    P(x) proportional to exp(-x^2 / (2 sigma^2)), |x| <= 19): frequencies of
+    |x| <= 6 within five standard errors of the definition's probabilities,
+    the sign symmetric, the variance sigma^2 up to sampling error."""
+    n = 400000
+    e = np.concatenate([_ref.sample_gauss(7, 5, i, n // 4) for i in range(4)])
+    xs = np.arange(-19, 20)
+    rho = np.exp(-xs.astype(float) ** 2 / (2 * 3.2 ** 2))
+    prob = rho / rho.sum()
+    for x in range(-6, 7):
+        p = prob[x + 19]
+        f = np.mean(e == x)
+        assert abs(f - p) < 5 * np.sqrt(p * (1 - p) / n), (x, f, p)
+    assert abs(np.mean(e)) < 0.03
+    assert abs(np.var(e) - float((prob * xs ** 2).sum())) < 0.15
+    assert abs(float((prob * xs ** 2).sum()) - 3.2 ** 2) < 1e-3
 
 
 def test_encrypt_decrypt_and_add(ctx10):
