@@ -182,6 +182,9 @@ typedef struct {
     int min_out_level;  /* lowest level the output may reach */
     int n_sampled;      /* n in J(t;F,n); 0 = mean row length of A-hat, rounded */
     int in_level;       /* level of the input ciphertexts; 0 = the top level L */
+    int no_encode;      /* 1 = leave every mask zero (no encoding or upload): a plan
+                           for timing only, whose layer computes nothing meaningful
+                           (the kernels' work does not depend on the values) */
 } fg_plan_opts;
 
 /* Plan of one layer (paper Sec. 3.2-3.3): packing t, combination constants,
@@ -233,6 +236,12 @@ int fg_plan_dry_run(const fg_params *params, const int32_t *row_ptr, const int32
  * malformed CSR. */
 int fg_node_order(const int32_t *row_ptr, const int32_t *col, int V, int M, int TH,
                   int32_t *perm_out, int *n_regions);
+/* fg_node_order with a choice of the order in which the regions take their
+ * turns in the interleaving (the paper leaves it open): region_order 0 =
+ * the order the search found them (fg_node_order), 1 = larger regions first
+ * (ties: search order). */
+int fg_node_order_ex(const int32_t *row_ptr, const int32_t *col, int V, int M, int TH,
+                     int region_order, int32_t *perm_out, int *n_regions);
 /* Inter-CA plan (paper Sec. 3.1, Table 1; the first-layer mode): the client
  * sends n copies of X, copy k holding row nbr[v][k] of X at node v's slot
  * (fg_pack_features of the gathered rows; nbr -1: no neighbour), and the
@@ -280,6 +289,10 @@ int fg_select_mode(const fg_params *params, const int32_t *row_ptr, const int32_
 int fg_plan_features(const fg_params *params, const int32_t *row_ptr, const int32_t *col,
                      const double *val, int V, const double *W, int F, int Fp,
                      const int32_t *perm, const fg_plan_opts *opts, float *feat);
+/* The same statistics of a plan already built (SpIntra-CA plans; the graph
+ * it was built from is passed again as its CSR row_ptr, col). */
+int fg_plan_features_built(const fg_plan *plan, const int32_t *row_ptr, const int32_t *col,
+                           float *feat);
 
 /* The learned planner's latency model (the paper's packing and ordering
  * choices, Sec. 3.2 and 3.4, made by a model instead of a search): a

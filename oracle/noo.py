@@ -127,9 +127,14 @@ def conflict_count(pos, nb, L):
     return total
 
 
-def node_order(row_ptr, col, V, M, TH):
-    """pi as an int64 array: node -> slot in [0, M)."""
+def node_order(row_ptr, col, V, M, TH, region_order=0):
+    """pi as an int64 array: node -> slot in [0, M).  region_order 0: the
+    regions take their interleaving turns in the order the search found
+    them; 1: larger regions first, ties in search order (the paper leaves
+    the order open)."""
     regions, nb, deg = regions_bfs(row_ptr, col, V, TH)
+    if region_order == 1:
+        regions = sorted(regions, key=len, reverse=True)   # stable: ties keep search order
     slots = interleave(regions, V, M)
     perm = np.full(V, -1, dtype=np.int64)
     for region, sl in zip(regions, slots):

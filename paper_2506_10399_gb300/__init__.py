@@ -276,6 +276,16 @@ class Plan:
         _check(self.ctx, _lib().lib.fg_plan_describe(self._h, _ptr(out), ln.value, ctypes.byref(ln)))
         return out
 
+    def features(self, row_ptr, col):
+        """The learned planner's statistics of this plan (its graph's CSR)."""
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        out = np.zeros(N_PLAN_FEATURES, np.float32)
+        _check(self.ctx, _lib().lib.fg_plan_features_built(self._h, ctypes.c_void_p(row_ptr.ctypes.data),
+                                                           ctypes.c_void_p(col.ctypes.data),
+                                                           ctypes.c_void_p(out.ctypes.data)))
+        return out
+
     def set_plaintext(self, mask, coeffs):
         coeffs = coeffs if _is_torch(coeffs) else np.ascontiguousarray(coeffs, dtype=np.uint64)
         _check(self.ctx, _lib().lib.fg_plan_set_plaintext(self._h, int(mask), _ptr(coeffs)))
@@ -301,7 +311,7 @@ def plan_build_inter(ctx, nbr, wts, W, perm, min_out_level=0, in_level=0):
     perm = np.ascontiguousarray(perm, dtype=np.int32)
     V, n = nbr.shape
     F, Fp = W.shape
-    o = nat.PlanOpts(1, 0, 1, int(min_out_level), 0, int(in_level))
+    o = nat.PlanOpts(1, 0, 1, int(min_out_level), 0, int(in_level), 0)
     h = ctypes.c_void_p()
     _check(ctx, nat.lib.fg_plan_build_inter(ctx._h, ctypes.c_void_p(nbr.ctypes.data), _ptr(wts), V, n,
                                             _ptr(W), F, Fp, ctypes.c_void_p(perm.ctypes.data),
@@ -328,7 +338,9 @@ def pack_neighbor_copies(ctx, sk, seed, X, nbr, perm, out=None):
 
 
 def plan_build(ctx, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=True, min_out_level=0,
-               n_sampled=0, in_level=0):
+               n_sampled=0, in_level=0, no_encode=False):
+    """Plan of one layer; no_encode leaves every mask zero (a plan for timing
+    only)."""
     nat = _lib()
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
     col = np.ascontiguousarray(col, dtype=np.int32)
@@ -338,7 +350,7 @@ def plan_build(ctx, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=True, min
     V = row_ptr.size - 1
     F, Fp = W.shape
     o = nat.PlanOpts(int(t), int(radix_bits), 1 if aoo else 0, int(min_out_level), int(n_sampled),
-                     int(in_level))
+                     int(in_level), 1 if no_encode else 0)
     h = ctypes.c_void_p()
     _check(ctx, nat.lib.fg_plan_build(ctx._h, ctypes.c_void_p(row_ptr.ctypes.data),
                                       ctypes.c_void_p(col.ctypes.data), _ptr(val), V, _ptr(W), F, Fp,
@@ -347,16 +359,18 @@ def plan_build(ctx, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=True, min
     return Plan(ctx, h)
 
 
-def node_order(row_ptr, col, slots, th):
-    """(perm node -> slot, number of regions) by node order optimisation."""
+def node_order(row_ptr, col, slots, th, region_order=0):
+    """(perm node -> slot, number of regions) by node order optimisation;
+    region_order 1 interleaves larger regions first."""
     nat = _lib()
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
     col = np.ascontiguousarray(col, dtype=np.int32)
     V = row_ptr.size - 1
     perm = np.empty(V, np.int32)
     nr = ctypes.c_int()
-    rc = nat.lib.fg_node_order(ctypes.c_void_p(row_ptr.ctypes.data), ctypes.c_void_p(col.ctypes.data),
-                               V, int(slots), int(th), ctypes.c_void_p(perm.ctypes.data), ctypes.byref(nr))
+    rc = nat.lib.fg_node_order_ex(ctypes.c_void_p(row_ptr.ctypes.data), ctypes.c_void_p(col.ctypes.data),
+                                  V, int(slots), int(th), int(region_order),
+                                  ctypes.c_void_p(perm.ctypes.data), ctypes.byref(nr))
     if rc != 0:
         raise FicgcnError(rc, "node order failed")
     return perm, nr.value
@@ -378,7 +392,7 @@ def plan_dry_run(params, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=True
     perm = np.ascontiguousarray(perm, dtype=np.int32)
     F, Fp = W.shape
     o = nat.PlanOpts(int(t), int(radix_bits), 1 if aoo else 0, int(min_out_level), int(n_sampled),
-                     int(in_level))
+                     int(in_level), 0)
     args = [ctypes.byref(prm), ctypes.c_void_p(row_ptr.ctypes.data), ctypes.c_void_p(col.ctypes.data),
             _ptr(val), row_ptr.size - 1, _ptr(W), F, Fp, ctypes.c_void_p(perm.ctypes.data),
             ctypes.byref(o)]
@@ -443,7 +457,7 @@ def plan_features(params, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=Tru
     perm = np.ascontiguousarray(perm, dtype=np.int32)
     F, Fp = W.shape
     o = nat.PlanOpts(int(t), int(radix_bits), 1 if aoo else 0, int(min_out_level), int(n_sampled),
-                     int(in_level))
+                     int(in_level), 0)
     out = np.zeros(N_PLAN_FEATURES, np.float32)
     rc = nat.lib.fg_plan_features(ctypes.byref(prm), ctypes.c_void_p(row_ptr.ctypes.data),
                                   ctypes.c_void_p(col.ctypes.data), ctypes.c_void_p(val.ctypes.data),
@@ -477,7 +491,7 @@ def select_mode(params, row_ptr, col, val, W, perm, layer, n_copies, lat=(20.0, 
     perm = np.ascontiguousarray(perm, dtype=np.int32)
     F, Fp = W.shape
     o = nat.PlanOpts(int(t), int(radix_bits), 1 if aoo else 0, int(min_out_level), int(n_sampled),
-                     int(in_level))
+                     int(in_level), 0)
     la = np.ascontiguousarray(lat, dtype=np.float64)
     mode = ctypes.c_int()
     cost = np.zeros(2, np.float64)

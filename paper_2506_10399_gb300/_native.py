@@ -27,7 +27,7 @@ class Params(ctypes.Structure):
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("t", c_int), ("radix_bits", c_int), ("aoo", c_int), ("min_out_level", c_int),
-                ("n_sampled", c_int), ("in_level", c_int)]
+                ("n_sampled", c_int), ("in_level", c_int), ("no_encode", c_int)]
 
 
 class BatchOpts(ctypes.Structure):
@@ -71,10 +71,12 @@ SIGS = {
     "fg_plan_dry_run": (c_int, [P(Params), c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_int,
                                 c_void_p, P(PlanOpts), c_void_p, c_size, P(c_size)]),
     "fg_node_order": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, P(c_int)]),
+    "fg_node_order_ex": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_void_p, P(c_int)]),
     "fg_plan_build_inter": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p, c_int, c_int,
                                     c_void_p, P(PlanOpts), P(c_void_p)]),
     "fg_plan_features": (c_int, [P(Params), c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_int,
                                  c_void_p, P(PlanOpts), c_void_p]),
+    "fg_plan_features_built": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "fg_select_mode": (c_int, [P(Params), c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_int,
                                c_void_p, P(PlanOpts), c_int, c_int, c_void_p, c_double, P(c_int),
                                c_void_p, c_void_p]),

@@ -77,13 +77,20 @@ extern "C" {
 
 // masks encoded on the host (all cores), uploaded, NTT, Montgomery form;
 // the combination constants in Montgomery form for every limb
-static void finish_plan(fg_ctx *ctx, fg_plan *pl)
+static void finish_plan(fg_ctx *ctx, fg_plan *pl, bool no_encode)
 {
     const int N = ctx->n, F = pl->F, Fp = pl->Fp;
     const int nm = (int)pl->masks.size();
+    if (no_encode) {   // timing-only plan: zero masks, no host encoding
+        for (MaskC &m : pl->masks) {
+            const size_t bytes = (size_t)ctx->ext(m.level) * N * 8;
+            CUDA_TRY(cudaMalloc(&m.d, bytes));
+            CUDA_TRY(cudaMemsetAsync(m.d, 0, bytes, ctx->stream));
+        }
+    }
     const int chunk = 32;
     std::vector<std::vector<u64>> enc(chunk);
-    for (int m0 = 0; m0 < nm; m0 += chunk) {
+    for (int m0 = 0; m0 < (no_encode ? 0 : nm); m0 += chunk) {
         const int cn = std::min(chunk, nm - m0);
         int bad = 0;
 #pragma omp parallel for schedule(dynamic) reduction(| : bad)
@@ -127,12 +134,12 @@ int fg_plan_build(fg_ctx *ctx, const int32_t *row_ptr, const int32_t *col, const
     try {
         FG_CHECK(row_ptr && (col || V == 0) && W && perm && out, FG_EINVAL, "null argument");
         *out = nullptr;
-        fg_plan_opts o{0, 0, 1, 0, 0, 0};
+        fg_plan_opts o{0, 0, 1, 0, 0, 0, 0};
         if (opts) o = *opts;
         pl = new fg_plan;
         pl->ctx = ctx;
         planner::build(*pl, *ctx, row_ptr, col, val, V, W, F, Fp, perm, o);
-        finish_plan(ctx, pl);
+        finish_plan(ctx, pl, o.no_encode != 0);
         *out = pl;
         return FG_OK;
     } catch (const fg_error &e) {
@@ -155,12 +162,12 @@ int fg_plan_build_inter(fg_ctx *ctx, const int32_t *nbr, const double *wts, int 
     try {
         FG_CHECK(nbr && wts && W && perm && out, FG_EINVAL, "null argument");
         *out = nullptr;
-        fg_plan_opts o{0, 0, 1, 0, 0, 0};
+        fg_plan_opts o{0, 0, 1, 0, 0, 0, 0};
         if (opts) o = *opts;
         pl = new fg_plan;
         pl->ctx = ctx;
         planner::build_inter(*pl, *ctx, nbr, wts, V, n, W, F, Fp, perm, o);
-        finish_plan(ctx, pl);
+        finish_plan(ctx, pl, o.no_encode != 0);
         *out = pl;
         return FG_OK;
     } catch (const fg_error &e) {
@@ -298,7 +305,7 @@ static void host_plan(const fg_params *prm, const int32_t *row_ptr, const int32_
     std::vector<int> bits(prm->q_bits, prm->q_bits + prm->n_q);
     bits.insert(bits.end(), prm->p_bits, prm->p_bits + prm->n_p);
     c.primes = hm::gen_primes(c.log_n, bits);
-    fg_plan_opts o{0, 0, 1, 0, 0, 0};
+    fg_plan_opts o{0, 0, 1, 0, 0, 0, 0};
     if (opts) o = *opts;
     planner::build(pl, c, row_ptr, col, val, V, W, F, Fp, perm, o);
 }
@@ -345,6 +352,46 @@ int fg_select_mode(const fg_params *prm, const int32_t *row_ptr, const int32_t *
     return FG_OK;
 }
 
+// the learned planner's statistics of a plan (see fg_plan_features)
+static void plan_features_of(const fg_plan &pl, int np, const int32_t *row_ptr, const int32_t *col,
+                             int F, float *feat)
+{
+    const int V = pl.V, B = pl.B;
+    const int32_t *perm = pl.perm.data();
+    int maxdeg = 0;
+    double shift_bits = 0;
+    long long edges = 0;
+    for (int v = 0; v < V; v++) {
+        maxdeg = std::max(maxdeg, row_ptr[v + 1] - row_ptr[v]);
+        for (int e = row_ptr[v]; e < row_ptr[v + 1]; e++) {
+            const int u = col[e];
+            if (u == v) continue;
+            int d = ((perm[u] - perm[v]) % B + B) % B;
+            if (d > B / 2) d -= B;
+            shift_bits += 32 - __builtin_clz((unsigned)std::abs(d) | 1u);
+            edges++;
+        }
+    }
+    double rots = 0, terms = 0, ks_work = 0, mac_work = 0;
+    int lanes = 1;
+    for (const GroupC &g : pl.groups) {
+        rots += (double)g.rots.size();
+        terms += (double)g.terms.size();
+        ks_work += (double)g.rots.size() * (g.level + 1 + np);
+        mac_work += (double)g.terms.size() * (g.level + 1 + np);
+        lanes = std::max(lanes, g.n_out);
+    }
+    const float f[FG_PLAN_FEATURES] = {
+        (float)std::log2((double)V), (float)std::log2((double)F),
+        (float)((double)row_ptr[V] / V), (float)std::log2(1.0 + maxdeg),
+        (float)std::log2((double)pl.t), (float)pl.radix_bits,
+        (float)(edges ? shift_bits / edges : 0.0), (float)pl.groups.size(),
+        (float)std::log2(1.0 + rots), (float)std::log2(1.0 + terms), (float)lanes,
+        (float)std::log2(1.0 + ks_work), (float)std::log2(1.0 + mac_work),
+        (float)std::log2((double)F * (pl.in_level + 1)), (float)pl.in_level};
+    for (int i = 0; i < FG_PLAN_FEATURES; i++) feat[i] = f[i];
+}
+
 int fg_plan_features(const fg_params *prm, const int32_t *row_ptr, const int32_t *col,
                      const double *val, int V, const double *W, int F, int Fp, const int32_t *perm,
                      const fg_plan_opts *opts, float *feat)
@@ -354,45 +401,24 @@ int fg_plan_features(const fg_params *prm, const int32_t *row_ptr, const int32_t
         fg_ctx c;
         fg_plan pl;
         host_plan(prm, row_ptr, col, val, V, W, F, Fp, perm, opts, c, pl);
-        const int M = c.slots, B = pl.B;
-        int maxdeg = 0;
-        double shift_bits = 0;
-        long long edges = 0;
-        for (int v = 0; v < V; v++) {
-            maxdeg = std::max(maxdeg, row_ptr[v + 1] - row_ptr[v]);
-            for (int e = row_ptr[v]; e < row_ptr[v + 1]; e++) {
-                const int u = col[e];
-                if (u == v) continue;
-                int d = ((perm[u] - perm[v]) % B + B) % B;
-                if (d > B / 2) d -= B;
-                shift_bits += 32 - __builtin_clz((unsigned)std::abs(d) | 1u);
-                edges++;
-            }
-        }
-        double rots = 0, terms = 0, ks_work = 0, mac_work = 0;
-        int lanes = 1;
-        for (const GroupC &g : pl.groups) {
-            rots += (double)g.rots.size();
-            terms += (double)g.terms.size();
-            ks_work += (double)g.rots.size() * (g.level + 1 + c.np);
-            mac_work += (double)g.terms.size() * (g.level + 1 + c.np);
-            lanes = std::max(lanes, g.n_out);
-        }
-        const float f[FG_PLAN_FEATURES] = {
-            (float)std::log2((double)V), (float)std::log2((double)F),
-            (float)((double)row_ptr[V] / V), (float)std::log2(1.0 + maxdeg),
-            (float)std::log2((double)pl.t), (float)pl.radix_bits,
-            (float)(edges ? shift_bits / edges : 0.0), (float)pl.groups.size(),
-            (float)std::log2(1.0 + rots), (float)std::log2(1.0 + terms), (float)lanes,
-            (float)std::log2(1.0 + ks_work), (float)std::log2(1.0 + mac_work),
-            (float)std::log2((double)F * (pl.in_level + 1)), (float)pl.in_level};
-        (void)M;
-        for (int i = 0; i < FG_PLAN_FEATURES; i++) feat[i] = f[i];
+        plan_features_of(pl, c.np, row_ptr, col, F, feat);
     } catch (const fg_error &e) {
         return e.code;
     } catch (const std::exception &) {
         return FG_EOOM;
     }
+    return FG_OK;
+}
+
+int fg_plan_features_built(const fg_plan *pl, const int32_t *row_ptr, const int32_t *col, float *feat)
+{
+    if (!pl || !pl->ctx || !row_ptr || !col || !feat) return FG_EINVAL;
+    if (pl->n_copies) return FG_EINVAL;
+    for (int v = 0; v < pl->V; v++)
+        if (row_ptr[v + 1] < row_ptr[v]) return FG_EINVAL;
+    for (int e = 0; e < row_ptr[pl->V]; e++)
+        if (col[e] < 0 || col[e] >= pl->V) return FG_EINVAL;
+    plan_features_of(*pl, pl->ctx->np, row_ptr, col, pl->F, feat);
     return FG_OK;
 }
 

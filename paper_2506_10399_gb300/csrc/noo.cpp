@@ -5,7 +5,9 @@
 //    placed (ties: lowest id), enqueueing siblings (nodes that share an
 //    aggregation target) rather than neighbours, until the region holds TH
 //    nodes or the queue runs empty.
-// 2. Interleaving: the regions take turns, one slot each (ABCABC...); a
+// 2. Interleaving: the regions take turns, one slot each (ABCABC...), in
+//    the order the search found them or, as an option, larger regions
+//    first (the paper leaves the order open); a
 //    region out of nodes gives its turn to a blank slot while any of the
 //    M - V blanks remain, after that its turn is skipped.
 // 3. Inside a region: the highest-degree node takes the region's first
@@ -113,13 +115,17 @@ std::vector<std::vector<int>> interleave(const std::vector<std::vector<int>> &re
 
 }  // namespace
 
-extern "C" int fg_node_order(const int32_t *row_ptr, const int32_t *col, int V, int M, int TH,
-                             int32_t *perm_out, int *n_regions)
+extern "C" int fg_node_order_ex(const int32_t *row_ptr, const int32_t *col, int V, int M, int TH,
+                                int region_order, int32_t *perm_out, int *n_regions)
 {
-    if (!row_ptr || !col || !perm_out || V < 1 || M < V || TH < 1) return FG_EINVAL;
+    if (!row_ptr || !col || !perm_out || V < 1 || M < V || TH < 1 || region_order < 0 || region_order > 1)
+        return FG_EINVAL;
     try {
         const Graph g = neighbours(row_ptr, col, V);
-        const auto regions = regions_bfs(g, V, TH);
+        auto regions = regions_bfs(g, V, TH);
+        if (region_order == 1)   // larger regions take their turns first
+            std::stable_sort(regions.begin(), regions.end(),
+                             [](const std::vector<int> &a, const std::vector<int> &b) { return a.size() > b.size(); });
         const auto slots = interleave(regions, V, M);
         std::vector<int> idx(V, -1);   // slot index of a node within its region
         std::vector<int> region_of(V, -1);
@@ -215,4 +221,10 @@ extern "C" int fg_node_order(const int32_t *row_ptr, const int32_t *col, int V, 
         return FG_EOOM;
     }
     return FG_OK;
+}
+
+extern "C" int fg_node_order(const int32_t *row_ptr, const int32_t *col, int V, int M, int TH,
+                             int32_t *perm_out, int *n_regions)
+{
+    return fg_node_order_ex(row_ptr, col, V, M, TH, 0, perm_out, n_regions);
 }

@@ -1,23 +1,29 @@
 """The learned planner (the paper's packing and ordering choices, Sec. 3.2
 and 3.4, made by a latency model instead of a search).
 
-Every graph has a few candidate plans (radix of the SpIntra-CA groups,
-random or NOO node order; the packing t follows the J(t) rule).  The
-exhaustive planner builds and runs every candidate and keeps the fastest.
-The learned planner computes each candidate's statistics on the host
-(fg_plan_features, no GPU work), scores them with a three-layer perceptron
-trained on measured latencies (fg_mlp_*, FP32 kernels on the GPU), and
-builds only the candidate it predicts fastest.
+Every graph has candidate plans over the decisions the paper leaves to a
+search: the packing t (the J(t) rule's choice, or its neighbour: t = 1
+when the rule packs, else t = 2), the radix of the SpIntra-CA groups (2, 3
+or 4 bits), and the node order (a seeded random order, or node order
+optimisation, Alg. 1, with region size TH = 256 or 1024 and the regions
+interleaved in search order or larger first).  The exhaustive planner builds
+and runs every candidate and keeps the fastest.  The learned planner
+computes each candidate's statistics on the host (fg_plan_features, no GPU
+work), scores them with a three-layer perceptron trained on measured
+latencies (fg_mlp_*, FP32 kernels on the GPU), and builds only the
+candidate it predicts fastest.
 
   python -m paper_2506_10399_gb300.learn_planner measure OUT.jsonl [--budget S]
       layer latencies of every candidate of the held-out graphs (seeds
       2000-2019), then of the training graphs (seeds 1000-1199) until the
-      time budget runs out; one JSON line per graph
+      time budget runs out; one JSON line per graph.  Plans are built for
+      timing only (masks left zero: the kernels' work does not depend on the
+      values), inputs are random residues.
   python -m paper_2506_10399_gb300.learn_planner train DATA.jsonl MODEL.json
       (the measured data of this repository: data/planner_latencies.jsonl)
       fit the model on the training graphs (GPU) and report, on the held-out
       graphs, the latency of its choices against the exhaustive planner's
-      and against the default plan (radix 4, random order)
+      and against the default plan (radix 4, random order, t by the rule)
 """
 import json
 import sys
@@ -25,12 +31,20 @@ import time
 
 import numpy as np
 
-CANDIDATES = [dict(radix_bits=2, order="random"), dict(radix_bits=3, order="random"),
-              dict(radix_bits=4, order="random"), dict(radix_bits=2, order="noo")]
-DEFAULT = 0            # radix 4 (2 bits), random order: the plain method's plan
+CANDIDATES = [
+    dict(radix_bits=2, order="random", t="rule"),          # the default plan
+    dict(radix_bits=3, order="random", t="rule"),
+    dict(radix_bits=4, order="random", t="rule"),
+    dict(radix_bits=2, order="random", t="alt"),
+    dict(radix_bits=3, order="random", t="alt"),
+    dict(radix_bits=2, order="noo", TH=256, region_order=0, t="rule"),
+    dict(radix_bits=2, order="noo", TH=256, region_order=1, t="rule"),
+    dict(radix_bits=2, order="noo", TH=1024, region_order=0, t="rule"),
+    dict(radix_bits=3, order="noo", TH=256, region_order=1, t="rule"),
+]
+DEFAULT = 0            # radix 4 (2 bits), random order, t by the rule: the plain method's plan
 HELD_OUT = list(range(2000, 2020))
 TRAIN = list(range(1000, 1200))
-NOO_TH = 2048
 HIDDEN = 64
 DATA = __file__.rsplit("/", 1)[0] + "/data/planner_latencies.jsonl"
 MODEL = __file__.rsplit("/", 1)[0] + "/data/planner_model.json"
@@ -48,9 +62,25 @@ def packing_t(fg, P, w):
     return int(round(2.0 ** float(f[4])))
 
 
-def candidate_perm(fg, wl, w, slots, cand, seed):
+def candidate_t(cand, t_rule, V, M):
+    """The candidate's t: the rule's, or its neighbour (1 when the rule
+    packs, else 2 when two blocks of M/2 slots hold the graph); None when
+    the neighbour does not exist."""
+    if cand["t"] == "rule":
+        return t_rule
+    if t_rule > 1:
+        return 1
+    return 2 if 2 * V <= M else None
+
+
+def candidate_perm(fg, wl, w, slots, cand, seed, cache=None):
     if cand["order"] == "noo":
-        perm, _ = fg.node_order(w.row_ptr, w.col, slots, NOO_TH)
+        key = (slots, cand["TH"], cand["region_order"])
+        if cache is not None and key in cache:
+            return cache[key]
+        perm, _ = fg.node_order(w.row_ptr, w.col, slots, cand["TH"], cand["region_order"])
+        if cache is not None:
+            cache[key] = perm
         return perm
     return wl.random_order(w.V, slots, seed)
 
@@ -110,19 +140,24 @@ def measure(out_path, budget_s=1500.0):
             if time.time() - t0 > budget_s:
                 break
             w = wl.planner_graphs([s])[0]
-            t = packing_t(fg, P, w)
+            t_rule = packing_t(fg, P, w)
             rows = []
-            x = None
+            cache = {}
+            xs = {}
             for ci, c in enumerate(CANDIDATES):
-                perm = candidate_perm(fg, wl, w, M // t, c, s)
-                feat = fg.plan_features(P, w.row_ptr, w.col, w.val, w.W, perm, t=t, radix_bits=c["radix_bits"])
+                t = candidate_t(c, t_rule, w.V, M)
+                if t is None:
+                    continue
+                perm = candidate_perm(fg, wl, w, M // t, c, s, cache)
                 plan = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=t,
-                                     radix_bits=CANDIDATES[ci]["radix_bits"])
+                                     radix_bits=c["radix_bits"], no_encode=True)
+                feat = plan.features(w.row_ptr, w.col)
                 info = plan.info()
-                if x is None:
+                if t not in xs:
                     # the timing does not depend on the values: random residues
-                    x = torch.randint(0, 1 << 40, (info["n_in"], 2, ctx.nq, ctx.n), dtype=torch.int64,
-                                      device="cuda", generator=g)
+                    xs[t] = torch.randint(0, 1 << 40, (info["n_in"], 2, ctx.nq, ctx.n), dtype=torch.int64,
+                                          device="cuda", generator=g)
+                x = xs[t]
                 out = torch.empty((info["n_out"], 2, info["out_level"] + 1, ctx.n), dtype=torch.int64,
                                   device="cuda")
                 fg.gcn_layer_axw(ctx, keys, plan, x, out=out)
@@ -132,13 +167,14 @@ def measure(out_path, budget_s=1500.0):
                 fg.gcn_layer_axw(ctx, keys, plan, x, out=out)
                 e1.record()
                 torch.cuda.synchronize()
-                rows.append({"cand": ci, "ms": e0.elapsed_time(e1), "features": [float(v) for v in feat],
+                rows.append({"cand": ci, "t": t, "ms": e0.elapsed_time(e1),
+                             "features": [float(v) for v in feat],
                              "rotations": info["rotations"], "groups": info["n_groups"]})
                 plan.close()
                 del out
-            f.write(json.dumps({"seed": s, "V": w.V, "F": w.X.shape[1], "t": t, "cands": rows}) + "\n")
+            f.write(json.dumps({"seed": s, "V": w.V, "F": w.X.shape[1], "t_rule": t_rule, "cands": rows}) + "\n")
             f.flush()
-            del x
+            del xs
     print(json.dumps({"graphs_measured": sum(1 for _ in open(out_path)), "seconds": round(time.time() - t0)}))
 
 
@@ -192,6 +228,11 @@ def load_model(path=MODEL):
     return m, np.array(d["mean"]), np.array(d["std"])
 
 
+def default_ms(r):
+    """Measured latency of a graph's default candidate."""
+    return next(c["ms"] for c in r["cands"] if c["cand"] == DEFAULT)
+
+
 def choose(m, mu, sd, features):
     """Index of the candidate the model predicts fastest (features as rows)."""
     b, _ = m.choose((np.asarray(features, dtype=np.float64) - mu) / sd)
@@ -208,7 +249,7 @@ def evaluate(m, mu, sd, rows):
         ms = [c["ms"] for c in r["cands"]]
         chosen.append(ms[b])
         best.append(min(ms))
-        default.append(ms[DEFAULT])
+        default.append(default_ms(r))
         hits += int(ms[b] == min(ms))
     if not rows:
         return {}

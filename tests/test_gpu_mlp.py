@@ -83,3 +83,22 @@ def test_trained_planner_choices_on_the_gpu(fg):
         srt = np.sort(f)
         if srt[1] - srt[0] > 1e-4:        # a clear winner: both must pick it
             assert lp.choose(m, mu, sd, F) == int(np.argmin(f))
+
+
+def test_features_of_a_built_plan_equal_the_host_features():
+    """fg_plan_features_built (used while measuring) gives the statistics
+    fg_plan_features computes from the same inputs."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    fg = __graft_entry__.build()
+    from paper_2506_10399_gb300 import workloads as wl
+    P = dict(log_n=13, q_bits=[60] + [45] * 7, p_bits=[60] * 2, alpha=4, log_scale=45)
+    ctx = fg.Context(**P)
+    w = wl.make_workload(graph="chung_lu", V=900, deg=4.0, gamma=2.5, F=20, Fp=4, seed=3)
+    for t, r in ((1, 2), (2, 3)):
+        perm = wl.random_order(w.V, ctx.slots // t, t)
+        plan = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=t, radix_bits=r, no_encode=True)
+        want = fg.plan_features(P, w.row_ptr, w.col, w.val, w.W, perm, t=t, radix_bits=r)
+        np.testing.assert_array_equal(plan.features(w.row_ptr, w.col), want)

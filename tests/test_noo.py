@@ -124,14 +124,26 @@ def test_greedy_slot_has_least_conflicts(seed):
 
 @pytest.mark.parametrize("case", [("er", 64, 4.0, None, 128, 16), ("chung_lu", 300, 4.0, 2.5, 512, 48),
                                   ("chung_lu", 400, 3.9, 2.2, 1024, 64)])
-def test_library_node_order_matches_oracle(case):
+@pytest.mark.parametrize("region_order", [0, 1])
+def test_library_node_order_matches_oracle(case, region_order):
     import paper_2506_10399_gb300 as fg
     graph, V, d, gamma, M, TH = case
     w = wl.make_workload(graph=graph, V=V, deg=d, gamma=gamma, F=4, Fp=2, seed=11)
-    want, nr = noo.node_order(w.row_ptr, w.col, w.V, M, TH)
-    got, nr2 = fg.node_order(w.row_ptr, w.col, M, TH)
+    want, nr = noo.node_order(w.row_ptr, w.col, w.V, M, TH, region_order)
+    got, nr2 = fg.node_order(w.row_ptr, w.col, M, TH, region_order)
     assert nr2 == nr
     np.testing.assert_array_equal(got, want)
+
+
+def test_region_order_larger_first():
+    """region_order 1: the interleaving turns go to larger regions first (the
+    star-plus-path graph's regions have sizes 1, 1, 3, 2, 1)."""
+    rp, col, _ = _star_plus_path()
+    regions, _, _ = noo.regions_bfs(rp, col, 8, TH=8)
+    ordered = sorted(regions, key=len, reverse=True)
+    assert ordered[0] == [1, 2, 3] and ordered[1] == [4, 6]
+    perm, _ = noo.node_order(rp, col, 8, 8, 8, region_order=1)
+    assert perm[1] == 0 and perm[4] == 1       # first turns: regions {1,2,3}, {4,6}
 
 
 def test_library_node_order_rejects_bad_input():
