@@ -271,6 +271,48 @@ def run_ntt(args, fg=None):
             "alg_GB_per_s": round(count * ctx.n * 16 / (ms / 1e3) / 1e9, 1)}
 
 
+# ------------------------------------------------------------------ ALU roofline
+def alu_roofline(fg, ctx, plan, breakdown, F, Fp, alpha):
+    """The integer-multiply roof of the three contraction kernels.  Peak: the
+    measured rate of mad.wide.u32 (32 x 32 -> 64-bit multiply-add, the step
+    of the split products; fg_int_mul_peak, eight independent chains per
+    thread on every SM).  Achieved: the products each kernel's arithmetic
+    performs, counted on the plan, times four mad.wide.u32 per product (a
+    product of two split words, 23- or 30-bit halves: lo x lo, lo x hi,
+    hi x lo, hi x hi), over the kernel class's measured time in one layer:
+      group_mac: terms x 2F' polynomials x E limbs x N (E = extended limbs at
+                 the group's level);
+      ks_ip:     rotations x F' columns x E limbs x N x 2 parts x beta digits;
+      comb:      F x F' x 2 parts x (L+1) limbs x N.
+    Instruction counts of the integer pipes from ncu, where captured, are in
+    profiles/."""
+    peak = fg.int_mul_peak(ctx, "mad.wide.u32")
+    rec = plan.describe()
+    V, Fi = int(rec[4]), int(rec[5])
+    t = int(rec[2])
+    i = 13 + V
+    i += Fi * Fp if t == 1 else -(-Fi // t) * Fp + 1 + int(rec[13 + V + -(-Fi // t) * Fp])
+    N, np_ = ctx.n, ctx.np
+    prods = {"group_mac": 0.0, "ks_ip": 0.0, "comb": float(F) * Fp * 2 * (int(rec[7]) + 1) * N}
+    for _ in range(int(rec[11])):
+        lvl, nrot = int(rec[i + 2]), int(rec[i + 5])
+        E = lvl + 1 + np_
+        beta = -(-(lvl + 1) // alpha)
+        i += 6 + 2 * nrot
+        nterm = int(rec[i])
+        i += 1 + 4 * nterm
+        prods["group_mac"] += float(nterm) * 2 * Fp * E * N
+        prods["ks_ip"] += float(nrot) * Fp * E * N * 2 * beta
+    out = {"unit": "mad.wide.u32/s", "peak": peak, "peak_kind": "measured (fg_int_mul_peak)",
+           "per_product": 4, "kernels": {}}
+    for k, pr in prods.items():
+        ms = breakdown.get(k, {}).get("ms") or 0
+        if ms > 0:
+            a = 4 * pr / (ms / 1e3)
+            out["kernels"][k] = {"achieved": a, "frac": round(a / peak, 4), "products": pr}
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import torch
@@ -361,6 +403,7 @@ def run_ours(args):
                           "GB_per_s": round(by / ms / 1e6, 1) if ms > 0 else None}
     ctx.time_kernels(None)
     dominant = max(breakdown, key=lambda k: breakdown[k]["ms"])
+    alu = alu_roofline(fg, ctx, plan, breakdown, w.X.shape[1], Fp=info["n_out"], alpha=c["alpha"])
 
     # ---- timed region: K steps, HBM-resident inputs
     clocks = Clocks(local)
@@ -421,6 +464,7 @@ def run_ours(args):
                      "calls_timed": k_calls,
                      "alg_bytes_per_call": round(k_bytes / max(1, k_calls))},
         "breakdown_ms": breakdown,
+        "alu": alu,
         "e2e": {"value": round(e2e_ms, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -637,8 +681,9 @@ def run_inter(args):
 def run_batched(args):
     """Many single-layer queries of uneven size (the batch recipe of
     workloads.batch_queries) on one GPU: one at a time through
-    fg_gcn_layer_axw, then all at once through fg_gcn_layer_batch (streams
-    chosen by timing, one CUDA graph).  Checks that both give the same
+    fg_gcn_layer_axw, then all at once through fg_gcn_layer_batch (kernel
+    launch configuration and stream count chosen by timing on the first call,
+    one CUDA graph).  Checks that both give the same
     ciphertexts word for word and that two queries decrypt within 2^-20."""
     import torch
     import __graft_entry__
@@ -693,7 +738,7 @@ def run_batched(args):
     used = {}
 
     def batched():
-        lv, s = fg.gcn_layer_batch(ctx, keys, plans, ins, outs)
+        lv, s = fg.gcn_layer_batch(ctx, keys, plans, ins, outs, tune=True)
         used["streams"] = s
 
     for _ in range(args.warmup):
@@ -712,6 +757,7 @@ def run_batched(args):
             "unit": "ms/batch", "higher_is_better": False, "queries": nq,
             "plain_ms": round(plain_ms, 3), "batched_ms": round(batch_ms, 3),
             "speedup": round(plain_ms / batch_ms, 3), "streams": used.get("streams"),
+            "tuning": dict(zip(("config", "pass_ms_per_candidate"), fg.batch_tuning(ctx))),
             "bit_exact_vs_plain": exact, "decrypt_max_abs_err_vs_fp64": err,
             "rotations_per_batch": rot, "rotations_per_s_batched": round(rot / (batch_ms / 1e3), 1),
             "gpu_launches_per_batch": {"plain": plain_launches, "batched": batch_launches},
@@ -739,7 +785,7 @@ def main():
     ap.add_argument("--ntt", action="store_true", help="NTT throughput only")
     ap.add_argument("--batched", action="store_true",
                     help="batched form: many queries one at a time vs all at once")
-    ap.add_argument("--queries", type=int, default=16, help="queries in the batched form")
+    ap.add_argument("--queries", type=int, default=32, help="queries in the batched form")
     ap.add_argument("--two-layer", action="store_true", help="two-layer GCN with x^2 between")
     ap.add_argument("--workload", default="pubmed_like", choices=["pubmed_like", "cora_like"],
                     help="workload of --two-layer")

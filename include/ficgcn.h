@@ -111,6 +111,10 @@ void fg_free(void *blob);
 int fg_ctx_time_kernels(fg_ctx *ctx, const char *kernel_class);
 int fg_ctx_kernel_times(fg_ctx *ctx, double *ms, int64_t *calls, double *alg_bytes);
 int fg_ctx_launch_count(const fg_ctx *ctx, int64_t *launches);
+/* Wait for the device, then free the context's workspace (the scratch
+ * buffers its calls grow on demand and keep for reuse); later calls
+ * allocate again.  Keys, plans and tables stay. */
+int fg_ctx_release_workspace(fg_ctx *ctx);
 
 /* ---------------------------------------------------------------- client */
 
@@ -336,16 +340,35 @@ int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *plan,
  * its own stream and workspace; opts->streams = 0 picks the count by timing
  * 8, 4, 2 and 1 on the first call (*streams_used, may be NULL, receives it).
  * With opts->graph = 1 the batch is captured into a CUDA graph on the first
- * call and replayed by later calls with the same plans and buffers.  Every
- * query runs exactly the kernels of fg_gcn_layer_axw, so the outputs are
- * the same word for word.  opts NULL = {0, 1}.  Host buffers: FG_EINVAL. */
+ * call and replayed by later calls with the same plans and buffers.  With
+ * opts->tune = 1 the first call also picks, by timing whole batch passes,
+ * the launch configuration of the batch's kernels: the N = 2^16 NTT tile
+ * (pass A columns and pass B rows per CTA, 16 or 8 each), the key switch's
+ * register budget (its launch bound at the default or one CTA per SM
+ * fewer) and the output count from which a group-MAC CTA runs three thread
+ * groups (7, 4 or 13); fg_batch_tuning reports the choice.  Every
+ * configuration computes the same words, and every query runs the kernels
+ * of fg_gcn_layer_axw, so the outputs are the same word for word.  opts
+ * NULL = {0, 1, 0}.  Host buffers: FG_EINVAL. */
 typedef struct {
     int streams;   /* 1..16 layers in flight, 0 = chosen by timing */
     int graph;     /* 1 = capture once, replay while the arguments repeat */
+    int tune;      /* 1 = choose the kernels' launch configuration by timing */
 } fg_batch_opts;
 int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *plans, int n,
                        const uint64_t *const *in_cts, uint64_t *const *out_cts,
                        const fg_batch_opts *opts, int *out_levels, int *streams_used);
+/* The batched form's launch configuration: cfg = {NTT pass-A columns, NTT
+ * pass-B rows, key-switch bound one CTA per SM fewer (0/1), group-MAC
+ * three-group threshold}; ms[0..*n) the batch pass time of each
+ * configuration tried (the default first), at most cap entries.  Before any
+ * tuned batch call cfg holds the defaults and *n = 0. */
+int fg_batch_tuning(const fg_ctx *ctx, int cfg[4], double *ms, int cap, int *n);
+/* Fix the launch configuration every later call of this context uses
+ * outside tuned batches (the same four fields as fg_batch_tuning; NTT tiles
+ * 16 or 8, key-switch flag 0 or 1, group-MAC threshold >= 1).  Results do
+ * not change; speed may.  FG_EINVAL for other values. */
+int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[4]);
 
 /* Ciphertext products (paper Sec. 2.1 CMult; the x^2 activation between
  * GCN layers multiplies a ciphertext by itself): for each of n pairs,
@@ -400,6 +423,15 @@ int fg_poly_mul_noalloc(fg_ctx *ctx, const uint64_t *a, const uint64_t *b, int l
  * measurements. */
 int fg_ntt(fg_ctx *ctx, uint64_t *data, int count, const int *prime_idx, int period,
            int inverse);
+
+/* Measured integer-multiply throughput of the context's GPU (the ALU roof
+ * of the modular kernels; the paper has no counterpart): eight independent
+ * chains of one instruction per thread on eight 256-thread CTAs per SM,
+ * timed with CUDA events.  op 0 = mad.wide.u32 (32 x 32 -> 64-bit product
+ * plus a 64-bit addend, the step of the split products), 1 = mul.hi.u32,
+ * 2 = mad.lo.u32.  *ops_per_s: instructions per second (one per thread)
+ * over the whole GPU. */
+int fg_int_mul_peak(fg_ctx *ctx, int op, double *ops_per_s);
 
 #ifdef __cplusplus
 }

@@ -105,6 +105,10 @@ class Context:
         _check(self, _lib().lib.fg_ctx_device_bytes(self._h, ctypes.byref(b)))
         return b.value
 
+    def release_workspace(self):
+        """Free the scratch buffers the context keeps between calls."""
+        _check(self, _lib().lib.fg_ctx_release_workspace(self._h))
+
     def time_kernels(self, kernel_class):
         """Start CUDA-event timing of one kernel class (None stops)."""
         _check(self, _lib().lib.fg_ctx_time_kernels(
@@ -421,9 +425,10 @@ def gcn_layer_axw(ctx, keys, plan, in_cts, out=None):
     return out, lvl.value, sc.value
 
 
-def gcn_layer_batch(ctx, keys, plans, ins, outs, streams=0, graph=True):
+def gcn_layer_batch(ctx, keys, plans, ins, outs, streams=0, graph=True, tune=False):
     """Several layers at once (device tensors only): query q runs plans[q] on
-    ins[q] into outs[q].  Returns (output levels, streams used)."""
+    ins[q] into outs[q]; tune picks the kernels' launch configuration by
+    timing on the first call.  Returns (output levels, streams used)."""
     nat = _lib()
     n = len(plans)
     assert len(ins) == n and len(outs) == n
@@ -432,10 +437,27 @@ def gcn_layer_batch(ctx, keys, plans, ins, outs, streams=0, graph=True):
     O = (ctypes.c_void_p * n)(*[_ptr(x).value for x in outs])
     lv = (ctypes.c_int * n)()
     su = ctypes.c_int()
-    o = nat.BatchOpts(int(streams), 1 if graph else 0)
+    o = nat.BatchOpts(int(streams), 1 if graph else 0, 1 if tune else 0)
     _check(ctx, nat.lib.fg_gcn_layer_batch(ctx._h, keys._h, P, n, I, O, ctypes.byref(o), lv,
                                            ctypes.byref(su)))
     return list(lv), su.value
+
+
+def batch_tuning(ctx):
+    """({"ntt_cols", "ntt_rows", "ks_split", "gmac_groups"}, [ms of each
+    configuration tried, the default first])."""
+    cfg = (ctypes.c_int * 4)()
+    ms = np.zeros(64, np.float64)
+    n = ctypes.c_int()
+    _check(ctx, _lib().lib.fg_batch_tuning(ctx._h, cfg, ctypes.c_void_p(ms.ctypes.data), 64, ctypes.byref(n)))
+    keys = ("ntt_cols", "ntt_rows", "ks_split", "gmac_groups")
+    return dict(zip(keys, list(cfg))), [float(v) for v in ms[:n.value]]
+
+
+def set_tuning(ctx, ntt_cols=16, ntt_rows=16, ks_split=0, gmac_groups=7):
+    """Fix the launch configuration of the context's later calls."""
+    cfg = (ctypes.c_int * 4)(ntt_cols, ntt_rows, ks_split, gmac_groups)
+    _check(ctx, _lib().lib.fg_ctx_set_tuning(ctx._h, cfg))
 
 
 N_PLAN_FEATURES = 15
@@ -467,6 +489,17 @@ def plan_features(params, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=Tru
     if rc != 0:
         raise FicgcnError(rc, "plan features failed")
     return out
+
+
+INT_MUL_OPS = {"mad.wide.u32": 0, "mul.hi.u32": 1, "mad.lo.u32": 2}
+
+
+def int_mul_peak(ctx, op="mad.wide.u32"):
+    """Measured rate (instructions per second, whole GPU) of one 32-bit
+    multiply instruction: the ALU roof of the modular kernels."""
+    r = ctypes.c_double()
+    _check(ctx, _lib().lib.fg_int_mul_peak(ctx._h, INT_MUL_OPS[op], ctypes.byref(r)))
+    return r.value
 
 
 MODE_SPINTRA, MODE_INTER = 0, 1

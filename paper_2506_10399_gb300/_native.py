@@ -31,7 +31,7 @@ class PlanOpts(ctypes.Structure):
 
 
 class BatchOpts(ctypes.Structure):
-    _fields_ = [("streams", c_int), ("graph", c_int)]
+    _fields_ = [("streams", c_int), ("graph", c_int), ("tune", c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -90,6 +90,9 @@ SIGS = {
     "fg_mul_relin_rescale": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "fg_gcn_layer_batch": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
                                    P(BatchOpts), c_void_p, P(c_int)]),
+    "fg_ctx_set_tuning": (c_int, [c_void_p, c_void_p]),
+    "fg_ctx_release_workspace": (c_int, [c_void_p]),
+    "fg_batch_tuning": (c_int, [c_void_p, c_void_p, c_void_p, c_int, P(c_int)]),
     "fg_gcn_layer_axw": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int,
                                  P(c_int), P(c_double)]),
     "fg_rotate": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
@@ -97,6 +100,7 @@ SIGS = {
     "fg_poly_mul": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "fg_poly_mul_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "fg_ntt": (c_int, [c_void_p, c_void_p, c_int, P(c_int), c_int, c_int]),
+    "fg_int_mul_peak": (c_int, [c_void_p, c_int, P(c_double)]),
 }
 
 for _name, (_res, _args) in SIGS.items():

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libficgcn.so")
 BUILD = os.path.join(HERE, "_build")
 
-CUDA_SRCS = ["kernels.cu", "api.cu", "layer.cu", "noalloc.cu", "mlp.cu"]
+CUDA_SRCS = ["kernels.cu", "api.cu", "layer.cu", "noalloc.cu", "mlp.cu", "peak.cu"]
 HOST_SRCS = ["host_math.cpp", "planner.cpp", "noo.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -125,6 +125,23 @@ void *fg_ctx::buf(const std::string &name0, size_t bytes)
     return p;
 }
 
+extern "C" int fg_ctx_release_workspace(fg_ctx *ctx)
+{
+    if (!ctx) return FG_EINVAL;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        ctx->err = "device synchronisation failed";
+        return FG_ECUDA;
+    }
+    for (auto &kv : ctx->ws) cudaFree(kv.second.first);
+    ctx->ws.clear();
+    if (ctx->batch.exec) {   // a captured batch refers to the workspace
+        cudaGraphExecDestroy(ctx->batch.exec);
+        ctx->batch.exec = nullptr;
+        ctx->batch.args.clear();
+    }
+    return FG_OK;
+}
+
 cudaEvent_t fg_ctx::event()
 {
     if (ev_next == ev_pool.size()) {

@@ -83,7 +83,26 @@ struct ConvTab {
     u64 negb[72];             // -B mod out prime, same form (the centred conversion's correction)
 };
 
+// kernel launch configurations that compute the same words and differ in
+// speed only; the batched form tunes them per shape (defaults: the
+// configurations measured best on the benchmark layer)
+struct Tune {
+    int ntt_cols = 16;     // N = 2^16 NTT pass A: columns per CTA (16 or 8)
+    int ntt_rows = 16;     // N = 2^16 NTT pass B: rows per CTA (16 or 8)
+    int ks_split = 0;      // key switch: 0 = launch bounds by digit count, 1 = one CTA per SM fewer
+    int gmac_groups = 7;   // group MAC: outputs from which a CTA runs three thread groups
+    bool operator==(const Tune &o) const
+    {
+        return ntt_cols == o.ntt_cols && ntt_rows == o.ntt_rows && ks_split == o.ks_split &&
+               gmac_groups == o.gmac_groups;
+    }
+};
+
 struct fg_ctx {
+    Tune tune;                   // launch configurations in use
+    Tune batch_tune;             // ... inside batched calls (chosen by timing)
+    bool batch_tuned = false;
+    std::vector<double> tune_ms; // the batch's time under each configuration tried
     // parameters
     int log_n = 0, n = 0, slots = 0;
     int nq = 0, np = 0, alpha = 0;

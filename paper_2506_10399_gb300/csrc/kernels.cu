@@ -138,10 +138,15 @@ __device__ __forceinline__ void gs16(u64 (&v)[16], const ulonglong2 (&w)[15], u6
 constexpr int kR16Row = 272;   // 256 elements + 16 pad words per row (pass B shared memory)
 __device__ __forceinline__ int pad16(int pos) { return pos + (pos >> 4); }
 
-template <bool LAZY>
+// Tiles: pass A takes COLS (16 or 8) of the 256 columns per CTA, one
+// thread per (column, group of 16 rows), 16 x COLS threads; pass B takes
+// ROWS (16 or 8) of the 256 rows per CTA, 16 threads per row.  Both tile
+// sizes compute the same transform word for word; the batched form picks
+// one per shape by timing.
+template <bool LAZY, int COLS>
 __device__ __forceinline__ void fwd_a16_body(const u64 *s, u64 *d, const ulonglong2 *stw, u64 q, u64 *sm)
 {
-    const int t = threadIdx.x, c = t & 15, r = t >> 4;   // r: r0 in round 1, r1 in round 2
+    const int t = threadIdx.x, c = t % COLS, r = t / COLS;   // r: r0 in round 1, r1 in round 2
     constexpr int N2 = 256;
     const u64 q2 = 2 * q;
     u64 v[16];
@@ -152,10 +157,10 @@ __device__ __forceinline__ void fwd_a16_body(const u64 *s, u64 *d, const ulonglo
     for (int k = 0; k < 15; k++) w[k] = stw[k + 1];   // stage st, group g at (1 << st) + g
     ct16<LAZY>(v, w, q, q2);
 #pragma unroll
-    for (int m = 0; m < 16; m++) sm[(r + 16 * m) * 16 + c] = v[m];
+    for (int m = 0; m < 16; m++) sm[(r + 16 * m) * COLS + c] = v[m];
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < 16; m++) v[m] = sm[(16 * r + m) * 16 + c];
+    for (int m = 0; m < 16; m++) v[m] = sm[(16 * r + m) * COLS + c];
 #pragma unroll
     for (int st = 0; st < 4; st++)
 #pragma unroll
@@ -165,24 +170,25 @@ __device__ __forceinline__ void fwd_a16_body(const u64 *s, u64 *d, const ulonglo
     for (int m = 0; m < 16; m++) d[(size_t)(16 * r + m) * N2 + c] = v[m];   // lazy
 }
 
-__global__ void __launch_bounds__(256, 3)
+template <int COLS>
+__global__ void __launch_bounds__(16 * COLS, 48 / COLS)
 ntt16_fwd_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ tw)
 {
     const int limb = blockIdx.y;
     const int col = limb % bt.per_row, row = limb / bt.per_row;
     const int pi = bt.pidx[col];
     if (pi < 0) return;
-    __shared__ u64 sm[256 * 16];
+    __shared__ u64 sm[256 * COLS];
     __shared__ ulonglong2 stw[256];
     const u64 q = primes[pi].q;
     const ulonglong2 *twp = tw + (size_t)pi * 65536;
-    stw[threadIdx.x] = twp[threadIdx.x];
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) stw[k] = twp[k];
     __syncthreads();
-    const int c0 = blockIdx.x * 16;
+    const int c0 = blockIdx.x * COLS;
     const u64 *src = bt.src + ((size_t)row * bt.src_stride + col) * 65536 + c0;
     u64 *dst = bt.dst + ((size_t)row * bt.dst_stride + col) * 65536 + c0;
-    if (q < (1ull << 47)) fwd_a16_body<true>(src, dst, stw, q, sm);
-    else fwd_a16_body<false>(src, dst, stw, q, sm);
+    if (q < (1ull << 47)) fwd_a16_body<true, COLS>(src, dst, stw, q, sm);
+    else fwd_a16_body<false, COLS>(src, dst, stw, q, sm);
 }
 
 template <bool LAZY>
@@ -220,7 +226,8 @@ __device__ __forceinline__ void fwd_b16_body(u64 *d, const ulonglong2 *twp, cons
                         : make_ulonglong2(reduce4(v[m], q), reduce4(v[m + 1], q));
 }
 
-__global__ void __launch_bounds__(256, 3)
+template <int ROWS>
+__global__ void __launch_bounds__(16 * ROWS, 48 / ROWS)
 ntt16_fwd_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ tw,
             const ulonglong2 *__restrict__ tw_rows)
 {
@@ -228,10 +235,10 @@ ntt16_fwd_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 
     const int col = limb % bt.per_row, row = limb / bt.per_row;
     const int pi = bt.pidx[col];
     if (pi < 0) return;
-    __shared__ u64 sm[16 * kR16Row];
+    __shared__ u64 sm[ROWS * kR16Row];
     const PrimeC P = primes[pi];
     const ulonglong2 *twp = tw + (size_t)pi * 65536;
-    const int row0 = blockIdx.x * 16;
+    const int row0 = blockIdx.x * ROWS;
     u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * 65536 + (size_t)row0 * 256;
     const ulonglong2 *rows = tw_rows + (size_t)pi * 256 * 15 * 16;
     if (P.q < (1ull << 47)) fwd_b16_body<true>(d, twp, rows, row0, P, sm);
@@ -274,7 +281,8 @@ __device__ __forceinline__ void inv_b16_body(const u64 *s, u64 *d, const ulonglo
     for (int m = 0; m < 16; m++) drow[j + 16 * m] = v[m];   // lazy (< 2^9 q or < 2q)
 }
 
-__global__ void __launch_bounds__(256, 3)
+template <int ROWS>
+__global__ void __launch_bounds__(16 * ROWS, 48 / ROWS)
 ntt16_inv_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ itw,
             const ulonglong2 *__restrict__ itw_rows)
 {
@@ -282,10 +290,10 @@ ntt16_inv_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 
     const int col = limb % bt.per_row, row = limb / bt.per_row;
     const int pi = bt.pidx[col];
     if (pi < 0) return;
-    __shared__ u64 sm[16 * kR16Row];
+    __shared__ u64 sm[ROWS * kR16Row];
     const u64 q = primes[pi].q;
     const ulonglong2 *twp = itw + (size_t)pi * 65536;
-    const int row0 = blockIdx.x * 16;
+    const int row0 = blockIdx.x * ROWS;
     const u64 *s = bt.src + ((size_t)row * bt.src_stride + col) * 65536 + (size_t)row0 * 256;
     u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * 65536 + (size_t)row0 * 256;
     const ulonglong2 *rows = itw_rows + (size_t)pi * 256 * 15 * 16;
@@ -293,11 +301,11 @@ ntt16_inv_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 
     else inv_b16_body<false>(s, d, twp, rows, row0, q, sm);
 }
 
-template <bool LAZY>
+template <bool LAZY, int COLS>
 __device__ __forceinline__ void inv_a16_body(u64 *d, const ulonglong2 *stw, u64 q, u64 ni, u64 nis,
                                              u64 *sm)
 {
-    const int t = threadIdx.x, c = t & 15, r = t >> 4;
+    const int t = threadIdx.x, c = t % COLS, r = t / COLS;
     constexpr int N2 = 256;
     const u64 q2 = 2 * q;
     u64 v[16];
@@ -310,10 +318,10 @@ __device__ __forceinline__ void inv_a16_body(u64 *d, const ulonglong2 *stw, u64 
         for (int g = 0; g < (1 << st); g++) w[(1 << st) - 1 + g] = stw[(1 << (st + 4)) + (r << st) + g];
     gs16<LAZY>(v, w, q, q2, 8);
 #pragma unroll
-    for (int m = 0; m < 16; m++) sm[(16 * r + m) * 16 + c] = v[m];
+    for (int m = 0; m < 16; m++) sm[(16 * r + m) * COLS + c] = v[m];
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < 16; m++) v[m] = sm[(r + 16 * m) * 16 + c];
+    for (int m = 0; m < 16; m++) v[m] = sm[(r + 16 * m) * COLS + c];
 #pragma unroll
     for (int k = 0; k < 15; k++) w[k] = stw[k + 1];
     gs16<LAZY>(v, w, q, q2, 12);
@@ -321,7 +329,8 @@ __device__ __forceinline__ void inv_a16_body(u64 *d, const ulonglong2 *stw, u64 
     for (int m = 0; m < 16; m++) d[(size_t)(r + 16 * m) * N2 + c] = shoup_mul(v[m], ni, nis, q);
 }
 
-__global__ void __launch_bounds__(256, 3)
+template <int COLS>
+__global__ void __launch_bounds__(16 * COLS, 48 / COLS)
 ntt16_inv_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ itw,
             const u64 *__restrict__ ninv)
 {
@@ -329,17 +338,17 @@ ntt16_inv_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 
     const int col = limb % bt.per_row, row = limb / bt.per_row;
     const int pi = bt.pidx[col];
     if (pi < 0) return;
-    __shared__ u64 sm[256 * 16];
+    __shared__ u64 sm[256 * COLS];
     __shared__ ulonglong2 stw[256];
     const u64 q = primes[pi].q;
     const ulonglong2 *twp = itw + (size_t)pi * 65536;
-    stw[threadIdx.x] = twp[threadIdx.x];
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) stw[k] = twp[k];
     __syncthreads();
-    const int c0 = blockIdx.x * 16;
+    const int c0 = blockIdx.x * COLS;
     u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * 65536 + c0;
     const u64 ni = ninv[2 * pi], nis = ninv[2 * pi + 1];
-    if (q < (1ull << 47)) inv_a16_body<true>(d, stw, q, ni, nis, sm);
-    else inv_a16_body<false>(d, stw, q, ni, nis, sm);
+    if (q < (1ull << 47)) inv_a16_body<true, COLS>(d, stw, q, ni, nis, sm);
+    else inv_a16_body<false, COLS>(d, stw, q, ni, nis, sm);
 }
 
 // Stages are taken two at a time (radix-4 rounds: four elements, four
@@ -966,8 +975,15 @@ struct KsSet {
 // With pmodq given, part 0 also receives P phi_g(c0) on the limbs of Q
 // (P mod q_i and its Shoup companion at pmodq[2i], pmodq[2i+1]), so that
 // ModDown of u is Rot(c) itself: ModDown(A + P B) = ModDown(A) + B exactly.
-template <int BETA>
-__global__ void __launch_bounds__(256, BETA <= 4 ? 4 : BETA <= 5 ? 3 : 2)
+// LESS: CTAs per SM one fewer than the default bound (more registers per
+// thread, fewer spills, lower occupancy); a tuning choice of the batched form.
+constexpr int ks_min_blocks(int beta, int less)
+{
+    return (beta <= 4 ? 4 : beta <= 5 ? 3 : 2) - less > 0 ? (beta <= 4 ? 4 : beta <= 5 ? 3 : 2) - less : 1;
+}
+
+template <int BETA, int LESS>
+__global__ void __launch_bounds__(256, ks_min_blocks(BETA, LESS))
 k_ks_ip(const KsSet ks, int KL, const u64 *__restrict__ lane, int ls,
         const u64 *__restrict__ digits, int ncol, int level, int E, int alpha, int nq,
         int log_n, const PrimeC *__restrict__ primes, const u64 *__restrict__ pmodq)
@@ -1450,23 +1466,34 @@ KTimer::~KTimer()
 }
 
 
-static void ntt16_launch(fg_ctx *ctx, const Batch &bt, int count, bool inverse)
+template <int COLS, int ROWS>
+static void ntt16_launch_t(fg_ctx *ctx, const Batch &bt, int count, bool inverse)
 {
     const auto *fwd = (const ulonglong2 *)ctx->d_fwd;
     const auto *inv = (const ulonglong2 *)ctx->d_inv;
-    dim3 gA(16, count), gB(16, count);
+    dim3 gA(256 / COLS, count), gB(256 / ROWS, count);
     Batch b2 = bt;
     b2.src = b2.dst;
     b2.src_stride = b2.dst_stride;
     if (!inverse) {
-        ntt16_fwd_a<<<gA, 256, 0, ctx->stream>>>(bt, ctx->d_primes, fwd);
-        ntt16_fwd_b<<<gB, 256, 0, ctx->stream>>>(b2, ctx->d_primes, fwd,
-                                                 (const ulonglong2 *)ctx->d_fwd_rows);
+        ntt16_fwd_a<COLS><<<gA, 16 * COLS, 0, ctx->stream>>>(bt, ctx->d_primes, fwd);
+        ntt16_fwd_b<ROWS><<<gB, 16 * ROWS, 0, ctx->stream>>>(b2, ctx->d_primes, fwd,
+                                                            (const ulonglong2 *)ctx->d_fwd_rows);
     } else {
-        ntt16_inv_b<<<gB, 256, 0, ctx->stream>>>(bt, ctx->d_primes, inv,
-                                                 (const ulonglong2 *)ctx->d_inv_rows);
-        ntt16_inv_a<<<gA, 256, 0, ctx->stream>>>(b2, ctx->d_primes, inv, ctx->d_ninv);
+        ntt16_inv_b<ROWS><<<gB, 16 * ROWS, 0, ctx->stream>>>(bt, ctx->d_primes, inv,
+                                                            (const ulonglong2 *)ctx->d_inv_rows);
+        ntt16_inv_a<COLS><<<gA, 16 * COLS, 0, ctx->stream>>>(b2, ctx->d_primes, inv, ctx->d_ninv);
     }
+}
+
+// the tile of the N = 2^16 transform from the context's tuning
+static void ntt16_launch(fg_ctx *ctx, const Batch &bt, int count, bool inverse)
+{
+    const bool ca = ctx->tune.ntt_cols == 8, rb = ctx->tune.ntt_rows == 8;
+    if (!ca && !rb) ntt16_launch_t<16, 16>(ctx, bt, count, inverse);
+    else if (ca && !rb) ntt16_launch_t<8, 16>(ctx, bt, count, inverse);
+    else if (!ca && rb) ntt16_launch_t<16, 8>(ctx, bt, count, inverse);
+    else ntt16_launch_t<8, 8>(ctx, bt, count, inverse);
 }
 
 template <int LOGN>
@@ -1711,10 +1738,16 @@ static void ks_launch(fg_ctx *ctx, const std::vector<const KeyDev *> &keys, cons
                              (double)ks.n * (2.0 * beta * E + 2.0 * ncol * E)) * N * 8);
 #define FG_KS_CASE(B)                                                                          \
     case B:                                                                                    \
-        k_ks_ip<B><<<g1, 256, 0, ctx->stream>>>(ks, KL, lane, ls, digits, ncol, level, E,      \
-                                                ctx->alpha, ctx->nq, ctx->log_n, ctx->d_primes, \
-                                                pmodq);                                        \
+        if (less)                                                                              \
+            k_ks_ip<B, (B <= 8 ? 1 : 0)><<<g1, 256, 0, ctx->stream>>>(                          \
+                ks, KL, lane, ls, digits, ncol, level, E, ctx->alpha, ctx->nq, ctx->log_n,     \
+                ctx->d_primes, pmodq);                                                         \
+        else                                                                                   \
+            k_ks_ip<B, 0><<<g1, 256, 0, ctx->stream>>>(ks, KL, lane, ls, digits, ncol, level,   \
+                                                       E, ctx->alpha, ctx->nq, ctx->log_n,     \
+                                                       ctx->d_primes, pmodq);                  \
         break;
+    const bool less = ctx->tune.ks_split != 0;
     switch (beta) {
         FG_KS_CASE(1) FG_KS_CASE(2) FG_KS_CASE(3) FG_KS_CASE(4) FG_KS_CASE(5) FG_KS_CASE(6)
         FG_KS_CASE(7) FG_KS_CASE(8) FG_KS_CASE(9) FG_KS_CASE(10) FG_KS_CASE(11) FG_KS_CASE(12)
@@ -1839,7 +1872,7 @@ void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vec
     pg.dfirst[X] = n;
     // thread groups and their output slices, cut where the running term
     // count passes k / G of the total
-    const int G = X >= 7 ? kGmacGroups : 1;
+    const int G = X >= ctx->tune.gmac_groups ? kGmacGroups : 1;
     pg.groups = G;
     pg.gfirst[0] = 0;
     int k = 1;

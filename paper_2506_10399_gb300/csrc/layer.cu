@@ -793,6 +793,49 @@ static double time_pass(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *
 // the batch runs from ctx->batch_stream (a non-blocking stream that can be
 // captured, which the legacy default stream cannot), joined to ctx->stream
 // before and after
+// the kernels' launch configuration for the batch, chosen by timing whole
+// passes on one stream: coordinate descent over the knobs of Tune, each
+// candidate timed twice (the faster counts), from the defaults
+static void tune_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *plans, int n,
+                       const uint64_t *const *in_cts, uint64_t *const *out_cts, int *levels)
+{
+    ctx->tune_ms.clear();
+    Tune best = ctx->tune;
+    auto timed = [&](const Tune &t) {
+        ctx->tune = t;
+        double ms = 0;
+        for (int rep = 0; rep < 2; rep++) {
+            const double m = time_pass(ctx, keys, plans, n, in_cts, out_cts, 1, levels);
+            ms = rep == 0 ? m : std::min(ms, m);
+        }
+        ctx->tune_ms.push_back(ms);
+        return ms;
+    };
+    double best_ms = timed(best);
+    const int cols[2] = {16, 8}, rows[2] = {16, 8}, split[2] = {0, 1}, groups[3] = {7, 4, 13};
+    auto knob = [&](auto field, const int *vals, int nv) {
+        Tune base = best;
+        for (int k = 0; k < nv; k++) {
+            Tune t = base;
+            t.*field = vals[k];
+            if (t == base) continue;
+            const double ms = timed(t);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
+        }
+    };
+    if (ctx->log_n == 16) {
+        knob(&Tune::ntt_cols, cols, 2);
+        knob(&Tune::ntt_rows, rows, 2);
+    }
+    knob(&Tune::ks_split, split, 2);
+    knob(&Tune::gmac_groups, groups, 3);
+    ctx->batch_tune = best;
+    ctx->batch_tuned = true;
+}
+
 static void batch_body(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *plans, int n,
                        const uint64_t *const *in_cts, uint64_t *const *out_cts, const fg_batch_opts &o,
                        const std::vector<const void *> &args, int *out_levels, int *streams_used)
@@ -806,6 +849,18 @@ static void batch_body(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
         if (streams_used) *streams_used = ctx->batch.streams;
         return;
     }
+    // the batch's launch configuration stays in force for this call only
+    struct KeepTune {
+        fg_ctx *c;
+        Tune t;
+        ~KeepTune() { c->tune = t; }
+    } keep{ctx, ctx->tune};
+    if (o.tune && !ctx->batch_tuned) {
+        batch_pass(ctx, keys, plans, n, in_cts, out_cts, 1, out_levels);   // workspaces, warm-up
+        CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        tune_batch(ctx, keys, plans, n, in_cts, out_cts, out_levels);
+    }
+    if (o.tune && ctx->batch_tuned) ctx->tune = ctx->batch_tune;
     // first call: one pass with every workspace allocated (this pass gives
     // the results), then the stream count, then the capture
     int S = o.streams ? std::min(o.streams, n) : 1;
@@ -857,6 +912,33 @@ static void batch_body(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
     if (streams_used) *streams_used = S;
 }
 
+extern "C" int fg_batch_tuning(const fg_ctx *ctx, int cfg[4], double *ms, int cap, int *n)
+{
+    if (!ctx || !cfg || !n || cap < 0) return FG_EINVAL;
+    const Tune &t = ctx->batch_tuned ? ctx->batch_tune : ctx->tune;
+    cfg[0] = t.ntt_cols;
+    cfg[1] = t.ntt_rows;
+    cfg[2] = t.ks_split;
+    cfg[3] = t.gmac_groups;
+    *n = ctx->batch_tuned ? (int)ctx->tune_ms.size() : 0;
+    if (ms)
+        for (int i = 0; i < std::min(cap, *n); i++) ms[i] = ctx->tune_ms[i];
+    return FG_OK;
+}
+
+extern "C" int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[4])
+{
+    if (!ctx || !cfg) return FG_EINVAL;
+    if ((cfg[0] != 16 && cfg[0] != 8) || (cfg[1] != 16 && cfg[1] != 8) || (cfg[2] != 0 && cfg[2] != 1) ||
+        cfg[3] < 1)
+        return FG_EINVAL;
+    ctx->tune.ntt_cols = cfg[0];
+    ctx->tune.ntt_rows = cfg[1];
+    ctx->tune.ks_split = cfg[2];
+    ctx->tune.gmac_groups = cfg[3];
+    return FG_OK;
+}
+
 extern "C" int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *plans, int n,
                                   const uint64_t *const *in_cts, uint64_t *const *out_cts,
                                   const fg_batch_opts *opts, int *out_levels, int *streams_used)
@@ -865,7 +947,7 @@ extern "C" int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_pla
     cudaStream_t home = ctx->stream;
     try {
         FG_CHECK(keys && plans && in_cts && out_cts && out_levels && n >= 1, FG_EINVAL, "null argument");
-        fg_batch_opts o{0, 1};
+        fg_batch_opts o{0, 1, 0};
         if (opts) o = *opts;
         FG_CHECK(o.streams >= 0 && o.streams <= 16, FG_EINVAL, "streams must be 0..16");
         std::vector<const void *> args;

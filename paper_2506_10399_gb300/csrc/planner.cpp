@@ -23,6 +23,7 @@
 // rescale that closes the group keeps the ciphertext scale at Delta.
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <map>
 #include <unordered_map>
 
@@ -232,22 +233,23 @@ void build(fg_plan &pl, const fg_ctx &ctx, const int32_t *row_ptr, const int32_t
                     kv.second[0]);
             }
         }
-        std::vector<std::unordered_map<int, int>> out_slots;   // slot -> content
+        // per output lane, the content held at each slot (kEmpty: free);
+        // content ids are node ids >= 0 or carrier ids < 0
+        constexpr int kEmpty = std::numeric_limits<int>::min();
+        std::vector<std::vector<int>> out_slots;
         auto place = [&](int p, int content, bool &joined) {
-            for (size_t l = 0; l < out_slots.size(); l++) {
-                auto f = out_slots[l].find(p);
-                if (f != out_slots[l].end() && f->second == content) {
+            for (size_t l = 0; l < out_slots.size(); l++)
+                if (out_slots[l][p] == content) {
                     joined = true;
                     return (int)l;
                 }
-            }
             joined = false;
             for (size_t l = 0; l < out_slots.size(); l++)
-                if (!out_slots[l].count(p)) {
+                if (out_slots[l][p] == kEmpty) {
                     out_slots[l][p] = content;
                     return (int)l;
                 }
-            out_slots.emplace_back();
+            out_slots.emplace_back(M, kEmpty);
             out_slots.back()[p] = content;
             return (int)out_slots.size() - 1;
         };

@@ -174,7 +174,9 @@ def measure(out_path, budget_s=1500.0):
                 del out
             f.write(json.dumps({"seed": s, "V": w.V, "F": w.X.shape[1], "t_rule": t_rule, "cands": rows}) + "\n")
             f.flush()
-            del xs
+            del xs, x
+            ctx.release_workspace()
+            torch.cuda.empty_cache()
     print(json.dumps({"graphs_measured": sum(1 for _ in open(out_path)), "seconds": round(time.time() - t0)}))
 
 

@@ -92,3 +92,55 @@ def test_batch_rejects_host_buffers(env):
     with pytest.raises(fg.FicgcnError) as e:
         fg.gcn_layer_batch(ctx, keys, [qs[0][2]], [data[0][0].cpu()], [data[0][1]])
     assert e.value.code == -1
+
+
+def test_tuned_batch_equals_one_at_a_time(env):
+    """The tuned form (launch configuration chosen by timing whole passes)
+    gives the same words; the choice is one of the candidates and each
+    candidate tried was timed."""
+    fg, ctx, sk, keys, qs, data = env
+    want = _one_at_a_time(fg, ctx, keys, qs, data)
+    plans = [q[2] for q in qs]
+    outs = [d[1] for d in data]
+    for o in outs:
+        o.zero_()
+    fg.gcn_layer_batch(ctx, keys, plans, [d[0] for d in data], outs, streams=2, graph=True, tune=True)
+    for (o_w, _), o in zip(want, outs):
+        assert bool((o == o_w).all())
+    cfg, ms = fg.batch_tuning(ctx)
+    assert cfg["ks_split"] in (0, 1) and cfg["gmac_groups"] in (7, 4, 13)
+    assert cfg["ntt_cols"] == 16 and cfg["ntt_rows"] == 16      # N = 2^13: the N = 2^16 tiles stay
+    assert len(ms) == 4 and all(m > 0 for m in ms)              # default, ks_split, two thresholds
+
+
+def test_every_ntt16_tile_and_key_switch_bound_give_the_same_layer():
+    """N = 2^16 (the tiles the tuner chooses among): the layer under each
+    configuration the tuner can pick equals the default one word for word,
+    through the batched entry point with tuning on."""
+    import torch
+    import __graft_entry__
+    fg = __graft_entry__.build()
+    P = dict(log_n=16, q_bits=[60] + [45] * 5, p_bits=[60, 60], alpha=3, log_scale=45)
+    ctx = fg.Context(**P)
+    w = wl.make_workload(graph="chung_lu", V=3000, deg=4.0, gamma=2.5, F=12, Fp=2, x="tfidf", w="glorot",
+                         seed=7)
+    perm = wl.random_order(w.V, ctx.slots, 7)
+    plan = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=1, radix_bits=4)
+    sk, evk = fg.keygen(ctx, 3, plan.rotation_amounts())
+    keys = fg.load_evk(ctx, evk)
+    cin = torch.from_numpy(fg.pack_features(ctx, sk, 4, w.X, perm, 1).view(np.int64)).cuda()
+    want, lvl, _ = fg.gcn_layer_axw(ctx, keys, plan, cin)
+    want = want.clone()
+    for cols, rows, split, groups in ((8, 16, 0, 7), (16, 8, 0, 7), (8, 8, 1, 4), (16, 16, 1, 13)):
+        fg.set_tuning(ctx, cols, rows, split, groups)
+        got, _, _ = fg.gcn_layer_axw(ctx, keys, plan, cin)
+        assert bool((got == want).all()), (cols, rows, split, groups)
+    fg.set_tuning(ctx)
+    out = torch.empty_like(want)
+    fg.gcn_layer_batch(ctx, keys, [plan], [cin], [out], streams=1, graph=False, tune=True)
+    assert bool((out == want).all())
+    cfg, ms = fg.batch_tuning(ctx)
+    assert len(ms) == 6 and cfg["ntt_cols"] in (16, 8) and cfg["ntt_rows"] in (16, 8)
+    d = fg.decrypt_decode(ctx, sk, out[0].contiguous(), lvl, ctx.scale)
+    assert np.max(np.abs(d[perm] - w.reference_output()[:, 0])) < 2 ** -20
+    ctx.close()
