@@ -343,7 +343,9 @@ int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *plan,
  * call and replayed by later calls with the same plans and buffers.  With
  * opts->tune = 1 the first call also picks, by timing whole batch passes,
  * the launch configuration of the batch's kernels: the N = 2^16 NTT tile
- * (pass A columns and pass B rows per CTA, 16 or 8 each), the key switch's
+ * (pass A columns and pass B rows per CTA, 16 or 8 each) and twiddle form
+ * (held in registers per round, or loaded where used at one more CTA per
+ * SM), the key switch's
  * register budget (its launch bound at the default or one CTA per SM
  * fewer) and the output count from which a group-MAC CTA runs three thread
  * groups (7, 4 or 13); fg_batch_tuning reports the choice.  Every
@@ -359,16 +361,17 @@ int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
                        const uint64_t *const *in_cts, uint64_t *const *out_cts,
                        const fg_batch_opts *opts, int *out_levels, int *streams_used);
 /* The batched form's launch configuration: cfg = {NTT pass-A columns, NTT
- * pass-B rows, key-switch bound one CTA per SM fewer (0/1), group-MAC
- * three-group threshold}; ms[0..*n) the batch pass time of each
- * configuration tried (the default first), at most cap entries.  Before any
- * tuned batch call cfg holds the defaults and *n = 0. */
-int fg_batch_tuning(const fg_ctx *ctx, int cfg[4], double *ms, int cap, int *n);
+ * pass-B rows, NTT twiddles loaded where used (0/1), key-switch bound one
+ * CTA per SM fewer (0/1), group-MAC three-group threshold}; ms[0..*n) the
+ * batch pass time of each configuration tried (the default first), at most
+ * cap entries.  Before any tuned batch call cfg holds the context's
+ * configuration and *n = 0. */
+int fg_batch_tuning(const fg_ctx *ctx, int cfg[5], double *ms, int cap, int *n);
 /* Fix the launch configuration every later call of this context uses
- * outside tuned batches (the same four fields as fg_batch_tuning; NTT tiles
- * 16 or 8, key-switch flag 0 or 1, group-MAC threshold >= 1).  Results do
- * not change; speed may.  FG_EINVAL for other values. */
-int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[4]);
+ * outside tuned batches (the same five fields as fg_batch_tuning; NTT tiles
+ * 16 or 8, flags 0 or 1, group-MAC threshold >= 1).  Results do not change;
+ * speed may.  FG_EINVAL for other values. */
+int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[5]);
 
 /* Ciphertext products (paper Sec. 2.1 CMult; the x^2 activation between
  * GCN layers multiplies a ciphertext by itself): for each of n pairs,

@@ -89,12 +89,14 @@ struct ConvTab {
 struct Tune {
     int ntt_cols = 16;     // N = 2^16 NTT pass A: columns per CTA (16 or 8)
     int ntt_rows = 16;     // N = 2^16 NTT pass B: rows per CTA (16 or 8)
+    int ntt_tw = 0;        // N = 2^16 NTT twiddles: 0 = held in registers per round (3 CTAs of
+                           // 256 threads per SM), 1 = loaded where used (4 per SM)
     int ks_split = 0;      // key switch: 0 = launch bounds by digit count, 1 = one CTA per SM fewer
     int gmac_groups = 7;   // group MAC: outputs from which a CTA runs three thread groups
     bool operator==(const Tune &o) const
     {
-        return ntt_cols == o.ntt_cols && ntt_rows == o.ntt_rows && ks_split == o.ks_split &&
-               gmac_groups == o.gmac_groups;
+        return ntt_cols == o.ntt_cols && ntt_rows == o.ntt_rows && ntt_tw == o.ntt_tw &&
+               ks_split == o.ks_split && gmac_groups == o.gmac_groups;
     }
 };
 

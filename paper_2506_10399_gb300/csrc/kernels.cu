@@ -87,8 +87,9 @@ __device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, const ulonglong2 w, u64 
 // q < 2^47); one reduction at the end restores [0, q).  Larger primes keep
 // Harvey's bounds (< 4q, < 2q).
 // ------------------------------------------------------------------------
-template <bool LAZY>
-__device__ __forceinline__ void ct16(u64 (&v)[16], const ulonglong2 (&w)[15], u64 q, u64 q2)
+// tw(st, g): twiddle of group g at stage st (0..3) of the 16-point round
+template <bool LAZY, class TW>
+__device__ __forceinline__ void ct16(u64 (&v)[16], TW tw, u64 q, u64 q2)
 {
 #pragma unroll
     for (int st = 0; st < 4; st++) {
@@ -96,15 +97,15 @@ __device__ __forceinline__ void ct16(u64 (&v)[16], const ulonglong2 (&w)[15], u6
 #pragma unroll
         for (int m = 0; m < 16; m++) {
             if ((m & h) == 0) {
-                const ulonglong2 tw = w[(1 << st) - 1 + (m >> (4 - st))];
+                const ulonglong2 w = tw(st, m >> (4 - st));
                 u64 X = v[m], Y = v[m + h];
                 if (LAZY) {
-                    const u64 T = shoup_lazy4(Y, tw.x, tw.y, q);
+                    const u64 T = shoup_lazy4(Y, w.x, w.y, q);
                     v[m + h] = X - T + 4 * q;
                     v[m] = X + T;
                 } else {
                     X = X >= q2 ? X - q2 : X;
-                    const u64 T = shoup_lazy(Y, tw.x, tw.y, q);
+                    const u64 T = shoup_lazy(Y, w.x, w.y, q);
                     v[m + h] = X - T + q2;
                     v[m] = X + T;
                 }
@@ -114,8 +115,8 @@ __device__ __forceinline__ void ct16(u64 (&v)[16], const ulonglong2 (&w)[15], u6
 }
 
 // k0: number of inverse stages already applied to these values (lazy bound 2^k0 q)
-template <bool LAZY>
-__device__ __forceinline__ void gs16(u64 (&v)[16], const ulonglong2 (&w)[15], u64 q, u64 q2, int k0)
+template <bool LAZY, class TW>
+__device__ __forceinline__ void gs16(u64 (&v)[16], TW tw, u64 q, u64 q2, int k0)
 {
 #pragma unroll
     for (int st = 3; st >= 0; st--) {
@@ -124,16 +125,40 @@ __device__ __forceinline__ void gs16(u64 (&v)[16], const ulonglong2 (&w)[15], u6
 #pragma unroll
         for (int m = 0; m < 16; m++) {
             if ((m & h) == 0) {
-                const ulonglong2 tw = w[(1 << st) - 1 + (m >> (4 - st))];
+                const ulonglong2 w = tw(st, m >> (4 - st));
                 const u64 U = v[m], V = v[m + h];
                 const u64 S = U + V;
                 v[m] = LAZY ? S : (S >= q2 ? S - q2 : S);
-                v[m + h] = LAZY ? shoup_lazy4(U - V + qb, tw.x, tw.y, q)
-                                : shoup_lazy(U - V + qb, tw.x, tw.y, q);
+                v[m + h] = LAZY ? shoup_lazy4(U - V + qb, w.x, w.y, q)
+                                : shoup_lazy(U - V + qb, w.x, w.y, q);
             }
         }
     }
 }
+
+// A round's 15 twiddles either held in registers for the whole round
+// (OD = false: loaded up front) or loaded where each stage uses them (OD =
+// true: fewer live registers, so more CTAs per SM).
+template <bool OD, class F>
+struct Twiddles {
+    ulonglong2 w[OD ? 1 : 15];
+    F f;
+    __device__ __forceinline__ explicit Twiddles(F g) : f(g)
+    {
+        if (!OD) {
+#pragma unroll
+            for (int st = 0; st < 4; st++)
+#pragma unroll
+                for (int gg = 0; gg < (1 << st); gg++) w[OD ? 0 : (1 << st) - 1 + gg] = f(st, gg);
+        }
+    }
+    __device__ __forceinline__ ulonglong2 operator()(int st, int g) const
+    {
+        return OD ? f(st, g) : w[OD ? 0 : (1 << st) - 1 + g];
+    }
+};
+template <bool OD, class F>
+__device__ __forceinline__ Twiddles<OD, F> twiddles(F f) { return Twiddles<OD, F>(f); }
 
 constexpr int kR16Row = 272;   // 256 elements + 16 pad words per row (pass B shared memory)
 __device__ __forceinline__ int pad16(int pos) { return pos + (pos >> 4); }
@@ -143,35 +168,29 @@ __device__ __forceinline__ int pad16(int pos) { return pos + (pos >> 4); }
 // ROWS (16 or 8) of the 256 rows per CTA, 16 threads per row.  Both tile
 // sizes compute the same transform word for word; the batched form picks
 // one per shape by timing.
-template <bool LAZY, int COLS>
+template <bool LAZY, int COLS, bool OD>
 __device__ __forceinline__ void fwd_a16_body(const u64 *s, u64 *d, const ulonglong2 *stw, u64 q, u64 *sm)
 {
     const int t = threadIdx.x, c = t % COLS, r = t / COLS;   // r: r0 in round 1, r1 in round 2
     constexpr int N2 = 256;
     const u64 q2 = 2 * q;
     u64 v[16];
-    ulonglong2 w[15];
 #pragma unroll
     for (int m = 0; m < 16; m++) v[m] = s[(size_t)(r + 16 * m) * N2 + c];
-#pragma unroll
-    for (int k = 0; k < 15; k++) w[k] = stw[k + 1];   // stage st, group g at (1 << st) + g
-    ct16<LAZY>(v, w, q, q2);
+    // stage st, group g at (1 << st) + g
+    ct16<LAZY>(v, twiddles<OD>([&](int st, int g) { return stw[(1 << st) + g]; }), q, q2);
 #pragma unroll
     for (int m = 0; m < 16; m++) sm[(r + 16 * m) * COLS + c] = v[m];
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < 16; m++) v[m] = sm[(16 * r + m) * COLS + c];
-#pragma unroll
-    for (int st = 0; st < 4; st++)
-#pragma unroll
-        for (int g = 0; g < (1 << st); g++) w[(1 << st) - 1 + g] = stw[(1 << (st + 4)) + (r << st) + g];
-    ct16<LAZY>(v, w, q, q2);
+    ct16<LAZY>(v, twiddles<OD>([&](int st, int g) { return stw[(1 << (st + 4)) + (r << st) + g]; }), q, q2);
 #pragma unroll
     for (int m = 0; m < 16; m++) d[(size_t)(16 * r + m) * N2 + c] = v[m];   // lazy
 }
 
-template <int COLS>
-__global__ void __launch_bounds__(16 * COLS, 48 / COLS)
+template <int COLS, bool OD>
+__global__ void __launch_bounds__(16 * COLS, (OD ? 64 : 48) / COLS)
 ntt16_fwd_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ tw)
 {
     const int limb = blockIdx.y;
@@ -187,11 +206,11 @@ ntt16_fwd_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 
     const int c0 = blockIdx.x * COLS;
     const u64 *src = bt.src + ((size_t)row * bt.src_stride + col) * 65536 + c0;
     u64 *dst = bt.dst + ((size_t)row * bt.dst_stride + col) * 65536 + c0;
-    if (q < (1ull << 47)) fwd_a16_body<true, COLS>(src, dst, stw, q, sm);
-    else fwd_a16_body<false, COLS>(src, dst, stw, q, sm);
+    if (q < (1ull << 47)) fwd_a16_body<true, COLS, OD>(src, dst, stw, q, sm);
+    else fwd_a16_body<false, COLS, OD>(src, dst, stw, q, sm);
 }
 
-template <bool LAZY>
+template <bool LAZY, bool OD>
 __device__ __forceinline__ void fwd_b16_body(u64 *d, const ulonglong2 *twp, const ulonglong2 *rows,
                                              int row0, const PrimeC &P, u64 *sm)
 {
@@ -199,16 +218,11 @@ __device__ __forceinline__ void fwd_b16_body(u64 *d, const ulonglong2 *twp, cons
     constexpr int S1 = 8;
     const u64 q = P.q, q2 = 2 * q;
     u64 v[16];
-    ulonglong2 w[15];
     const int grow = row0 + r;
     u64 *drow = d + (size_t)r * 256;
 #pragma unroll
     for (int m = 0; m < 16; m++) v[m] = drow[j + 16 * m];
-#pragma unroll
-    for (int st = 0; st < 4; st++)
-#pragma unroll
-        for (int g = 0; g < (1 << st); g++) w[(1 << st) - 1 + g] = twp[(1 << (S1 + st)) + (grow << st) + g];
-    ct16<LAZY>(v, w, q, q2);
+    ct16<LAZY>(v, twiddles<OD>([&](int st, int g) { return twp[(1 << (S1 + st)) + (grow << st) + g]; }), q, q2);
     u64 *srow = sm + r * kR16Row;
 #pragma unroll
     for (int m = 0; m < 16; m++) srow[pad16(j + 16 * m)] = v[m];
@@ -216,9 +230,8 @@ __device__ __forceinline__ void fwd_b16_body(u64 *d, const ulonglong2 *twp, cons
 #pragma unroll
     for (int m = 0; m < 16; m++) v[m] = srow[pad16(16 * j + m)];
     // row stages 12..15 from the row-blocked table (consecutive per row)
-#pragma unroll
-    for (int k = 0; k < 15; k++) w[k] = rows[((size_t)grow * 15 + k) * 16 + j];
-    ct16<LAZY>(v, w, q, q2);
+    ct16<LAZY>(v, twiddles<OD>([&](int st, int g) { return rows[((size_t)grow * 15 + (1 << st) - 1 + g) * 16 + j]; }),
+               q, q2);
     ulonglong2 *o = reinterpret_cast<ulonglong2 *>(drow + 16 * j);
 #pragma unroll
     for (int m = 0; m < 16; m += 2)
@@ -226,8 +239,8 @@ __device__ __forceinline__ void fwd_b16_body(u64 *d, const ulonglong2 *twp, cons
                         : make_ulonglong2(reduce4(v[m], q), reduce4(v[m + 1], q));
 }
 
-template <int ROWS>
-__global__ void __launch_bounds__(16 * ROWS, 48 / ROWS)
+template <int ROWS, bool OD>
+__global__ void __launch_bounds__(16 * ROWS, (OD ? 64 : 48) / ROWS)
 ntt16_fwd_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ tw,
             const ulonglong2 *__restrict__ tw_rows)
 {
@@ -241,11 +254,11 @@ ntt16_fwd_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 
     const int row0 = blockIdx.x * ROWS;
     u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * 65536 + (size_t)row0 * 256;
     const ulonglong2 *rows = tw_rows + (size_t)pi * 256 * 15 * 16;
-    if (P.q < (1ull << 47)) fwd_b16_body<true>(d, twp, rows, row0, P, sm);
-    else fwd_b16_body<false>(d, twp, rows, row0, P, sm);
+    if (P.q < (1ull << 47)) fwd_b16_body<true, OD>(d, twp, rows, row0, P, sm);
+    else fwd_b16_body<false, OD>(d, twp, rows, row0, P, sm);
 }
 
-template <bool LAZY>
+template <bool LAZY, bool OD>
 __device__ __forceinline__ void inv_b16_body(const u64 *s, u64 *d, const ulonglong2 *twp,
                                              const ulonglong2 *rows, int row0, u64 q, u64 *sm)
 {
@@ -253,7 +266,6 @@ __device__ __forceinline__ void inv_b16_body(const u64 *s, u64 *d, const ulonglo
     constexpr int S1 = 8;
     const u64 q2 = 2 * q;
     u64 v[16];
-    ulonglong2 w[15];
     const int grow = row0 + r;
     const ulonglong2 *in = reinterpret_cast<const ulonglong2 *>(s + (size_t)r * 256 + 16 * j);
 #pragma unroll
@@ -262,27 +274,22 @@ __device__ __forceinline__ void inv_b16_body(const u64 *s, u64 *d, const ulonglo
         v[m] = a.x;
         v[m + 1] = a.y;
     }
-#pragma unroll
-    for (int k = 0; k < 15; k++) w[k] = rows[((size_t)grow * 15 + k) * 16 + j];
-    gs16<LAZY>(v, w, q, q2, 0);
+    gs16<LAZY>(v, twiddles<OD>([&](int st, int g) { return rows[((size_t)grow * 15 + (1 << st) - 1 + g) * 16 + j]; }),
+               q, q2, 0);
     u64 *srow = sm + r * kR16Row;
 #pragma unroll
     for (int m = 0; m < 16; m++) srow[pad16(16 * j + m)] = v[m];
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < 16; m++) v[m] = srow[pad16(j + 16 * m)];
-#pragma unroll
-    for (int st = 0; st < 4; st++)
-#pragma unroll
-        for (int g = 0; g < (1 << st); g++) w[(1 << st) - 1 + g] = twp[(1 << (S1 + st)) + (grow << st) + g];
-    gs16<LAZY>(v, w, q, q2, 4);
+    gs16<LAZY>(v, twiddles<OD>([&](int st, int g) { return twp[(1 << (S1 + st)) + (grow << st) + g]; }), q, q2, 4);
     u64 *drow = d + (size_t)r * 256;
 #pragma unroll
     for (int m = 0; m < 16; m++) drow[j + 16 * m] = v[m];   // lazy (< 2^9 q or < 2q)
 }
 
-template <int ROWS>
-__global__ void __launch_bounds__(16 * ROWS, 48 / ROWS)
+template <int ROWS, bool OD>
+__global__ void __launch_bounds__(16 * ROWS, (OD ? 64 : 48) / ROWS)
 ntt16_inv_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ itw,
             const ulonglong2 *__restrict__ itw_rows)
 {
@@ -297,11 +304,11 @@ ntt16_inv_b(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 
     const u64 *s = bt.src + ((size_t)row * bt.src_stride + col) * 65536 + (size_t)row0 * 256;
     u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * 65536 + (size_t)row0 * 256;
     const ulonglong2 *rows = itw_rows + (size_t)pi * 256 * 15 * 16;
-    if (q < (1ull << 47)) inv_b16_body<true>(s, d, twp, rows, row0, q, sm);
-    else inv_b16_body<false>(s, d, twp, rows, row0, q, sm);
+    if (q < (1ull << 47)) inv_b16_body<true, OD>(s, d, twp, rows, row0, q, sm);
+    else inv_b16_body<false, OD>(s, d, twp, rows, row0, q, sm);
 }
 
-template <bool LAZY, int COLS>
+template <bool LAZY, int COLS, bool OD>
 __device__ __forceinline__ void inv_a16_body(u64 *d, const ulonglong2 *stw, u64 q, u64 ni, u64 nis,
                                              u64 *sm)
 {
@@ -309,28 +316,21 @@ __device__ __forceinline__ void inv_a16_body(u64 *d, const ulonglong2 *stw, u64 
     constexpr int N2 = 256;
     const u64 q2 = 2 * q;
     u64 v[16];
-    ulonglong2 w[15];
 #pragma unroll
     for (int m = 0; m < 16; m++) v[m] = d[(size_t)(16 * r + m) * N2 + c];
-#pragma unroll
-    for (int st = 0; st < 4; st++)
-#pragma unroll
-        for (int g = 0; g < (1 << st); g++) w[(1 << st) - 1 + g] = stw[(1 << (st + 4)) + (r << st) + g];
-    gs16<LAZY>(v, w, q, q2, 8);
+    gs16<LAZY>(v, twiddles<OD>([&](int st, int g) { return stw[(1 << (st + 4)) + (r << st) + g]; }), q, q2, 8);
 #pragma unroll
     for (int m = 0; m < 16; m++) sm[(16 * r + m) * COLS + c] = v[m];
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < 16; m++) v[m] = sm[(r + 16 * m) * COLS + c];
-#pragma unroll
-    for (int k = 0; k < 15; k++) w[k] = stw[k + 1];
-    gs16<LAZY>(v, w, q, q2, 12);
+    gs16<LAZY>(v, twiddles<OD>([&](int st, int g) { return stw[(1 << st) + g]; }), q, q2, 12);
 #pragma unroll
     for (int m = 0; m < 16; m++) d[(size_t)(r + 16 * m) * N2 + c] = shoup_mul(v[m], ni, nis, q);
 }
 
-template <int COLS>
-__global__ void __launch_bounds__(16 * COLS, 48 / COLS)
+template <int COLS, bool OD>
+__global__ void __launch_bounds__(16 * COLS, (OD ? 64 : 48) / COLS)
 ntt16_inv_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ itw,
             const u64 *__restrict__ ninv)
 {
@@ -347,8 +347,8 @@ ntt16_inv_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 
     const int c0 = blockIdx.x * COLS;
     u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * 65536 + c0;
     const u64 ni = ninv[2 * pi], nis = ninv[2 * pi + 1];
-    if (q < (1ull << 47)) inv_a16_body<true, COLS>(d, stw, q, ni, nis, sm);
-    else inv_a16_body<false, COLS>(d, stw, q, ni, nis, sm);
+    if (q < (1ull << 47)) inv_a16_body<true, COLS, OD>(d, stw, q, ni, nis, sm);
+    else inv_a16_body<false, COLS, OD>(d, stw, q, ni, nis, sm);
 }
 
 // Stages are taken two at a time (radix-4 rounds: four elements, four
@@ -1466,7 +1466,7 @@ KTimer::~KTimer()
 }
 
 
-template <int COLS, int ROWS>
+template <int COLS, int ROWS, bool OD>
 static void ntt16_launch_t(fg_ctx *ctx, const Batch &bt, int count, bool inverse)
 {
     const auto *fwd = (const ulonglong2 *)ctx->d_fwd;
@@ -1476,24 +1476,31 @@ static void ntt16_launch_t(fg_ctx *ctx, const Batch &bt, int count, bool inverse
     b2.src = b2.dst;
     b2.src_stride = b2.dst_stride;
     if (!inverse) {
-        ntt16_fwd_a<COLS><<<gA, 16 * COLS, 0, ctx->stream>>>(bt, ctx->d_primes, fwd);
-        ntt16_fwd_b<ROWS><<<gB, 16 * ROWS, 0, ctx->stream>>>(b2, ctx->d_primes, fwd,
-                                                            (const ulonglong2 *)ctx->d_fwd_rows);
+        ntt16_fwd_a<COLS, OD><<<gA, 16 * COLS, 0, ctx->stream>>>(bt, ctx->d_primes, fwd);
+        ntt16_fwd_b<ROWS, OD><<<gB, 16 * ROWS, 0, ctx->stream>>>(b2, ctx->d_primes, fwd,
+                                                                (const ulonglong2 *)ctx->d_fwd_rows);
     } else {
-        ntt16_inv_b<ROWS><<<gB, 16 * ROWS, 0, ctx->stream>>>(bt, ctx->d_primes, inv,
-                                                            (const ulonglong2 *)ctx->d_inv_rows);
-        ntt16_inv_a<COLS><<<gA, 16 * COLS, 0, ctx->stream>>>(b2, ctx->d_primes, inv, ctx->d_ninv);
+        ntt16_inv_b<ROWS, OD><<<gB, 16 * ROWS, 0, ctx->stream>>>(bt, ctx->d_primes, inv,
+                                                                (const ulonglong2 *)ctx->d_inv_rows);
+        ntt16_inv_a<COLS, OD><<<gA, 16 * COLS, 0, ctx->stream>>>(b2, ctx->d_primes, inv, ctx->d_ninv);
     }
 }
 
-// the tile of the N = 2^16 transform from the context's tuning
-static void ntt16_launch(fg_ctx *ctx, const Batch &bt, int count, bool inverse)
+// the tile and twiddle form of the N = 2^16 transform from the context's tuning
+template <bool OD>
+static void ntt16_launch_od(fg_ctx *ctx, const Batch &bt, int count, bool inverse)
 {
     const bool ca = ctx->tune.ntt_cols == 8, rb = ctx->tune.ntt_rows == 8;
-    if (!ca && !rb) ntt16_launch_t<16, 16>(ctx, bt, count, inverse);
-    else if (ca && !rb) ntt16_launch_t<8, 16>(ctx, bt, count, inverse);
-    else if (!ca && rb) ntt16_launch_t<16, 8>(ctx, bt, count, inverse);
-    else ntt16_launch_t<8, 8>(ctx, bt, count, inverse);
+    if (!ca && !rb) ntt16_launch_t<16, 16, OD>(ctx, bt, count, inverse);
+    else if (ca && !rb) ntt16_launch_t<8, 16, OD>(ctx, bt, count, inverse);
+    else if (!ca && rb) ntt16_launch_t<16, 8, OD>(ctx, bt, count, inverse);
+    else ntt16_launch_t<8, 8, OD>(ctx, bt, count, inverse);
+}
+
+static void ntt16_launch(fg_ctx *ctx, const Batch &bt, int count, bool inverse)
+{
+    if (ctx->tune.ntt_tw) ntt16_launch_od<true>(ctx, bt, count, inverse);
+    else ntt16_launch_od<false>(ctx, bt, count, inverse);
 }
 
 template <int LOGN>

@@ -812,7 +812,7 @@ static void tune_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
         return ms;
     };
     double best_ms = timed(best);
-    const int cols[2] = {16, 8}, rows[2] = {16, 8}, split[2] = {0, 1}, groups[3] = {7, 4, 13};
+    const int cols[2] = {16, 8}, rows[2] = {16, 8}, tw[2] = {0, 1}, split[2] = {0, 1}, groups[3] = {7, 4, 13};
     auto knob = [&](auto field, const int *vals, int nv) {
         Tune base = best;
         for (int k = 0; k < nv; k++) {
@@ -829,6 +829,7 @@ static void tune_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
     if (ctx->log_n == 16) {
         knob(&Tune::ntt_cols, cols, 2);
         knob(&Tune::ntt_rows, rows, 2);
+        knob(&Tune::ntt_tw, tw, 2);
     }
     knob(&Tune::ks_split, split, 2);
     knob(&Tune::gmac_groups, groups, 3);
@@ -912,30 +913,32 @@ static void batch_body(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
     if (streams_used) *streams_used = S;
 }
 
-extern "C" int fg_batch_tuning(const fg_ctx *ctx, int cfg[4], double *ms, int cap, int *n)
+extern "C" int fg_batch_tuning(const fg_ctx *ctx, int cfg[5], double *ms, int cap, int *n)
 {
     if (!ctx || !cfg || !n || cap < 0) return FG_EINVAL;
     const Tune &t = ctx->batch_tuned ? ctx->batch_tune : ctx->tune;
     cfg[0] = t.ntt_cols;
     cfg[1] = t.ntt_rows;
-    cfg[2] = t.ks_split;
-    cfg[3] = t.gmac_groups;
+    cfg[2] = t.ntt_tw;
+    cfg[3] = t.ks_split;
+    cfg[4] = t.gmac_groups;
     *n = ctx->batch_tuned ? (int)ctx->tune_ms.size() : 0;
     if (ms)
         for (int i = 0; i < std::min(cap, *n); i++) ms[i] = ctx->tune_ms[i];
     return FG_OK;
 }
 
-extern "C" int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[4])
+extern "C" int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[5])
 {
     if (!ctx || !cfg) return FG_EINVAL;
     if ((cfg[0] != 16 && cfg[0] != 8) || (cfg[1] != 16 && cfg[1] != 8) || (cfg[2] != 0 && cfg[2] != 1) ||
-        cfg[3] < 1)
+        (cfg[3] != 0 && cfg[3] != 1) || cfg[4] < 1)
         return FG_EINVAL;
     ctx->tune.ntt_cols = cfg[0];
     ctx->tune.ntt_rows = cfg[1];
-    ctx->tune.ks_split = cfg[2];
-    ctx->tune.gmac_groups = cfg[3];
+    ctx->tune.ntt_tw = cfg[2];
+    ctx->tune.ks_split = cfg[3];
+    ctx->tune.gmac_groups = cfg[4];
     return FG_OK;
 }
 

@@ -109,7 +109,7 @@ def test_tuned_batch_equals_one_at_a_time(env):
         assert bool((o == o_w).all())
     cfg, ms = fg.batch_tuning(ctx)
     assert cfg["ks_split"] in (0, 1) and cfg["gmac_groups"] in (7, 4, 13)
-    assert cfg["ntt_cols"] == 16 and cfg["ntt_rows"] == 16      # N = 2^13: the N = 2^16 tiles stay
+    assert cfg["ntt_cols"] == 16 and cfg["ntt_rows"] == 16 and cfg["ntt_tw"] == 0   # N = 2^13: N = 2^16 forms stay
     assert len(ms) == 4 and all(m > 0 for m in ms)              # default, ks_split, two thresholds
 
 
@@ -120,27 +120,28 @@ def test_every_ntt16_tile_and_key_switch_bound_give_the_same_layer():
     import torch
     import __graft_entry__
     fg = __graft_entry__.build()
-    P = dict(log_n=16, q_bits=[60] + [45] * 5, p_bits=[60, 60], alpha=3, log_scale=45)
+    P = dict(log_n=16, q_bits=[60] + [45] * 5, p_bits=[60] * 3, alpha=2, log_scale=45)
     ctx = fg.Context(**P)
     w = wl.make_workload(graph="chung_lu", V=3000, deg=4.0, gamma=2.5, F=12, Fp=2, x="tfidf", w="glorot",
                          seed=7)
     perm = wl.random_order(w.V, ctx.slots, 7)
-    plan = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=1, radix_bits=4)
+    plan = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=1, radix_bits=5)
+    assert plan.info()["out_level"] == 1
     sk, evk = fg.keygen(ctx, 3, plan.rotation_amounts())
     keys = fg.load_evk(ctx, evk)
     cin = torch.from_numpy(fg.pack_features(ctx, sk, 4, w.X, perm, 1).view(np.int64)).cuda()
     want, lvl, _ = fg.gcn_layer_axw(ctx, keys, plan, cin)
     want = want.clone()
-    for cols, rows, split, groups in ((8, 16, 0, 7), (16, 8, 0, 7), (8, 8, 1, 4), (16, 16, 1, 13)):
-        fg.set_tuning(ctx, cols, rows, split, groups)
+    for cfg in ((8, 16, 0, 0, 7), (16, 8, 0, 0, 7), (16, 16, 1, 0, 7), (8, 8, 1, 1, 4), (16, 16, 0, 1, 13)):
+        fg.set_tuning(ctx, *cfg)
         got, _, _ = fg.gcn_layer_axw(ctx, keys, plan, cin)
-        assert bool((got == want).all()), (cols, rows, split, groups)
+        assert bool((got == want).all()), cfg
     fg.set_tuning(ctx)
     out = torch.empty_like(want)
     fg.gcn_layer_batch(ctx, keys, [plan], [cin], [out], streams=1, graph=False, tune=True)
     assert bool((out == want).all())
     cfg, ms = fg.batch_tuning(ctx)
-    assert len(ms) == 6 and cfg["ntt_cols"] in (16, 8) and cfg["ntt_rows"] in (16, 8)
+    assert len(ms) == 7 and cfg["ntt_cols"] in (16, 8) and cfg["ntt_rows"] in (16, 8) and cfg["ntt_tw"] in (0, 1)
     d = fg.decrypt_decode(ctx, sk, out[0].contiguous(), lvl, ctx.scale)
     assert np.max(np.abs(d[perm] - w.reference_output()[:, 0])) < 2 ** -20
     ctx.close()
