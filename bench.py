@@ -302,6 +302,8 @@ def run_ntt(args, fg=None):
     from paper_2506_10399_gb300 import workloads as wl
     c = wl.CONFIGS[WORKLOAD]
     ctx = fg.Context(**c)
+    if getattr(args, "tuning", ""):
+        fg.set_tuning(ctx, *[int(v) for v in args.tuning.split(",")])
     nl, count = 15, 480
     pidx = list(range(nl))
     g = torch.Generator(device="cuda").manual_seed(1)
@@ -417,6 +419,8 @@ def run_ours(args):
     perm = wl.random_order(w.V, 1 << (c["log_n"] - 1), SEED)
     t_setup = time.perf_counter()
     ctx = fg.Context(**c)
+    if args.tuning:
+        fg.set_tuning(ctx, *[int(v) for v in args.tuning.split(",")])
     plan = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=1, radix_bits=radix,
                          min_out_level=min_out)
     info = plan.info()
@@ -529,6 +533,7 @@ def run_ours(args):
                      "alg_bytes_per_call": round(k_bytes / max(1, k_calls))},
         "breakdown_ms": breakdown,
         "alu": alu,
+        "launch_config": fg.batch_tuning(ctx)[0],
         "e2e": {"value": round(e2e_ms, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -855,6 +860,8 @@ def main():
     ap.add_argument("--workload", default="pubmed_like", choices=["pubmed_like", "cora_like"],
                     help="workload of --two-layer")
     ap.add_argument("--inter", action="store_true", help="the layer in Inter-CA mode")
+    ap.add_argument("--tuning", default="", help="launch configuration ntt_cols,ntt_rows,ntt_tw,ks_split,"
+                                                  "gmac_groups (default: the library's)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
