@@ -92,11 +92,12 @@ struct Tune {
     int ntt_tw = 0;        // N = 2^16 NTT twiddles: 0 = held in registers per round (3 CTAs of
                            // 256 threads per SM), 1 = loaded where used (4 per SM)
     int ks_split = 0;      // key switch: 0 = launch bounds by digit count, 1 = one CTA per SM fewer
+    int ks_cols = 1;       // key switch: launches the columns are split over (1 or 2)
     int gmac_groups = 7;   // group MAC: outputs from which a CTA runs three thread groups
     bool operator==(const Tune &o) const
     {
         return ntt_cols == o.ntt_cols && ntt_rows == o.ntt_rows && ntt_tw == o.ntt_tw &&
-               ks_split == o.ks_split && gmac_groups == o.gmac_groups;
+               ks_split == o.ks_split && ks_cols == o.ks_cols && gmac_groups == o.gmac_groups;
     }
 };
 

@@ -1910,14 +1910,25 @@ void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vec
     check_launch("group_mac");
 }
 
+// With ctx->tune.ks_cols = 2 the columns are split over two launches, so
+// that the digits a limb's CTAs gather from L2 are half as many (the keys
+// are then read once per half).
 void ks_multi(fg_ctx *ctx, const std::vector<const KeyDev *> &keys, const std::vector<u64 *> &us,
               const u64 *lane, int ls, int ncol, int level, const u64 *digits)
 {
-    for (size_t r0 = 0; r0 < keys.size(); r0 += kKsMulti) {
-        const size_t r1 = std::min(keys.size(), r0 + kKsMulti);
-        ks_launch(ctx, std::vector<const KeyDev *>(keys.begin() + r0, keys.begin() + r1),
-                  std::vector<u64 *>(us.begin() + r0, us.begin() + r1), lane, ls, ncol, level, digits,
-                  true);
+    const int E = ctx->ext(level), beta = ctx->n_digits(level), N = ctx->n;
+    const int parts = std::max(1, std::min(ctx->tune.ks_cols, ncol));
+    for (int h = 0; h < parts; h++) {
+        const int f0 = ncol * h / parts, f1 = ncol * (h + 1) / parts;
+        if (f1 == f0) continue;
+        for (size_t r0 = 0; r0 < keys.size(); r0 += kKsMulti) {
+            const size_t r1 = std::min(keys.size(), r0 + kKsMulti);
+            std::vector<u64 *> uh;
+            for (size_t r = r0; r < r1; r++) uh.push_back(us[r] + (size_t)f0 * 2 * E * N);
+            ks_launch(ctx, std::vector<const KeyDev *>(keys.begin() + r0, keys.begin() + r1), uh,
+                      lane + (size_t)f0 * 2 * ls * N, ls, f1 - f0, level,
+                      digits + (size_t)f0 * beta * E * N, true);
+        }
     }
 }
 
