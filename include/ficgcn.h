@@ -156,6 +156,16 @@ int fg_pack_features(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t s
                      const double *X, int V, int F, const int32_t *perm, int t,
                      uint64_t *out_cts, int *n_out);
 
+/* The client's Inter-CA input (paper Sec. 3.1: the node arrangements the
+ * client encrypts offline): for every neighbour slot k < n, the rows
+ * nbr[v][k] of X (zero where nbr is -1) packed as fg_pack_features does with
+ * t = 1, copy k encrypted under seed + k.  nbr: [V][n] row-major; out_cts:
+ * room for n*F ciphertexts [2][L+1][N], copy-major (copy k, column f at
+ * k*F + f); host or device. */
+int fg_pack_neighbor_copies(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t seed,
+                            const double *X, int V, int F, const int32_t *nbr, int n,
+                            const int32_t *perm, uint64_t *out_cts);
+
 /* Decryption m = c0 + c1 s mod q_i (paper Sec. 2.1).  out_pt: [level+1][N]. */
 int fg_decrypt(fg_ctx *ctx, const void *sk_blob, size_t sk_len, const uint64_t *ct,
                int level, uint64_t *out_pt);

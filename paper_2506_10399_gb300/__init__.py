@@ -324,21 +324,21 @@ def plan_build_inter(ctx, nbr, wts, W, perm, min_out_level=0, in_level=0):
 
 
 def pack_neighbor_copies(ctx, sk, seed, X, nbr, perm, out=None):
-    """The client's Inter-CA input: for every neighbour slot k, the rows
-    nbr[:, k] of X (zero where nbr is -1) packed as fg_pack_features does,
-    copy k encrypted under seed + k; [n*F][2][L+1][N], copy-major."""
-    X = np.asarray(X, dtype=np.float64)
-    nbr = np.asarray(nbr)
-    V, n = nbr.shape
-    F = X.shape[1]
-    parts = []
-    for k in range(n):
-        Xk = np.where((nbr[:, k] >= 0)[:, None], X[np.maximum(nbr[:, k], 0)], 0.0)
-        if out is not None:
-            pack_features(ctx, sk, seed + k, Xk, perm, 1, out=out[k * F:(k + 1) * F])
-        else:
-            parts.append(pack_features(ctx, sk, seed + k, Xk, perm, 1))
-    return out if out is not None else np.concatenate(parts)
+    """The client's Inter-CA input (fg_pack_neighbor_copies): for every
+    neighbour slot k, the rows nbr[:, k] of X (zero where nbr is -1) packed
+    as pack_features does, copy k encrypted under seed + k;
+    [n*F][2][L+1][N], copy-major."""
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+    nbr = np.ascontiguousarray(np.asarray(nbr), dtype=np.int32)
+    perm = np.ascontiguousarray(np.asarray(perm, dtype=np.int32))
+    V, F = X.shape
+    n = nbr.shape[1]
+    if out is None:
+        out = np.empty((n * F, 2, ctx.nq, ctx.n), np.uint64)
+    _check(ctx, _lib().lib.fg_pack_neighbor_copies(ctx._h, sk, len(sk), int(seed), _ptr(X), V, F,
+                                                   ctypes.c_void_p(nbr.ctypes.data), n,
+                                                   ctypes.c_void_p(perm.ctypes.data), _ptr(out)))
+    return out
 
 
 def plan_build(ctx, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=True, min_out_level=0,

@@ -57,6 +57,8 @@ SIGS = {
     "fg_pack_features": (c_int, [c_void_p, c_void_p, c_size, c_u64, c_void_p, c_int, c_int,
                                  c_void_p, c_int, c_void_p, P(c_int)]),
     "fg_decrypt": (c_int, [c_void_p, c_void_p, c_size, c_void_p, c_int, c_void_p]),
+    "fg_pack_neighbor_copies": (c_int, [c_void_p, c_void_p, c_size, ctypes.c_uint64, c_void_p, c_int,
+                                        c_int, c_void_p, c_int, c_void_p, c_void_p]),
     "fg_decrypt_decode": (c_int, [c_void_p, c_void_p, c_size, c_void_p, c_int, c_double, c_void_p]),
     "fg_load_evk": (c_int, [c_void_p, c_void_p, c_size, P(c_void_p)]),
     "fg_keys_destroy": (c_int, [c_void_p]),

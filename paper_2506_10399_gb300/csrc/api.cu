@@ -838,6 +838,30 @@ int fg_pack_features(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t s
     API_CATCH(ctx)
 }
 
+int fg_pack_neighbor_copies(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t seed,
+                            const double *X, int V, int F, const int32_t *nbr, int n, const int32_t *perm,
+                            uint64_t *out_cts)
+{
+    if (!ctx) return FG_EINVAL;
+    API_TRY
+    FG_CHECK(X && nbr && perm && out_cts && V >= 1 && F >= 1 && n >= 1, FG_EINVAL,
+             "bad neighbour-copy arguments");
+    for (size_t e = 0; e < (size_t)V * n; e++)
+        FG_CHECK(nbr[e] >= -1 && nbr[e] < V, FG_EINVAL, "neighbour index out of range");
+    const size_t ct_w = (size_t)2 * ctx->nq * ctx->n;
+    std::vector<double> Xk((size_t)V * F);
+    for (int k = 0; k < n; k++) {
+        for (int v = 0; v < V; v++) {
+            const int u = nbr[(size_t)v * n + k];
+            for (int f = 0; f < F; f++) Xk[(size_t)v * F + f] = u >= 0 ? X[(size_t)u * F + f] : 0.0;
+        }
+        const int rc = fg_pack_features(ctx, sk_blob, sk_len, seed + (uint64_t)k, Xk.data(), V, F, perm, 1,
+                                        out_cts + (size_t)k * F * ct_w, nullptr);
+        if (rc != FG_OK) return rc;
+    }
+    API_CATCH(ctx)
+}
+
 int fg_decrypt(fg_ctx *ctx, const void *sk_blob, size_t sk_len, const uint64_t *ct, int level,
                uint64_t *out_pt)
 {
