@@ -868,14 +868,30 @@ static void batch_body(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
     // the results), then the stream count, then the capture
     int S = o.streams ? std::min(o.streams, n) : 1;
     if (o.streams == 0) {
+        // every stream needs a workspace like stream 0's: as many streams as
+        // the free device memory holds (with a margin), at most 8
+        batch_pass(ctx, keys, plans, n, in_cts, out_cts, 1, out_levels);
+        CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        size_t per_stream = 0, free_b = 0, total_b = 0;
+        for (const auto &kv : ctx->ws)
+            if (kv.first.rfind("b0/", 0) == 0) per_stream += kv.second.second;
+        CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        const int smax = (int)std::max<size_t>(
+            1, std::min<size_t>(8, 1 + (size_t)(0.8 * (double)free_b) / std::max<size_t>(per_stream, 1)));
         // the largest candidate first, so that every workspace exists
         // before the timed passes
         const int cand[4] = {8, 4, 2, 1};
-        batch_pass(ctx, keys, plans, n, in_cts, out_cts, std::min(8, n), out_levels);
+        int top = 1;
+        for (int c : cand)
+            if (c <= n && c <= smax) {
+                top = c;
+                break;
+            }
+        batch_pass(ctx, keys, plans, n, in_cts, out_cts, top, out_levels);
         CUDA_TRY(cudaStreamSynchronize(ctx->stream));
         double best = 0;
         for (int c : cand) {
-            if (c > n) continue;
+            if (c > top) continue;
             const double ms = time_pass(ctx, keys, plans, n, in_cts, out_cts, c, out_levels);
             if (best == 0 || ms < best) {
                 best = ms;
