@@ -280,6 +280,31 @@ const u64 *fg_ctx::pinv_tab(int level)
     return d;
 }
 
+// per limb i of q_0..q_level in digit D_j: N^-1 (D_j / q_i)^-1 mod q_i, so
+// that an inverse NTT scaled by it yields the base conversion's inputs
+// y_i = [x_i (D_j / q_i)^-1]_{q_i} directly
+const u64 *fg_ctx::modup_scale_tab(int level)
+{
+    auto it = modup_scale_tabs.find(level);
+    if (it != modup_scale_tabs.end()) return it->second;
+    std::vector<u64> h(2 * (level + 1));
+    for (int i = 0; i <= level; i++) {
+        const u64 q = primes[i];
+        const int d = i / alpha;
+        u64 hd = 1;
+        for (int j = d * alpha; j < std::min((d + 1) * alpha, level + 1); j++)
+            if (j != i) hd = hm::mulmod(hd, primes[j] % q, q);
+        const u64 ninv = hm::invmod((u64)n % q, q);
+        h[2 * i] = hm::mulmod(ninv, hm::invmod(hd, q), q);
+        h[2 * i + 1] = hm::shoup(h[2 * i], q);
+    }
+    u64 *dptr = nullptr;
+    CUDA_TRY(cudaMalloc(&dptr, h.size() * 8));
+    CUDA_TRY(cudaMemcpy(dptr, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
+    modup_scale_tabs[level] = dptr;
+    return dptr;
+}
+
 const u64 *fg_ctx::moddown_rescale_tab(int level)
 {
     auto it = mdr_tabs.find(level);
@@ -562,6 +587,7 @@ int fg_ctx_destroy(fg_ctx *ctx)
     for (auto &kv : ctx->pinv_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->mdr_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->mdr_half_tabs) cudaFree(kv.second);
+    for (auto &kv : ctx->modup_scale_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->ws) cudaFree(kv.second.first);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->batch.exec) cudaGraphExecDestroy(ctx->batch.exec);

@@ -168,15 +168,14 @@ __device__ __forceinline__ int pad16(int pos) { return pos + (pos >> 4); }
 // ROWS (16 or 8) of the 256 rows per CTA, 16 threads per row.  Both tile
 // sizes compute the same transform word for word; the batched form picks
 // one per shape by timing.
+// pass A's two rounds on values already in registers (element (r + 16 m) of
+// this thread's column), written to d (the tile's first column)
 template <bool LAZY, int COLS, bool OD>
-__device__ __forceinline__ void fwd_a16_body(const u64 *s, u64 *d, const ulonglong2 *stw, u64 q, u64 *sm)
+__device__ __forceinline__ void fwd_a16_rounds(u64 (&v)[16], u64 *d, const ulonglong2 *stw, u64 q, u64 *sm)
 {
     const int t = threadIdx.x, c = t % COLS, r = t / COLS;   // r: r0 in round 1, r1 in round 2
     constexpr int N2 = 256;
     const u64 q2 = 2 * q;
-    u64 v[16];
-#pragma unroll
-    for (int m = 0; m < 16; m++) v[m] = s[(size_t)(r + 16 * m) * N2 + c];
     // stage st, group g at (1 << st) + g
     ct16<LAZY>(v, twiddles<OD>([&](int st, int g) { return stw[(1 << st) + g]; }), q, q2);
 #pragma unroll
@@ -187,6 +186,17 @@ __device__ __forceinline__ void fwd_a16_body(const u64 *s, u64 *d, const ulonglo
     ct16<LAZY>(v, twiddles<OD>([&](int st, int g) { return stw[(1 << (st + 4)) + (r << st) + g]; }), q, q2);
 #pragma unroll
     for (int m = 0; m < 16; m++) d[(size_t)(16 * r + m) * N2 + c] = v[m];   // lazy
+}
+
+template <bool LAZY, int COLS, bool OD>
+__device__ __forceinline__ void fwd_a16_body(const u64 *s, u64 *d, const ulonglong2 *stw, u64 q, u64 *sm)
+{
+    const int t = threadIdx.x, c = t % COLS, r = t / COLS;
+    constexpr int N2 = 256;
+    u64 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; m++) v[m] = s[(size_t)(r + 16 * m) * N2 + c];
+    fwd_a16_rounds<LAZY, COLS, OD>(v, d, stw, q, sm);
 }
 
 template <int COLS, bool OD>
@@ -329,10 +339,12 @@ __device__ __forceinline__ void inv_a16_body(u64 *d, const ulonglong2 *stw, u64 
     for (int m = 0; m < 16; m++) d[(size_t)(r + 16 * m) * N2 + c] = shoup_mul(v[m], ni, nis, q);
 }
 
+// col_scale (may be null): per limb column of the batch, a constant (and
+// its Shoup companion) that replaces N^-1 in the final scaling
 template <int COLS, bool OD>
 __global__ void __launch_bounds__(16 * COLS, (OD ? 64 : 48) / COLS)
 ntt16_inv_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ itw,
-            const u64 *__restrict__ ninv)
+            const u64 *__restrict__ ninv, const u64 *__restrict__ col_scale)
 {
     const int limb = blockIdx.y;
     const int col = limb % bt.per_row, row = limb / bt.per_row;
@@ -346,9 +358,58 @@ ntt16_inv_a(const Batch bt, const PrimeC *__restrict__ primes, const ulonglong2 
     __syncthreads();
     const int c0 = blockIdx.x * COLS;
     u64 *d = bt.dst + ((size_t)row * bt.dst_stride + col) * 65536 + c0;
-    const u64 ni = ninv[2 * pi], nis = ninv[2 * pi + 1];
+    const u64 ni = col_scale ? col_scale[2 * col] : ninv[2 * pi];
+    const u64 nis = col_scale ? col_scale[2 * col + 1] : ninv[2 * pi + 1];
     if (q < (1ull << 47)) inv_a16_body<true, COLS, OD>(d, stw, q, ni, nis, sm);
     else inv_a16_body<false, COLS, OD>(d, stw, q, ni, nis, sm);
+}
+
+// ModUp, N = 2^16: the base conversion of one digit to one output prime,
+// fused into the first pass (column stages 0..7) of that output limb's
+// forward NTT.  y: [ncol][nl][N], the conversion's inputs y_i = [x_i (D_j /
+// q_i)^-1]_{q_i} in the coefficient domain (the inverse NTT of c1, scaled
+// by modup_scale_tab); digits: [ncol][beta][E][N], pass-A output of every
+// limb outside the digit (pass B follows as for any forward NTT).  Grid:
+// (256 / COLS column tiles, output index t, column f x beta + digit).
+template <int NMAX, int COLS, bool OD>
+__global__ void __launch_bounds__(16 * COLS, (OD ? 64 : 48) / COLS)
+k_modup_ntt16_a(const u64 *__restrict__ y, int nl, u64 *digits, int beta, int E,
+                const ConvTab *__restrict__ tabs, const PrimeC *__restrict__ primes,
+                const ulonglong2 *__restrict__ tw)
+{
+    const int f = blockIdx.z / beta, dg = blockIdx.z % beta, t = blockIdx.y;
+    const ConvTab &T = tabs[dg];
+    if (t >= T.n_out) return;
+    __shared__ u64 sm[256 * COLS];
+    __shared__ ulonglong2 stw[256];
+    const int pi = T.out_p[t];
+    const PrimeC P = primes[pi];
+    const ulonglong2 *twp = tw + (size_t)pi * 65536;
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) stw[k] = twp[k];
+    u64 hm_[NMAX];
+    const u64 *src[NMAX];
+#pragma unroll
+    for (int k = 0; k < NMAX; k++) {
+        hm_[k] = k < T.n_in ? T.hmod[k][t] : 0;
+        src[k] = y + ((size_t)f * nl + (k < T.n_in ? T.in_l[k] : 0)) * 65536;
+    }
+    const int c = threadIdx.x % COLS, r = threadIdx.x / COLS, c0 = blockIdx.x * COLS;
+    u64 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; m++) {
+        const size_t idx = (size_t)(r + 16 * m) * 256 + c0 + c;
+        u64 a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+        for (int k = 0; k < NMAX; k++)
+            if (k < T.n_in) mac_split(a0, a1, a2, split30(src[k][idx]), hm_[k]);
+        u64 hi = 0, lo = 0;
+        fold30(hi, lo, a0, a1, a2);
+        v[m] = redc(hi, lo, P);
+    }
+    __syncthreads();   // stw
+    u64 *d = digits + (((size_t)f * beta + dg) * E + T.out_l[t]) * 65536 + c0;
+    if (P.q < (1ull << 47)) fwd_a16_rounds<true, COLS, OD>(v, d, stw, P.q, sm);
+    else fwd_a16_rounds<false, COLS, OD>(v, d, stw, P.q, sm);
 }
 
 // Stages are taken two at a time (radix-4 rounds: four elements, four
@@ -1467,7 +1528,7 @@ KTimer::~KTimer()
 
 
 template <int COLS, int ROWS, bool OD>
-static void ntt16_launch_t(fg_ctx *ctx, const Batch &bt, int count, bool inverse)
+static void ntt16_launch_t(fg_ctx *ctx, const Batch &bt, int count, bool inverse, const u64 *col_scale)
 {
     const auto *fwd = (const ulonglong2 *)ctx->d_fwd;
     const auto *inv = (const ulonglong2 *)ctx->d_inv;
@@ -1482,25 +1543,39 @@ static void ntt16_launch_t(fg_ctx *ctx, const Batch &bt, int count, bool inverse
     } else {
         ntt16_inv_b<ROWS, OD><<<gB, 16 * ROWS, 0, ctx->stream>>>(bt, ctx->d_primes, inv,
                                                                 (const ulonglong2 *)ctx->d_inv_rows);
-        ntt16_inv_a<COLS, OD><<<gA, 16 * COLS, 0, ctx->stream>>>(b2, ctx->d_primes, inv, ctx->d_ninv);
+        ntt16_inv_a<COLS, OD><<<gA, 16 * COLS, 0, ctx->stream>>>(b2, ctx->d_primes, inv, ctx->d_ninv,
+                                                                col_scale);
     }
 }
 
 // the tile and twiddle form of the N = 2^16 transform from the context's tuning
 template <bool OD>
-static void ntt16_launch_od(fg_ctx *ctx, const Batch &bt, int count, bool inverse)
+static void ntt16_launch_od(fg_ctx *ctx, const Batch &bt, int count, bool inverse, const u64 *col_scale)
 {
     const bool ca = ctx->tune.ntt_cols == 8, rb = ctx->tune.ntt_rows == 8;
-    if (!ca && !rb) ntt16_launch_t<16, 16, OD>(ctx, bt, count, inverse);
-    else if (ca && !rb) ntt16_launch_t<8, 16, OD>(ctx, bt, count, inverse);
-    else if (!ca && rb) ntt16_launch_t<16, 8, OD>(ctx, bt, count, inverse);
-    else ntt16_launch_t<8, 8, OD>(ctx, bt, count, inverse);
+    if (!ca && !rb) ntt16_launch_t<16, 16, OD>(ctx, bt, count, inverse, col_scale);
+    else if (ca && !rb) ntt16_launch_t<8, 16, OD>(ctx, bt, count, inverse, col_scale);
+    else if (!ca && rb) ntt16_launch_t<16, 8, OD>(ctx, bt, count, inverse, col_scale);
+    else ntt16_launch_t<8, 8, OD>(ctx, bt, count, inverse, col_scale);
 }
 
-static void ntt16_launch(fg_ctx *ctx, const Batch &bt, int count, bool inverse)
+static void ntt16_launch(fg_ctx *ctx, const Batch &bt, int count, bool inverse,
+                         const u64 *col_scale = nullptr)
 {
-    if (ctx->tune.ntt_tw) ntt16_launch_od<true>(ctx, bt, count, inverse);
-    else ntt16_launch_od<false>(ctx, bt, count, inverse);
+    if (ctx->tune.ntt_tw) ntt16_launch_od<true>(ctx, bt, count, inverse, col_scale);
+    else ntt16_launch_od<false>(ctx, bt, count, inverse, col_scale);
+}
+
+// N = 2^16 forward pass B alone (after a fused first pass), in place on bt.dst
+template <bool OD>
+static void ntt16_pass_b_od(fg_ctx *ctx, const Batch &bt, int count)
+{
+    const auto *fwd = (const ulonglong2 *)ctx->d_fwd;
+    const auto *rows = (const ulonglong2 *)ctx->d_fwd_rows;
+    if (ctx->tune.ntt_rows == 8)
+        ntt16_fwd_b<8, OD><<<dim3(32, count), 128, 0, ctx->stream>>>(bt, ctx->d_primes, fwd, rows);
+    else
+        ntt16_fwd_b<16, OD><<<dim3(16, count), 256, 0, ctx->stream>>>(bt, ctx->d_primes, fwd, rows);
 }
 
 template <int LOGN>
@@ -1693,8 +1768,62 @@ void rescale_ntt(fg_ctx *ctx, u64 *ct, int ls, int npoly, int level)
     check_launch("rescale_finish");
 }
 
+// ModUp at N = 2^16 with the conversion fused into the digits' first NTT
+// pass: the inverse NTT of c1 scaled to give the conversion's inputs y_i,
+// one kernel per (column, digit, output limb, column tile) converting and
+// running stages 0..7, then pass B over every digit limb
+template <bool OD>
+static void modup16_fused(fg_ctx *ctx, const u64 *lane, int ls, int ncol, int level, u64 *digits)
+{
+    const int N = ctx->n, nl = level + 1, E = ctx->ext(level), beta = ctx->n_digits(level);
+    u64 *y = (u64 *)ctx->buf("modup_c1", (size_t)ncol * nl * N * 8);
+    std::vector<int> pid(nl);
+    for (int i = 0; i < nl; i++) pid[i] = i;
+    {
+        Batch bt = make_batch(const_cast<u64 *>(lane) + (size_t)ls * N, 2 * ls, y, nl, nl, ncol, pid);
+        KTimer kt(ctx, "ntt", (double)nl * ncol * N * 8 * 2);
+        ntt16_launch(ctx, bt, ncol * nl, true, ctx->modup_scale_tab(level));
+        check_launch("ntt", 2);
+    }
+    const int nmax = std::min(ctx->alpha, nl);
+    int n_out = 0;
+    for (int d = 0; d < beta; d++) n_out = std::max(n_out, E - std::min(ctx->alpha, nl - d * ctx->alpha));
+    const ConvTab *tabs = ctx->modup_tabs(level);
+    const auto *fwd = (const ulonglong2 *)ctx->d_fwd;
+    {
+        KTimer kt(ctx, "modup_conv", (double)ncol * (nl + (double)beta * (E - ctx->alpha)) * N * 8);
+        const bool c8 = ctx->tune.ntt_cols == 8;
+        dim3 g(c8 ? 32 : 16, n_out, ncol * beta);
+#define FG_LAUNCH(M)                                                                                  \
+        if (c8)                                                                                       \
+            k_modup_ntt16_a<M, 8, OD><<<g, 128, 0, ctx->stream>>>(y, nl, digits, beta, E, tabs,       \
+                                                                  ctx->d_primes, fwd);                \
+        else                                                                                          \
+            k_modup_ntt16_a<M, 16, OD><<<g, 256, 0, ctx->stream>>>(y, nl, digits, beta, E, tabs,      \
+                                                                   ctx->d_primes, fwd)
+        FG_NIN_DISPATCH(nmax, FG_LAUNCH)
+#undef FG_LAUNCH
+        check_launch("modup_ntt16_a");
+    }
+    std::vector<int> dp(beta * E);
+    for (int d = 0; d < beta; d++)
+        for (int i = 0; i < E; i++)
+            dp[d * E + i] = (i <= level && i / ctx->alpha == d) ? -1 : ctx->ext_prime(level, i);
+    Batch bd = make_batch(digits, beta * E, digits, beta * E, beta * E, ncol, dp);
+    int active = 0;
+    for (int v : dp) active += v >= 0;
+    KTimer kt(ctx, "ntt", (double)active * ncol * N * 8 * 2 / 2);
+    ntt16_pass_b_od<OD>(ctx, bd, ncol * beta * E);
+    check_launch("ntt16_fwd_b");
+}
+
 void modup(fg_ctx *ctx, const u64 *lane, int ls, int ncol, int level, u64 *digits)
 {
+    if (ctx->log_n == 16 && ctx->tune.modup_fused) {
+        if (ctx->tune.ntt_tw) modup16_fused<true>(ctx, lane, ls, ncol, level, digits);
+        else modup16_fused<false>(ctx, lane, ls, ncol, level, digits);
+        return;
+    }
     const int N = ctx->n, nl = level + 1, E = ctx->ext(level), beta = ctx->n_digits(level);
     u64 *c1c = (u64 *)ctx->buf("modup_c1", (size_t)ncol * nl * N * 8);
     std::vector<int> pid(nl);
