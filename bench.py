@@ -806,6 +806,10 @@ def run_batched(args):
     plain_ms, plain_launches = timed(plain)
     want = [o.clone() for o in outs]
     used = {}
+    # the one-at-a-time workspace is not needed by the batch
+    ctx.release_workspace()
+    torch.cuda.empty_cache()
+    free_gb = torch.cuda.mem_get_info()[0] / 1e9
 
     def batched():
         lv, s = fg.gcn_layer_batch(ctx, keys, plans, ins, outs, tune=True)
@@ -827,6 +831,7 @@ def run_batched(args):
             "unit": "ms/batch", "higher_is_better": False, "queries": nq,
             "plain_ms": round(plain_ms, 3), "batched_ms": round(batch_ms, 3),
             "speedup": round(plain_ms / batch_ms, 3), "streams": used.get("streams"),
+            "free_gb_before_batch": round(free_gb, 1),
             "tuning": dict(zip(("config", "pass_ms_per_candidate"), fg.batch_tuning(ctx))),
             "bit_exact_vs_plain": exact, "decrypt_max_abs_err_vs_fp64": err,
             "rotations_per_batch": rot, "rotations_per_s_batched": round(rot / (batch_ms / 1e3), 1),

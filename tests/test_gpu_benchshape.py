@@ -74,15 +74,24 @@ def test_benchshape_plan_reaches_the_benchmark_kernel_shapes(case):
     assert op.Fp == 16 and op.F > 128
 
 
-@pytest.mark.parametrize("where", ["device", "host"])
-def test_benchshape_layer_word_for_word(case, where):
+@pytest.mark.parametrize("where,tuning", [("device", {}), ("host", {}),
+                                          ("device", dict(modup_fused=1)),
+                                          ("device", dict(ntt_cols=8, ntt_rows=8, ntt_tw=1, ks_split=1,
+                                                          ks_cols=2, modup_fused=1, gmac_groups=4))])
+def test_benchshape_layer_word_for_word(case, where, tuning):
+    """Also under other launch configurations (the fused ModUp, the other
+    NTT tiles and twiddle form, the other key-switch and group-MAC choices)."""
     import torch
     fg, ctx, doc, op, plan, keys, x = case
     if where == "device":
         xin = torch.from_numpy(x.view(np.int64)).cuda()
     else:
         xin = x
-    out, lvl, _ = fg.gcn_layer_axw(ctx, keys, plan, xin)
+    fg.set_tuning(ctx, **tuning)
+    try:
+        out, lvl, _ = fg.gcn_layer_axw(ctx, keys, plan, xin)
+    finally:
+        fg.set_tuning(ctx)
     assert lvl == doc["out_level"] == op.out_level
     for j, want in doc["columns"].items():
         o = out[int(j)]
