@@ -61,16 +61,21 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def traffic_for(cls):
-    """dram bytes per call of a kernel class from the committed ncu summary,
-    or None when absent or taken on a different version of the kernels."""
+def traffic_for(cls, alg_bytes_per_call):
+    """DRAM bytes per call of a kernel class: the ratio of ncu's DRAM bytes
+    (dram__bytes_read.sum + dram__bytes_write.sum) to the class's algorithmic
+    bytes, captured on the small case (bench.py --profile --small: same ring
+    and 16 columns, 8 + 2 primes, 4000 nodes) and committed in
+    profiles/ncu_traffic.json, times this workload's algorithmic bytes per
+    call; None when absent or taken on other kernels than these."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             t = json.load(f)
         src = open(os.path.join(ROOT, "paper_2506_10399_gb300", "csrc", "kernels.cu"), "rb").read()
         if t.get("kernels_sha256") != hashlib.sha256(src).hexdigest():
             return None
-        return t["per_call_bytes"].get(cls)
+        r = t["dram_over_algorithmic"].get(cls)
+        return None if r is None else r * alg_bytes_per_call
     except Exception:
         return None
 
@@ -515,7 +520,7 @@ def run_ours(args):
 
     peak, peak_kind = peaks()
     achieved = k_bytes / (k_ms / 1e3) / 1e9 if k_ms > 0 else 0.0
-    traffic = traffic_for(dominant)
+    traffic = traffic_for(dominant, k_bytes / max(1, k_calls))
     rotations = info["rotations"]
     line = {
         "metric": METRIC, "value": round(ms, 3), "unit": UNIT, "n_gpus": world,
@@ -866,7 +871,8 @@ def main():
                     help="workload of --two-layer")
     ap.add_argument("--inter", action="store_true", help="the layer in Inter-CA mode")
     ap.add_argument("--tuning", default="", help="launch configuration ntt_cols,ntt_rows,ntt_tw,ks_split,"
-                                                  "ks_cols,modup_fused,gmac_groups (default: the library's)")
+                                                  "ks_cols,modup_fused,moddown_fused,gmac_groups (default: the "
+                                                  "library's)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -305,6 +305,37 @@ const u64 *fg_ctx::modup_scale_tab(int level)
     return dptr;
 }
 
+// per extended limb of level l (positions 0..E-1): at position l, N^-1 mod
+// q_l; at the special limb of p_k, N^-1 (P / p_k)^-1 mod p_k (an inverse NTT
+// scaled by it yields the centred conversion's inputs before centring);
+// other positions unused
+const u64 *fg_ctx::moddown_scale_tab(int level)
+{
+    auto it = moddown_scale_tabs.find(level);
+    if (it != moddown_scale_tabs.end()) return it->second;
+    const int E = ext(level);
+    std::vector<u64> h(2 * E, 0);
+    {
+        const u64 q = primes[level];
+        h[2 * level] = hm::invmod((u64)n % q, q);
+        h[2 * level + 1] = hm::shoup(h[2 * level], q);
+    }
+    for (int k = 0; k < np; k++) {
+        const u64 p = primes[nq + k];
+        u64 hk = 1;
+        for (int j = 0; j < np; j++)
+            if (j != k) hk = hm::mulmod(hk, primes[nq + j] % p, p);
+        const int i = level + 1 + k;
+        h[2 * i] = hm::mulmod(hm::invmod((u64)n % p, p), hm::invmod(hk, p), p);
+        h[2 * i + 1] = hm::shoup(h[2 * i], p);
+    }
+    u64 *dptr = nullptr;
+    CUDA_TRY(cudaMalloc(&dptr, h.size() * 8));
+    CUDA_TRY(cudaMemcpy(dptr, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
+    moddown_scale_tabs[level] = dptr;
+    return dptr;
+}
+
 const u64 *fg_ctx::moddown_rescale_tab(int level)
 {
     auto it = mdr_tabs.find(level);
@@ -588,6 +619,7 @@ int fg_ctx_destroy(fg_ctx *ctx)
     for (auto &kv : ctx->mdr_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->mdr_half_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->modup_scale_tabs) cudaFree(kv.second);
+    for (auto &kv : ctx->moddown_scale_tabs) cudaFree(kv.second);
     for (auto &kv : ctx->ws) cudaFree(kv.second.first);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->batch.exec) cudaGraphExecDestroy(ctx->batch.exec);

@@ -94,12 +94,13 @@ struct Tune {
     int ks_split = 0;      // key switch: 0 = launch bounds by digit count, 1 = one CTA per SM fewer
     int ks_cols = 1;       // key switch: launches the columns are split over (1 or 2)
     int modup_fused = 0;   // N = 2^16 ModUp: 1 = conversion fused into the digits' first NTT pass
+    int moddown_fused = 0; // N = 2^16 ModDown + rescale: 1 = conversion fused into the first NTT pass
     int gmac_groups = 7;   // group MAC: outputs from which a CTA runs three thread groups
     bool operator==(const Tune &o) const
     {
         return ntt_cols == o.ntt_cols && ntt_rows == o.ntt_rows && ntt_tw == o.ntt_tw &&
                ks_split == o.ks_split && ks_cols == o.ks_cols && modup_fused == o.modup_fused &&
-               gmac_groups == o.gmac_groups;
+               moddown_fused == o.moddown_fused && gmac_groups == o.gmac_groups;
     }
 };
 
@@ -135,6 +136,7 @@ struct fg_ctx {
     std::map<int, u64 *> rescale_tabs;   // level -> [level][2] q_l^-1 mod q_i + Shoup
     std::map<int, u64 *> pinv_tabs;      // level -> [level+1][2] P^-1 mod q_i + Shoup
     std::map<int, u64 *> modup_scale_tabs;   // level -> [level+1][2] N^-1 (D_j/q_i)^-1 mod q_i + Shoup
+    std::map<int, u64 *> moddown_scale_tabs; // level -> [E][2]: limb l N^-1, special k N^-1 (P/p_k)^-1
     std::map<int, u64 *> mdr_tabs;       // level -> [level][2] (P q_l)^-1 mod q_i + Shoup
     std::map<int, u64 *> mdr_half_tabs;  // level -> [level+1] P (q_l - 1)/2 mod q_i (rounded rescale)
 
@@ -184,6 +186,7 @@ struct fg_ctx {
     const u64 *rescale_tab(int level);
     const u64 *pinv_tab(int level);
     const u64 *modup_scale_tab(int level);
+    const u64 *moddown_scale_tab(int level);
     const u64 *moddown_rescale_tab(int level);
     const u64 *moddown_rescale_half_tab(int level);
 };

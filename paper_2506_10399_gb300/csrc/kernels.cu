@@ -1466,6 +1466,82 @@ k_moddown_rescale_finish(const u64 *__restrict__ ext, int E, const u64 *__restri
     }
 }
 
+// ModDown + rescale at N = 2^16, the conversion fused into the first NTT
+// pass of w (see k_moddown_rescale_conv for what w is).  First
+// k_moddown_prep, per coefficient of each polynomial: y_k (the inverse NTT
+// of the special limbs scaled to [u_k (P/p_k)^-1]_{p_k}), c = #{y_k > p_k/2},
+// o_l = ((ext_l + [H]_{q_l}) - Conv_l(y) + c [P]_{q_l}) P^-1 mod q_l, and
+// o_l | c << 60 written over limb l (q_l < 2^60; limb l is not read again).
+// Then k_moddown_ntt16_a per (column tile, kept limb t, polynomial): w_t =
+// Conv_t(y, c) + P o_l - [H]_{q_t} mod q_t, straight into pass A of w_t.
+template <int NMAX>
+__global__ void __launch_bounds__(256)
+k_moddown_prep(u64 *ext, int E, int l, const ConvTab *__restrict__ tab, const u64 *__restrict__ pinv,
+               const u64 *__restrict__ hq, const PrimeC *__restrict__ primes, int N)
+{
+    const int poly = blockIdx.y;
+    const ConvTab &T = *tab;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    u64 y[NMAX];
+    int c = 0;
+    const u64 *src = ext + (size_t)poly * E * N + x;
+#pragma unroll
+    for (int k = 0; k < NMAX; k++)
+        if (k < T.n_in) {
+            const u64 yk = src[(size_t)T.in_l[k] * N];
+            c += yk > (primes[T.in_p[k]].q >> 1);
+            y[k] = split30(yk);
+        }
+    const PrimeC Pl = primes[l];
+    u64 *el = ext + ((size_t)poly * E + l) * N + x;
+    const u64 e = add_mod(*el, hq[l], Pl.q);
+    const u64 ol = shoup_mul(sub_mod(e, conv_point<NMAX>(T, y, l, Pl, c), Pl.q), pinv[2 * l], pinv[2 * l + 1], Pl.q);
+    *el = ol | ((u64)c << 60);
+}
+
+template <int NMAX, bool OD>
+__global__ void __launch_bounds__(256, OD ? 4 : 3)
+k_moddown_ntt16_a(const u64 *__restrict__ ext, int E, u64 *w, int l, const ConvTab *__restrict__ tab,
+                  const u64 *__restrict__ pmodq, const u64 *__restrict__ hq,
+                  const PrimeC *__restrict__ primes, const ulonglong2 *__restrict__ tw)
+{
+    const int t = blockIdx.y, poly = blockIdx.z;
+    const ConvTab &T = *tab;
+    __shared__ u64 sm[256 * 16];
+    __shared__ ulonglong2 stw[256];
+    const PrimeC P = primes[t];
+    const ulonglong2 *twp = tw + (size_t)t * 65536;
+    stw[threadIdx.x] = twp[threadIdx.x];
+    const u64 pw = pmodq[2 * t], pws = pmodq[2 * t + 1], ht = hq[t];
+    u64 hm_[NMAX], nb = T.negb[t];
+#pragma unroll
+    for (int k = 0; k < NMAX; k++) hm_[k] = k < T.n_in ? T.hmod[k][t] : 0;
+    const u64 *base = ext + (size_t)poly * E * 65536;
+    const int c = threadIdx.x & 15, r = threadIdx.x >> 4, c0 = blockIdx.x * 16;
+    u64 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; m++) {
+        const size_t idx = (size_t)(r + 16 * m) * 256 + c0 + c;
+        const u64 pk = base[(size_t)l * 65536 + idx];
+        const u64 ol = pk & ((1ull << 60) - 1);
+        const int cc = (int)(pk >> 60);
+        u64 a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+        for (int k = 0; k < NMAX; k++)
+            if (k < T.n_in) mac_split(a0, a1, a2, split30(base[(size_t)T.in_l[k] * 65536 + idx]), hm_[k]);
+        if (cc) mac_split(a0, a1, a2, (u64)cc, nb);
+        u64 hi = 0, lo = 0;
+        fold30(hi, lo, a0, a1, a2);
+        const u64 conv = redc(hi, lo, P);
+        v[m] = sub_mod(add_mod(conv, shoup_mul(ol, pw, pws, P.q), P.q), ht, P.q);
+    }
+    __syncthreads();   // stw
+    u64 *d = w + ((size_t)poly * l + t) * 65536 + c0;
+    if (P.q < (1ull << 47)) fwd_a16_rounds<true, 16, OD>(v, d, stw, P.q, sm);
+    else fwd_a16_rounds<false, 16, OD>(v, d, stw, P.q, sm);
+}
+
 // residues mod the special primes of a polynomial given by its limb 0,
 // read as a centred integer (valid when |coefficient| < q_0 / 2)
 __global__ void k_lift_special(const u64 *limb0, u64 q0, u64 *out, int np, int nq,
@@ -2061,8 +2137,63 @@ void ks_multi(fg_ctx *ctx, const std::vector<const KeyDev *> &keys, const std::v
     }
 }
 
+// ModDown + rescale at N = 2^16 with the conversion fused into w's first
+// NTT pass (see k_moddown_ntt16_a)
+template <bool OD>
+static void moddown16_fused(fg_ctx *ctx, u64 *ext, int ncol, int level, u64 *out, int ls)
+{
+    const int N = ctx->n, l = level, E = ctx->ext(level), npoly = 2 * ncol;
+    std::vector<int> pp(E, -1);
+    pp[l] = l;
+    for (int i = l + 1; i < E; i++) pp[i] = ctx->ext_prime(level, i);
+    {
+        Batch bt = make_batch(ext, E, ext, E, E, npoly, pp);
+        KTimer kt(ctx, "ntt", (double)npoly * (ctx->np + 1) * N * 8 * 2);
+        ntt16_launch(ctx, bt, npoly * E, true, ctx->moddown_scale_tab(level));
+        check_launch("ntt", 2);
+    }
+    u64 *w = (u64 *)ctx->buf("ks_conv", (size_t)npoly * l * N * 8);
+    const ConvTab *tab = ctx->moddown_tab(level);
+    const u64 *hq = ctx->moddown_rescale_half_tab(level);
+    {
+        KTimer kt(ctx, "moddown_conv", (double)npoly * (ctx->np + 2 + l) * N * 8);
+        dim3 g1((N + 255) / 256, npoly);
+#define FG_LAUNCH(M) \
+        k_moddown_prep<M><<<g1, 256, 0, ctx->stream>>>(ext, E, l, tab, ctx->pinv_tab(level), hq, ctx->d_primes, N)
+        FG_NIN_DISPATCH(ctx->np, FG_LAUNCH)
+#undef FG_LAUNCH
+        check_launch("moddown_prep");
+        dim3 g2(16, l, npoly);
+#define FG_LAUNCH(M)                                                                                \
+        k_moddown_ntt16_a<M, OD><<<g2, 256, 0, ctx->stream>>>(ext, E, w, l, tab, ctx->d_pmodq, hq,    \
+                                                              ctx->d_primes,                          \
+                                                              (const ulonglong2 *)ctx->d_fwd)
+        FG_NIN_DISPATCH(ctx->np, FG_LAUNCH)
+#undef FG_LAUNCH
+        check_launch("moddown_ntt16_a");
+    }
+    {
+        std::vector<int> pq(l);
+        for (int i = 0; i < l; i++) pq[i] = i;
+        Batch bw = make_batch(w, l, w, l, l, npoly, pq);
+        KTimer kt(ctx, "ntt", (double)npoly * l * N * 8 * 2 / 2);
+        ntt16_pass_b_od<OD>(ctx, bw, npoly * l);
+        check_launch("ntt16_fwd_b");
+    }
+    KTimer kt(ctx, "moddown_store", (double)npoly * l * 3 * N * 8);
+    dim3 g3((N / 2 + 255) / 256, l);
+    k_moddown_rescale_finish<<<g3, 256, 0, ctx->stream>>>(ext, E, w, out, ls, npoly, l,
+                                                          ctx->moddown_rescale_tab(level), ctx->d_primes, N);
+    check_launch("moddown_rescale_finish");
+}
+
 void moddown_rescale_to_lane(fg_ctx *ctx, u64 *ext, int ncol, int level, u64 *out, int ls)
 {
+    if (ctx->log_n == 16 && ctx->tune.moddown_fused && level >= 1) {
+        if (ctx->tune.ntt_tw) moddown16_fused<true>(ctx, ext, ncol, level, out, ls);
+        else moddown16_fused<false>(ctx, ext, ncol, level, out, ls);
+        return;
+    }
     FG_CHECK(level >= 1, FG_ELEVEL, "rescale needs level >= 1");
     const int N = ctx->n, l = level, E = ctx->ext(level), npoly = 2 * ncol;
     std::vector<int> pp(E, -1);

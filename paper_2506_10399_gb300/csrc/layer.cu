@@ -814,6 +814,7 @@ static void tune_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
     double best_ms = timed(best);
     const int cols[2] = {16, 8}, rows[2] = {16, 8}, tw[2] = {0, 1}, split[2] = {0, 1}, kcols[2] = {1, 2},
               fused[2] = {0, 1}, groups[3] = {7, 4, 13};
+    const int dfused[2] = {0, 1};
     auto knob = [&](auto field, const int *vals, int nv) {
         Tune base = best;
         for (int k = 0; k < nv; k++) {
@@ -832,6 +833,7 @@ static void tune_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
         knob(&Tune::ntt_rows, rows, 2);
         knob(&Tune::ntt_tw, tw, 2);
         knob(&Tune::modup_fused, fused, 2);
+        knob(&Tune::moddown_fused, dfused, 2);
     }
     knob(&Tune::ks_split, split, 2);
     knob(&Tune::ks_cols, kcols, 2);
@@ -932,7 +934,7 @@ static void batch_body(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
     if (streams_used) *streams_used = S;
 }
 
-extern "C" int fg_batch_tuning(const fg_ctx *ctx, int cfg[7], double *ms, int cap, int *n)
+extern "C" int fg_batch_tuning(const fg_ctx *ctx, int cfg[8], double *ms, int cap, int *n)
 {
     if (!ctx || !cfg || !n || cap < 0) return FG_EINVAL;
     const Tune &t = ctx->batch_tuned ? ctx->batch_tune : ctx->tune;
@@ -942,19 +944,20 @@ extern "C" int fg_batch_tuning(const fg_ctx *ctx, int cfg[7], double *ms, int ca
     cfg[3] = t.ks_split;
     cfg[4] = t.ks_cols;
     cfg[5] = t.modup_fused;
-    cfg[6] = t.gmac_groups;
+    cfg[6] = t.moddown_fused;
+    cfg[7] = t.gmac_groups;
     *n = ctx->batch_tuned ? (int)ctx->tune_ms.size() : 0;
     if (ms)
         for (int i = 0; i < std::min(cap, *n); i++) ms[i] = ctx->tune_ms[i];
     return FG_OK;
 }
 
-extern "C" int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[7])
+extern "C" int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[8])
 {
     if (!ctx || !cfg) return FG_EINVAL;
     if ((cfg[0] != 16 && cfg[0] != 8) || (cfg[1] != 16 && cfg[1] != 8) || (cfg[2] != 0 && cfg[2] != 1) ||
         (cfg[3] != 0 && cfg[3] != 1) || (cfg[4] != 1 && cfg[4] != 2) || (cfg[5] != 0 && cfg[5] != 1) ||
-        cfg[6] < 1)
+        (cfg[6] != 0 && cfg[6] != 1) || cfg[7] < 1)
         return FG_EINVAL;
     ctx->tune.ntt_cols = cfg[0];
     ctx->tune.ntt_rows = cfg[1];
@@ -962,7 +965,8 @@ extern "C" int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[7])
     ctx->tune.ks_split = cfg[3];
     ctx->tune.ks_cols = cfg[4];
     ctx->tune.modup_fused = cfg[5];
-    ctx->tune.gmac_groups = cfg[6];
+    ctx->tune.moddown_fused = cfg[6];
+    ctx->tune.gmac_groups = cfg[7];
     return FG_OK;
 }
 
