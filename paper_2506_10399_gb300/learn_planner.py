@@ -123,19 +123,53 @@ def _record_amounts(rec, M):
 
 
 def measure(out_path, budget_s=1500.0):
+    """Append to out_path the measurements of the graphs it does not hold
+    yet (held-out seeds first), until the time budget runs out.  A candidate
+    whose layer does not fit the device (FG_EOOM, after the workspace was
+    released once) is left out of its graph's record."""
+    import os
     import torch
     fg = _fg()
     from . import workloads as wl
     P = wl.BATCH_PARAMS
     t0 = time.time()
+    done = set()
+    if os.path.exists(out_path):
+        done = {json.loads(l)["seed"] for l in open(out_path) if l.strip()}
     ctx = fg.Context(**P)
     M = ctx.slots
-    seeds = HELD_OUT + TRAIN
+    seeds = [s for s in HELD_OUT + TRAIN if s not in done]
     sk, evk = fg.keygen(ctx, 1, sorted(all_amounts(M)))
     keys = fg.load_evk(ctx, evk)
     del evk
     g = torch.Generator(device="cuda").manual_seed(0)
-    with open(out_path, "w") as f:
+
+    def run_candidate(w, c, t, perm, xs):
+        plan = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=t,
+                             radix_bits=c["radix_bits"], no_encode=True)
+        try:
+            feat = plan.features(w.row_ptr, w.col)
+            info = plan.info()
+            if t not in xs:
+                # the timing does not depend on the values: random residues
+                xs[t] = torch.randint(0, 1 << 40, (info["n_in"], 2, ctx.nq, ctx.n), dtype=torch.int64,
+                                      device="cuda", generator=g)
+            x = xs[t]
+            out = torch.empty((info["n_out"], 2, info["out_level"] + 1, ctx.n), dtype=torch.int64,
+                              device="cuda")
+            fg.gcn_layer_axw(ctx, keys, plan, x, out=out)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            fg.gcn_layer_axw(ctx, keys, plan, x, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            return {"t": t, "ms": e0.elapsed_time(e1), "features": [float(v) for v in feat],
+                    "rotations": info["rotations"], "groups": info["n_groups"]}
+        finally:
+            plan.close()
+
+    with open(out_path, "a") as f:
         for s in seeds:
             if time.time() - t0 > budget_s:
                 break
@@ -149,32 +183,21 @@ def measure(out_path, budget_s=1500.0):
                 if t is None:
                     continue
                 perm = candidate_perm(fg, wl, w, M // t, c, s, cache)
-                plan = fg.plan_build(ctx, w.row_ptr, w.col, w.val, w.W, perm, t=t,
-                                     radix_bits=c["radix_bits"], no_encode=True)
-                feat = plan.features(w.row_ptr, w.col)
-                info = plan.info()
-                if t not in xs:
-                    # the timing does not depend on the values: random residues
-                    xs[t] = torch.randint(0, 1 << 40, (info["n_in"], 2, ctx.nq, ctx.n), dtype=torch.int64,
-                                          device="cuda", generator=g)
-                x = xs[t]
-                out = torch.empty((info["n_out"], 2, info["out_level"] + 1, ctx.n), dtype=torch.int64,
-                                  device="cuda")
-                fg.gcn_layer_axw(ctx, keys, plan, x, out=out)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                torch.cuda.synchronize()
-                e0.record()
-                fg.gcn_layer_axw(ctx, keys, plan, x, out=out)
-                e1.record()
-                torch.cuda.synchronize()
-                rows.append({"cand": ci, "t": t, "ms": e0.elapsed_time(e1),
-                             "features": [float(v) for v in feat],
-                             "rotations": info["rotations"], "groups": info["n_groups"]})
-                plan.close()
-                del out
+                for attempt in range(2):
+                    try:
+                        r = run_candidate(w, c, t, perm, xs)
+                        r["cand"] = ci
+                        rows.append(r)
+                        break
+                    except fg.FicgcnError as e:
+                        if e.code != -5:
+                            raise
+                        xs.clear()
+                        ctx.release_workspace()
+                        torch.cuda.empty_cache()
             f.write(json.dumps({"seed": s, "V": w.V, "F": w.X.shape[1], "t_rule": t_rule, "cands": rows}) + "\n")
             f.flush()
-            del xs, x
+            xs.clear()
             ctx.release_workspace()
             torch.cuda.empty_cache()
     print(json.dumps({"graphs_measured": sum(1 for _ in open(out_path)), "seconds": round(time.time() - t0)}))
@@ -182,6 +205,12 @@ def measure(out_path, budget_s=1500.0):
 
 def load(path):
     return [json.loads(l) for l in open(path)]
+
+
+def complete(rows):
+    """Graphs whose record holds the default candidate (needed to judge the
+    gain over it)."""
+    return [r for r in rows if any(c["cand"] == DEFAULT for c in r["cands"])]
 
 
 def _xy(rows):
@@ -199,7 +228,7 @@ def _xy(rows):
 
 def train(data_path, model_path, steps=3000, lr=3e-3, seed=0):
     fg = _fg()
-    data = load(data_path)
+    data = complete(load(data_path))
     held = [r for r in data if r["seed"] in HELD_OUT]
     tr = [r for r in data if r["seed"] not in HELD_OUT]
     X, y = _xy(tr)
@@ -214,7 +243,15 @@ def train(data_path, model_path, steps=3000, lr=3e-3, seed=0):
     model = {"n_in": n_in, "hidden": HIDDEN, "mean": mu.tolist(), "std": sd.tolist(),
              "params": [float(v) for v in params], "train_graphs": len(tr), "train_rows": int(X.shape[0]),
              "final_loss": float(losses[-1]), "candidates": CANDIDATES}
-    report = evaluate(m, mu, sd, held)
+    # the fallback margin: the default plan is kept unless a candidate is
+    # predicted faster by more than the margin (log2 units), chosen on the
+    # training graphs
+    margins = [0.0, 0.02, 0.05, 0.1, 0.2, 0.3, 0.5]
+    gains = [evaluate(m, mu, sd, tr, mg)["gain_vs_default"] for mg in margins]
+    margin = margins[int(np.argmax(gains))]
+    model["margin"] = margin
+    model["train_gain_by_margin"] = dict(zip(map(str, margins), gains))
+    report = evaluate(m, mu, sd, held, margin)
     model["held_out"] = report
     with open(model_path, "w") as f:
         json.dump(model, f)
@@ -241,13 +278,24 @@ def choose(m, mu, sd, features):
     return b
 
 
-def evaluate(m, mu, sd, rows):
-    """Per held-out graph: measured latency of the model's choice, of the
-    exhaustive planner's (the fastest candidate) and of the default plan."""
+def pick(pred, cands, margin):
+    """The candidate the learned planner builds: the lowest prediction, unless
+    it beats the default plan's prediction by no more than margin (log2
+    latency), in which case the default (the exhaustive planner's fallback)."""
+    b = int(np.argmin(pred))
+    d = next(i for i, c in enumerate(cands) if c["cand"] == DEFAULT)
+    return b if pred[b] < pred[d] - margin else d
+
+
+def evaluate(m, mu, sd, rows, margin=0.0):
+    """Per graph: measured latency of the learned planner's choice (pick),
+    of the exhaustive planner's (the fastest candidate) and of the default
+    plan."""
     chosen, best, default, hits = [], [], [], 0
     for r in rows:
         F = (np.array([c["features"] for c in r["cands"]]) - mu) / sd
-        b, _ = m.choose(F)
+        _, pred = m.choose(F)
+        b = pick(pred, r["cands"], margin)
         ms = [c["ms"] for c in r["cands"]]
         chosen.append(ms[b])
         best.append(min(ms))
