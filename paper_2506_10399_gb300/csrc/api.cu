@@ -606,7 +606,8 @@ int fg_ctx_destroy(fg_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     for (cudaStream_t st : ctx->pool) cudaStreamSynchronize(st);
     if (ctx->batch_stream) cudaStreamSynchronize(ctx->batch_stream);
-    if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+    for (auto &kv : ctx->copies)
+        if (kv.second.st) cudaStreamSynchronize(kv.second.st);
     cudaFree(ctx->d_primes);
     cudaFree(ctx->d_fwd);
     cudaFree(ctx->d_inv);
@@ -625,8 +626,10 @@ int fg_ctx_destroy(fg_ctx *ctx)
     if (ctx->batch.exec) cudaGraphExecDestroy(ctx->batch.exec);
     for (cudaStream_t st : ctx->pool) cudaStreamDestroy(st);
     if (ctx->batch_stream) cudaStreamDestroy(ctx->batch_stream);
-    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
-    for (cudaEvent_t e : ctx->copy_events) cudaEventDestroy(e);
+    for (auto &kv : ctx->copies) {
+        if (kv.second.st) cudaStreamDestroy(kv.second.st);
+        for (cudaEvent_t e : kv.second.ev) cudaEventDestroy(e);
+    }
     for (cudaEvent_t e : ctx->pool_events) cudaEventDestroy(e);
     auto s = g_sk.find(ctx);
     if (s != g_sk.end()) {

@@ -166,8 +166,13 @@ struct fg_ctx {
     cudaStream_t batch_stream = nullptr;   // the batch's own origin (capturable)
     // host inputs: copied in chunks on their own stream, each chunk's part of
     // the combination starting when the chunk has arrived
-    cudaStream_t copy_stream = nullptr;
-    std::vector<cudaEvent_t> copy_events;
+    // (one copy stream and its events per workspace prefix, so that layers
+    // in flight on different streams copy independently)
+    struct CopyRes {
+        cudaStream_t st = nullptr;
+        std::vector<cudaEvent_t> ev;
+    };
+    std::map<std::string, CopyRes> copies;
     struct BatchGraph {
         std::vector<const void *> args;   // plans, inputs, outputs
         int streams = 0;

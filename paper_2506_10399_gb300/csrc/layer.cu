@@ -37,6 +37,16 @@ bool is_dev(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+bool is_pinned(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 std::vector<int> iota(int n, int start = 0)
 {
     std::vector<int> v(n);
@@ -467,22 +477,22 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
         if (!is_dev(in_cts)) {
             u64 *d = (u64 *)ctx->buf("layer_in", in_w * 8);
             if (chunked) {
-                if (!ctx->copy_stream)
-                    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
-                while ((int)ctx->copy_events.size() < n_chunks + 1) {
+                fg_ctx::CopyRes &cr = ctx->copies[ctx->ws_prefix];
+                if (!cr.st) CUDA_TRY(cudaStreamCreateWithFlags(&cr.st, cudaStreamNonBlocking));
+                while ((int)cr.ev.size() < n_chunks + 1) {
                     cudaEvent_t e;
                     CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-                    ctx->copy_events.push_back(e);
+                    cr.ev.push_back(e);
                 }
                 // the buffer is free once the work queued before this layer is done
-                CUDA_TRY(cudaEventRecord(ctx->copy_events[n_chunks], ctx->stream));
-                CUDA_TRY(cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_events[n_chunks], 0));
+                CUDA_TRY(cudaEventRecord(cr.ev[n_chunks], ctx->stream));
+                CUDA_TRY(cudaStreamWaitEvent(cr.st, cr.ev[n_chunks], 0));
                 const size_t ct_w = (size_t)2 * nl0 * N;
                 for (int c = 0; c < n_chunks; c++) {
                     const int fb = c * kChunk, fn = std::min(kChunk, F - fb);
                     CUDA_TRY(cudaMemcpyAsync(d + fb * ct_w, in_cts + fb * ct_w, fn * ct_w * 8,
-                                             cudaMemcpyHostToDevice, ctx->copy_stream));
-                    CUDA_TRY(cudaEventRecord(ctx->copy_events[c], ctx->copy_stream));
+                                             cudaMemcpyHostToDevice, cr.st));
+                    CUDA_TRY(cudaEventRecord(cr.ev[c], cr.st));
                 }
             } else {
                 CUDA_TRY(cudaMemcpyAsync(d, in_cts, in_w * 8, cudaMemcpyHostToDevice, ctx->stream));
@@ -536,7 +546,7 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
             u64 *Zc = (u64 *)ctx->buf("comb_z", (size_t)Fp * 2 * nl0 * N * 8);
             if (chunked) {
                 for (int c = 0; c < n_chunks; c++) {
-                    CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->copy_events[c], 0));
+                    CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->copies[ctx->ws_prefix].ev[c], 0));
                     kern::comb_const_mac(ctx, X, F, Fp, l0, pl->d_comb, Zc, nl0, c * kChunk,
                                          std::min(F, (c + 1) * kChunk), c > 0);
                 }
@@ -985,8 +995,8 @@ extern "C" int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_pla
         for (int q = 0; q < n; q++) {
             FG_CHECK(plans[q] && plans[q]->ctx == ctx && keys->ctx == ctx, FG_EINVAL,
                      "plan or keys of another context");
-            FG_CHECK(in_cts[q] && out_cts[q] && is_dev(in_cts[q]) && is_dev(out_cts[q]), FG_EINVAL,
-                     "batched layers take device buffers");
+            FG_CHECK(in_cts[q] && out_cts[q] && (is_dev(in_cts[q]) || is_pinned(in_cts[q])) && is_dev(out_cts[q]),
+                     FG_EINVAL, "batched layers take device or page-locked host inputs and device outputs");
             args.insert(args.end(), {plans[q], in_cts[q], out_cts[q]});
         }
         if (!ctx->batch_stream)

@@ -147,3 +147,22 @@ def test_every_ntt16_tile_and_key_switch_bound_give_the_same_layer():
     d = fg.decrypt_decode(ctx, sk, out[0].contiguous(), lvl, ctx.scale)
     assert np.max(np.abs(d[perm] - w.reference_output()[:, 0])) < 2 ** -20
     ctx.close()
+
+
+@pytest.mark.parametrize("streams,graph", [(2, True), (3, False)])
+def test_batch_from_page_locked_host_inputs(env, streams, graph):
+    """Inputs in page-locked host memory (copied inside the batch, each
+    stream with its own copy stream): the same words as one at a time."""
+    import torch
+    fg, ctx, sk, keys, qs, data = env
+    want = _one_at_a_time(fg, ctx, keys, qs, data)
+    plans = [q[2] for q in qs]
+    ins = [d[0].cpu().pin_memory() for d in data]
+    outs = [d[1] for d in data]
+    for rep in range(2):
+        for o in outs:
+            o.zero_()
+        fg.gcn_layer_batch(ctx, keys, plans, ins, outs, streams=streams, graph=graph)
+        torch.cuda.synchronize()
+        for (o_w, _), o in zip(want, outs):
+            assert bool((o == o_w).all())
