@@ -881,8 +881,8 @@ def main():
                     help="workload of --two-layer")
     ap.add_argument("--inter", action="store_true", help="the layer in Inter-CA mode")
     ap.add_argument("--tuning", default="", help="launch configuration ntt_cols,ntt_rows,ntt_tw,ks_split,"
-                                                  "ks_cols,modup_fused,moddown_fused,gmac_groups (default: the "
-                                                  "library's)")
+                                                  "ks_cols,modup_fused,moddown_fused,gmac_groups,gmac_regs "
+                                                  "(default: the library's)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

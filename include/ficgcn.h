@@ -373,16 +373,17 @@ int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
 /* The batched form's launch configuration: cfg = {NTT pass-A columns, NTT
  * pass-B rows, NTT twiddles loaded where used (0/1), key-switch bound one
  * CTA per SM fewer (0/1), key-switch column launches (1/2), fused ModUp
- * (0/1), fused ModDown (0/1), group-MAC three-group threshold}; ms[0..*n) the
+ * (0/1), fused ModDown (0/1), group-MAC three-group threshold, group-MAC
+ * registers for three CTAs per SM (0/1)}; ms[0..*n) the
  * batch pass time of each configuration tried (the default first), at most
  * cap entries.  Before any tuned batch call cfg holds the context's
  * configuration and *n = 0. */
-int fg_batch_tuning(const fg_ctx *ctx, int cfg[8], double *ms, int cap, int *n);
+int fg_batch_tuning(const fg_ctx *ctx, int cfg[9], double *ms, int cap, int *n);
 /* Fix the launch configuration every later call of this context uses
- * outside tuned batches (the same eight fields as fg_batch_tuning; NTT
+ * outside tuned batches (the same nine fields as fg_batch_tuning; NTT
  * tiles 16 or 8, flags 0 or 1, column launches 1 or 2, group-MAC threshold
  * >= 1).  Results do not change; speed may.  FG_EINVAL for other values. */
-int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[8]);
+int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[9]);
 
 /* Ciphertext products (paper Sec. 2.1 CMult; the x^2 activation between
  * GCN layers multiplies a ciphertext by itself): for each of n pairs,

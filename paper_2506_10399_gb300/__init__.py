@@ -445,22 +445,22 @@ def gcn_layer_batch(ctx, keys, plans, ins, outs, streams=0, graph=True, tune=Fal
 
 def batch_tuning(ctx):
     """({"ntt_cols", "ntt_rows", "ntt_tw", "ks_split", "ks_cols",
-    "modup_fused", "moddown_fused", "gmac_groups"}, [ms of each
-    configuration tried, the default first])."""
-    cfg = (ctypes.c_int * 8)()
+    "modup_fused", "moddown_fused", "gmac_groups", "gmac_regs"}, [ms of
+    each configuration tried, the default first])."""
+    cfg = (ctypes.c_int * 9)()
     ms = np.zeros(64, np.float64)
     n = ctypes.c_int()
     _check(ctx, _lib().lib.fg_batch_tuning(ctx._h, cfg, ctypes.c_void_p(ms.ctypes.data), 64, ctypes.byref(n)))
     keys = ("ntt_cols", "ntt_rows", "ntt_tw", "ks_split", "ks_cols", "modup_fused", "moddown_fused",
-            "gmac_groups")
+            "gmac_groups", "gmac_regs")
     return dict(zip(keys, list(cfg))), [float(v) for v in ms[:n.value]]
 
 
 def set_tuning(ctx, ntt_cols=16, ntt_rows=16, ntt_tw=0, ks_split=0, ks_cols=1, modup_fused=0,
-               moddown_fused=0, gmac_groups=7):
+               moddown_fused=0, gmac_groups=7, gmac_regs=0):
     """Fix the launch configuration of the context's later calls."""
-    cfg = (ctypes.c_int * 8)(ntt_cols, ntt_rows, ntt_tw, ks_split, ks_cols, modup_fused, moddown_fused,
-                             gmac_groups)
+    cfg = (ctypes.c_int * 9)(ntt_cols, ntt_rows, ntt_tw, ks_split, ks_cols, modup_fused, moddown_fused,
+                             gmac_groups, gmac_regs)
     _check(ctx, _lib().lib.fg_ctx_set_tuning(ctx._h, cfg))
 
 

@@ -96,11 +96,12 @@ struct Tune {
     int modup_fused = 0;   // N = 2^16 ModUp: 1 = conversion fused into the digits' first NTT pass
     int moddown_fused = 0; // N = 2^16 ModDown + rescale: 1 = conversion fused into the first NTT pass
     int gmac_groups = 7;   // group MAC: outputs from which a CTA runs three thread groups
+    int gmac_regs = 0;     // group MAC: 0 = registers for 2 CTAs of 384 threads per SM, 1 = for 3
     bool operator==(const Tune &o) const
     {
         return ntt_cols == o.ntt_cols && ntt_rows == o.ntt_rows && ntt_tw == o.ntt_tw &&
                ks_split == o.ks_split && ks_cols == o.ks_cols && modup_fused == o.modup_fused &&
-               moddown_fused == o.moddown_fused && gmac_groups == o.gmac_groups;
+               moddown_fused == o.moddown_fused && gmac_groups == o.gmac_groups && gmac_regs == o.gmac_regs;
     }
 };
 

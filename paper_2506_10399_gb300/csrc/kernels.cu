@@ -1299,7 +1299,10 @@ __device__ __forceinline__ ulonglong2 lds128(u32 addr)
     return v;
 }
 
-__global__ void __launch_bounds__(kGmacThreads, 2)
+// MINB: CTAs of kGmacThreads threads per SM the registers are budgeted for
+// (2: up to 85 registers a thread; 3: up to 56, more warps resident)
+template <int MINB>
+__global__ void __launch_bounds__(kGmacThreads, MINB)
 k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
             const u64 *__restrict__ pmodq, const PrimeC *__restrict__ primes, int nq)
 {
@@ -2105,13 +2108,19 @@ void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vec
                (double)X * npoly * E * (accumulate ? 2 : 1)) * N * 8);
     // raised once per process and size (not a stream operation, and kept out
     // of the launches a CUDA graph capture records)
-    static size_t sm_set = 48 * 1024;
-    if (sm > sm_set) {
-        CUDA_TRY(cudaFuncSetAttribute(k_group_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        sm_set = sm;
+    static size_t sm_set[2] = {48 * 1024, 48 * 1024};
+    const int v = ctx->tune.gmac_regs ? 1 : 0;
+    if (sm > sm_set[v]) {
+        if (v) CUDA_TRY(cudaFuncSetAttribute(k_group_mac<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        else CUDA_TRY(cudaFuncSetAttribute(k_group_mac<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        sm_set[v] = sm;
     }
-    k_group_mac<<<g, G * kGmacTile, sm, ctx->stream>>>(pg, ncol, level, E, ls, ctx->log_n,
-                                                      ctx->d_pmodq, ctx->d_primes, ctx->nq);
+    if (v)
+        k_group_mac<3><<<g, G * kGmacTile, sm, ctx->stream>>>(pg, ncol, level, E, ls, ctx->log_n,
+                                                             ctx->d_pmodq, ctx->d_primes, ctx->nq);
+    else
+        k_group_mac<2><<<g, G * kGmacTile, sm, ctx->stream>>>(pg, ncol, level, E, ls, ctx->log_n,
+                                                             ctx->d_pmodq, ctx->d_primes, ctx->nq);
     check_launch("group_mac");
 }
 
