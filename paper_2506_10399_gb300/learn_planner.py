@@ -125,8 +125,8 @@ def _record_amounts(rec, M):
 def measure(out_path, budget_s=1500.0):
     """Append to out_path the measurements of the graphs it does not hold
     yet (held-out seeds first), until the time budget runs out.  A candidate
-    whose layer does not fit the device (FG_EOOM, after the workspace was
-    released once) is left out of its graph's record."""
+    whose layer does not fit the device (out of memory, after the workspace
+    was released once) is left out of its graph's record."""
     import os
     import torch
     fg = _fg()
@@ -190,7 +190,7 @@ def measure(out_path, budget_s=1500.0):
                         rows.append(r)
                         break
                     except fg.FicgcnError as e:
-                        if e.code != -5:
+                        if e.code not in (-4, -5) or "out of memory" not in str(e):
                             raise
                         xs.clear()
                         ctx.release_workspace()
