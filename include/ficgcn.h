@@ -371,8 +371,8 @@ int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
                        const uint64_t *const *in_cts, uint64_t *const *out_cts,
                        const fg_batch_opts *opts, int *out_levels, int *streams_used);
 /* The batched form's launch configuration: cfg = {NTT pass-A columns, NTT
- * pass-B rows, NTT twiddles loaded where used (0/1), key-switch bound one
- * CTA per SM fewer (0/1), key-switch column launches (1/2), fused ModUp
+ * pass-B rows, NTT twiddles loaded where used (0/1), key-switch registers
+ * (0 default, 1 one CTA per SM fewer, 2 keys in shared memory), key-switch column launches (1/2), fused ModUp
  * (0/1), fused ModDown (0/1), group-MAC three-group threshold, group-MAC
  * registers for three CTAs per SM (0/1)}; ms[0..*n) the
  * batch pass time of each configuration tried (the default first), at most
@@ -381,8 +381,8 @@ int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
 int fg_batch_tuning(const fg_ctx *ctx, int cfg[9], double *ms, int cap, int *n);
 /* Fix the launch configuration every later call of this context uses
  * outside tuned batches (the same nine fields as fg_batch_tuning; NTT
- * tiles 16 or 8, flags 0 or 1, column launches 1 or 2, group-MAC threshold
- * >= 1).  Results do not change; speed may.  FG_EINVAL for other values. */
+ * tiles 16 or 8, key-switch registers 0 to 2, other flags 0 or 1, column
+ * launches 1 or 2, group-MAC threshold >= 1).  Results do not change; speed may.  FG_EINVAL for other values. */
 int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[9]);
 
 /* Ciphertext products (paper Sec. 2.1 CMult; the x^2 activation between

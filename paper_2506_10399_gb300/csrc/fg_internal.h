@@ -91,7 +91,8 @@ struct Tune {
     int ntt_rows = 16;     // N = 2^16 NTT pass B: rows per CTA (16 or 8)
     int ntt_tw = 0;        // N = 2^16 NTT twiddles: 0 = held in registers per round (3 CTAs of
                            // 256 threads per SM), 1 = loaded where used (4 per SM)
-    int ks_split = 0;      // key switch: 0 = launch bounds by digit count, 1 = one CTA per SM fewer
+    int ks_split = 0;      // key switch registers: 0 = launch bounds by digit count, 1 = one CTA per
+                           // SM fewer, 2 = key words parked in shared memory (one CTA more)
     int ks_cols = 1;       // key switch: launches the columns are split over (1 or 2)
     int modup_fused = 0;   // N = 2^16 ModUp: 1 = conversion fused into the digits' first NTT pass
     int moddown_fused = 0; // N = 2^16 ModDown + rescale: 1 = conversion fused into the first NTT pass

@@ -1043,12 +1043,16 @@ constexpr int ks_min_blocks(int beta, int less)
     return (beta <= 4 ? 4 : beta <= 5 ? 3 : 2) - less > 0 ? (beta <= 4 ? 4 : beta <= 5 ? 3 : 2) - less : 1;
 }
 
-template <int BETA, int LESS>
-__global__ void __launch_bounds__(256, ks_min_blocks(BETA, LESS))
+// KSM: the thread's split key words are parked in shared memory (its own
+// 2 x BETA entries, no sharing, so no barrier) instead of registers, which
+// frees about 40 registers for one more CTA per SM; a tuning choice.
+template <int BETA, int LESS, bool KSM>
+__global__ void __launch_bounds__(256, KSM ? (BETA <= 4 ? 5 : 4) : ks_min_blocks(BETA, LESS))
 k_ks_ip(const KsSet ks, int KL, const u64 *__restrict__ lane, int ls,
         const u64 *__restrict__ digits, int ncol, int level, int E, int alpha, int nq,
         int log_n, const PrimeC *__restrict__ primes, const u64 *__restrict__ pmodq)
 {
+    extern __shared__ ulonglong2 kpark[];   // KSM: [BETA][2][blockDim.x]
     const int N = 1 << log_n;
     const int rot = blockIdx.y, i = blockIdx.z;
     const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -1066,16 +1070,25 @@ k_ks_ip(const KsSet ks, int KL, const u64 *__restrict__ lane, int ls,
     // term; more digits take the 128-bit sums.  The total, below
     // BETA 2^60 q, keeps its high word below q for the Montgomery step.
     constexpr bool SPLIT = BETA <= 8;
-    ulonglong2 kb[BETA], ka[BETA];
+    ulonglong2 kb[KSM ? 1 : BETA], ka[KSM ? 1 : BETA];
 #pragma unroll
     for (int d = 0; d < BETA; d++) {
-        kb[d] = *reinterpret_cast<const ulonglong2 *>(key + (((size_t)d * 2 + 0) * KL + pi) * N + x);
-        ka[d] = *reinterpret_cast<const ulonglong2 *>(key + (((size_t)d * 2 + 1) * KL + pi) * N + x);
+        ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(key + (((size_t)d * 2 + 0) * KL + pi) * N + x);
+        ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(key + (((size_t)d * 2 + 1) * KL + pi) * N + x);
         if (SPLIT) {
-            kb[d] = make_ulonglong2(split30(kb[d].x), split30(kb[d].y));
-            ka[d] = make_ulonglong2(split30(ka[d].x), split30(ka[d].y));
+            b = make_ulonglong2(split30(b.x), split30(b.y));
+            a = make_ulonglong2(split30(a.x), split30(a.y));
+        }
+        if (KSM) {
+            kpark[(d * 2 + 0) * blockDim.x + threadIdx.x] = b;
+            kpark[(d * 2 + 1) * blockDim.x + threadIdx.x] = a;
+        } else {
+            kb[KSM ? 0 : d] = b;
+            ka[KSM ? 0 : d] = a;
         }
     }
+    auto KB = [&](int d) { return KSM ? kpark[(d * 2 + 0) * blockDim.x + threadIdx.x] : kb[KSM ? 0 : d]; };
+    auto KA = [&](int d) { return KSM ? kpark[(d * 2 + 1) * blockDim.x + threadIdx.x] : ka[KSM ? 0 : d]; };
     for (int f = 0; f < ncol; f++) {
         ulonglong2 r0, r1;
         if (SPLIT) {
@@ -1086,10 +1099,11 @@ k_ks_ip(const KsSet ks, int KL, const u64 *__restrict__ lane, int ls,
                                            : digits + (((size_t)f * BETA + d) * E + i) * N;
                 ulonglong2 v = gather_pair(limb, sx, swap);
                 v = make_ulonglong2(split30(v.x), split30(v.y));
-                mac_split(a[0], a[1], a[2], v.x, kb[d].x);
-                mac_split(a[3], a[4], a[5], v.y, kb[d].y);
-                mac_split(a[6], a[7], a[8], v.x, ka[d].x);
-                mac_split(a[9], a[10], a[11], v.y, ka[d].y);
+                const ulonglong2 b = KB(d), kk = KA(d);
+                mac_split(a[0], a[1], a[2], v.x, b.x);
+                mac_split(a[3], a[4], a[5], v.y, b.y);
+                mac_split(a[6], a[7], a[8], v.x, kk.x);
+                mac_split(a[9], a[10], a[11], v.y, kk.y);
             }
             u64 h[4] = {0, 0, 0, 0}, l[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -1103,10 +1117,11 @@ k_ks_ip(const KsSet ks, int KL, const u64 *__restrict__ lane, int ls,
                 const u64 *limb = d == own ? lane + (((size_t)f * 2 + 1) * ls + i) * N
                                            : digits + (((size_t)f * BETA + d) * E + i) * N;
                 const ulonglong2 v = gather_pair(limb, sx, swap);
-                mac128(h0, l0, v.x, kb[d].x);
-                mac128(h1, l1, v.y, kb[d].y);
-                mac128(h2, l2, v.x, ka[d].x);
-                mac128(h3, l3, v.y, ka[d].y);
+                const ulonglong2 b = KB(d), kk = KA(d);
+                mac128(h0, l0, v.x, b.x);
+                mac128(h1, l1, v.y, b.y);
+                mac128(h2, l2, v.x, kk.x);
+                mac128(h3, l3, v.y, kk.y);
             }
             r0 = make_ulonglong2(redc(h0, l0, P), redc(h1, l1, P));
             r1 = make_ulonglong2(redc(h2, l2, P), redc(h3, l3, P));
@@ -1953,16 +1968,20 @@ static void ks_launch(fg_ctx *ctx, const std::vector<const KeyDev *> &keys, cons
                              (double)ks.n * (2.0 * beta * E + 2.0 * ncol * E)) * N * 8);
 #define FG_KS_CASE(B)                                                                          \
     case B:                                                                                    \
-        if (less)                                                                              \
-            k_ks_ip<B, (B <= 8 ? 1 : 0)><<<g1, 256, 0, ctx->stream>>>(                          \
+        if (ksm && B <= 6)                                                                     \
+            k_ks_ip<B, 0, (B <= 6)><<<g1, 256, (size_t)B * 2 * 256 * 16, ctx->stream>>>(         \
+                ks, KL, lane, ls, digits, ncol, level, E, ctx->alpha, ctx->nq, ctx->log_n,     \
+                ctx->d_primes, pmodq);                                                         \
+        else if (less)                                                                         \
+            k_ks_ip<B, (B <= 8 ? 1 : 0), false><<<g1, 256, 0, ctx->stream>>>(                   \
                 ks, KL, lane, ls, digits, ncol, level, E, ctx->alpha, ctx->nq, ctx->log_n,     \
                 ctx->d_primes, pmodq);                                                         \
         else                                                                                   \
-            k_ks_ip<B, 0><<<g1, 256, 0, ctx->stream>>>(ks, KL, lane, ls, digits, ncol, level,   \
-                                                       E, ctx->alpha, ctx->nq, ctx->log_n,     \
-                                                       ctx->d_primes, pmodq);                  \
+            k_ks_ip<B, 0, false><<<g1, 256, 0, ctx->stream>>>(ks, KL, lane, ls, digits, ncol,   \
+                                                              level, E, ctx->alpha, ctx->nq,   \
+                                                              ctx->log_n, ctx->d_primes, pmodq); \
         break;
-    const bool less = ctx->tune.ks_split != 0;
+    const bool less = ctx->tune.ks_split == 1, ksm = ctx->tune.ks_split == 2;
     switch (beta) {
         FG_KS_CASE(1) FG_KS_CASE(2) FG_KS_CASE(3) FG_KS_CASE(4) FG_KS_CASE(5) FG_KS_CASE(6)
         FG_KS_CASE(7) FG_KS_CASE(8) FG_KS_CASE(9) FG_KS_CASE(10) FG_KS_CASE(11) FG_KS_CASE(12)

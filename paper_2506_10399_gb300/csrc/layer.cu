@@ -822,7 +822,7 @@ static void tune_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
         return ms;
     };
     double best_ms = timed(best);
-    const int cols[2] = {16, 8}, rows[2] = {16, 8}, tw[2] = {0, 1}, split[2] = {0, 1}, kcols[2] = {1, 2},
+    const int cols[2] = {16, 8}, rows[2] = {16, 8}, tw[2] = {0, 1}, split[3] = {0, 1, 2}, kcols[2] = {1, 2},
               fused[2] = {0, 1}, groups[3] = {7, 4, 13};
     const int dfused[2] = {0, 1}, gregs[2] = {0, 1};
     auto knob = [&](auto field, const int *vals, int nv) {
@@ -845,7 +845,7 @@ static void tune_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
         knob(&Tune::modup_fused, fused, 2);
         knob(&Tune::moddown_fused, dfused, 2);
     }
-    knob(&Tune::ks_split, split, 2);
+    knob(&Tune::ks_split, split, 3);
     knob(&Tune::ks_cols, kcols, 2);
     knob(&Tune::gmac_groups, groups, 3);
     knob(&Tune::gmac_regs, gregs, 2);
@@ -968,7 +968,7 @@ extern "C" int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[9])
 {
     if (!ctx || !cfg) return FG_EINVAL;
     if ((cfg[0] != 16 && cfg[0] != 8) || (cfg[1] != 16 && cfg[1] != 8) || (cfg[2] != 0 && cfg[2] != 1) ||
-        (cfg[3] != 0 && cfg[3] != 1) || (cfg[4] != 1 && cfg[4] != 2) || (cfg[5] != 0 && cfg[5] != 1) ||
+        (cfg[3] < 0 || cfg[3] > 2) || (cfg[4] != 1 && cfg[4] != 2) || (cfg[5] != 0 && cfg[5] != 1) ||
         (cfg[6] != 0 && cfg[6] != 1) || cfg[7] < 1 || (cfg[8] != 0 && cfg[8] != 1))
         return FG_EINVAL;
     ctx->tune.ntt_cols = cfg[0];

@@ -76,6 +76,7 @@ def test_benchshape_plan_reaches_the_benchmark_kernel_shapes(case):
 
 @pytest.mark.parametrize("where,tuning", [("device", {}), ("host", {}),
                                           ("device", dict(modup_fused=1, moddown_fused=1)),
+                                          ("device", dict(ks_split=2)),
                                           ("device", dict(ntt_cols=8, ntt_rows=8, ntt_tw=1, ks_split=1,
                                                           ks_cols=2, modup_fused=1, moddown_fused=1,
                                                           gmac_groups=4, gmac_regs=1))])
