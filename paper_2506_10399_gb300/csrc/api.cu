@@ -629,6 +629,7 @@ int fg_ctx_destroy(fg_ctx *ctx)
     for (auto &kv : ctx->copies) {
         if (kv.second.st) cudaStreamDestroy(kv.second.st);
         for (cudaEvent_t e : kv.second.ev) cudaEventDestroy(e);
+        if (kv.second.free_ev) cudaEventDestroy(kv.second.free_ev);
     }
     for (cudaEvent_t e : ctx->pool_events) cudaEventDestroy(e);
     auto s = g_sk.find(ctx);

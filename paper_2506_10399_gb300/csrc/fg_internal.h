@@ -172,9 +172,12 @@ struct fg_ctx {
     // in flight on different streams copy independently)
     struct CopyRes {
         cudaStream_t st = nullptr;
-        std::vector<cudaEvent_t> ev;
+        std::vector<cudaEvent_t> ev;       // per chunk arrived, then "layer started"
+        cudaEvent_t free_ev = nullptr;     // the previous layer has read its staged inputs
+        bool have_free = false;            // free_ev was recorded in this batch pass
     };
     std::map<std::string, CopyRes> copies;
+    bool in_batch = false;                 // layers of a batch pass are being enqueued
     struct BatchGraph {
         std::vector<const void *> args;   // plans, inputs, outputs
         int streams = 0;

@@ -470,35 +470,53 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
 
         const size_t in_w = (size_t)nb * 2 * nl0 * N;
         const u64 *X = in_cts;
-        // host inputs of a t = 1 layer: copied in chunks of columns on a side
-        // stream, the combination of each chunk starting when it has arrived
-        const bool chunked = !is_dev(in_cts) && t == 1 && !pl->n_copies;
-        const int kChunk = 64, n_chunks = (F + kChunk - 1) / kChunk;
-        if (!is_dev(in_cts)) {
+        // host inputs: staged into this workspace's buffer on its own copy
+        // stream; for t = 1 in chunks of columns, the combination of each
+        // chunk starting when it has arrived.  Inside a batch pass the copy
+        // starts as soon as the previous layer of this workspace has read the
+        // staging buffer (its combination), so it overlaps that layer's
+        // aggregation and the other streams' work.
+        const bool host_in = !is_dev(in_cts);
+        const bool chunked = host_in && t == 1 && !pl->n_copies;
+        const int kChunk = 64, n_chunks = chunked ? (F + kChunk - 1) / kChunk : 1;
+        fg_ctx::CopyRes *cr = nullptr;
+        if (host_in) {
             u64 *d = (u64 *)ctx->buf("layer_in", in_w * 8);
+            cr = &ctx->copies[ctx->ws_prefix];
+            if (!cr->st) CUDA_TRY(cudaStreamCreateWithFlags(&cr->st, cudaStreamNonBlocking));
+            if (!cr->free_ev) CUDA_TRY(cudaEventCreateWithFlags(&cr->free_ev, cudaEventDisableTiming));
+            while ((int)cr->ev.size() < n_chunks + 1) {
+                cudaEvent_t e;
+                CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                cr->ev.push_back(e);
+            }
+            if (ctx->in_batch && cr->have_free) {
+                CUDA_TRY(cudaStreamWaitEvent(cr->st, cr->free_ev, 0));
+            } else {   // the buffer is free once the work queued before this layer is done
+                CUDA_TRY(cudaEventRecord(cr->ev[n_chunks], ctx->stream));
+                CUDA_TRY(cudaStreamWaitEvent(cr->st, cr->ev[n_chunks], 0));
+            }
             if (chunked) {
-                fg_ctx::CopyRes &cr = ctx->copies[ctx->ws_prefix];
-                if (!cr.st) CUDA_TRY(cudaStreamCreateWithFlags(&cr.st, cudaStreamNonBlocking));
-                while ((int)cr.ev.size() < n_chunks + 1) {
-                    cudaEvent_t e;
-                    CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-                    cr.ev.push_back(e);
-                }
-                // the buffer is free once the work queued before this layer is done
-                CUDA_TRY(cudaEventRecord(cr.ev[n_chunks], ctx->stream));
-                CUDA_TRY(cudaStreamWaitEvent(cr.st, cr.ev[n_chunks], 0));
                 const size_t ct_w = (size_t)2 * nl0 * N;
                 for (int c = 0; c < n_chunks; c++) {
                     const int fb = c * kChunk, fn = std::min(kChunk, F - fb);
                     CUDA_TRY(cudaMemcpyAsync(d + fb * ct_w, in_cts + fb * ct_w, fn * ct_w * 8,
-                                             cudaMemcpyHostToDevice, cr.st));
-                    CUDA_TRY(cudaEventRecord(cr.ev[c], cr.st));
+                                             cudaMemcpyHostToDevice, cr->st));
+                    CUDA_TRY(cudaEventRecord(cr->ev[c], cr->st));
                 }
             } else {
-                CUDA_TRY(cudaMemcpyAsync(d, in_cts, in_w * 8, cudaMemcpyHostToDevice, ctx->stream));
+                CUDA_TRY(cudaMemcpyAsync(d, in_cts, in_w * 8, cudaMemcpyHostToDevice, cr->st));
+                CUDA_TRY(cudaEventRecord(cr->ev[0], cr->st));
+                CUDA_TRY(cudaStreamWaitEvent(ctx->stream, cr->ev[0], 0));
             }
             X = d;
         }
+        // the staged inputs have been read (by the combination's kernels)
+        auto inputs_read = [&]() {
+            if (!cr) return;
+            CUDA_TRY(cudaEventRecord(cr->free_ev, ctx->stream));
+            cr->have_free = ctx->in_batch;
+        };
         const int l1 = l0 - 1, LS = l1 + 1;           // lanes keep a fixed limb stride
         const size_t lane_w = (size_t)Fp * 2 * LS * N;
         const int max_lanes = std::max(1, pl->max_lanes);
@@ -523,6 +541,7 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
                 kern::ntt_fwd(ctx, z, z);
                 kern::stay_mac(ctx, bufA[0], LS, Fp, l1, {{acc, pl->masks[k].d}}, LS);
             }
+            inputs_read();
             kern::rescale_ntt(ctx, acc, LS, Fp * 2, l1);
             const int level = l1 - 1, nlo = level + 1;
             FG_CHECK(level == pl->out_level, FG_ELEVEL, "plan output level mismatch");
@@ -546,13 +565,14 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
             u64 *Zc = (u64 *)ctx->buf("comb_z", (size_t)Fp * 2 * nl0 * N * 8);
             if (chunked) {
                 for (int c = 0; c < n_chunks; c++) {
-                    CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->copies[ctx->ws_prefix].ev[c], 0));
+                    CUDA_TRY(cudaStreamWaitEvent(ctx->stream, cr->ev[c], 0));
                     kern::comb_const_mac(ctx, X, F, Fp, l0, pl->d_comb, Zc, nl0, c * kChunk,
                                          std::min(F, (c + 1) * kChunk), c > 0);
                 }
             } else {
                 kern::comb_const_mac(ctx, X, F, Fp, l0, pl->d_comb, Zc, nl0);
             }
+            inputs_read();
             kern::rescale_coef(ctx, Zc, nl0, bufA[0], LS, Fp * 2, l0);
             kern::LimbSet z{bufA[0], LS, LS, Fp * 2, pid_l1};
             kern::ntt_fwd(ctx, z, z);
@@ -561,6 +581,7 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
             u64 *Xn = (u64 *)ctx->buf("comb_xn", in_w * 8);
             kern::LimbSet xs{const_cast<u64 *>(X), nl0, nl0, nb * 2, pid0}, xd{Xn, nl0, nl0, nb * 2, pid0};
             kern::ntt_fwd(ctx, xs, xd);
+            inputs_read();
             u64 *Za = (u64 *)ctx->buf("comb_acc", (size_t)Fp * 2 * nl0 * N * 8);
             CUDA_TRY(cudaMemsetAsync(Za, 0, (size_t)Fp * 2 * nl0 * N * 8, ctx->stream));
             for (int b = 0; b < nb; b++) {
@@ -762,6 +783,8 @@ static void batch_pass(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
     cudaStream_t origin = ctx->stream;
     CUDA_TRY(cudaEventRecord(ctx->pool_events[S], origin));
     for (int s = 0; s < S; s++) CUDA_TRY(cudaStreamWaitEvent(ctx->pool[s], ctx->pool_events[S], 0));
+    for (auto &kv : ctx->copies) kv.second.have_free = false;
+    ctx->in_batch = true;
     try {
         for (int q = 0; q < n; q++) {
             const fg_plan *pl = plans[q];
@@ -773,10 +796,13 @@ static void batch_pass(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
     } catch (...) {
         ctx->stream = origin;
         ctx->ws_prefix.clear();
+        ctx->in_batch = false;
         throw;
     }
     ctx->stream = origin;
     ctx->ws_prefix.clear();
+    ctx->in_batch = false;
+    for (auto &kv : ctx->copies) kv.second.have_free = false;
     for (int s = 0; s < S; s++) {
         CUDA_TRY(cudaEventRecord(ctx->pool_events[s], ctx->pool[s]));
         CUDA_TRY(cudaStreamWaitEvent(origin, ctx->pool_events[s], 0));
