@@ -61,18 +61,30 @@ def peaks():
         return 6800.0, "fallback"
 
 
+TRAFFIC_SOURCES = ("kernels.cu", "modarith.cuh", "fg_internal.h")
+
+
+def sources_sha256():
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2506_10399_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def traffic_for(cls, alg_bytes_per_call):
     """DRAM bytes per call of a kernel class: the ratio of ncu's DRAM bytes
     (dram__bytes_read.sum + dram__bytes_write.sum) to the class's algorithmic
     bytes, captured on the small case (bench.py --profile --small: same ring
     and 16 columns, 8 + 2 primes, 4000 nodes) and committed in
     profiles/ncu_traffic.json, times this workload's algorithmic bytes per
-    call; None when absent or taken on other kernels than these."""
+    call; None when absent or taken on other kernels (or another default
+    launch configuration) than these: the file records the sha256 of
+    TRAFFIC_SOURCES, concatenated, as they were when it was captured."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             t = json.load(f)
-        src = open(os.path.join(ROOT, "paper_2506_10399_gb300", "csrc", "kernels.cu"), "rb").read()
-        if t.get("kernels_sha256") != hashlib.sha256(src).hexdigest():
+        if t.get("sources_sha256") != sources_sha256():
             return None
         r = t["dram_over_algorithmic"].get(cls)
         return None if r is None else r * alg_bytes_per_call
@@ -343,28 +355,36 @@ def run_ntt(args, fg=None):
 
 
 # ------------------------------------------------------------------ ALU roofline
-def alu_roofline(fg, ctx, plan, breakdown, F, Fp, alpha):
+def alu_roofline(fg, ctx, plan, breakdown, F, Fp, alpha, kara=1):
     """The integer-multiply roof of the three contraction kernels.  Peak: the
-    measured rate of mad.wide.u32 (32 x 32 -> 64-bit multiply-add, the step
-    of the split products; fg_int_mul_peak, eight independent chains per
-    thread on every SM).  Achieved: the products each kernel's arithmetic
-    performs, counted on the plan, times four mad.wide.u32 per product (a
-    product of two split words, 23- or 30-bit halves: lo x lo, lo x hi,
-    hi x lo, hi x hi), over the kernel class's measured time in one layer:
-      group_mac: terms x 2F' polynomials x E limbs x N (E = extended limbs at
-                 the group's level);
-      ks_ip:     rotations x F' columns x E limbs x N x 2 parts x beta digits;
-      comb:      F x F' x 2 parts x (L+1) limbs x N.
+    measured rate of a 32 x 32 -> 64-bit product added to a 64-bit sum in
+    the hardware's fastest form, one mad.wide.u32 (fg_int_mul_peak, eight
+    independent chains per thread on every SM).  The kernels add each
+    product by a carry-chained mad.lo.cc.u32 / madc.hi.u32 pair, whose
+    measured rate (about half) is reported beside it: in the kernels the
+    pairs measured faster than mad.wide.u32, which cost more registers and
+    instructions there than in the peak loop.  Achieved: the 32 x 32-bit products each
+    kernel's arithmetic performs, counted on the plan, over the kernel
+    class's measured time in one layer.  A product of two split words takes
+    four 32 x 32-bit products (lo x lo, lo x hi, hi x lo, hi x hi), three in
+    the group MAC's Karatsuba form (limbs below 2^46, when kara is set):
+      group_mac: terms x 2F' polynomials x N x (3 or 4 per limb of the E
+                 extended limbs at the group's level);
+      ks_ip:     rotations x F' columns x E limbs x N x 2 parts x beta digits x 4;
+      comb:      F x F' x 2 parts x (L+1) limbs x N x 4 (the 60-bit limb's
+                 64 x 64-bit products counted as four as well).
     Instruction counts of the integer pipes from ncu, where captured, are in
     profiles/."""
     peak = fg.int_mul_peak(ctx, "mad.wide.u32")
+    pair = fg.int_mul_peak(ctx, "mad.cc.pair")
     rec = plan.describe()
     V, Fi = int(rec[4]), int(rec[5])
     t = int(rec[2])
     i = 13 + V
     i += Fi * Fp if t == 1 else -(-Fi // t) * Fp + 1 + int(rec[13 + V + -(-Fi // t) * Fp])
     N, np_ = ctx.n, ctx.np
-    prods = {"group_mac": 0.0, "ks_ip": 0.0, "comb": float(F) * Fp * 2 * (int(rec[7]) + 1) * N}
+    small = [q < (1 << 46) for q in ctx.q]
+    prods = {"group_mac": 0.0, "ks_ip": 0.0, "comb": 4.0 * F * Fp * 2 * (int(rec[7]) + 1) * N}
     for _ in range(int(rec[11])):
         lvl, nrot = int(rec[i + 2]), int(rec[i + 5])
         E = lvl + 1 + np_
@@ -372,15 +392,17 @@ def alu_roofline(fg, ctx, plan, breakdown, F, Fp, alpha):
         i += 6 + 2 * nrot
         nterm = int(rec[i])
         i += 1 + 4 * nterm
-        prods["group_mac"] += float(nterm) * 2 * Fp * E * N
-        prods["ks_ip"] += float(nrot) * Fp * E * N * 2 * beta
-    out = {"unit": "mad.wide.u32/s", "peak": peak, "peak_kind": "measured (fg_int_mul_peak)",
-           "per_product": 4, "kernels": {}}
+        per_limb = sum((3 if (kara and small[j]) else 4) for j in range(lvl + 1)) + 4 * np_
+        prods["group_mac"] += float(nterm) * 2 * Fp * N * per_limb
+        prods["ks_ip"] += 4.0 * nrot * Fp * E * N * 2 * beta
+    out = {"unit": "32x32-bit multiply-accumulates/s", "peak": peak,
+           "peak_kind": "measured (fg_int_mul_peak, mad.wide.u32)", "peak_carry_chained_pair": pair,
+           "kernels": {}}
     for k, pr in prods.items():
         ms = breakdown.get(k, {}).get("ms") or 0
         if ms > 0:
-            a = 4 * pr / (ms / 1e3)
-            out["kernels"][k] = {"achieved": a, "frac": round(a / peak, 4), "products": pr}
+            a = pr / (ms / 1e3)
+            out["kernels"][k] = {"achieved": a, "frac": round(a / peak, 4), "mults": pr}
     return out
 
 
@@ -476,7 +498,8 @@ def run_ours(args):
                           "GB_per_s": round(by / ms / 1e6, 1) if ms > 0 else None}
     ctx.time_kernels(None)
     dominant = max(breakdown, key=lambda k: breakdown[k]["ms"])
-    alu = alu_roofline(fg, ctx, plan, breakdown, w.X.shape[1], Fp=info["n_out"], alpha=c["alpha"])
+    alu = alu_roofline(fg, ctx, plan, breakdown, w.X.shape[1], Fp=info["n_out"], alpha=c["alpha"],
+                       kara=fg.batch_tuning(ctx)[0]["kara"])
 
     # ---- timed region: K steps, HBM-resident inputs
     clocks = Clocks(local)
@@ -881,7 +904,7 @@ def main():
                     help="workload of --two-layer")
     ap.add_argument("--inter", action="store_true", help="the layer in Inter-CA mode")
     ap.add_argument("--tuning", default="", help="launch configuration ntt_cols,ntt_rows,ntt_tw,ks_split,"
-                                                  "ks_cols,modup_fused,moddown_fused,gmac_groups,gmac_regs "
+                                                  "ks_cols,modup_fused,moddown_fused,gmac_groups,gmac_regs,kara "
                                                   "(default: the library's)")
     args = ap.parse_args()
     if args.impl == "reference":

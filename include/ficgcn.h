@@ -374,16 +374,17 @@ int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
  * pass-B rows, NTT twiddles loaded where used (0/1), key-switch registers
  * (0 default, 1 one CTA per SM fewer, 2 keys in shared memory), key-switch column launches (1/2), fused ModUp
  * (0/1), fused ModDown (0/1), group-MAC three-group threshold, group-MAC
- * registers for three CTAs per SM (0/1)}; ms[0..*n) the
+ * registers for three CTAs per SM (0/1), group-MAC products below 2^46 in
+ * Karatsuba's form, three multiplies instead of four (1, the default, or 0)}; ms[0..*n) the
  * batch pass time of each configuration tried (the default first), at most
  * cap entries.  Before any tuned batch call cfg holds the context's
  * configuration and *n = 0. */
-int fg_batch_tuning(const fg_ctx *ctx, int cfg[9], double *ms, int cap, int *n);
+int fg_batch_tuning(const fg_ctx *ctx, int cfg[10], double *ms, int cap, int *n);
 /* Fix the launch configuration every later call of this context uses
- * outside tuned batches (the same nine fields as fg_batch_tuning; NTT
+ * outside tuned batches (the same ten fields as fg_batch_tuning; NTT
  * tiles 16 or 8, key-switch registers 0 to 2, other flags 0 or 1, column
  * launches 1 or 2, group-MAC threshold >= 1).  Results do not change; speed may.  FG_EINVAL for other values. */
-int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[9]);
+int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[10]);
 
 /* Ciphertext products (paper Sec. 2.1 CMult; the x^2 activation between
  * GCN layers multiplies a ciphertext by itself): for each of n pairs,
@@ -443,9 +444,11 @@ int fg_ntt(fg_ctx *ctx, uint64_t *data, int count, const int *prime_idx, int per
  * of the modular kernels; the paper has no counterpart): eight independent
  * chains of one instruction per thread on eight 256-thread CTAs per SM,
  * timed with CUDA events.  op 0 = mad.wide.u32 (32 x 32 -> 64-bit product
- * plus a 64-bit addend, the step of the split products), 1 = mul.hi.u32,
- * 2 = mad.lo.u32.  *ops_per_s: instructions per second (one per thread)
- * over the whole GPU. */
+ * plus a 64-bit addend), 1 = mul.hi.u32, 2 = mad.lo.u32, 3 = the pair
+ * mad.lo.cc.u32 + madc.hi.u32 that adds a 32 x 32 -> 64-bit product to a
+ * 64-bit sum (the step of the split products; the pair counts as one).
+ * *ops_per_s: operations per second (one per thread) over the whole GPU.
+ * FG_EINVAL for another op. */
 int fg_int_mul_peak(fg_ctx *ctx, int op, double *ops_per_s);
 
 #ifdef __cplusplus

@@ -443,24 +443,25 @@ def gcn_layer_batch(ctx, keys, plans, ins, outs, streams=0, graph=True, tune=Fal
     return list(lv), su.value
 
 
+TUNING_FIELDS = ("ntt_cols", "ntt_rows", "ntt_tw", "ks_split", "ks_cols", "modup_fused", "moddown_fused",
+                 "gmac_groups", "gmac_regs", "kara")
+
+
 def batch_tuning(ctx):
-    """({"ntt_cols", "ntt_rows", "ntt_tw", "ks_split", "ks_cols",
-    "modup_fused", "moddown_fused", "gmac_groups", "gmac_regs"}, [ms of
-    each configuration tried, the default first])."""
-    cfg = (ctypes.c_int * 9)()
+    """({field: value for each of TUNING_FIELDS}, [ms of each configuration
+    tried, the default first])."""
+    cfg = (ctypes.c_int * len(TUNING_FIELDS))()
     ms = np.zeros(64, np.float64)
     n = ctypes.c_int()
     _check(ctx, _lib().lib.fg_batch_tuning(ctx._h, cfg, ctypes.c_void_p(ms.ctypes.data), 64, ctypes.byref(n)))
-    keys = ("ntt_cols", "ntt_rows", "ntt_tw", "ks_split", "ks_cols", "modup_fused", "moddown_fused",
-            "gmac_groups", "gmac_regs")
-    return dict(zip(keys, list(cfg))), [float(v) for v in ms[:n.value]]
+    return dict(zip(TUNING_FIELDS, list(cfg))), [float(v) for v in ms[:n.value]]
 
 
-def set_tuning(ctx, ntt_cols=16, ntt_rows=16, ntt_tw=0, ks_split=0, ks_cols=1, modup_fused=0,
-               moddown_fused=0, gmac_groups=7, gmac_regs=0):
+def set_tuning(ctx, ntt_cols=8, ntt_rows=8, ntt_tw=0, ks_split=0, ks_cols=1, modup_fused=1,
+               moddown_fused=0, gmac_groups=7, gmac_regs=1, kara=1):
     """Fix the launch configuration of the context's later calls."""
-    cfg = (ctypes.c_int * 9)(ntt_cols, ntt_rows, ntt_tw, ks_split, ks_cols, modup_fused, moddown_fused,
-                             gmac_groups, gmac_regs)
+    cfg = (ctypes.c_int * len(TUNING_FIELDS))(ntt_cols, ntt_rows, ntt_tw, ks_split, ks_cols, modup_fused,
+                                              moddown_fused, gmac_groups, gmac_regs, kara)
     _check(ctx, _lib().lib.fg_ctx_set_tuning(ctx._h, cfg))
 
 
@@ -495,12 +496,14 @@ def plan_features(params, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=Tru
     return out
 
 
-INT_MUL_OPS = {"mad.wide.u32": 0, "mul.hi.u32": 1, "mad.lo.u32": 2}
+INT_MUL_OPS = {"mad.wide.u32": 0, "mul.hi.u32": 1, "mad.lo.u32": 2, "mad.cc.pair": 3}
 
 
 def int_mul_peak(ctx, op="mad.wide.u32"):
-    """Measured rate (instructions per second, whole GPU) of one 32-bit
-    multiply instruction: the ALU roof of the modular kernels."""
+    """Measured rate (operations per second, whole GPU) of one 32-bit
+    multiply form (INT_MUL_OPS; "mad.cc.pair" = a 32 x 32 -> 64-bit product
+    added to a 64-bit sum by a carry-chained pair, the step of the split
+    products): the ALU roof of the modular kernels."""
     r = ctypes.c_double()
     _check(ctx, _lib().lib.fg_int_mul_peak(ctx._h, INT_MUL_OPS[op], ctypes.byref(r)))
     return r.value

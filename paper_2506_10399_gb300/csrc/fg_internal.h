@@ -87,22 +87,25 @@ struct ConvTab {
 // speed only; the batched form tunes them per shape (defaults: the
 // configurations measured best on the benchmark layer)
 struct Tune {
-    int ntt_cols = 16;     // N = 2^16 NTT pass A: columns per CTA (16 or 8)
-    int ntt_rows = 16;     // N = 2^16 NTT pass B: rows per CTA (16 or 8)
+    int ntt_cols = 8;      // N = 2^16 NTT pass A: columns per CTA (8 or 16)
+    int ntt_rows = 8;      // N = 2^16 NTT pass B: rows per CTA (8 or 16)
     int ntt_tw = 0;        // N = 2^16 NTT twiddles: 0 = held in registers per round (3 CTAs of
                            // 256 threads per SM), 1 = loaded where used (4 per SM)
     int ks_split = 0;      // key switch registers: 0 = launch bounds by digit count, 1 = one CTA per
                            // SM fewer, 2 = key words parked in shared memory (one CTA more)
     int ks_cols = 1;       // key switch: launches the columns are split over (1 or 2)
-    int modup_fused = 0;   // N = 2^16 ModUp: 1 = conversion fused into the digits' first NTT pass
+    int modup_fused = 1;   // N = 2^16 ModUp: 1 = conversion fused into the digits' first NTT pass
     int moddown_fused = 0; // N = 2^16 ModDown + rescale: 1 = conversion fused into the first NTT pass
     int gmac_groups = 7;   // group MAC: outputs from which a CTA runs three thread groups
-    int gmac_regs = 0;     // group MAC: 0 = registers for 2 CTAs of 384 threads per SM, 1 = for 3
+    int gmac_regs = 1;     // group MAC: 1 = registers for 3 CTAs of 384 threads per SM, 0 = for 2
+    int kara = 1;          // group MAC, split products below 2^46: 1 = three products
+                           // (Karatsuba), 0 = four
     bool operator==(const Tune &o) const
     {
         return ntt_cols == o.ntt_cols && ntt_rows == o.ntt_rows && ntt_tw == o.ntt_tw &&
                ks_split == o.ks_split && ks_cols == o.ks_cols && modup_fused == o.modup_fused &&
-               moddown_fused == o.moddown_fused && gmac_groups == o.gmac_groups && gmac_regs == o.gmac_regs;
+               moddown_fused == o.moddown_fused && gmac_groups == o.gmac_groups &&
+               gmac_regs == o.gmac_regs && kara == o.kara;
     }
 };
 

@@ -1315,8 +1315,10 @@ __device__ __forceinline__ ulonglong2 lds128(u32 addr)
 }
 
 // MINB: CTAs of kGmacThreads threads per SM the registers are budgeted for
-// (2: up to 85 registers a thread; 3: up to 56, more warps resident)
-template <int MINB>
+// (2: up to 85 registers a thread; 3: up to 56, more warps resident).
+// KARA: the 23-bit split products in Karatsuba's form (mac_kara: three
+// products instead of four; the same sums).
+template <int MINB, bool KARA>
 __global__ void __launch_bounds__(kGmacThreads, MINB)
 k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
             const u64 *__restrict__ pmodq, const PrimeC *__restrict__ primes, int nq)
@@ -1394,13 +1396,23 @@ k_group_mac(const GProg pg, int ncol, int level, int E, int ls, int log_n,
         ulonglong2 r;
         if (split) {
             u64 a0 = 0, a1 = 0, a2 = 0, c0 = 0, c1 = 0, c2 = 0;
-            for (int t = t0; t < t1; t++, maddr += mstep) {
-                const ulonglong2 v = lds128(vbase + pg.tvoff[t]);
-                const ulonglong2 m = lds128(maddr);
-                mac_split(a0, a1, a2, v.x, m.x);
-                mac_split(c0, c1, c2, v.y, m.y);
+            if (KARA) {
+                for (int t = t0; t < t1; t++, maddr += mstep) {
+                    const ulonglong2 v = lds128(vbase + pg.tvoff[t]);
+                    const ulonglong2 m = lds128(maddr);
+                    mac_kara(a0, a1, a2, v.x, m.x);
+                    mac_kara(c0, c1, c2, v.y, m.y);
+                }
+                r = make_ulonglong2(fold_kara(a0, a1, a2, P), fold_kara(c0, c1, c2, P));
+            } else {
+                for (int t = t0; t < t1; t++, maddr += mstep) {
+                    const ulonglong2 v = lds128(vbase + pg.tvoff[t]);
+                    const ulonglong2 m = lds128(maddr);
+                    mac_split(a0, a1, a2, v.x, m.x);
+                    mac_split(c0, c1, c2, v.y, m.y);
+                }
+                r = make_ulonglong2(fold_split(a0, a1, a2, P), fold_split(c0, c1, c2, P));
             }
-            r = make_ulonglong2(fold_split(a0, a1, a2, P), fold_split(c0, c1, c2, P));
         } else {
             // 30-bit halves: partial sums folded into 128 bits every 8 terms
             u64 lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
@@ -2127,19 +2139,16 @@ void group_mac(fg_ctx *ctx, const std::vector<GroupSource> &srcs, const std::vec
                (double)X * npoly * E * (accumulate ? 2 : 1)) * N * 8);
     // raised once per process and size (not a stream operation, and kept out
     // of the launches a CUDA graph capture records)
-    static size_t sm_set[2] = {48 * 1024, 48 * 1024};
-    const int v = ctx->tune.gmac_regs ? 1 : 0;
+    static size_t sm_set[4] = {48 * 1024, 48 * 1024, 48 * 1024, 48 * 1024};
+    const int v = (ctx->tune.gmac_regs ? 1 : 0) + (ctx->tune.kara ? 2 : 0);
+    auto kern = v == 0 ? k_group_mac<2, false> : v == 1 ? k_group_mac<3, false>
+              : v == 2 ? k_group_mac<2, true> : k_group_mac<3, true>;
     if (sm > sm_set[v]) {
-        if (v) CUDA_TRY(cudaFuncSetAttribute(k_group_mac<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        else CUDA_TRY(cudaFuncSetAttribute(k_group_mac<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         sm_set[v] = sm;
     }
-    if (v)
-        k_group_mac<3><<<g, G * kGmacTile, sm, ctx->stream>>>(pg, ncol, level, E, ls, ctx->log_n,
-                                                             ctx->d_pmodq, ctx->d_primes, ctx->nq);
-    else
-        k_group_mac<2><<<g, G * kGmacTile, sm, ctx->stream>>>(pg, ncol, level, E, ls, ctx->log_n,
-                                                             ctx->d_pmodq, ctx->d_primes, ctx->nq);
+    kern<<<g, G * kGmacTile, sm, ctx->stream>>>(pg, ncol, level, E, ls, ctx->log_n, ctx->d_pmodq,
+                                                ctx->d_primes, ctx->nq);
     check_launch("group_mac");
 }
 

@@ -850,7 +850,7 @@ static void tune_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
     double best_ms = timed(best);
     const int cols[2] = {16, 8}, rows[2] = {16, 8}, tw[2] = {0, 1}, split[3] = {0, 1, 2}, kcols[2] = {1, 2},
               fused[2] = {0, 1}, groups[3] = {7, 4, 13};
-    const int dfused[2] = {0, 1}, gregs[2] = {0, 1};
+    const int dfused[2] = {0, 1}, gregs[2] = {0, 1}, kara[2] = {0, 1};
     auto knob = [&](auto field, const int *vals, int nv) {
         Tune base = best;
         for (int k = 0; k < nv; k++) {
@@ -874,6 +874,7 @@ static void tune_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
     knob(&Tune::ks_split, split, 3);
     knob(&Tune::ks_cols, kcols, 2);
     knob(&Tune::gmac_groups, groups, 3);
+    knob(&Tune::kara, kara, 2);
     knob(&Tune::gmac_regs, gregs, 2);
     ctx->batch_tune = best;
     ctx->batch_tuned = true;
@@ -971,7 +972,7 @@ static void batch_body(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
     if (streams_used) *streams_used = S;
 }
 
-extern "C" int fg_batch_tuning(const fg_ctx *ctx, int cfg[9], double *ms, int cap, int *n)
+extern "C" int fg_batch_tuning(const fg_ctx *ctx, int cfg[10], double *ms, int cap, int *n)
 {
     if (!ctx || !cfg || !n || cap < 0) return FG_EINVAL;
     const Tune &t = ctx->batch_tuned ? ctx->batch_tune : ctx->tune;
@@ -984,18 +985,20 @@ extern "C" int fg_batch_tuning(const fg_ctx *ctx, int cfg[9], double *ms, int ca
     cfg[6] = t.moddown_fused;
     cfg[7] = t.gmac_groups;
     cfg[8] = t.gmac_regs;
+    cfg[9] = t.kara;
     *n = ctx->batch_tuned ? (int)ctx->tune_ms.size() : 0;
     if (ms)
         for (int i = 0; i < std::min(cap, *n); i++) ms[i] = ctx->tune_ms[i];
     return FG_OK;
 }
 
-extern "C" int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[9])
+extern "C" int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[10])
 {
     if (!ctx || !cfg) return FG_EINVAL;
     if ((cfg[0] != 16 && cfg[0] != 8) || (cfg[1] != 16 && cfg[1] != 8) || (cfg[2] != 0 && cfg[2] != 1) ||
         (cfg[3] < 0 || cfg[3] > 2) || (cfg[4] != 1 && cfg[4] != 2) || (cfg[5] != 0 && cfg[5] != 1) ||
-        (cfg[6] != 0 && cfg[6] != 1) || cfg[7] < 1 || (cfg[8] != 0 && cfg[8] != 1))
+        (cfg[6] != 0 && cfg[6] != 1) || cfg[7] < 1 || (cfg[8] != 0 && cfg[8] != 1) ||
+        (cfg[9] != 0 && cfg[9] != 1))
         return FG_EINVAL;
     ctx->tune.ntt_cols = cfg[0];
     ctx->tune.ntt_rows = cfg[1];
@@ -1006,6 +1009,7 @@ extern "C" int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[9])
     ctx->tune.moddown_fused = cfg[6];
     ctx->tune.gmac_groups = cfg[7];
     ctx->tune.gmac_regs = cfg[8];
+    ctx->tune.kara = cfg[9];
     return FG_OK;
 }
 

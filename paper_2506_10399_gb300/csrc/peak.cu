@@ -36,10 +36,16 @@ __global__ void __launch_bounds__(256) k_mul_peak(u64 *out, u32 seed)
                 u32 h;
                 asm volatile("mul.hi.u32 %0, %1, %2;" : "=r"(h) : "r"(a[c]), "r"(b));
                 a[c] = h ^ (u32)it;
-            } else {   // 32-bit multiply-add, low word
+            } else if (OP == 2) {   // 32-bit multiply-add, low word
                 u32 l;
                 asm volatile("mad.lo.u32 %0, %1, %2, %3;" : "=r"(l) : "r"(a[c]), "r"(b), "r"((u32)acc[c]));
                 acc[c] = l;
+            } else {   // 32 x 32 -> 64-bit product added to a 64-bit sum by a carry-chained
+                       // pair (the step of the split products): counted as one
+                asm volatile("{\n\t.reg .u32 l, h;\n\tmov.b64 {l, h}, %0;\n\t"
+                             "mad.lo.cc.u32 l, %1, %2, l;\n\tmadc.hi.u32 h, %1, %2, h;\n\t"
+                             "mov.b64 %0, {l, h};\n\t}"
+                             : "+l"(acc[c]) : "r"(a[c]), "r"(b));
             }
         }
     }
@@ -53,7 +59,7 @@ __global__ void __launch_bounds__(256) k_mul_peak(u64 *out, u32 seed)
 
 extern "C" int fg_int_mul_peak(fg_ctx *ctx, int op, double *ops_per_s)
 {
-    if (!ctx || !ops_per_s || op < 0 || op > 2) return FG_EINVAL;
+    if (!ctx || !ops_per_s || op < 0 || op > 3) return FG_EINVAL;
     try {
         int sms = 0;
         CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
@@ -67,7 +73,8 @@ extern "C" int fg_int_mul_peak(fg_ctx *ctx, int op, double *ops_per_s)
             CUDA_TRY(cudaEventRecord(e0, ctx->stream));
             if (op == 0) k_mul_peak<0><<<blocks, threads, 0, ctx->stream>>>(out, 12345u + rep);
             else if (op == 1) k_mul_peak<1><<<blocks, threads, 0, ctx->stream>>>(out, 12345u + rep);
-            else k_mul_peak<2><<<blocks, threads, 0, ctx->stream>>>(out, 12345u + rep);
+            else if (op == 2) k_mul_peak<2><<<blocks, threads, 0, ctx->stream>>>(out, 12345u + rep);
+            else k_mul_peak<3><<<blocks, threads, 0, ctx->stream>>>(out, 12345u + rep);
             CUDA_TRY(cudaGetLastError());
             CUDA_TRY(cudaEventRecord(e1, ctx->stream));
             CUDA_TRY(cudaEventSynchronize(e1));

@@ -109,8 +109,9 @@ def test_tuned_batch_equals_one_at_a_time(env):
         assert bool((o == o_w).all())
     cfg, ms = fg.batch_tuning(ctx)
     assert cfg["ks_split"] in (0, 1, 2) and cfg["ks_cols"] in (1, 2) and cfg["gmac_groups"] in (7, 4, 13)
-    assert cfg["ntt_cols"] == 16 and cfg["ntt_rows"] == 16 and cfg["ntt_tw"] == 0   # N = 2^13: N = 2^16 forms stay
-    assert len(ms) == 7 and all(m > 0 for m in ms)   # default, 2 ks_split, ks_cols, 2 thresholds, gmac_regs
+    assert cfg["ntt_cols"] == 8 and cfg["ntt_rows"] == 8 and cfg["ntt_tw"] == 0   # N = 2^13: N = 2^16 forms stay
+    assert cfg["kara"] in (0, 1)
+    assert len(ms) == 8 and all(m > 0 for m in ms)   # default, 2 ks_split, ks_cols, 2 thresholds, kara, gmac_regs
 
 
 def test_every_ntt16_tile_and_key_switch_bound_give_the_same_layer():
@@ -134,7 +135,8 @@ def test_every_ntt16_tile_and_key_switch_bound_give_the_same_layer():
     want = want.clone()
     for cfg in ((8, 16, 0, 0, 1, 0, 0, 7, 0), (16, 8, 0, 0, 1, 0, 0, 7, 0), (16, 16, 1, 0, 1, 0, 0, 7, 0),
                 (8, 8, 1, 1, 2, 0, 0, 4, 1), (16, 16, 0, 1, 2, 0, 0, 13, 0), (16, 16, 0, 0, 1, 1, 0, 7, 0),
-                (8, 8, 1, 0, 1, 1, 1, 7, 1), (16, 16, 0, 0, 1, 0, 1, 7, 0), (16, 16, 1, 0, 1, 1, 1, 7, 1), (16, 16, 0, 2, 1, 0, 0, 7, 0)):
+                (8, 8, 1, 0, 1, 1, 1, 7, 1), (16, 16, 0, 0, 1, 0, 1, 7, 0), (16, 16, 1, 0, 1, 1, 1, 7, 1), (16, 16, 0, 2, 1, 0, 0, 7, 0),
+                (16, 16, 0, 0, 1, 0, 0, 7, 0, 0), (8, 8, 1, 1, 2, 1, 1, 4, 1, 0), (16, 16, 0, 2, 1, 0, 0, 13, 0, 0)):
         fg.set_tuning(ctx, *cfg)
         got, _, _ = fg.gcn_layer_axw(ctx, keys, plan, cin)
         assert bool((got == want).all()), cfg
@@ -143,7 +145,7 @@ def test_every_ntt16_tile_and_key_switch_bound_give_the_same_layer():
     fg.gcn_layer_batch(ctx, keys, [plan], [cin], [out], streams=1, graph=False, tune=True)
     assert bool((out == want).all())
     cfg, ms = fg.batch_tuning(ctx)
-    assert len(ms) == 12 and cfg["ks_cols"] in (1, 2) and cfg["modup_fused"] in (0, 1) and cfg["ntt_cols"] in (16, 8) and cfg["ntt_rows"] in (16, 8) and cfg["ntt_tw"] in (0, 1)
+    assert len(ms) == 13 and cfg["ks_cols"] in (1, 2) and cfg["modup_fused"] in (0, 1) and cfg["ntt_cols"] in (16, 8) and cfg["ntt_rows"] in (16, 8) and cfg["ntt_tw"] in (0, 1)
     d = fg.decrypt_decode(ctx, sk, out[0].contiguous(), lvl, ctx.scale)
     assert np.max(np.abs(d[perm] - w.reference_output()[:, 0])) < 2 ** -20
     ctx.close()

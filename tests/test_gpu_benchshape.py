@@ -75,14 +75,18 @@ def test_benchshape_plan_reaches_the_benchmark_kernel_shapes(case):
 
 
 @pytest.mark.parametrize("where,tuning", [("device", {}), ("host", {}),
+                                          ("device", dict(ntt_cols=16, ntt_rows=16, modup_fused=0, gmac_regs=0)),
                                           ("device", dict(modup_fused=1, moddown_fused=1)),
                                           ("device", dict(ks_split=2)),
+                                          ("device", dict(kara=0)),
+                                          ("host", dict(kara=0, ks_split=1, gmac_regs=1)),
                                           ("device", dict(ntt_cols=8, ntt_rows=8, ntt_tw=1, ks_split=1,
                                                           ks_cols=2, modup_fused=1, moddown_fused=1,
                                                           gmac_groups=4, gmac_regs=1))])
 def test_benchshape_layer_word_for_word(case, where, tuning):
     """Also under other launch configurations (the fused ModUp, the other
-    NTT tiles and twiddle form, the other key-switch and group-MAC choices)."""
+    NTT tiles and twiddle form, the other key-switch and group-MAC choices,
+    the group MAC's products with four multiplies instead of Karatsuba's three)."""
     import torch
     fg, ctx, doc, op, plan, keys, x = case
     if where == "device":

@@ -6,7 +6,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("op", ["mad.wide.u32", "mul.hi.u32", "mad.lo.u32"])
+@pytest.mark.parametrize("op", ["mad.wide.u32", "mul.hi.u32", "mad.lo.u32", "mad.cc.pair"])
 def test_int_mul_peak_is_plausible(op):
     import torch
     if not torch.cuda.is_available():
