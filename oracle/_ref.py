@@ -42,6 +42,7 @@ _lib.ref_sample_ternary.argtypes = [_u64, _u64, _u64, _int, _i64p]
 _lib.ref_sample_gauss.argtypes = [_u64, _u64, _u64, _int, _i64p]
 _lib.ref_gauss_table.argtypes = [_u64p]
 _lib.ref_sample_uniform.argtypes = [_u64, _u64, _u64, _u64p, _int, _int, _u64p]
+_lib.ref_sample_uniform_wide.argtypes = [_u64, _u64, _u64, _u64p, _int, _int, _u64p]
 
 
 def _p(a):
@@ -177,4 +178,13 @@ def sample_uniform(seed, purpose, index, primes, n):
     pr = _arr(primes)
     out = np.zeros((len(primes), n), dtype=np.uint64)
     _lib.ref_sample_uniform(seed, purpose, index, _p(pr), len(primes), n, _p(out))
+    return out
+
+
+def sample_uniform_wide(seed, purpose, index, primes, n):
+    """Uniform residues [len(primes)][n], each from two stream words,
+    (w_hi 2^64 + w_lo) mod q, no rejection (see ckks_ref.c)."""
+    pr = _arr(primes)
+    out = np.zeros((len(primes), n), dtype=np.uint64)
+    _lib.ref_sample_uniform_wide(seed, purpose, index, _p(pr), len(primes), n, _p(out))
     return out

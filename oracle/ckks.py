@@ -25,6 +25,7 @@ PURPOSE_KEY_A = 2
 PURPOSE_KEY_E = 3
 PURPOSE_ENC_A = 4
 PURPOSE_ENC_E = 5
+PURPOSE_ENC_A_SEEDED = 6
 
 
 class Params:
@@ -325,6 +326,31 @@ def encrypt(params, seed, index, pt, s, level):
     c0 = neg_res(poly_mul(params, a, small_to_res(s, primes), primes), primes)
     c0 = add_res(add_res(c0, pt[:level + 1], primes), e, primes)
     return np.stack([c0, a])
+
+
+def seeded_a(params, seed, index, level):
+    """The uniform part of a seeded ciphertext: drawn coefficient by
+    coefficient from the stream (seed, 6, index) over q_0..q_level, two
+    words each (_ref.sample_uniform_wide), so the receiver can regenerate it
+    from (seed, index) alone."""
+    return _ref.sample_uniform_wide(seed, PURPOSE_ENC_A_SEEDED, index, params.q[:level + 1], params.n)
+
+
+def encrypt_seeded(params, seed, index, pt, s, level):
+    """Secret-key encryption with a regenerable uniform part (the seeded,
+    compressed form of a symmetric ciphertext): c0 = -a*s + m + e with a =
+    seeded_a(seed, index) and e from (seed, 5, index).  Only c0 (and the
+    seed) travels; expand_seeded rebuilds (c0, a)."""
+    primes = params.q[:level + 1]
+    a = seeded_a(params, seed, index, level)
+    e = small_to_res(_ref.sample_gauss(seed, PURPOSE_ENC_E, index, params.n), primes)
+    c0 = neg_res(poly_mul(params, a, small_to_res(s, primes), primes), primes)
+    return add_res(add_res(c0, pt[:level + 1], primes), e, primes)
+
+
+def expand_seeded(params, seed, index, c0):
+    """The full ciphertext (c0, a) of a seeded one."""
+    return np.stack([c0, seeded_a(params, seed, index, c0.shape[0] - 1)])
 
 
 def decrypt(params, ct, s):

@@ -426,6 +426,29 @@ void ref_sample_gauss(u64 seed, u64 purpose, u64 index, int n, i64 *out)
     }
 }
 
+/* uniform residues from two stream words each, without rejection, so that
+ * every coefficient can be drawn on its own: coefficient x of limb i takes
+ * the stream's words number 2(i n + x) and 2(i n + x) + 1 (counted from 0),
+ * w_lo and w_hi, and is (w_hi 2^64 + w_lo) mod q_i (a bias below
+ * q_i / 2^128).  The word number j of a SplitMix64 stream is
+ * mix(s0 + (j + 1) * 0x9E3779B97F4A7C15) with s0 the stream's start state.
+ * out: u64[n_limbs][n]. */
+void ref_sample_uniform_wide(u64 seed, u64 purpose, u64 index, const u64 *primes,
+                             int n_limbs, int n, u64 *out)
+{
+    const u64 s0 = sm_open(seed, purpose, index).s;
+    for (int i = 0; i < n_limbs; i++) {
+        const u64 q = primes[i];
+        for (int x = 0; x < n; x++) {
+            const u64 j = 2 * ((u64)i * (u64)n + (u64)x);
+            const u64 lo = sm_mix(s0 + (j + 1) * 0x9E3779B97F4A7C15ull);
+            const u64 hi = sm_mix(s0 + (j + 2) * 0x9E3779B97F4A7C15ull);
+            const unsigned __int128 w = ((unsigned __int128)hi << 64) | lo;
+            out[(size_t)i * n + x] = (u64)(w % q);
+        }
+    }
+}
+
 /* uniform residues: limb by limb in the order given, coefficient by
  * coefficient, draw r = next & (2^bitlen(q) - 1) until r < q.
  * out: u64[n_limbs][n]. */

@@ -379,6 +379,57 @@ def test_encrypt_decrypt_and_add(ctx10):
     assert max(abs(int(v)) for v in diff) <= 20
 
 
+def test_seeded_uniform_sampler_from_the_stream_words():
+    """The regenerable uniform sampler against its definition on the pinned
+    SplitMix64 stream: coefficient x of limb i is (w_{2k+1} 2^64 + w_{2k})
+    mod q_i with k = i n + x and w_j the stream's words (taken here from the
+    stream itself, the first 2 n_limbs n of them), for a 40-bit and a
+    60-bit prime; every coefficient can be drawn alone, so a different
+    index or purpose gives an unrelated sample."""
+    q = [int(v) for v in _ref.gen_primes(10, [40, 60])]
+    n = 64
+    seed, purpose, index = 9, 6, 3
+    w = [int(v) for v in _ref.splitmix(seed, purpose, index, 2 * len(q) * n)]
+    got = _ref.sample_uniform_wide(seed, purpose, index, q, n)
+    for i, qi in enumerate(q):
+        for x in range(n):
+            k = i * n + x
+            assert int(got[i, x]) == ((w[2 * k + 1] << 64) + w[2 * k]) % qi
+    assert not np.array_equal(got, _ref.sample_uniform_wide(seed, purpose, index + 1, q, n))
+
+
+def test_seeded_uniform_sampler_is_uniform():
+    """Frequencies of the sampler's values in 16 equal ranges of [0, q)
+    within five standard errors of 1/16, and its mean within five standard
+    errors of (q - 1)/2, for a 45-bit prime (a dropped high word would leave
+    (w_lo mod q), still nearly uniform: the definition test above catches
+    that; this one catches a biased or truncated reduction)."""
+    q = int(_ref.gen_primes(12, [45])[0])
+    u = _ref.sample_uniform_wide(11, 6, 0, [q], 1 << 16)[0].astype(np.float64)
+    n = u.size
+    counts = np.bincount(np.minimum((u / q * 16).astype(np.int64), 15), minlength=16) / n
+    assert np.all(np.abs(counts - 1 / 16) < 5 * np.sqrt((1 / 16) * (15 / 16) / n))
+    assert abs(u.mean() - (q - 1) / 2) < 5 * q / np.sqrt(12 * n)
+
+
+def test_seeded_encryption_decrypts_and_expands_to_a_ciphertext(ctx10):
+    """encrypt_seeded: c0 alone, (c0, a) rebuilt from (seed, index); the
+    rebuilt ciphertext decrypts to the message plus the Gaussian noise (all
+    of it within |e| <= 19, the sampler's tail), and its c1 is the seeded
+    uniform sample."""
+    P, s = ctx10
+    rng = np.random.default_rng(1)
+    z = rng.uniform(-1, 1, P.slots)
+    pt = ckks.encode(P, z, P.scale, P.L)
+    c0 = ckks.encrypt_seeded(P, 5, 2, pt, s, P.L)
+    ct = ckks.expand_seeded(P, 5, 2, c0)
+    np.testing.assert_array_equal(ct[1], _ref.sample_uniform_wide(5, 6, 2, P.q[:P.L + 1], P.n))
+    d = ckks.decrypt(P, ct, s)
+    diff = ckks.crt_centered(P, ckks.sub_res(d, pt[:P.L + 1], P.q))
+    assert max(abs(int(v)) for v in diff) <= 19
+    assert np.max(np.abs(ckks.decode(P, d, P.scale) - z)) < 2 ** -25
+
+
 def test_pmult_and_rescale(ctx10):
     P, s = ctx10
     rng = np.random.default_rng(1)
