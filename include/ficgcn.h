@@ -156,6 +156,25 @@ int fg_pack_features(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t s
                      const double *X, int V, int F, const int32_t *perm, int t,
                      uint64_t *out_cts, int *n_out);
 
+/* Seeded (compressed) client packing: the same packing and encryption, but
+ * the uniform part a of ciphertext b is drawn from the stream (seed, 6, b)
+ * coefficient by coefficient, (w_hi 2^64 + w_lo) mod q_i from the stream's
+ * words 2(i N + x) and 2(i N + x) + 1, so that the receiver regenerates it
+ * from (seed, b) alone; only c0 = -a s + m + e is written.  This is a
+ * transport form of the paper's client-encrypted features (Sec. 3.2), half
+ * the bytes of fg_pack_features.  out_c0 (host or device): room for
+ * ceil(F/t) polynomials [L+1][N]; *n_out receives ceil(F/t). */
+int fg_pack_features_seeded(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t seed,
+                            const double *X, int V, int F, const int32_t *perm, int t,
+                            uint64_t *out_c0, int *n_out);
+
+/* Full ciphertexts [n][2][level+1][N] of seeded ones 0..n-1 of a seed (c0:
+ * [n][level+1][N]; host or device, either side): c1 of ciphertext b
+ * regenerated on the device as fg_pack_features_seeded drew it.  FG_EINVAL
+ * for n outside 0..65535 or level outside 0..L. */
+int fg_expand_seeded(fg_ctx *ctx, uint64_t seed, const uint64_t *c0, int n, int level,
+                     uint64_t *out_cts);
+
 /* The client's Inter-CA input (paper Sec. 3.1: the node arrangements the
  * client encrypts offline): for every neighbour slot k < n, the rows
  * nbr[v][k] of X (zero where nbr is -1) packed as fg_pack_features does with
@@ -341,6 +360,16 @@ int fg_plan_set_plaintext(fg_plan *plan, int mask, const uint64_t *coeffs);
 int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *plan,
                      const uint64_t *in_cts, int n_in, uint64_t *out_cts, int n_out,
                      int *out_level, double *out_scale);
+/* The layer on seeded inputs (fg_pack_features_seeded): in_c0 = the n_in
+ * c0 polynomials [n_in][L+1][N] (host or device) of seed's ciphertexts
+ * 0..n_in-1.  Only c0 is copied from host memory (in column chunks that
+ * overlap the combination, as for fg_gcn_layer_axw); the uniform parts are
+ * regenerated on the device.  The outputs equal fg_gcn_layer_axw's on the
+ * expanded ciphertexts (fg_expand_seeded) word for word.  FG_EINVAL for an
+ * Inter-CA plan (its copies come from fg_pack_neighbor_copies). */
+int fg_gcn_layer_axw_seeded(fg_ctx *ctx, const fg_keys *keys, const fg_plan *plan,
+                            const uint64_t *in_c0, int n_in, uint64_t seed, uint64_t *out_cts,
+                            int n_out, int *out_level, double *out_scale);
 
 /* Batched layers (many queries, e.g. several graphs of one client, sharing
  * ctx and keys; the keys must hold every plan's rotations).  Query q runs

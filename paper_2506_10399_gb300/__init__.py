@@ -240,6 +240,32 @@ def pack_features(ctx, sk, seed, X, perm, t, out=None):
     return out
 
 
+def pack_features_seeded(ctx, sk, seed, X, perm, t, out=None):
+    """Seeded form of pack_features: the c0 parts [ceil(F/t)][L+1][N] only;
+    ciphertext b's uniform part is regenerated from (seed, b) by
+    expand_seeded or by gcn_layer_axw(..., seed=seed)."""
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+    perm = np.ascontiguousarray(np.asarray(perm, dtype=np.int32))
+    V, F = X.shape
+    nb = -(-F // t)
+    if out is None:
+        out = np.empty((nb, ctx.nq, ctx.n), np.uint64)
+    n = ctypes.c_int()
+    _check(ctx, _lib().lib.fg_pack_features_seeded(ctx._h, sk, len(sk), int(seed), _ptr(X), V, F,
+                                                   ctypes.c_void_p(perm.ctypes.data), t, _ptr(out),
+                                                   ctypes.byref(n)))
+    return out
+
+
+def expand_seeded(ctx, seed, c0, out=None):
+    """Full ciphertexts [n][2][l+1][N] of seeded ones (c0: [n][l+1][N])."""
+    n, nl = int(c0.shape[0]), int(c0.shape[1])
+    if out is None:
+        out = _like(c0, (n, 2, nl, ctx.n))
+    _check(ctx, _lib().lib.fg_expand_seeded(ctx._h, int(seed), _ptr(c0), n, nl - 1, _ptr(out)))
+    return out
+
+
 def decrypt(ctx, sk, ct, level, out=None):
     if out is None:
         out = _like(ct, (level + 1, ctx.n))
@@ -411,17 +437,25 @@ def plan_dry_run(params, row_ptr, col, val, W, perm, t=0, radix_bits=0, aoo=True
     return out
 
 
-def gcn_layer_axw(ctx, keys, plan, in_cts, out=None):
-    """(output ciphertexts [F'][2][l+1][N], output level l, scale)."""
+def gcn_layer_axw(ctx, keys, plan, in_cts, out=None, seed=None):
+    """(output ciphertexts [F'][2][l+1][N], output level l, scale).  With
+    seed given, in_cts are the c0 parts [n][in_level+1][N] of seeded
+    ciphertexts (pack_features_seeded)."""
     info = plan.info()
     if out is None:
         out = _like(in_cts, (info["n_out"], 2, info["out_level"] + 1, ctx.n))
     assert int(in_cts.shape[-1]) == ctx.n and int(in_cts.shape[-2]) == info["in_level"] + 1, \
-        "inputs must be [n][2][in_level+1][N]"
+        "inputs must be [n][2][in_level+1][N] ([n][in_level+1][N] when seeded)"
+    assert (seed is None) == (in_cts.ndim == 4), "seeded inputs are c0 parts [n][in_level+1][N]"
     lvl, sc = ctypes.c_int(), ctypes.c_double()
-    _check(ctx, _lib().lib.fg_gcn_layer_axw(ctx._h, keys._h, plan._h, _ptr(in_cts), int(in_cts.shape[0]),
-                                            _ptr(out), info["n_out"], ctypes.byref(lvl),
-                                            ctypes.byref(sc)))
+    if seed is None:
+        _check(ctx, _lib().lib.fg_gcn_layer_axw(ctx._h, keys._h, plan._h, _ptr(in_cts), int(in_cts.shape[0]),
+                                                _ptr(out), info["n_out"], ctypes.byref(lvl),
+                                                ctypes.byref(sc)))
+    else:
+        _check(ctx, _lib().lib.fg_gcn_layer_axw_seeded(ctx._h, keys._h, plan._h, _ptr(in_cts),
+                                                       int(in_cts.shape[0]), int(seed), _ptr(out),
+                                                       info["n_out"], ctypes.byref(lvl), ctypes.byref(sc)))
     return out, lvl.value, sc.value
 
 

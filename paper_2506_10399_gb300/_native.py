@@ -56,6 +56,9 @@ SIGS = {
     "fg_encrypt": (c_int, [c_void_p, c_void_p, c_size, c_u64, c_u64, c_void_p, c_int, c_void_p]),
     "fg_pack_features": (c_int, [c_void_p, c_void_p, c_size, c_u64, c_void_p, c_int, c_int,
                                  c_void_p, c_int, c_void_p, P(c_int)]),
+    "fg_pack_features_seeded": (c_int, [c_void_p, c_void_p, c_size, c_u64, c_void_p, c_int, c_int,
+                                        c_void_p, c_int, c_void_p, P(c_int)]),
+    "fg_expand_seeded": (c_int, [c_void_p, c_u64, c_void_p, c_int, c_int, c_void_p]),
     "fg_decrypt": (c_int, [c_void_p, c_void_p, c_size, c_void_p, c_int, c_void_p]),
     "fg_pack_neighbor_copies": (c_int, [c_void_p, c_void_p, c_size, ctypes.c_uint64, c_void_p, c_int,
                                         c_int, c_void_p, c_int, c_void_p, c_void_p]),
@@ -97,6 +100,8 @@ SIGS = {
     "fg_batch_tuning": (c_int, [c_void_p, c_void_p, c_void_p, c_int, P(c_int)]),
     "fg_gcn_layer_axw": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int,
                                  P(c_int), P(c_double)]),
+    "fg_gcn_layer_axw_seeded": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_u64, c_void_p,
+                                        c_int, P(c_int), P(c_double)]),
     "fg_rotate": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "fg_rescale": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
     "fg_poly_mul": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),

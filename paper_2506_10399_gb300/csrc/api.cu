@@ -840,12 +840,13 @@ int fg_encrypt(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t seed, u
     API_CATCH(ctx)
 }
 
-int fg_pack_features(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t seed,
-                     const double *X, int V, int F, const int32_t *perm, int t, uint64_t *out_cts,
-                     int *n_out)
+// Packing and encryption of the features (seeded: the uniform part drawn
+// by sample_uniform_wide and only c0 written, [nb][L+1][N]; otherwise full
+// ciphertexts [nb][2][L+1][N]).
+static void pack_features_impl(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t seed,
+                               const double *X, int V, int F, const int32_t *perm, int t,
+                               uint64_t *out_cts, int *n_out, bool seeded)
 {
-    if (!ctx) return FG_EINVAL;
-    API_TRY
     const int N = ctx->n, M = ctx->slots, L = ctx->L(), nl = L + 1;
     FG_CHECK(X && perm && out_cts && V >= 1 && F >= 1, FG_EINVAL, "bad packing arguments");
     FG_CHECK(t >= 1 && (t & (t - 1)) == 0 && t <= M, FG_EINVAL, "t must be a power of two");
@@ -853,8 +854,8 @@ int fg_pack_features(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t s
     FG_CHECK(V <= B, FG_EINVAL, "nodes do not fit a block");
     for (int v = 0; v < V; v++) FG_CHECK(perm[v] >= 0 && perm[v] < B, FG_EINVAL, "perm out of range");
     const u64 *S = secret_ntt(ctx, sk_blob, sk_len);
-    const bool dev_out = is_device_ptr(out_cts);
-    const size_t ct_w = (size_t)2 * nl * N;
+    const bool dev_out = is_device_ptr(out_cts) && !seeded;
+    const size_t ct_w = (size_t)2 * nl * N, out_w = seeded ? (size_t)nl * N : ct_w;
     const int chunk = 16;
     std::vector<std::vector<u64>> pts(chunk, std::vector<u64>((size_t)nl * N));
     std::vector<std::vector<u64>> as(chunk, std::vector<u64>((size_t)nl * N));
@@ -878,7 +879,11 @@ int fg_pack_features(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t s
             } catch (...) {
                 bad = 1;
             }
-            hm::sample_uniform(seed, 4, (u64)b, ctx->primes.data(), nl, N, as[c].data());
+            if (seeded)
+                hm::sample_uniform_wide(seed, hm::kSeededPurpose, (u64)b, ctx->primes.data(), nl, N,
+                                        as[c].data());
+            else
+                hm::sample_uniform(seed, 4, (u64)b, ctx->primes.data(), nl, N, as[c].data());
             hm::sample_gauss(seed, 5, (u64)b, N, es[c].data());
         }
         FG_CHECK(!bad, FG_EINVAL, "feature value cannot be encoded");
@@ -888,14 +893,58 @@ int fg_pack_features(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t s
                                      ctx->stream));
             u64 *o = dev_out ? out_cts + (size_t)b * ct_w : dct;
             encrypt_dev(ctx, S, seed, (u64)b, dpt, L, o, as[c].data(), es[c].data());
-            if (!dev_out) {
-                CUDA_TRY(cudaMemcpyAsync(out_cts + (size_t)b * ct_w, dct, ct_w * 8,
-                                         cudaMemcpyDeviceToHost, ctx->stream));
+            if (!dev_out) {   // seeded: c0 only
+                CUDA_TRY(cudaMemcpyAsync(out_cts + (size_t)b * out_w, dct, out_w * 8, cudaMemcpyDefault,
+                                         ctx->stream));
                 sync(ctx);
             }
         }
     }
     if (n_out) *n_out = nb;
+    sync(ctx);
+}
+
+int fg_pack_features(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t seed,
+                     const double *X, int V, int F, const int32_t *perm, int t, uint64_t *out_cts,
+                     int *n_out)
+{
+    if (!ctx) return FG_EINVAL;
+    API_TRY
+    pack_features_impl(ctx, sk_blob, sk_len, seed, X, V, F, perm, t, out_cts, n_out, false);
+    API_CATCH(ctx)
+}
+
+int fg_pack_features_seeded(fg_ctx *ctx, const void *sk_blob, size_t sk_len, uint64_t seed,
+                            const double *X, int V, int F, const int32_t *perm, int t, uint64_t *out_c0,
+                            int *n_out)
+{
+    if (!ctx) return FG_EINVAL;
+    API_TRY
+    pack_features_impl(ctx, sk_blob, sk_len, seed, X, V, F, perm, t, out_c0, n_out, true);
+    API_CATCH(ctx)
+}
+
+int fg_expand_seeded(fg_ctx *ctx, uint64_t seed, const uint64_t *c0, int n, int level, uint64_t *out_cts)
+{
+    if (!ctx) return FG_EINVAL;
+    API_TRY
+    FG_CHECK(c0 && out_cts && n >= 0 && n <= 65535 && level >= 0 && level < ctx->nq, FG_EINVAL,
+             "bad seeded-ciphertext arguments");
+    const int N = ctx->n, nl = level + 1;
+    const size_t c0_w = (size_t)nl * N, ct_w = 2 * c0_w;
+    const bool dev_out = is_device_ptr(out_cts);
+    u64 *d = dev_out ? out_cts : (u64 *)ctx->buf("expand_ct", (size_t)n * ct_w * 8);
+    if (n) {
+        const u64 *dc0 = c0;
+        if (!is_device_ptr(c0)) {
+            u64 *s = (u64 *)ctx->buf("expand_c0", (size_t)n * c0_w * 8);
+            CUDA_TRY(cudaMemcpyAsync(s, c0, (size_t)n * c0_w * 8, cudaMemcpyHostToDevice, ctx->stream));
+            dc0 = s;
+        }
+        kern::expand_uniform(ctx, ctx->stream, d, ct_w, dc0, n, nl, seed, 0);
+        if (!dev_out)
+            CUDA_TRY(cudaMemcpyAsync(out_cts, d, (size_t)n * ct_w * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    }
     sync(ctx);
     API_CATCH(ctx)
 }

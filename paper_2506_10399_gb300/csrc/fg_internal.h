@@ -61,6 +61,11 @@ void sample_ternary(u64 seed, u64 purpose, u64 index, int n, int8_t *out);
 void sample_gauss(u64 seed, u64 purpose, u64 index, int n, int8_t *out);
 void sample_uniform(u64 seed, u64 purpose, u64 index, const u64 *primes, int n_limbs,
                     int n, u64 *out);
+// uniform residues drawn coefficient by coefficient (two stream words each):
+// the regenerable part of seeded ciphertexts (purpose kSeededPurpose)
+void sample_uniform_wide(u64 seed, u64 purpose, u64 index, const u64 *primes, int n_limbs,
+                         int n, u64 *out);
+constexpr u64 kSeededPurpose = 6;
 
 // CKKS encoding (canonical embedding) in FP64: out [level+1][N]
 void encode(int log_n, const double *slots, int n_slots, double scale, const u64 *primes,
@@ -285,6 +290,11 @@ void scalar(fg_ctx *ctx, const u64 *a, u64 *c, int count, const std::vector<int>
 void automorphism(fg_ctx *ctx, const u64 *a, u64 *c, int nlimbs, uint32_t g);
 void small_to_res(fg_ctx *ctx, const int8_t *e, u64 *out, int n_limbs, const int *d_pidx);
 void copy_limbs(fg_ctx *ctx, const u64 *src, int src_ls, u64 *dst, int dst_ls, int npoly, int nl);
+// seeded ciphertexts index0 .. index0 + ncols - 1 at level nl - 1 into
+// ct + c * ct_pitch ([2][nl][N]) on stream st: the uniform part regenerated,
+// c0 copied from c0 + c * nl * N when c0 is not null (else already in place)
+void expand_uniform(fg_ctx *ctx, cudaStream_t st, u64 *ct, size_t ct_pitch, const u64 *c0, int ncols,
+                    int nl, u64 seed, u64 index0);
 
 // combination: Z[j][p][i] = sum_f c[i][f][j] X[f][p][i], coefficient domain;
 // X: [F][2][level+1][N], consts: [level+1][F][Fp] Montgomery form, Z limb stride z_ls

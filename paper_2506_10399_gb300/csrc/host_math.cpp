@@ -161,6 +161,24 @@ void sample_gauss(u64 seed, u64 purpose, u64 index, int n, int8_t *out)
     }
 }
 
+// Coefficient x of limb l from the stream's words 2(l n + x) and
+// 2(l n + x) + 1 (word j of a SplitMix64 stream is mix(s0 + (j + 1) gamma)),
+// (w_hi 2^64 + w_lo) mod q_l: every coefficient can be drawn on its own.
+void sample_uniform_wide(u64 seed, u64 purpose, u64 index, const u64 *primes, int n_limbs, int n,
+                         u64 *out)
+{
+    const u64 s0 = Stream(seed, purpose, index).s, gamma = 0x9E3779B97F4A7C15ull;
+    for (int l = 0; l < n_limbs; l++) {
+        const u64 q = primes[l];
+        for (int x = 0; x < n; x++) {
+            const u64 j = 2 * ((u64)l * (u64)n + (u64)x);
+            const u64 lo = sm_mix(s0 + (j + 1) * gamma), hi = sm_mix(s0 + (j + 2) * gamma);
+            const unsigned __int128 w = ((unsigned __int128)hi << 64) | lo;
+            out[(size_t)l * n + x] = (u64)(w % q);
+        }
+    }
+}
+
 void sample_uniform(u64 seed, u64 purpose, u64 index, const u64 *primes, int n_limbs, int n,
                     u64 *out)
 {

@@ -779,6 +779,39 @@ __global__ void k_small_to_res(const int8_t *e, u64 *out, const int *pidx, const
     }
 }
 
+// SplitMix64's output function (Steele, Lea and Flood, OOPSLA 2014)
+__device__ __forceinline__ u64 sm_mix_dev(u64 z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// The uniform part of seeded ciphertexts: column c is ciphertext index0 + c,
+// whose stream (seed, purpose, index) starts from s0 = mix(seed ^ (purpose
+// << 48) ^ index) and has word j = mix(s0 + (j + 1) gamma); coefficient x of
+// limb i is (w_hi 2^64 + w_lo) mod q_i with w_lo, w_hi the words 2(i N + x)
+// and 2(i N + x) + 1.  [w_hi]_q 2^64 mod q is the Montgomery product of
+// [w_hi]_q with R^2 mod q (R = 2^64).  Ciphertext c is written at ct + c *
+// ct_pitch: its uniform part at offset nl N, and, when c0 is given, its c0
+// copied from c0 + c * nl N.
+__global__ void k_expand_uniform(u64 *ct, size_t ct_pitch, const u64 *__restrict__ c0, int nl, u64 seed,
+                                 u64 purpose, u64 index0, const PrimeC *__restrict__ primes, int N)
+{
+    const int i = blockIdx.y, c = blockIdx.z;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    const PrimeC P = primes[i];
+    const u64 gamma = 0x9E3779B97F4A7C15ull;
+    const u64 s0 = sm_mix_dev(seed ^ (purpose << 48) ^ (index0 + (u64)c));
+    const u64 j = 2 * ((u64)i * (u64)N + (u64)x);
+    const u64 lo = sm_mix_dev(s0 + (j + 1) * gamma), hi = sm_mix_dev(s0 + (j + 2) * gamma);
+    const u64 h = mont_mul(reduce_word(hi, P), P.r2, P);
+    u64 *o = ct + (size_t)c * ct_pitch + (size_t)i * N + x;
+    o[(size_t)nl * N] = add_mod(h, reduce_word(lo, P), P.q);
+    if (c0) *o = c0[((size_t)c * nl + i) * N + x];
+}
+
 __global__ void k_copy_limbs(const u64 *src, int src_ls, u64 *dst, int dst_ls, int nl, int N)
 {
     const int poly = blockIdx.z, i = blockIdx.y;
@@ -1811,6 +1844,17 @@ void small_to_res(fg_ctx *ctx, const int8_t *e, u64 *out, int n_limbs, const int
     k_small_to_res<<<ew_grid(ctx->n, n_limbs), 256, 0, ctx->stream>>>(e, out, d_pidx,
                                                                       ctx->d_primes, ctx->n);
     check_launch("small_to_res");
+}
+
+void expand_uniform(fg_ctx *ctx, cudaStream_t st, u64 *ct, size_t ct_pitch, const u64 *c0, int ncols,
+                    int nl, u64 seed, u64 index0)
+{
+    if (!ncols || !nl) return;
+    FG_CHECK(ncols <= 65535 && nl <= ctx->nq, FG_EINVAL, "expand_uniform: bad shape");
+    dim3 g((ctx->n + 255) / 256, nl, ncols);
+    k_expand_uniform<<<g, 256, 0, st>>>(ct, ct_pitch, c0, nl, seed, hm::kSeededPurpose, index0,
+                                        ctx->d_primes, ctx->n);
+    check_launch("expand_uniform");
 }
 
 void copy_limbs(fg_ctx *ctx, const u64 *src, int src_ls, u64 *dst, int dst_ls, int npoly, int nl)

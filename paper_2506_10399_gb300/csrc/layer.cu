@@ -452,8 +452,12 @@ int fg_plan_set_plaintext(fg_plan *pl, int mask, const uint64_t *coeffs)
 // ------------------------------------------------------------------ the layer
 // Enqueues one layer on ctx->stream with the workspace names prefixed by
 // ctx->ws_prefix; waits for it only when sync is set (host buffers need it).
+// seed: null for full ciphertexts [n_in][2][l0+1][N]; else in_cts holds the
+// c0 parts [n_in][l0+1][N] of seeded ciphertexts 0..n_in-1 of that seed,
+// whose uniform parts are regenerated on the device (kern::expand_uniform).
 static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, const uint64_t *in_cts,
-                       int n_in, uint64_t *out_cts, int n_out, bool sync, int *out_level)
+                       int n_in, uint64_t *out_cts, int n_out, bool sync, int *out_level,
+                       const uint64_t *seed = nullptr)
 {
     {
         FG_CHECK(keys && pl && in_cts && out_cts, FG_EINVAL, "null argument");
@@ -469,6 +473,8 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
             for (auto &r : g.rots) keys->get(((r.second % M) + M) % M);
 
         const size_t in_w = (size_t)nb * 2 * nl0 * N;
+        const size_t c0_w = (size_t)nl0 * N, ct_w = 2 * c0_w;
+        FG_CHECK(!seed || !pl->n_copies, FG_EINVAL, "seeded inputs: not for neighbour copies");
         const u64 *X = in_cts;
         // host inputs: staged into this workspace's buffer on its own copy
         // stream; for t = 1 in chunks of columns, the combination of each
@@ -496,19 +502,34 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
                 CUDA_TRY(cudaEventRecord(cr->ev[n_chunks], ctx->stream));
                 CUDA_TRY(cudaStreamWaitEvent(cr->st, cr->ev[n_chunks], 0));
             }
-            if (chunked) {
-                const size_t ct_w = (size_t)2 * nl0 * N;
-                for (int c = 0; c < n_chunks; c++) {
-                    const int fb = c * kChunk, fn = std::min(kChunk, F - fb);
+            // columns fb .. fb + fn - 1 into the staging buffer (seeded: c0
+            // only; the uniform parts are regenerated on the compute stream
+            // once the chunk has arrived, so that the copies run back to back)
+            auto stage = [&](int fb, int fn) {
+                if (seed) {   // one strided copy (one copy per column measured slower)
+                    CUDA_TRY(cudaMemcpy2DAsync(d + fb * ct_w, ct_w * 8, in_cts + fb * c0_w, c0_w * 8, c0_w * 8,
+                                               fn, cudaMemcpyHostToDevice, cr->st));
+                } else {
                     CUDA_TRY(cudaMemcpyAsync(d + fb * ct_w, in_cts + fb * ct_w, fn * ct_w * 8,
                                              cudaMemcpyHostToDevice, cr->st));
+                }
+            };
+            if (chunked) {
+                for (int c = 0; c < n_chunks; c++) {
+                    const int fb = c * kChunk, fn = std::min(kChunk, F - fb);
+                    stage(fb, fn);
                     CUDA_TRY(cudaEventRecord(cr->ev[c], cr->st));
                 }
             } else {
-                CUDA_TRY(cudaMemcpyAsync(d, in_cts, in_w * 8, cudaMemcpyHostToDevice, cr->st));
+                stage(0, nb);
                 CUDA_TRY(cudaEventRecord(cr->ev[0], cr->st));
                 CUDA_TRY(cudaStreamWaitEvent(ctx->stream, cr->ev[0], 0));
+                if (seed) kern::expand_uniform(ctx, ctx->stream, d, ct_w, nullptr, nb, nl0, *seed, 0);
             }
+            X = d;
+        } else if (seed) {   // device c0: expanded into the staging buffer in stream order
+            u64 *d = (u64 *)ctx->buf("layer_in", in_w * 8);
+            kern::expand_uniform(ctx, ctx->stream, d, ct_w, in_cts, nb, nl0, *seed, 0);
             X = d;
         }
         // the staged inputs have been read (by the combination's kernels)
@@ -566,8 +587,11 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
             if (chunked) {
                 for (int c = 0; c < n_chunks; c++) {
                     CUDA_TRY(cudaStreamWaitEvent(ctx->stream, cr->ev[c], 0));
-                    kern::comb_const_mac(ctx, X, F, Fp, l0, pl->d_comb, Zc, nl0, c * kChunk,
-                                         std::min(F, (c + 1) * kChunk), c > 0);
+                    const int fb = c * kChunk, fe = std::min(F, (c + 1) * kChunk);
+                    if (seed)
+                        kern::expand_uniform(ctx, ctx->stream, const_cast<u64 *>(X) + fb * ct_w, ct_w, nullptr,
+                                             fe - fb, nl0, *seed, (u64)fb);
+                    kern::comb_const_mac(ctx, X, F, Fp, l0, pl->d_comb, Zc, nl0, fb, fe, c > 0);
                 }
             } else {
                 kern::comb_const_mac(ctx, X, F, Fp, l0, pl->d_comb, Zc, nl0);
@@ -1052,6 +1076,24 @@ extern "C" int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_pla
 }
 
 extern "C" {
+
+int fg_gcn_layer_axw_seeded(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, const uint64_t *in_c0,
+                            int n_in, uint64_t seed, uint64_t *out_cts, int n_out, int *out_level,
+                            double *out_scale)
+{
+    if (!ctx) return FG_EINVAL;
+    try {
+        layer_exec(ctx, keys, pl, in_c0, n_in, out_cts, n_out, true, out_level, &seed);
+        if (out_scale) *out_scale = ctx->scale;
+    } catch (const fg_error &e) {
+        ctx->err = e.what();
+        return e.code;
+    } catch (const std::exception &e) {
+        ctx->err = e.what();
+        return FG_EOOM;
+    }
+    return FG_OK;
+}
 
 int fg_gcn_layer_axw(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, const uint64_t *in_cts,
                      int n_in, uint64_t *out_cts, int n_out, int *out_level, double *out_scale)
