@@ -828,22 +828,30 @@ def run_batched(args):
     # timed region: one at a time each layer overlaps its copy with its own
     # combination only, the batch overlaps every query's copy with the other
     # queries' work
-    ins, outs = [], []
+    # (seeded ciphertexts by default: c0 only crosses the host link)
+    seeded = not args.full_inputs
+    ins, outs, seeds = [], [], []
     for i, (w, plan, perm, t) in enumerate(zip(ws, plans, perms, ts)):
         info = plan.info()
-        cin = torch.empty((info["n_in"], 2, ctx.nq, ctx.n), dtype=torch.int64, device="cuda")
-        fg.pack_features(ctx, sk, SEED + 100 + i, w.X, perm, t, out=cin)
-        host = torch.empty(cin.shape, dtype=torch.int64, pin_memory=True)
-        host.copy_(cin)
-        del cin
+        sd = SEED + 100 + i
+        if seeded:
+            host = torch.empty((info["n_in"], ctx.nq, ctx.n), dtype=torch.int64, pin_memory=True)
+            fg.pack_features_seeded(ctx, sk, sd, w.X, perm, t, out=host)
+        else:
+            cin = torch.empty((info["n_in"], 2, ctx.nq, ctx.n), dtype=torch.int64, device="cuda")
+            fg.pack_features(ctx, sk, sd, w.X, perm, t, out=cin)
+            host = torch.empty(cin.shape, dtype=torch.int64, pin_memory=True)
+            host.copy_(cin)
+            del cin
         ins.append(host)
+        seeds.append(sd)
         outs.append(torch.empty((info["n_out"], 2, info["out_level"] + 1, ctx.n), dtype=torch.int64,
                                 device="cuda"))
     setup_s = time.perf_counter() - t_setup
 
     def plain():
-        for plan, cin, out in zip(plans, ins, outs):
-            fg.gcn_layer_axw(ctx, keys, plan, cin, out=out)
+        for plan, cin, out, sd in zip(plans, ins, outs, seeds):
+            fg.gcn_layer_axw(ctx, keys, plan, cin, out=out, seed=sd if seeded else None)
 
     def timed(fn):
         torch.cuda.synchronize()
@@ -867,7 +875,7 @@ def run_batched(args):
     free_gb = torch.cuda.mem_get_info()[0] / 1e9
 
     def batched():
-        lv, s = fg.gcn_layer_batch(ctx, keys, plans, ins, outs, tune=True)
+        lv, s = fg.gcn_layer_batch(ctx, keys, plans, ins, outs, tune=True, seeds=seeds if seeded else None)
         used["streams"] = s
 
     for _ in range(args.warmup):
@@ -884,6 +892,8 @@ def run_batched(args):
     rot = sum(p.info()["rotations"] for p in plans)
     h2d = sum(x.numel() * 8 for x in ins)
     line = {"metric": "batched encrypted A.X.W layers: ms for the whole batch at N=2^16, inputs from host",
+            "inputs": ("seeded client ciphertexts (c0 over the host link, uniform parts regenerated on the "
+                       "device)" if seeded else "full ciphertexts"),
             "unit": "ms/batch", "higher_is_better": False, "queries": nq,
             "plain_ms": round(plain_ms, 3), "batched_ms": round(batch_ms, 3),
             "speedup": round(plain_ms / batch_ms, 3), "streams": used.get("streams"),
@@ -917,6 +927,8 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="batched form: many queries one at a time vs all at once")
     ap.add_argument("--queries", type=int, default=32, help="queries in the batched form")
+    ap.add_argument("--full-inputs", action="store_true",
+                    help="batched form: full ciphertexts from host memory instead of seeded ones")
     ap.add_argument("--two-layer", action="store_true", help="two-layer GCN with x^2 between")
     ap.add_argument("--workload", default="pubmed_like", choices=["pubmed_like", "cora_like"],
                     help="workload of --two-layer")

@@ -399,6 +399,16 @@ typedef struct {
 int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *plans, int n,
                        const uint64_t *const *in_cts, uint64_t *const *out_cts,
                        const fg_batch_opts *opts, int *out_levels, int *streams_used);
+/* fg_gcn_layer_batch on seeded inputs (fg_pack_features_seeded): in_c0[q]
+ * = query q's c0 parts [n_in][L+1][N] (device or page-locked host) of the
+ * ciphertexts 0..n_in-1 of seed seeds[q]; the uniform parts are regenerated
+ * on the device as in fg_gcn_layer_axw_seeded.  Same outputs, word for word,
+ * as the queries run one at a time through fg_gcn_layer_axw_seeded.
+ * FG_EINVAL for a null seeds array or an Inter-CA plan. */
+int fg_gcn_layer_batch_seeded(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *plans, int n,
+                              const uint64_t *const *in_c0, const uint64_t *seeds,
+                              uint64_t *const *out_cts, const fg_batch_opts *opts, int *out_levels,
+                              int *streams_used);
 /* The batched form's launch configuration: cfg = {NTT pass-A columns, NTT
  * pass-B rows, NTT twiddles loaded where used (0/1), key-switch registers
  * (0 default, 1 one CTA per SM fewer, 2 keys in shared memory), key-switch column launches (1/2), fused ModUp

@@ -459,10 +459,12 @@ def gcn_layer_axw(ctx, keys, plan, in_cts, out=None, seed=None):
     return out, lvl.value, sc.value
 
 
-def gcn_layer_batch(ctx, keys, plans, ins, outs, streams=0, graph=True, tune=False):
-    """Several layers at once (device tensors only): query q runs plans[q] on
-    ins[q] into outs[q]; tune picks the kernels' launch configuration by
-    timing on the first call.  Returns (output levels, streams used)."""
+def gcn_layer_batch(ctx, keys, plans, ins, outs, streams=0, graph=True, tune=False, seeds=None):
+    """Several layers at once (inputs on the device or in page-locked host
+    memory, outputs on the device): query q runs plans[q] on ins[q] into
+    outs[q]; tune picks the kernels' launch configuration by timing on the
+    first call.  With seeds given, ins[q] are the c0 parts of seeded
+    ciphertexts of seeds[q].  Returns (output levels, streams used)."""
     nat = _lib()
     n = len(plans)
     assert len(ins) == n and len(outs) == n
@@ -472,8 +474,14 @@ def gcn_layer_batch(ctx, keys, plans, ins, outs, streams=0, graph=True, tune=Fal
     lv = (ctypes.c_int * n)()
     su = ctypes.c_int()
     o = nat.BatchOpts(int(streams), 1 if graph else 0, 1 if tune else 0)
-    _check(ctx, nat.lib.fg_gcn_layer_batch(ctx._h, keys._h, P, n, I, O, ctypes.byref(o), lv,
-                                           ctypes.byref(su)))
+    if seeds is None:
+        _check(ctx, nat.lib.fg_gcn_layer_batch(ctx._h, keys._h, P, n, I, O, ctypes.byref(o), lv,
+                                               ctypes.byref(su)))
+    else:
+        assert len(seeds) == n
+        S = (ctypes.c_uint64 * n)(*[int(v) for v in seeds])
+        _check(ctx, nat.lib.fg_gcn_layer_batch_seeded(ctx._h, keys._h, P, n, I, S, O, ctypes.byref(o), lv,
+                                                      ctypes.byref(su)))
     return list(lv), su.value
 
 

@@ -95,6 +95,8 @@ SIGS = {
     "fg_mul_relin_rescale": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "fg_gcn_layer_batch": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
                                    P(BatchOpts), c_void_p, P(c_int)]),
+    "fg_gcn_layer_batch_seeded": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
+                                          P(BatchOpts), c_void_p, P(c_int)]),
     "fg_ctx_set_tuning": (c_int, [c_void_p, c_void_p]),
     "fg_ctx_release_workspace": (c_int, [c_void_p]),
     "fg_batch_tuning": (c_int, [c_void_p, c_void_p, c_void_p, c_int, P(c_int)]),

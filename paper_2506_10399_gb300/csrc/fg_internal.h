@@ -186,6 +186,7 @@ struct fg_ctx {
     };
     std::map<std::string, CopyRes> copies;
     bool in_batch = false;                 // layers of a batch pass are being enqueued
+    const uint64_t *batch_seeds = nullptr; // seeded batch: query q's inputs are c0 parts of seeds[q]
     struct BatchGraph {
         std::vector<const void *> args;   // plans, inputs, outputs
         int streams = 0;

@@ -815,7 +815,8 @@ static void batch_pass(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *p
             ctx->stream = ctx->pool[q % S];
             ctx->ws_prefix = "b" + std::to_string(q % S) + "/";
             const int nb = pl->n_copies ? pl->n_copies * pl->F : pl->t == 1 ? pl->F : (pl->F + pl->t - 1) / pl->t;
-            layer_exec(ctx, keys, pl, in_cts[q], nb, out_cts[q], pl->Fp, false, &levels[q]);
+            layer_exec(ctx, keys, pl, in_cts[q], nb, out_cts[q], pl->Fp, false, &levels[q],
+                       ctx->batch_seeds ? &ctx->batch_seeds[q] : nullptr);
         }
     } catch (...) {
         ctx->stream = origin;
@@ -1037,12 +1038,17 @@ extern "C" int fg_ctx_set_tuning(fg_ctx *ctx, const int cfg[10])
     return FG_OK;
 }
 
-extern "C" int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *plans, int n,
-                                  const uint64_t *const *in_cts, uint64_t *const *out_cts,
-                                  const fg_batch_opts *opts, int *out_levels, int *streams_used)
+static int layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *plans, int n,
+                       const uint64_t *const *in_cts, const uint64_t *seeds, uint64_t *const *out_cts,
+                       const fg_batch_opts *opts, int *out_levels, int *streams_used)
 {
     if (!ctx) return FG_EINVAL;
     cudaStream_t home = ctx->stream;
+    struct KeepSeeds {
+        fg_ctx *c;
+        ~KeepSeeds() { c->batch_seeds = nullptr; }
+    } keep{ctx};
+    ctx->batch_seeds = seeds;
     try {
         FG_CHECK(keys && plans && in_cts && out_cts && out_levels && n >= 1, FG_EINVAL, "null argument");
         fg_batch_opts o{0, 1, 0};
@@ -1055,7 +1061,9 @@ extern "C" int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_pla
             FG_CHECK(in_cts[q] && out_cts[q] && (is_dev(in_cts[q]) || is_pinned(in_cts[q])) && is_dev(out_cts[q]),
                      FG_EINVAL, "batched layers take device or page-locked host inputs and device outputs");
             args.insert(args.end(), {plans[q], in_cts[q], out_cts[q]});
+            if (seeds) args.push_back(reinterpret_cast<const void *>(static_cast<uintptr_t>(seeds[q])));
         }
+        args.push_back(seeds ? &ctx->batch_seeds : nullptr);   // seeded and full batches never match
         if (!ctx->batch_stream)
             CUDA_TRY(cudaStreamCreateWithFlags(&ctx->batch_stream, cudaStreamNonBlocking));
         CUDA_TRY(cudaStreamSynchronize(home));   // inputs written on the caller's stream
@@ -1073,6 +1081,26 @@ extern "C" int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_pla
         return FG_EOOM;
     }
     return FG_OK;
+}
+
+extern "C" int fg_gcn_layer_batch(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *plans, int n,
+                                  const uint64_t *const *in_cts, uint64_t *const *out_cts,
+                                  const fg_batch_opts *opts, int *out_levels, int *streams_used)
+{
+    return layer_batch(ctx, keys, plans, n, in_cts, nullptr, out_cts, opts, out_levels, streams_used);
+}
+
+extern "C" int fg_gcn_layer_batch_seeded(fg_ctx *ctx, const fg_keys *keys, const fg_plan *const *plans, int n,
+                                         const uint64_t *const *in_c0, const uint64_t *seeds,
+                                         uint64_t *const *out_cts, const fg_batch_opts *opts, int *out_levels,
+                                         int *streams_used)
+{
+    if (!ctx) return FG_EINVAL;
+    if (!seeds) {
+        ctx->err = "null seeds";
+        return FG_EINVAL;
+    }
+    return layer_batch(ctx, keys, plans, n, in_c0, seeds, out_cts, opts, out_levels, streams_used);
 }
 
 extern "C" {

@@ -168,3 +168,35 @@ def test_batch_from_page_locked_host_inputs(env, streams, graph):
         torch.cuda.synchronize()
         for (o_w, _), o in zip(want, outs):
             assert bool((o == o_w).all())
+
+
+@pytest.mark.parametrize("where,streams,graph", [("host", 2, True), ("device", 3, False)])
+def test_seeded_batch_equals_seeded_one_at_a_time(env, where, streams, graph):
+    """Seeded client inputs (c0 parts; uniform halves regenerated on the
+    device), page-locked host or device: the batch gives the same words as
+    the queries one at a time through fg_gcn_layer_axw_seeded, on every
+    call (the second replays the graph), and they decrypt to FP64."""
+    import torch
+    fg, ctx, sk, keys, qs, data = env
+    plans = [q[2] for q in qs]
+    seeds = [300 + i for i in range(len(qs))]
+    ins = []
+    for (w, perm, plan, t), sd in zip(qs, seeds):
+        c0 = torch.from_numpy(fg.pack_features_seeded(ctx, sk, sd, w.X, perm, t).view(np.int64))
+        ins.append(c0.pin_memory() if where == "host" else c0.cuda())
+    want = []
+    for plan, c0, sd in zip(plans, ins, seeds):
+        out, lvl, _ = fg.gcn_layer_axw(ctx, keys, plan, c0.cuda(), seed=sd)
+        want.append((out.clone(), lvl))
+    outs = [torch.empty_like(o) for o, _ in want]
+    for rep in range(2):
+        for o in outs:
+            o.zero_()
+        lv, _ = fg.gcn_layer_batch(ctx, keys, plans, ins, outs, streams=streams, graph=graph, seeds=seeds)
+        torch.cuda.synchronize()
+        for (o_w, l_w), o, l in zip(want, outs, lv):
+            assert l == l_w
+            assert bool((o == o_w).all())
+    for (w, perm, plan, t), o, l in zip(qs, outs, lv):
+        d = fg.decrypt_decode(ctx, sk, o[0].contiguous(), l, ctx.scale)
+        assert np.max(np.abs(d[perm] - w.reference_output()[:, 0])) < 2 ** -20
