@@ -486,8 +486,10 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
         const bool chunked = host_in && t == 1 && !pl->n_copies;
         const int kChunk = 64, n_chunks = chunked ? (F + kChunk - 1) / kChunk : 1;
         fg_ctx::CopyRes *cr = nullptr;
+        u64 *c0s = nullptr;   // seeded host inputs: c0 staged contiguously, then expanded into d
         if (host_in) {
             u64 *d = (u64 *)ctx->buf("layer_in", in_w * 8);
+            if (seed) c0s = (u64 *)ctx->buf("layer_in_c0", (size_t)nb * c0_w * 8);
             cr = &ctx->copies[ctx->ws_prefix];
             if (!cr->st) CUDA_TRY(cudaStreamCreateWithFlags(&cr->st, cudaStreamNonBlocking));
             if (!cr->free_ev) CUDA_TRY(cudaEventCreateWithFlags(&cr->free_ev, cudaEventDisableTiming));
@@ -503,12 +505,13 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
                 CUDA_TRY(cudaStreamWaitEvent(cr->st, cr->ev[n_chunks], 0));
             }
             // columns fb .. fb + fn - 1 into the staging buffer (seeded: c0
-            // only; the uniform parts are regenerated on the compute stream
-            // once the chunk has arrived, so that the copies run back to back)
+            // only, into a buffer of its own; the compute stream, once the
+            // chunk has arrived, moves it into place beside the regenerated
+            // uniform parts, so that the copies run back to back)
             auto stage = [&](int fb, int fn) {
-                if (seed) {   // one strided copy (one copy per column measured slower)
-                    CUDA_TRY(cudaMemcpy2DAsync(d + fb * ct_w, ct_w * 8, in_cts + fb * c0_w, c0_w * 8, c0_w * 8,
-                                               fn, cudaMemcpyHostToDevice, cr->st));
+                if (seed) {   // one plain copy of the chunk's c0 (strided copies varied more)
+                    CUDA_TRY(cudaMemcpyAsync(c0s + fb * c0_w, in_cts + fb * c0_w, fn * c0_w * 8,
+                                             cudaMemcpyHostToDevice, cr->st));
                 } else {
                     CUDA_TRY(cudaMemcpyAsync(d + fb * ct_w, in_cts + fb * ct_w, fn * ct_w * 8,
                                              cudaMemcpyHostToDevice, cr->st));
@@ -524,7 +527,7 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
                 stage(0, nb);
                 CUDA_TRY(cudaEventRecord(cr->ev[0], cr->st));
                 CUDA_TRY(cudaStreamWaitEvent(ctx->stream, cr->ev[0], 0));
-                if (seed) kern::expand_uniform(ctx, ctx->stream, d, ct_w, nullptr, nb, nl0, *seed, 0);
+                if (seed) kern::expand_uniform(ctx, ctx->stream, d, ct_w, c0s, nb, nl0, *seed, 0);
             }
             X = d;
         } else if (seed) {   // device c0: expanded into the staging buffer in stream order
@@ -589,8 +592,8 @@ static void layer_exec(fg_ctx *ctx, const fg_keys *keys, const fg_plan *pl, cons
                     CUDA_TRY(cudaStreamWaitEvent(ctx->stream, cr->ev[c], 0));
                     const int fb = c * kChunk, fe = std::min(F, (c + 1) * kChunk);
                     if (seed)
-                        kern::expand_uniform(ctx, ctx->stream, const_cast<u64 *>(X) + fb * ct_w, ct_w, nullptr,
-                                             fe - fb, nl0, *seed, (u64)fb);
+                        kern::expand_uniform(ctx, ctx->stream, const_cast<u64 *>(X) + fb * ct_w, ct_w,
+                                             c0s + fb * c0_w, fe - fb, nl0, *seed, (u64)fb);
                     kern::comb_const_mac(ctx, X, F, Fp, l0, pl->d_comb, Zc, nl0, fb, fe, c > 0);
                 }
             } else {
