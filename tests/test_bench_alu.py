@@ -64,3 +64,20 @@ def test_alu_product_counts_match_the_oracle_plan(kara):
     assert got["ks_ip"] == want_ks
     assert got["comb"] == want_comb
     assert out["kernels"]["group_mac"]["achieved"] == want_gm / 1e-3
+
+
+def test_traffic_ratio_only_for_the_profiled_sources(monkeypatch):
+    """roofline.traffic: the committed ratio of ncu DRAM bytes to algorithmic
+    bytes times this workload's algorithmic bytes, and null once the kernel
+    sources (or the launch defaults) differ from those that were profiled."""
+    sys.path.insert(0, ROOT)
+    import json
+    import bench
+    with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+        t = json.load(f)
+    assert t["sources_sha256"] == bench.sources_sha256(), "profiles/ncu_traffic.json is stale"
+    r = t["dram_over_algorithmic"]["group_mac"]
+    assert bench.traffic_for("group_mac", 1e9) == pytest.approx(r * 1e9)
+    assert bench.traffic_for("no_such_class", 1e9) is None
+    monkeypatch.setattr(bench, "sources_sha256", lambda: "0" * 64)
+    assert bench.traffic_for("group_mac", 1e9) is None
