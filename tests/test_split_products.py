@@ -55,3 +55,37 @@ def test_karatsuba_factor_and_product_bounds():
     assert 2 * h < 1 << 24
     assert (2 * h) ** 2 < 1 << 48
     assert (1 << 16) * (2 * h) ** 2 < 1 << 64
+
+
+M30 = np.uint64((1 << 30) - 1)
+
+
+def split30_sums(v, m):
+    v0, v1 = v & M30, v >> np.uint64(30)
+    m0, m1 = m & M30, m >> np.uint64(30)
+    with np.errstate(over="ignore"):
+        a0 = np.sum(v0 * m0, dtype=np.uint64)
+        a1 = np.sum(v0 * m1 + v1 * m0, dtype=np.uint64)
+        a2 = np.sum(v1 * m1, dtype=np.uint64)
+    return int(a0), int(a1), int(a2)
+
+
+@pytest.mark.parametrize("T", [1, 8])
+def test_thirty_bit_sums_hold_eight_terms_of_sixty_bit_words(T):
+    """Factors below 2^60 in 30-bit halves: the three partial sums of up to
+    eight products (the key switch's digits, the group MAC's fold period on
+    the 60-bit primes) do not wrap, so the 128-bit total is exact."""
+    w = np.full(T, (1 << 60) - 1, np.uint64)
+    a0, a1, a2 = split30_sums(w, w)
+    assert a0 + (a1 << 30) + (a2 << 60) == T * ((1 << 60) - 1) ** 2
+
+
+def test_montgomery_condition_for_the_group_mac_and_key_switch_sums():
+    """The unreduced sums stay below q 2^64, the condition of one Montgomery
+    reduction: 255 products of reduced factors (a group-MAC output per
+    launch) for q < 2^46, and up to 8 products of factors below 2^60 for a
+    60-bit q (the key switch's split path)."""
+    q46 = (1 << 46) - 1
+    assert 255 * q46 * q46 < q46 << 64
+    q60 = (1 << 60) - 1
+    assert 8 * ((1 << 60) - 1) * q60 < q60 << 64
